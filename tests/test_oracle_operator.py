@@ -1,0 +1,89 @@
+"""Pins of the oracle's discrete operator A w = w - chi (K * w) and its solver:
+dense assembly vs direct sum vs FFT convolution (Sec. II-C: the voxel grid
+makes the MoM matrix a convolution, applied by zero-padded FFTs), FFT size
+independence, and GMRES vs dense LU."""
+import math
+
+import numpy as np
+
+from oracle import vie
+
+K0 = 2.0 * math.pi
+
+
+def _case(n, seed):
+    rng = np.random.default_rng(seed)
+    chi = rng.uniform(0.0, 2.0, n)
+    w = rng.standard_normal((3,) + n) + 1j * rng.standard_normal((3,) + n)
+    return chi, w
+
+
+def test_dense_direct_fft_agree_nonsquare():
+    n = (5, 6, 4)
+    h = 0.08
+    chi, w = _case(n, 1)
+    A = vie.dense_operator(n, h, K0, chi)
+    yd = (A @ w.reshape(-1)).reshape(w.shape)
+    ys = vie.apply_direct(vie.kernel_table(n, h, K0), n, chi, w)
+    yf = vie.FFTOperator(n, h, K0, chi)(w)
+    s = np.abs(yd).max()
+    assert np.abs(yd - ys).max() <= 1e-12 * s
+    assert np.abs(yd - yf).max() <= 1e-12 * s
+
+
+def test_dense_8cubed_direct_sum():
+    n = (8, 8, 8)
+    h = 1.0 / 20.0
+    chi, w = _case(n, 2)
+    A = vie.dense_operator(n, h, K0, chi)
+    yd = (A @ w.reshape(-1)).reshape(w.shape)
+    ys = vie.apply_direct(vie.kernel_table(n, h, K0), n, chi, w)
+    assert np.abs(yd - ys).max() <= 1e-12 * np.abs(yd).max()
+
+
+def test_fft_padded_size_independence():
+    n = (7, 5, 6)
+    h = 0.1
+    chi, w = _case(n, 3)
+    y1 = vie.FFTOperator(n, h, K0, chi)(w)
+    y2 = vie.FFTOperator(n, h, K0, chi, P=(18, 15, 11))(w)
+    y3 = vie.FFTOperator(n, h, K0, chi, P=(13, 9, 12))(w)  # minimal 2n-1
+    s = np.abs(y1).max()
+    assert np.abs(y1 - y2).max() <= 1e-12 * s
+    assert np.abs(y1 - y3).max() <= 1e-12 * s
+
+
+def test_sampled_direct_points_match_table_sum():
+    n = (9, 7, 8)
+    h = 0.06
+    _, w = _case(n, 4)
+    T = vie.kernel_table(n, h, K0)
+    full = vie.convolve_direct(T, n, w)
+    pts = np.array([[0, 0, 0], [8, 6, 7], [4, 3, 2], [1, 5, 6]])
+    s = vie.convolve_direct_points(n, h, K0, w, pts)
+    ref = np.stack([full[:, a, b, c] for a, b, c in pts], axis=1)
+    assert np.abs(s - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_gmres_matches_lu_8cubed():
+    n = (8, 8, 8)
+    h = 1.0 / 20.0
+    rng = np.random.default_rng(5)
+    eps = 1.0 + rng.uniform(0.0, 3.0, n) * (rng.uniform(size=n) < 0.6)
+    chi = vie.contrast(eps)
+    b = vie.rhs(chi, vie.incident_field(n, h, K0, [0, 0, 1.0], [1.0, 0, 0]))
+    A = vie.dense_operator(n, h, K0, chi)
+    x_lu = np.linalg.solve(A, b.reshape(-1)).reshape(b.shape)
+    op = vie.FFTOperator(n, h, K0, chi)
+    x_g, info = vie.gmres(op, b, tol=1e-12, restart=30)
+    assert info["converged"]
+    assert np.abs(x_g - x_lu).max() <= 1e-10 * np.abs(x_lu).max()
+    # unknowns outside the body stay exactly zero
+    assert np.abs(x_lu[:, chi == 0]).max() < 1e-13 * np.abs(x_lu).max()
+
+
+def test_smooth_size():
+    assert vie.smooth_size(255) == 256
+    assert vie.smooth_size(73) == 75
+    assert vie.smooth_size(121) == 125
+    assert vie.smooth_size(191) == 192
