@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark: VIE solves/sec to an FP64 residual of 1e-6 on 128^3 random bodies.
+
+One step = one body of the 128^3 evaluation set (random unions of ellipsoids /
+cuboids, eps_r in [1.5, 6], h = lambda/40) solved for 32 incident channels (16
+Fibonacci directions x 2 polarisations) in one batched call: right-hand-side
+build, mixed-precision GMRES (FP32 FFT matvec, FP64 Arnoldi / Givens, FP64
+iterative refinement) down to the FP64 residual check.  The kernel spectrum of
+the (shared) grid is built once before timing; each step swaps the body with
+vie_set_eps_device.  Inputs (all bodies' eps grids) are resident in HBM when
+the timed region starts; the working set (kernel spectrum + Krylov bases, GBs)
+is far larger than L2, so no explicit flush is done.
+
+Reported on one JSON line (rank 0):
+  value        solved RHS per second, whole job (all ranks), device-resident inputs
+  e2e          same through the host-buffer C ABI (eps upload, solve, far field
+               at the two detector directions read back to the host)
+  plain_fp64   plain FP64 GMRES on the same body (subset of channels), for the
+               batched-mixed vs plain comparison
+  roofline     live CUDA-event timing of the dominant kernel (library timer) vs
+               the measured HBM copy bandwidth
+  cpu_baseline the FP64 oracle timed on this host on a bounded sample
+
+Multi-GPU: replicas (each rank solves its own bodies, no collective on the
+data path), weak scaling.  ``--impl reference`` times the oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VIE solves/sec to FP64 residual 1e-6 (128^3 random bodies, 32 RHS/body)"
+UNIT = "solves/s"
+N_AXIS = 128
+H = 1.0 / 40.0
+N_DIRS = 16  # x 2 polarisations = 32 RHS
+SEED0 = 20000
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=4)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--bodies", type=int, default=8)
+    p.add_argument("--restart", type=int, default=64)
+    p.add_argument("--plain-rhs", type=int, default=4)
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--max-iter", type=int, default=20000)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def body_seeds(rank, bodies):
+    return [SEED0 + rank * bodies + i for i in range(bodies)]
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- #
+# oracle timing (CPU baseline and the reference arm)
+# --------------------------------------------------------------------------- #
+def oracle_sample(iters_per_solve, n_iter=3):
+    """Time the FP64 oracle on this host at the bench workload: operator setup
+    once, then ``n_iter`` GMRES iterations on one right-hand side.  Returns
+    (solves/s extrapolated to ``iters_per_solve`` iterations, details)."""
+    import numpy as np
+
+    from oracle import vie as ovie
+    from paper_2508_16471_gb300 import inputs
+    wl = inputs.random_body_workload(SEED0, n_axis=N_AXIS, h=H, n_dirs=N_DIRS)
+    g = wl.grid
+    chi = ovie.contrast(wl.eps)
+    t0 = time.perf_counter()
+    op = ovie.FFTOperator(g.n, g.h, wl.k0, chi, workers=-1)
+    t_setup = time.perf_counter() - t0
+    c = wl.channels[0]
+    b = ovie.rhs(chi, ovie.incident_field(g.n, g.h, wl.k0, c.khat, c.pol))
+    t0 = time.perf_counter()
+    ovie.gmres(op, b, tol=1e-6, restart=64, maxiter=n_iter)
+    t_it = (time.perf_counter() - t0) / n_iter
+    per_solve = t_it * iters_per_solve
+    return 1.0 / per_solve, dict(setup_s=t_setup, s_per_iter=t_it, iters_per_solve=iters_per_solve,
+                                 cores=os.cpu_count())
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    iters = 400  # iterations per solve used for the extrapolation (see sample)
+    vals = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state beyond its setup, timed inside each step
+    t0 = time.perf_counter()
+    det = None
+    for _ in range(args.steps):
+        v, det = oracle_sample(iters, n_iter=2)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"random bodies {N_AXIS}^3, h=lambda/40, {2 * N_DIRS} RHS/body",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": det["cores"],
+                             "sample": (f"FP64 oracle (NumPy/SciPy FFT operator, GMRES) on body seed {SEED0}: "
+                                        f"setup {det['setup_s']:.1f}s + 2 GMRES iterations per step, "
+                                        f"{det['s_per_iter']:.2f} s/iteration, extrapolated to {iters} "
+                                        f"iterations per solve")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- #
+# our arm
+# --------------------------------------------------------------------------- #
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2508_16471_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary of this kernel,
+    if it was captured on the current sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{kernel}.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("csrc_sha256_16") != csrc_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2508_16471_gb300 import build as libbuild
+    from paper_2508_16471_gb300 import inputs
+    from paper_2508_16471_gb300 import vie as V
+    if rank == 0:
+        libbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    V.load()
+
+    seeds = body_seeds(rank, args.bodies)
+    wls = [inputs.random_body_workload(s, n_axis=N_AXIS, h=H, n_dirs=N_DIRS) for s in seeds]
+    g = wls[0].grid
+    chs = [(c.khat, c.pol) for c in wls[0].channels]
+    R = len(chs)
+    eps_dev = [torch.from_numpy(np.ascontiguousarray(w.eps)).cuda() for w in wls]
+    eps_host = [torch.from_numpy(np.ascontiguousarray(w.eps)).pin_memory() for w in wls]
+    hd = V.Handle(g.n, g.h, wls[0].eps, wls[0].k0)
+    stream = torch.cuda.ExternalStream(hd.stream())
+    opts = dict(tol=1e-6, restart=args.restart, precision=V.PREC_MIXED, max_iter=args.max_iter)
+
+    def step(i):
+        hd.set_eps_device(eps_dev[i % len(eps_dev)].data_ptr())
+        st = hd.solve(chs, allow_noconv=True, **opts)
+        return st
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    V.timer_reset()
+    V.timer_enable(True)
+    launches0 = V.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    t0 = time.perf_counter()
+    solved, iters, outers, relmax = 0, [], [], 0.0
+    for i in range(args.steps):
+        st = step(args.warmup + i)
+        solved += int(st["converged"])
+        iters.extend(st["iters"].tolist())
+        outers.append(st["outer_max"])
+        relmax = max(relmax, float(st["relres_max"]))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    V.timer_enable(False)
+    launches = V.kernel_launches() - launches0
+    timers = V.timer_read()
+    clk = clocks.stop()
+    t_max = ms
+    tot_solved = solved
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        s = torch.tensor([solved], device="cuda", dtype=torch.float64)
+        dist.all_reduce(s)
+        tot_solved = int(s.item())
+    value = tot_solved / (t_max / 1000.0)
+
+    # ---- e2e through the host-buffer C ABI ---------------------------------
+    e2e = None
+    if not args.no_e2e:
+        th = np.radians([60.0, 60.0])
+        ph = np.radians([0.0, 180.0])
+        dets = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], -1)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        solved_e2e = 0
+        for i in range(args.steps):
+            hd.set_eps(eps_host[(args.warmup + i) % len(eps_host)].numpy())
+            st = hd.solve(chs, allow_noconv=True, **opts)
+            F = hd.farfield_dirs(dets)
+            solved_e2e += int(st["converged"])
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+            s = torch.tensor([solved_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(s)
+            solved_e2e = int(s.item())
+        e2e = {"value": solved_e2e / te, "unit": UNIT, "h2d_bytes_per_step": int(8 * g.size + 72 * R),
+               "d2h_bytes_per_step": int(F.nbytes + 12 * R)}
+
+    # ---- plain FP64 GMRES on a subset (same body as step 0) ----------------
+    plain = None
+    if not args.no_plain and rank == 0:
+        hd.set_eps_device(eps_dev[0].data_ptr())
+        sub = chs[:args.plain_rhs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = hd.solve(sub, allow_noconv=True, tol=1e-6, restart=args.restart, precision=V.PREC_FP64,
+                      max_iter=args.max_iter)
+        torch.cuda.synchronize()
+        tp = time.perf_counter() - t0
+        plain = {"value": int(st["converged"]) / tp, "unit": UNIT, "rhs": len(sub),
+                 "converged": int(st["converged"]), "seconds": tp,
+                 "iters_mean": float(np.mean(st["iters"])), "precision": "f64",
+                 "body_seed": seeds[0]}
+
+    # ---- roofline of the dominant kernel -----------------------------------
+    peaks = load_peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    dom = max(timers.items(), key=lambda kv: kv[1][0])
+    name, (kms, kn, kbytes) = dom
+    achieved = kbytes / (kms / 1000.0) / 1e9 if kms > 0 else 0.0
+    kernels = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / max(1e-9, sum(x[0] for x in timers.values())), 4),
+                   "alg_GBps": round(v[2] / (v[0] / 1000.0) / 1e9, 1) if v[0] > 0 else None}
+               for k, v in timers.items() if v[1] > 0}
+    traffic = profiled_traffic(name)
+    roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks
+            else "fallback 6800 GB/s", "alg_bytes_per_launch": kbytes / max(1, kn),
+            "traffic": traffic}
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu:
+        its = float(np.mean(iters)) if iters else 100.0
+        try:
+            v, det = oracle_sample(its, n_iter=2)
+            cpu = {"value": v, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
+                   "sample": (f"FP64 oracle on body seed {SEED0} ({N_AXIS}^3, 1 RHS): operator setup "
+                              f"{det['setup_s']:.1f}s, 2 GMRES iterations at {det['s_per_iter']:.2f} s each, "
+                              f"extrapolated to the GPU run's mean {its:.0f} inner iterations per solve")}
+        except Exception as ex:  # pragma: no cover
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {ex}"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded random bodies)",
+        "config": {"workload": f"random bodies {N_AXIS}^3, h=lambda/40, eps_r in [1.5,6], "
+                               f"{R} RHS/body ({N_DIRS} Fibonacci directions x 2 pol), tol 1e-6",
+                   "solver": f"mixed FP32 matvec / FP64 Arnoldi GMRES({args.restart}) + FP64 refinement",
+                   "bodies_per_rank": args.bodies, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (no flush)"},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "roofline": roof, "cpu_baseline": cpu, "plain_fp64": plain,
+        "speedup_vs_plain": (value / plain["value"]) if plain and plain["value"] else None,
+        "solver_stats": {"solved": tot_solved, "rhs_total": args.steps * R * world,
+                         "iters_mean": float(np.mean(iters)) if iters else None,
+                         "iters_max": int(max(iters)) if iters else None, "outer_max": max(outers) if outers else None,
+                         "relres_max": relmax, "wall_s": wall},
+        "kernels": kernels,
+    }
+    print(json.dumps(line), flush=True)
+    hd.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

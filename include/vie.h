@@ -1,0 +1,257 @@
+/*
+ * vie.h -- C ABI of the GB300 FFT-VIE library (libvie.so).
+ *
+ * Computes, for a lossless dielectric body on a uniform voxel grid, the
+ * contrast current of every incident plane-wave channel by solving the volume
+ * integral equation (arXiv 2508.16471, Sec. II-C, Eq. 24) with FFT-accelerated
+ * matrix-vector products, projects the currents onto far-field amplitudes
+ * (Eq. 25, Eq. Eproj, Eq. 30) and forms the two-photon observables g2
+ * (Eq. 10), N~c(dtau) and the HOM visibility (Eqs. 18-22).
+ *
+ * Discretisation.  The unknown is the contrast current w = chi E_tot with
+ * chi = eps_r - 1 (Eq. Js_def: J = -i omega eps0 w).  On every body voxel n
+ *     w_n - chi_n sum_m K(n - m) w_m = chi_n E_inc(r_n)
+ * where each source voxel is the ball of volume h^3 (radius a), tested at
+ * voxel centres:  K(m != 0) = kappa k0^2 h^3 G(m h) with the dyadic Green's
+ * function G of Eq. dyadicG and kappa = 3 (sin ka - ka cos ka)/(ka)^3;
+ * K(0) = [2/3((1 - i ka) e^{i ka} - 1) - 1/3] I.  The far field is
+ *     F(rhat) = kappa k0^2 h^3/(4 pi) (I - rhat rhat) sum_n w_n e^{-i k0 rhat.r_n}
+ * with E_sca ~ F e^{i k0 r}/r, time convention e^{-i omega t}.
+ *
+ * Conventions shared by every entry point:
+ *   - Grid arrays are C-ordered [i][j][k] over (x, y, z), z fastest.  Voxel
+ *     (i,j,k) is centred at origin + ((i,j,k) - (n-1)/2) h.
+ *   - Complex numbers are interleaved (re, im) doubles unless stated.
+ *   - Host pointers are owned by the caller; the library copies from/to them.
+ *     Device pointers ("_device" entry points) must point to memory of the
+ *     device that was current at vie_setup; they are never freed by the
+ *     library.  All device memory of a handle is owned by the handle and
+ *     released by vie_destroy.
+ *   - A handle is not thread-safe; use one handle per host thread / stream.
+ *   - Every int-returning function returns VIE_OK (0) or a negative status;
+ *     vie_last_error() then describes the failure (thread-local string).
+ */
+#ifndef VIE_H
+#define VIE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define VIE_OK        0
+#define VIE_EINVAL   -1  /* bad argument: NaN, eps_r < 1, k0 <= 0, |pol.khat| > 1e-12,
+                            empty body, size out of range, NULL pointer          */
+#define VIE_ENOMEM   -2  /* device allocation failed                            */
+#define VIE_ENOCONV  -3  /* solve stopped at max_iter; stats hold the achieved
+                            FP64 residual and the currents are kept              */
+#define VIE_ETIMEOUT -4  /* a bounded device-side wait gave up                  */
+#define VIE_EUNDEF   -5  /* g2 or N~c undefined (zero denominator); NaN written  */
+#define VIE_EDEVICE  -6  /* CUDA runtime error                                  */
+#define VIE_ESTATE   -7  /* call out of order (e.g. far field before a solve)   */
+
+/* ---- precision modes --------------------------------------------------- */
+#define VIE_PREC_MIXED 0 /* FP32 FFT matvec inside GMRES (FP64 Arnoldi and
+                            Givens), iterative refinement on the FP64 residual  */
+#define VIE_PREC_FP64  1 /* plain FP64 GMRES(m): FP64 matvec and basis          */
+
+/* ---- far-field component bases (vie_farfield*) -------------------------- */
+#define VIE_BASIS_CART 0 /* (F_x, F_y, F_z)                                      */
+#define VIE_BASIS_SPH  1 /* (F_theta, F_phi, F_r)   (F_r = 0 up to rounding)     */
+#define VIE_BASIS_CIRC 2 /* (F_L, F_R, F_r), F_L,R = (F_theta +/- i F_phi)/sqrt2
+                            (Eq. 30)                                             */
+
+typedef struct vie_handle vie_handle;
+
+typedef struct vie_grid {
+    int n[3];          /* voxels along x, y, z (each >= 1, product <= 2^28)     */
+    double h;          /* voxel edge, same length unit as 1/k0 (> 0)            */
+    double origin[3];  /* position of the grid centre (phase origin)            */
+} vie_grid;
+
+typedef struct vie_channel {
+    double khat[3];    /* unit propagation direction                            */
+    double pol[6];     /* complex polarisation (x re, x im, y re, y im, z re, z im),
+                          transverse to khat; E_inc = pol e^{i k0 khat.r}         */
+} vie_channel;
+
+typedef struct vie_solve_opts {
+    double tol;        /* target ||b - A64 x||_2 / ||b||_2 per RHS (default 1e-6) */
+    int restart;       /* GMRES restart length m (default 30, 1..64)             */
+    int max_iter;      /* cap on inner iterations per RHS (default 5000)         */
+    int precision;     /* VIE_PREC_MIXED (default) or VIE_PREC_FP64              */
+    double inner_tol;  /* mixed mode: relative reduction asked of each FP32 inner
+                          solve (default 1e-3)                                    */
+    int use_x0;        /* 1: start from the currents stored in the handle (same
+                          n_rhs as the previous solve); 0: x0 = 0                 */
+    int reserved[3];
+} vie_solve_opts;
+
+typedef struct vie_solve_stats {
+    int n_rhs;         /* RHS solved                                             */
+    int converged;     /* RHS that reached tol                                   */
+    int iters_max;     /* largest inner-iteration count over the RHS             */
+    int outer_max;     /* largest number of FP64 refinement steps                */
+    long long matvecs32;   /* FP32 operator applications (per RHS, summed)       */
+    long long matvecs64;   /* FP64 operator applications (per RHS, summed)       */
+    double relres_max; /* largest final FP64 relative residual                   */
+    double seconds;    /* wall time of the solve (device-synchronised)           */
+    int* iters;        /* optional caller array [n_rhs]: inner iterations per RHS */
+    double* relres;    /* optional caller array [n_rhs]: final FP64 residual      */
+} vie_solve_stats;
+
+typedef struct vie_info {
+    int n[3];          /* grid                                                   */
+    int P[3];          /* padded FFT sizes (smallest 2,3,5,7-smooth >= 2n-1)     */
+    long long n_body;  /* voxels with eps_r > 1 (unknowns / 3)                   */
+    int n_rhs;         /* RHS held by the handle (last solve)                    */
+    int device;        /* CUDA device ordinal                                    */
+    double device_bytes; /* device memory held by the handle                     */
+} vie_info;
+
+/* Default options (tol 1e-6, restart 30, max_iter 5000, mixed, inner 1e-3). */
+void vie_default_opts(vie_solve_opts* opts);
+
+/*
+ * vie_setup -- build the operator for one grid and wavenumber.
+ * Sec. II-C: eps_r defines chi = eps_r - 1 (Eq. Js_def); the Green's tensor of
+ * Eq. dyadicG is sampled on every voxel offset (-(n-1)..n-1)^3, embedded in a
+ * zero-padded periodic array of size P and Fourier transformed once on the
+ * device (FP64), keeping one octant per tensor component (Eq. 24's convolution
+ * via FFT, the paragraph after Eq. Js_expand).
+ *   g      : grid (n, h, origin), copied.
+ *   eps_r  : host [n0][n1][n2] real relative permittivity, >= 1, finite.
+ *   k0     : free-space wavenumber > 0.
+ *   out    : receives the new handle (device = the current CUDA device).
+ * Errors: VIE_EINVAL (bad g, eps_r, k0; body empty), VIE_ENOMEM, VIE_EDEVICE.
+ */
+int vie_setup(const vie_grid* g, const double* eps_r, double k0, vie_handle** out);
+
+/* Replace the body on the same grid (keeps the kernel spectrum).  Host
+ * [n0][n1][n2] eps_r.  Discards stored currents.  Errors as vie_setup. */
+int vie_set_eps(vie_handle* hd, const double* eps_r);
+/* Same with a device pointer to [n0][n1][n2] doubles. */
+int vie_set_eps_device(vie_handle* hd, const double* eps_r_dev);
+
+/*
+ * vie_solve -- contrast currents of n_rhs incident channels (Sec. II-C, Eq. 24;
+ * the paper solves each channel separately, Sec. III).  The right-hand sides
+ * b_j = chi pol_j e^{i k0 khat_j.r} are built on the device; the solver is
+ * restarted GMRES (the paper uses BiCGStab; both converge to the same
+ * solution) over all channels at once.  The currents stay in the handle for
+ * vie_farfield / vie_get_current.
+ *   ch     : host array [n_rhs] of channels (|khat| = 1, pol transverse).
+ *   opts   : NULL for defaults.
+ *   stats  : optional output.
+ * Errors: VIE_EINVAL, VIE_ENOMEM, VIE_ENOCONV (currents kept), VIE_EDEVICE.
+ */
+int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_opts* opts,
+              vie_solve_stats* stats);
+
+/*
+ * vie_farfield -- far-field amplitudes of every stored current on a product
+ * grid of directions (Eq. 25 with C_inf = kappa k0^2 h^3/(4 pi); components
+ * per Eq. Eproj / Eq. 30).  The incident plane wave contributes only in its
+ * own forward direction and is omitted (E_tot,inf = F off-forward).
+ *   theta[nt], phi[np] : angles in radians (host).
+ *   basis              : VIE_BASIS_*.
+ *   out                : host [n_rhs][nt][np][3] complex (interleaved doubles).
+ * Errors: VIE_EINVAL, VIE_ESTATE (no solve yet), VIE_ENOMEM, VIE_EDEVICE.
+ */
+int vie_farfield(vie_handle* hd, const double* theta, int nt, const double* phi, int np,
+                 int basis, double* out);
+
+/* Same for an arbitrary list of unit vectors dirs[D][3] (host); out as above
+ * with D directions: [n_rhs][D][3] complex.  Evaluated in FP64. */
+int vie_farfield_dirs(vie_handle* hd, const double* dirs, int D, int basis, double* out);
+
+/* Device variant of vie_farfield_dirs: dirs_dev [D][3] doubles and out_dev
+ * [n_rhs][D][3] complex doubles on the device; enqueued on the handle's stream
+ * and synchronised before return. */
+int vie_farfield_dirs_device(vie_handle* hd, const double* dirs_dev, int D, int basis,
+                             double* out_dev);
+
+/*
+ * hom_transfer -- two-photon observables of one detector pair and channel pair
+ * (Sec. II-A/B).  E[8] = complex far-field amplitudes [det][ch] (det 0 = a at
+ * r1, det 1 = b at r2; ch 0 = k1, ch 1 = k2), interleaved.  omega[2]: channel
+ * frequencies (NULL = equal).  Outputs (any may be NULL):
+ *   g2[1]      : Eq. 10, omega1 omega2 |E_a1 E_b2 + E_a2 E_b1|^2 /
+ *                (sum_l omega_l |E_al|^2 sum_l omega_l |E_bl|^2)
+ *   Nc[n_tau]  : N~c(dtau) = 1 + 2 Re(A_dir A_ex*) e^{-dtau^2/sigma^2} /
+ *                (|A_dir|^2 + |A_ex|^2), A_dir = T_a1 T_b2, A_ex = T_a2 T_b1,
+ *                T_aj = sqrt(omega_j) E_aj (Eqs. 18-22 with a Gaussian
+ *                envelope, Eq. HOM_envelope)
+ *   visibility : 1 - N~c(0)
+ * Host-side scalar arithmetic (the same function the device map kernel runs).
+ * Returns VIE_EUNDEF with NaN outputs when a denominator is zero.
+ */
+int hom_transfer(const double E[8], const double omega[2], double sigma, const double* dtau,
+                 int n_tau, double* g2, double* Nc, double* visibility);
+
+/*
+ * vie_hom_map -- g2, HOM visibility and the normalised classical
+ * intensity-product correlation (Eq. 27) for every detector pair (r1 in set A,
+ * r2 in set B) of one channel pair, on the device.
+ *   Ea [2][nA] complex: detector-projected amplitudes of channels 1, 2 at the
+ *                       directions of set A (component e_a);
+ *   Eb [2][nB] complex: same at set B (component e_b);
+ *   g2, vis, p2 : host [nA][nB] doubles (any may be NULL); NaN where undefined;
+ *                 p2 is divided by its maximum over the map.
+ * Errors: VIE_EINVAL, VIE_ENOMEM, VIE_EDEVICE.
+ */
+int vie_hom_map(const double* Ea, int nA, const double* Eb, int nB, double sigma, double* g2,
+                double* vis, double* p2);
+
+/* Copy the stored current of RHS `rhs` to host out[3][n0][n1][n2] complex
+ * (zero outside the body).  Errors: VIE_EINVAL, VIE_ESTATE. */
+int vie_get_current(vie_handle* hd, int rhs, double* out);
+
+/*
+ * vie_apply -- one operator application y = w - chi (K * w) (Eq. 24 in the w
+ * unknown) for n_rhs vectors, in the given precision, through the same FFT
+ * kernels the solver uses.  w, y: host [n_rhs][3][n0][n1][n2] complex; w must
+ * vanish outside the body (y is w there).  Errors: VIE_EINVAL, VIE_ENOMEM,
+ * VIE_EDEVICE.
+ */
+int vie_apply(vie_handle* hd, const double* w, double* y, int n_rhs, int precision);
+
+/* Device variant on the compact body-voxel layout: w_dev, y_dev are
+ * [n_rhs][3][n_body] complex (float2 for VIE_PREC_MIXED, double2 for
+ * VIE_PREC_FP64), body voxels in C order.  Enqueued on the handle's stream;
+ * not synchronised. */
+int vie_apply_device(vie_handle* hd, const void* w_dev, void* y_dev, int n_rhs, int precision);
+
+/* Kernel-level check: batched 1-D complex DFT of `count` contiguous lines of
+ * length L (2,3,5,7-smooth, <= 1024) by the library's FFT engine, host
+ * in/out [count][L] complex doubles, forward (sign -1) when inverse == 0,
+ * unnormalised inverse otherwise, in FP32 (precision MIXED) or FP64. */
+int vie_fft_lines(const double* in, double* out, int L, int count, int inverse, int precision);
+
+int vie_get_info(const vie_handle* hd, vie_info* info);
+
+/* Launch statistics: number of library kernels launched by this process. */
+long long vie_kernel_launches(void);
+
+/* Optional per-kernel timing: when enabled, every library kernel launch is
+ * bracketed by CUDA events on its stream and its duration accumulated under
+ * a kernel id (0 .. vie_timer_count()-1; names from vie_timer_name), together
+ * with the algorithmic bytes of the launch (each input read once, each output
+ * written once).  Adds two event records per launch; off by default. */
+void vie_timer_enable(int on);
+void vie_timer_reset(void);
+int vie_timer_read(int id, double* total_ms, long long* launches, double* bytes);
+const char* vie_timer_name(int id);
+int vie_timer_count(void);
+
+/* Device stream used by the handle (cudaStream_t as void*). */
+void* vie_stream(vie_handle* hd);
+
+void vie_destroy(vie_handle* hd);
+
+const char* vie_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VIE_H */

@@ -199,6 +199,20 @@ def convolve_direct_points(n, h, k0, w, targets):
     return out
 
 
+def convolve_direct_points_multi(n, h, k0, W, targets):
+    """``convolve_direct_points`` for a stack of fields W (R, 3, n0, n1, n2),
+    evaluating K once per target.  Returns (R, 3, T)."""
+    n = tuple(n)
+    src = np.stack(np.unravel_index(np.arange(int(np.prod(n))), n), axis=-1)
+    Wf = np.asarray(W).reshape(len(W), 3, -1)
+    out = np.zeros((len(W), 3, len(targets)), dtype=np.complex128)
+    for t, tv in enumerate(np.asarray(targets)):
+        K = kernel_at(tv[None, :] - src, h, k0)  # (N, 6)
+        for i in range(3):
+            out[:, i, t] = sum(Wf[:, j] @ K[:, CIDX[i][j]] for j in range(3))
+    return out
+
+
 def apply_direct(Ktab, n, chi, w):
     """y = w - chi (K * w) with the direct-sum convolution."""
     return w - chi[None] * convolve_direct(Ktab, n, w)

@@ -1,0 +1,488 @@
+// C ABI of libvie.so (declarations and contracts in include/vie.h).
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "farfield.cuh"
+
+struct vie_handle {
+    vie::Operator op;
+    vie::Solver S;
+    int device = 0;
+    int n_rhs = 0;
+    bool have_solution = false;
+    std::vector<int> vox_host;  // body voxel list (for host-side scatter/gather)
+};
+
+namespace vie {
+
+static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char* where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? VIE_ENOMEM : VIE_EDEVICE;
+}
+void count_launch(long long n) { g_launches += n; }
+
+int dev_alloc(Operator& op, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(VIE_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    op.bytes += (double)bytes;
+    return VIE_OK;
+}
+void dev_free(Operator& op, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    op.bytes -= (double)bytes;
+}
+
+}  // namespace vie
+
+using namespace vie;
+
+static int check_grid(const vie_grid* g) {
+    if (!g) return fail(VIE_EINVAL, "grid is NULL");
+    long long N = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (g->n[a] < 1 || g->n[a] > 512) return fail(VIE_EINVAL, "grid size per axis must be in 1..512");
+        N *= g->n[a];
+    }
+    if (N > (1LL << 28)) return fail(VIE_EINVAL, "grid has more than 2^28 voxels");
+    if (!(g->h > 0) || !std::isfinite(g->h)) return fail(VIE_EINVAL, "voxel size h must be positive and finite");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(g->origin[a])) return fail(VIE_EINVAL, "origin must be finite");
+    return VIE_OK;
+}
+
+static int check_eps_host(const double* eps, long long N) {
+    if (!eps) return fail(VIE_EINVAL, "eps_r is NULL");
+    long long nb = 0;
+    for (long long i = 0; i < N; ++i) {
+        const double e = eps[i];
+        if (!std::isfinite(e) || e < 1.0) return fail(VIE_EINVAL, "eps_r must be finite and >= 1 (lossless dielectric)");
+        nb += e > 1.0;
+    }
+    if (nb == 0) return fail(VIE_EINVAL, "the body is empty (no voxel with eps_r > 1)");
+    return VIE_OK;
+}
+
+static int refresh_vox_host(vie_handle* hd) {
+    hd->vox_host.resize(hd->op.Nb);
+    VIE_CUDA(cudaMemcpy(hd->vox_host.data(), hd->op.vox, sizeof(int) * hd->op.Nb, cudaMemcpyDeviceToHost));
+    return VIE_OK;
+}
+
+static int set_eps_dev(vie_handle* hd, const double* eps_dev) {
+    hd->S.release(hd->op);
+    hd->have_solution = false;
+    hd->n_rhs = 0;
+    VIE_TRY(op_set_body_device(hd->op, eps_dev));
+    return refresh_vox_host(hd);
+}
+
+extern "C" {
+
+void vie_default_opts(vie_solve_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-6;
+    o->restart = 30;
+    o->max_iter = 5000;
+    o->precision = VIE_PREC_MIXED;
+    o->inner_tol = 1e-3;
+    o->use_x0 = 0;
+}
+
+const char* vie_last_error(void) { return g_err.c_str(); }
+
+long long vie_kernel_launches(void) { return g_launches.load(); }
+
+int vie_setup(const vie_grid* g, const double* eps_r, double k0, vie_handle** out) {
+    if (!out) return fail(VIE_EINVAL, "out is NULL");
+    *out = nullptr;
+    VIE_TRY(check_grid(g));
+    if (!(k0 > 0) || !std::isfinite(k0)) return fail(VIE_EINVAL, "k0 must be positive and finite");
+    const long long N = (long long)g->n[0] * g->n[1] * g->n[2];
+    VIE_TRY(check_eps_host(eps_r, N));
+    vie_handle* hd = new vie_handle();
+    int st = VIE_OK;
+    cudaError_t e = cudaGetDevice(&hd->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hd->op.stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) st = cuda_fail(e, "device / stream setup");
+    Operator& op = hd->op;
+    for (int a = 0; a < 3; ++a) {
+        op.n[a] = g->n[a];
+        op.origin[a] = g->origin[a];
+    }
+    op.N = N;
+    op.h = g->h;
+    op.k0 = k0;
+    if (st == VIE_OK) st = op_init_axes(op);
+    if (st == VIE_OK) st = op_build_kernel(op);
+    double* deps = nullptr;
+    if (st == VIE_OK) {
+        e = cudaMalloc(&deps, sizeof(double) * N);
+        if (e == cudaSuccess) e = cudaMemcpy(deps, eps_r, sizeof(double) * N, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(e, "eps upload");
+    }
+    if (st == VIE_OK) st = set_eps_dev(hd, deps);
+    cudaFree(deps);
+    if (st != VIE_OK) {
+        vie_destroy(hd);
+        return st;
+    }
+    *out = hd;
+    return VIE_OK;
+}
+
+int vie_set_eps(vie_handle* hd, const double* eps_r) {
+    if (!hd) return fail(VIE_EINVAL, "handle is NULL");
+    VIE_TRY(check_eps_host(eps_r, hd->op.N));
+    VIE_CUDA(cudaSetDevice(hd->device));
+    double* deps = nullptr;
+    VIE_CUDA(cudaMalloc(&deps, sizeof(double) * hd->op.N));
+    cudaError_t e = cudaMemcpy(deps, eps_r, sizeof(double) * hd->op.N, cudaMemcpyHostToDevice);
+    int st = e == cudaSuccess ? set_eps_dev(hd, deps) : cuda_fail(e, "eps upload");
+    cudaFree(deps);
+    return st;
+}
+
+int vie_set_eps_device(vie_handle* hd, const double* eps_dev) {
+    if (!hd || !eps_dev) return fail(VIE_EINVAL, "NULL argument");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    return set_eps_dev(hd, eps_dev);
+}
+
+int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_opts* opts, vie_solve_stats* stats) {
+    if (!hd || !ch) return fail(VIE_EINVAL, "NULL argument");
+    if (n_rhs < 1 || n_rhs > 65535) return fail(VIE_EINVAL, "n_rhs must be in 1..65535");
+    vie_solve_opts o;
+    if (opts) o = *opts;
+    else vie_default_opts(&o);
+    if (!(o.tol > 0) || o.restart < 1 || o.restart > MAX_RESTART || o.max_iter < 1 ||
+        (o.precision != VIE_PREC_MIXED && o.precision != VIE_PREC_FP64) || !(o.inner_tol > 0))
+        return fail(VIE_EINVAL, "invalid solve options (tol > 0, restart 1..64, max_iter >= 1, precision 0/1)");
+    for (int r = 0; r < n_rhs; ++r) {
+        const double* k = ch[r].khat;
+        const double* p = ch[r].pol;
+        double kn = 0, pn = 0;
+        bool fin = true;
+        for (int q = 0; q < 3; ++q) {
+            kn += k[q] * k[q];
+            fin = fin && std::isfinite(k[q]);
+        }
+        for (int q = 0; q < 6; ++q) {
+            pn += p[q] * p[q];
+            fin = fin && std::isfinite(p[q]);
+        }
+        if (!fin || std::fabs(kn - 1.0) > 1e-9) return fail(VIE_EINVAL, "khat must be a finite unit vector");
+        if (!(pn > 0)) return fail(VIE_EINVAL, "polarisation must be nonzero");
+        const double dr = p[0] * k[0] + p[2] * k[1] + p[4] * k[2];
+        const double di = p[1] * k[0] + p[3] * k[1] + p[5] * k[2];
+        if (std::sqrt(dr * dr + di * di) > 1e-10 * std::sqrt(pn))
+            return fail(VIE_EINVAL, "polarisation must be transverse to khat");
+    }
+    if (o.use_x0 && (!hd->have_solution || hd->n_rhs != n_rhs || hd->S.m != o.restart || hd->S.prec != o.precision))
+        return fail(VIE_ESTATE, "use_x0 needs a stored solution with the same n_rhs, restart and precision");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    auto t0 = std::chrono::steady_clock::now();
+    VIE_TRY(hd->S.alloc(hd->op, n_rhs, o.restart, o.precision));
+    hd->have_solution = false;
+    VIE_TRY(build_rhs(hd->op, hd->S, ch, n_rhs));
+    SolveResult res;
+    int st = solver_run(hd->op, hd->S, o, res);
+    VIE_CUDA(cudaStreamSynchronize(hd->op.stream));
+    auto t1 = std::chrono::steady_clock::now();
+    if (st != VIE_OK) return st;
+    hd->n_rhs = n_rhs;
+    hd->have_solution = true;
+    if (stats) {
+        stats->n_rhs = n_rhs;
+        stats->converged = res.converged;
+        stats->iters_max = res.iters_max;
+        stats->outer_max = res.outer_max;
+        stats->matvecs32 = res.matvecs32;
+        stats->matvecs64 = res.matvecs64;
+        stats->relres_max = res.relres_max;
+        stats->seconds = std::chrono::duration<double>(t1 - t0).count();
+        if (stats->iters)
+            for (int r = 0; r < n_rhs; ++r) stats->iters[r] = res.iters[r];
+        if (stats->relres)
+            for (int r = 0; r < n_rhs; ++r) stats->relres[r] = res.relres[r];
+    }
+    if (res.converged < n_rhs)
+        return fail(VIE_ENOCONV, "solve stopped before reaching tol; largest FP64 residual " +
+                                     std::to_string(res.relres_max));
+    return VIE_OK;
+}
+
+int vie_farfield_dirs_device(vie_handle* hd, const double* dirs_dev, int D, int basis, double* out_dev) {
+    if (!hd || !dirs_dev || !out_dev || D < 1) return fail(VIE_EINVAL, "bad arguments");
+    if (basis < 0 || basis > 2) return fail(VIE_EINVAL, "basis must be 0, 1 or 2");
+    if (!hd->have_solution) return fail(VIE_ESTATE, "no solution stored: call vie_solve first");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    return farfield_dirs(hd->op, hd->S.x, hd->S.n3, hd->n_rhs, dirs_dev, D, basis, (c64*)out_dev);
+}
+
+int vie_farfield_dirs(vie_handle* hd, const double* dirs, int D, int basis, double* out) {
+    if (!hd || !dirs || !out || D < 1) return fail(VIE_EINVAL, "bad arguments");
+    for (int d = 0; d < D; ++d) {
+        const double n2 = dirs[3 * d] * dirs[3 * d] + dirs[3 * d + 1] * dirs[3 * d + 1] + dirs[3 * d + 2] * dirs[3 * d + 2];
+        if (!(std::fabs(n2 - 1.0) < 1e-9)) return fail(VIE_EINVAL, "directions must be unit vectors");
+    }
+    if (!hd->have_solution) return fail(VIE_ESTATE, "no solution stored: call vie_solve first");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    double* dd = nullptr;
+    double* dout = nullptr;
+    const size_t ob = sizeof(double) * 6 * (size_t)D * hd->n_rhs;
+    VIE_CUDA(cudaMalloc(&dd, sizeof(double) * 3 * D));
+    cudaError_t e = cudaMalloc(&dout, ob);
+    int st = VIE_OK;
+    if (e == cudaSuccess) e = cudaMemcpy(dd, dirs, sizeof(double) * 3 * D, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = cuda_fail(e, "far-field buffers");
+    if (st == VIE_OK) st = farfield_dirs(hd->op, hd->S.x, hd->S.n3, hd->n_rhs, dd, D, basis, (c64*)dout);
+    if (st == VIE_OK) {
+        e = cudaMemcpy(out, dout, ob, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "far-field copy");
+    }
+    cudaFree(dd);
+    cudaFree(dout);
+    return st;
+}
+
+int vie_farfield(vie_handle* hd, const double* theta, int nt, const double* phi, int np, int basis, double* out) {
+    if (!hd || !theta || !phi || !out || nt < 1 || np < 1) return fail(VIE_EINVAL, "bad arguments");
+    if (basis < 0 || basis > 2) return fail(VIE_EINVAL, "basis must be 0, 1 or 2");
+    for (int i = 0; i < nt; ++i)
+        if (!std::isfinite(theta[i])) return fail(VIE_EINVAL, "theta must be finite");
+    for (int i = 0; i < np; ++i)
+        if (!std::isfinite(phi[i])) return fail(VIE_EINVAL, "phi must be finite");
+    if (!hd->have_solution) return fail(VIE_ESTATE, "no solution stored: call vie_solve first");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    double *dth = nullptr, *dph = nullptr, *dout = nullptr;
+    const size_t ob = sizeof(double) * 6 * (size_t)nt * np * hd->n_rhs;
+    int st = VIE_OK;
+    cudaError_t e = cudaMalloc(&dth, sizeof(double) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&dph, sizeof(double) * np);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, ob);
+    if (e == cudaSuccess) e = cudaMemcpy(dth, theta, sizeof(double) * nt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dph, phi, sizeof(double) * np, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = cuda_fail(e, "far-field buffers");
+    if (st == VIE_OK) st = farfield_grid(hd->op, hd->S.x, hd->S.n3, hd->n_rhs, dth, nt, dph, np, basis, (c64*)dout);
+    if (st == VIE_OK) {
+        e = cudaMemcpy(out, dout, ob, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "far-field copy");
+    }
+    cudaFree(dth);
+    cudaFree(dph);
+    cudaFree(dout);
+    return st;
+}
+
+int hom_transfer(const double E[8], const double omega[2], double sigma, const double* dtau, int n_tau, double* g2,
+                 double* Nc, double* visibility) {
+    if (!E || (n_tau > 0 && (!dtau || !Nc)) || n_tau < 0) return fail(VIE_EINVAL, "bad arguments");
+    for (int i = 0; i < 8; ++i)
+        if (!std::isfinite(E[i])) return fail(VIE_EINVAL, "amplitudes must be finite");
+    const double w1 = omega ? omega[0] : 1.0, w2 = omega ? omega[1] : 1.0;
+    if (!(w1 > 0) || !(w2 > 0)) return fail(VIE_EINVAL, "omega must be positive");
+    if (n_tau > 0 && !(sigma > 0)) return fail(VIE_EINVAL, "sigma must be positive");
+    const HomScalars s = hom_scalars(E, w1, w2);
+    if (g2) *g2 = s.g2;
+    for (int i = 0; i < n_tau; ++i) Nc[i] = hom_nc(s, dtau[i], sigma);
+    if (visibility) *visibility = s.undefined_nc ? NAN : 1.0 - s.nc0;
+    if (s.undefined_g2 || (s.undefined_nc && (n_tau > 0 || visibility)))
+        return fail(VIE_EUNDEF, "g2 or N~c undefined: a channel is absent at the detectors (0/0)");
+    return VIE_OK;
+}
+
+int vie_hom_map(const double* Ea, int nA, const double* Eb, int nB, double sigma, double* g2, double* vis,
+                double* p2) {
+    (void)sigma;
+    if (!Ea || !Eb || nA < 1 || nB < 1) return fail(VIE_EINVAL, "bad arguments");
+    const long long n = (long long)nA * nB;
+    void *dA = nullptr, *dB = nullptr, *dg = nullptr, *dv = nullptr, *dp = nullptr;
+    int st = VIE_OK;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&dA, sizeof(c64) * 2 * nA);
+    if (e == cudaSuccess) e = cudaMalloc(&dB, sizeof(c64) * 2 * nB);
+    if (e == cudaSuccess && g2) e = cudaMalloc(&dg, sizeof(double) * n);
+    if (e == cudaSuccess && vis) e = cudaMalloc(&dv, sizeof(double) * n);
+    if (e == cudaSuccess && p2) e = cudaMalloc(&dp, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(dA, Ea, sizeof(c64) * 2 * nA, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dB, Eb, sizeof(c64) * 2 * nB, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = cuda_fail(e, "hom map buffers");
+    if (st == VIE_OK) st = hom_map_device((const c64*)dA, nA, (const c64*)dB, nB, (double*)dg, (double*)dv,
+                                          (double*)dp, s);
+    if (st == VIE_OK) {
+        e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && g2) e = cudaMemcpy(g2, dg, sizeof(double) * n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && vis) e = cudaMemcpy(vis, dv, sizeof(double) * n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && p2) e = cudaMemcpy(p2, dp, sizeof(double) * n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "hom map copy");
+    }
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dg);
+    cudaFree(dv);
+    cudaFree(dp);
+    if (s) cudaStreamDestroy(s);
+    return st;
+}
+
+int vie_get_current(vie_handle* hd, int rhs, double* out) {
+    if (!hd || !out) return fail(VIE_EINVAL, "NULL argument");
+    if (!hd->have_solution) return fail(VIE_ESTATE, "no solution stored");
+    if (rhs < 0 || rhs >= hd->n_rhs) return fail(VIE_EINVAL, "rhs index out of range");
+    const long long Nb = hd->op.Nb, N = hd->op.N;
+    std::vector<double> buf(6 * Nb);
+    VIE_CUDA(cudaMemcpy(buf.data(), hd->S.x + rhs * hd->S.n3, sizeof(c64) * 3 * Nb, cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(double) * 6 * N);
+    for (int c = 0; c < 3; ++c)
+        for (long long v = 0; v < Nb; ++v) {
+            const long long o = (c * N + hd->vox_host[v]) * 2;
+            out[o] = buf[(c * Nb + v) * 2];
+            out[o + 1] = buf[(c * Nb + v) * 2 + 1];
+        }
+    return VIE_OK;
+}
+
+int vie_apply_device(vie_handle* hd, const void* w_dev, void* y_dev, int n_rhs, int precision) {
+    if (!hd || !w_dev || !y_dev || n_rhs < 1) return fail(VIE_EINVAL, "bad arguments");
+    if (precision != VIE_PREC_MIXED && precision != VIE_PREC_FP64) return fail(VIE_EINVAL, "bad precision");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    std::vector<int> list(n_rhs);
+    for (int r = 0; r < n_rhs; ++r) list[r] = r;
+    VIE_TRY(op_set_list(hd->op, list.data(), n_rhs));
+    const long long n3 = 3 * hd->op.Nb;
+    return op_apply(hd->op, precision, w_dev, n3, y_dev, n3, hd->op.d_list, n_rhs);
+}
+
+int vie_apply(vie_handle* hd, const double* w, double* y, int n_rhs, int precision) {
+    if (!hd || !w || !y || n_rhs < 1) return fail(VIE_EINVAL, "bad arguments");
+    if (precision != VIE_PREC_MIXED && precision != VIE_PREC_FP64) return fail(VIE_EINVAL, "bad precision");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    const long long Nb = hd->op.Nb, N = hd->op.N, n3 = 3 * Nb;
+    const size_t esz = precision == VIE_PREC_FP64 ? sizeof(c64) : sizeof(c32);
+    std::vector<unsigned char> hbuf(esz * n3 * n_rhs);
+    for (int r = 0; r < n_rhs; ++r)
+        for (int c = 0; c < 3; ++c)
+            for (long long v = 0; v < Nb; ++v) {
+                const long long i = ((long long)r * 3 * N + c * N + hd->vox_host[v]) * 2;
+                const long long o = (long long)r * n3 + c * Nb + v;
+                if (precision == VIE_PREC_FP64) reinterpret_cast<c64*>(hbuf.data())[o] = c64{w[i], w[i + 1]};
+                else reinterpret_cast<c32*>(hbuf.data())[o] = c32{(float)w[i], (float)w[i + 1]};
+            }
+    void *dw = nullptr, *dy = nullptr;
+    VIE_CUDA(cudaMalloc(&dw, hbuf.size()));
+    cudaError_t e = cudaMalloc(&dy, hbuf.size());
+    int st = VIE_OK;
+    if (e == cudaSuccess) e = cudaMemcpy(dw, hbuf.data(), hbuf.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = cuda_fail(e, "apply buffers");
+    if (st == VIE_OK) st = vie_apply_device(hd, dw, dy, n_rhs, precision);
+    if (st == VIE_OK) {
+        e = cudaStreamSynchronize(hd->op.stream);
+        if (e == cudaSuccess) e = cudaMemcpy(hbuf.data(), dy, hbuf.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "apply");
+    }
+    cudaFree(dw);
+    cudaFree(dy);
+    if (st != VIE_OK) return st;
+    std::memcpy(y, w, sizeof(double) * 2 * 3 * N * n_rhs);  // y = w outside the body
+    for (int r = 0; r < n_rhs; ++r)
+        for (int c = 0; c < 3; ++c)
+            for (long long v = 0; v < Nb; ++v) {
+                const long long i = ((long long)r * 3 * N + c * N + hd->vox_host[v]) * 2;
+                const long long o = (long long)r * n3 + c * Nb + v;
+                if (precision == VIE_PREC_FP64) {
+                    const c64 a = reinterpret_cast<c64*>(hbuf.data())[o];
+                    y[i] = a.x;
+                    y[i + 1] = a.y;
+                } else {
+                    const c32 a = reinterpret_cast<c32*>(hbuf.data())[o];
+                    y[i] = a.x;
+                    y[i + 1] = a.y;
+                }
+            }
+    return VIE_OK;
+}
+
+int vie_fft_lines(const double* in, double* out, int L, int count, int inverse, int precision) {
+    if (!in || !out || L < 1 || count < 1) return fail(VIE_EINVAL, "bad arguments");
+    const size_t n = (size_t)L * count;
+    const size_t esz = precision == VIE_PREC_FP64 ? sizeof(c64) : sizeof(c32);
+    std::vector<unsigned char> h(esz * n);
+    for (size_t i = 0; i < n; ++i) {
+        if (precision == VIE_PREC_FP64) reinterpret_cast<c64*>(h.data())[i] = c64{in[2 * i], in[2 * i + 1]};
+        else reinterpret_cast<c32*>(h.data())[i] = c32{(float)in[2 * i], (float)in[2 * i + 1]};
+    }
+    void *di = nullptr, *dout = nullptr;
+    VIE_CUDA(cudaMalloc(&di, h.size()));
+    cudaError_t e = cudaMalloc(&dout, h.size());
+    int st = VIE_OK;
+    if (e == cudaSuccess) e = cudaMemcpy(di, h.data(), h.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = cuda_fail(e, "fft buffers");
+    if (st == VIE_OK) st = fft_lines_device(di, dout, L, count, inverse, precision, 0);
+    if (st == VIE_OK) {
+        e = cudaMemcpy(h.data(), dout, h.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "fft copy");
+    }
+    cudaFree(di);
+    cudaFree(dout);
+    if (st != VIE_OK) return st;
+    for (size_t i = 0; i < n; ++i) {
+        if (precision == VIE_PREC_FP64) {
+            const c64 a = reinterpret_cast<c64*>(h.data())[i];
+            out[2 * i] = a.x;
+            out[2 * i + 1] = a.y;
+        } else {
+            const c32 a = reinterpret_cast<c32*>(h.data())[i];
+            out[2 * i] = a.x;
+            out[2 * i + 1] = a.y;
+        }
+    }
+    return VIE_OK;
+}
+
+int vie_get_info(const vie_handle* hd, vie_info* info) {
+    if (!hd || !info) return fail(VIE_EINVAL, "NULL argument");
+    for (int a = 0; a < 3; ++a) {
+        info->n[a] = hd->op.n[a];
+        info->P[a] = hd->op.P[a];
+    }
+    info->n_body = hd->op.Nb;
+    info->n_rhs = hd->n_rhs;
+    info->device = hd->device;
+    info->device_bytes = hd->op.bytes;
+    return VIE_OK;
+}
+
+void* vie_stream(vie_handle* hd) { return hd ? (void*)hd->op.stream : nullptr; }
+
+void vie_destroy(vie_handle* hd) {
+    if (!hd) return;
+    cudaSetDevice(hd->device);
+    if (hd->op.stream) cudaStreamSynchronize(hd->op.stream);
+    hd->S.release(hd->op);
+    op_free(hd->op);
+    if (hd->op.stream) cudaStreamDestroy(hd->op.stream);
+    delete hd;
+}
+
+}  // extern "C"

@@ -1,0 +1,483 @@
+// Right-hand sides, far-field projection (Eq. 25), detector components
+// (Eq. Eproj, Eq. 30) and the two-photon observables (Eq. 10, Eqs. 18-22, 27).
+//
+// Far field F(rhat) = C (I - rhat rhat) S(rhat),  S = sum_v w_v e^{-i k0 rhat.r_v},
+// C = kappa k0^2 h^3 / (4 pi).  The phase factorises over the grid axes,
+// e^{-i k0 rhat.r} = ex(i) ey(j) ez(k), so
+//   * an arbitrary direction list is summed directly in FP64 with per-block
+//     1-D phase tables (two complex multiplies per voxel and direction);
+//   * a (theta, phi) product grid is contracted axis by axis:
+//       A[rc][x][y][t]   = sum_z W[rc][x][y][z] ez(t, z)          (depends on theta)
+//       B[t][rc][x][p]   = sum_y A[rc][x][y][t] ey(t, p, y)
+//       S[rc][t][p]      = sum_x B[t][rc][x][p] ex(t, p, x)
+//     in FP32 with short (<= n) accumulations and FP64-computed phase tables.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "farfield.cuh"
+
+namespace vie {
+
+// ---------------------------------------------------------------------------
+// right-hand sides (Eq. 24's right side in the w unknown: chi E_inc)
+// ---------------------------------------------------------------------------
+__global__ void k_rhs(c64* __restrict__ b, long long n3, const int* __restrict__ vox, const double* __restrict__ chi,
+                      long long Nb, int n1, int n2, double h, double cx, double cy, double cz, double k0,
+                      const double* __restrict__ ch) {
+    const int r = blockIdx.y;
+    const double* c = ch + 9 * r;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < Nb;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int lin = vox[v];
+        const int k = lin % n2;
+        const int j = (lin / n2) % n1;
+        const int i = lin / (n1 * n2);
+        const double px = cx + i * h, py = cy + j * h, pz = cz + k * h;
+        const double ph = k0 * (c[0] * px + c[1] * py + c[2] * pz);
+        double s, co;
+        sincos(ph, &s, &co);
+        const double x = chi[v];
+        for (int q = 0; q < 3; ++q) {
+            const double pr = c[3 + 2 * q], pi = c[4 + 2 * q];
+            b[r * n3 + q * Nb + v] = c64{x * (pr * co - pi * s), x * (pr * s + pi * co)};
+        }
+    }
+}
+
+int build_rhs(Operator& op, Solver& S, const vie_channel* chs, int n_rhs) {
+    std::vector<double> hc(9 * n_rhs);
+    for (int r = 0; r < n_rhs; ++r) {
+        for (int q = 0; q < 3; ++q) hc[9 * r + q] = chs[r].khat[q];
+        for (int q = 0; q < 6; ++q) hc[9 * r + 3 + q] = chs[r].pol[q];
+    }
+    double* d = nullptr;
+    VIE_CUDA(cudaMalloc(&d, sizeof(double) * hc.size()));
+    cudaError_t e = cudaMemcpyAsync(d, hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice, op.stream);
+    if (e == cudaSuccess) {
+        const double cx = op.origin[0] - 0.5 * (op.n[0] - 1) * op.h;
+        const double cy = op.origin[1] - 0.5 * (op.n[1] - 1) * op.h;
+        const double cz = op.origin[2] - 0.5 * (op.n[2] - 1) * op.h;
+        k_rhs<<<dim3(std::max(1, std::min(1024, ceil_div(op.Nb, 256))), n_rhs), 256, 0, op.stream>>>(
+            S.b, S.n3, op.vox, op.chi64, op.Nb, op.n[1], op.n[2], op.h, cx, cy, cz, op.k0, d);
+        count_launch();
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(op.stream);
+    }
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "rhs build");
+    return VIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// far field on a direction list (FP64)
+// ---------------------------------------------------------------------------
+constexpr int FF_DB = 2;  // directions per block
+
+// Sraw[r][d][3] = sum_v w[r][c][v] e^{-i k0 d.r_v}
+__global__ void k_ff_dirs(const c64* __restrict__ x, long long n3, const int* __restrict__ vox, long long Nb, int n0,
+                          int n1, int n2, double h, double cx, double cy, double cz, double k0,
+                          const double* __restrict__ dirs, int D, c64* __restrict__ Sraw) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c64* tab = reinterpret_cast<c64*>(smraw);  // [FF_DB][n0 + n1 + n2]
+    const int nt = n0 + n1 + n2;
+    const int r = blockIdx.y;
+    const int d0 = blockIdx.x * FF_DB;
+    for (int e = threadIdx.x; e < FF_DB * nt; e += blockDim.x) {
+        const int q = e / nt, a = e - q * nt;
+        const int d = min(d0 + q, D - 1);
+        double coord, dc;
+        if (a < n0) {
+            coord = cx + a * h;
+            dc = dirs[3 * d + 0];
+        } else if (a < n0 + n1) {
+            coord = cy + (a - n0) * h;
+            dc = dirs[3 * d + 1];
+        } else {
+            coord = cz + (a - n0 - n1) * h;
+            dc = dirs[3 * d + 2];
+        }
+        double s, c;
+        sincos(-k0 * dc * coord, &s, &c);
+        tab[e] = c64{c, s};
+    }
+    __syncthreads();
+    double acc[FF_DB][3][2];
+#pragma unroll
+    for (int q = 0; q < FF_DB; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[q][c][0] = acc[q][c][1] = 0.0;
+    const c64* xr = x + r * n3;
+    for (long long v = threadIdx.x; v < Nb; v += blockDim.x) {
+        const int lin = vox[v];
+        const int k = lin % n2;
+        const int j = (lin / n2) % n1;
+        const int i = lin / (n1 * n2);
+        const c64 w0 = xr[v], w1 = xr[Nb + v], w2 = xr[2 * Nb + v];
+#pragma unroll
+        for (int q = 0; q < FF_DB; ++q) {
+            const c64* t = tab + q * nt;
+            const c64 ph = t[i] * t[n0 + j] * t[n0 + n1 + k];
+            const c64 p0 = ph * w0, p1 = ph * w1, p2 = ph * w2;
+            acc[q][0][0] += p0.x;
+            acc[q][0][1] += p0.y;
+            acc[q][1][0] += p1.x;
+            acc[q][1][1] += p1.y;
+            acc[q][2][0] += p2.x;
+            acc[q][2][1] += p2.y;
+        }
+    }
+    __shared__ double red[32][FF_DB * 6];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < FF_DB; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                double v = acc[q][c][u];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) red[wid][q * 6 + c * 2 + u] = v;
+            }
+    __syncthreads();
+    if (threadIdx.x < FF_DB * 6) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+        const int q = threadIdx.x / 6, c = (threadIdx.x / 2) % 3, u = threadIdx.x & 1;
+        const int d = d0 + q;
+        if (d < D) reinterpret_cast<double*>(Sraw)[((long long)r * D + d) * 6 + c * 2 + u] = t;
+    }
+}
+
+// out[r][d][3] = basis components of C (I - dd) S
+__global__ void k_ff_project(const c64* __restrict__ Sraw, const double* __restrict__ dirs, int D, int R,
+                             double C, int basis, c64* __restrict__ out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)D * R) return;
+    const int d = (int)(i % D);
+    const double dx = dirs[3 * d], dy = dirs[3 * d + 1], dz = dirs[3 * d + 2];
+    const c64* s = Sraw + i * 3;
+    const c64 ds = {dx * s[0].x + dy * s[1].x + dz * s[2].x, dx * s[0].y + dy * s[1].y + dz * s[2].y};
+    c64 F[3] = {{C * (s[0].x - dx * ds.x), C * (s[0].y - dx * ds.y)},
+                {C * (s[1].x - dy * ds.x), C * (s[1].y - dy * ds.y)},
+                {C * (s[2].x - dz * ds.x), C * (s[2].y - dz * ds.y)}};
+    c64* o = out + i * 3;
+    if (basis == VIE_BASIS_CART) {
+        o[0] = F[0];
+        o[1] = F[1];
+        o[2] = F[2];
+        return;
+    }
+    const double th = acos(fmin(1.0, fmax(-1.0, dz)));
+    const double ph = atan2(dy, dx);
+    double st, ct, sp, cp;
+    sincos(th, &st, &ct);
+    sincos(ph, &sp, &cp);
+    const double et[3] = {ct * cp, ct * sp, -st}, ep[3] = {-sp, cp, 0.0};
+    const c64 Ft = {et[0] * F[0].x + et[1] * F[1].x + et[2] * F[2].x, et[0] * F[0].y + et[1] * F[1].y + et[2] * F[2].y};
+    const c64 Fp = {ep[0] * F[0].x + ep[1] * F[1].x, ep[0] * F[0].y + ep[1] * F[1].y};
+    const c64 Fr = {dx * F[0].x + dy * F[1].x + dz * F[2].x, dx * F[0].y + dy * F[1].y + dz * F[2].y};
+    if (basis == VIE_BASIS_SPH) {
+        o[0] = Ft;
+        o[1] = Fp;
+        o[2] = Fr;
+    } else {
+        const double s2 = 0.70710678118654752440;
+        o[0] = c64{s2 * (Ft.x - Fp.y), s2 * (Ft.y + Fp.x)};  // (Ft + i Fp)/sqrt2
+        o[1] = c64{s2 * (Ft.x + Fp.y), s2 * (Ft.y - Fp.x)};  // (Ft - i Fp)/sqrt2
+        o[2] = Fr;
+    }
+}
+
+static double ff_constant(const Operator& op) {
+    const double a = op.h * std::cbrt(3.0 / (4.0 * M_PI));
+    const double ka = op.k0 * a;
+    double kap;
+    if (ka < 1e-3) kap = 1.0 - ka * ka / 10.0 + ka * ka * ka * ka / 280.0;
+    else kap = 3.0 * (std::sin(ka) - ka * std::cos(ka)) / (ka * ka * ka);
+    return kap * op.k0 * op.k0 * op.h * op.h * op.h / (4.0 * M_PI);
+}
+
+int farfield_dirs(Operator& op, const c64* x, long long n3, int R, const double* ddirs, int D, int basis,
+                  c64* dout) {
+    c64* Sraw = nullptr;
+    VIE_CUDA(cudaMalloc(&Sraw, sizeof(c64) * 3 * (size_t)D * R));
+    const double cx = op.origin[0] - 0.5 * (op.n[0] - 1) * op.h;
+    const double cy = op.origin[1] - 0.5 * (op.n[1] - 1) * op.h;
+    const double cz = op.origin[2] - 0.5 * (op.n[2] - 1) * op.h;
+    const size_t sm = sizeof(c64) * FF_DB * (op.n[0] + op.n[1] + op.n[2]);
+    cudaFuncSetAttribute(k_ff_dirs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    k_ff_dirs<<<dim3(ceil_div(D, FF_DB), R), 256, sm, op.stream>>>(x, n3, op.vox, op.Nb, op.n[0], op.n[1], op.n[2],
+                                                                   op.h, cx, cy, cz, op.k0, ddirs, D, Sraw);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_ff_project<<<ceil_div((long long)D * R, 256), 256, 0, op.stream>>>(Sraw, ddirs, D, R, ff_constant(op), basis,
+                                                                             dout);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op.stream);
+    cudaFree(Sraw);
+    if (e != cudaSuccess) return cuda_fail(e, "far field (directions)");
+    return VIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// far field on a (theta, phi) product grid: separable contraction (FP32)
+// ---------------------------------------------------------------------------
+// full-grid FP32 copy of the currents: W[r][c][x][y][z]
+__global__ void k_scatter_full(const c64* __restrict__ x, long long n3, const int* __restrict__ vox, long long Nb,
+                               long long N, c32* __restrict__ W) {
+    const int rc = blockIdx.y;  // r*3 + c
+    const int r = rc / 3, c = rc % 3;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < Nb;
+         v += (long long)gridDim.x * blockDim.x) {
+        const c64 a = x[r * n3 + c * Nb + v];
+        W[(long long)rc * N + vox[v]] = c32{(float)a.x, (float)a.y};
+    }
+}
+
+// Batched complex GEMM C[b](m,n) = sum_k A[b](m,k) B[b](k,n), FP32, generic strides.
+constexpr int GT = 32;  // tile
+__global__ void k_cgemm(int M, int N, int K, const c32* __restrict__ A, long long sAb, long long sAm, long long sAk,
+                        const c32* __restrict__ B, long long sBb, long long sBk, long long sBn, c32* __restrict__ C,
+                        long long sCb, long long sCm, long long sCn) {
+    __shared__ c32 As[GT][GT + 1];
+    __shared__ c32 Bs[GT][GT + 1];
+    const int bz = blockIdx.z;
+    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2x2 outputs each
+    A += bz * sAb;
+    B += bz * sBb;
+    C += bz * sCb;
+    float acc[2][2][2] = {};
+    for (int k0 = 0; k0 < K; k0 += GT) {
+        for (int e = threadIdx.x; e < GT * GT; e += 256) {
+            const int i = e / GT, kk = e % GT;
+            const int m = m0 + i, k = k0 + kk;
+            As[i][kk] = (m < M && k < K) ? A[m * sAm + k * sAk] : c32{0.f, 0.f};
+            const int k2 = k0 + i, n = n0 + kk;
+            Bs[i][kk] = (k2 < K && n < N) ? B[k2 * sBk + n * sBn] : c32{0.f, 0.f};
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < GT; ++kk) {
+            c32 a0 = As[ty * 2][kk], a1 = As[ty * 2 + 1][kk];
+            c32 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+            const c32 av[2] = {a0, a1}, bv[2] = {b0, b1};
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    acc[p][q][0] += av[p].x * bv[q].x - av[p].y * bv[q].y;
+                    acc[p][q][1] += av[p].x * bv[q].y + av[p].y * bv[q].x;
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int m = m0 + ty * 2 + p, n = n0 + tx * 2 + q;
+            if (m < M && n < N) C[m * sCm + n * sCn] = c32{acc[p][q][0], acc[p][q][1]};
+        }
+}
+
+// phase tables: ez[t][z] = e^{-i k0 cos(th_t) z}, ey[t][p][y] = e^{-i k0 sin th sin ph y},
+// ex[t][p][x] = e^{-i k0 sin th cos ph x}
+__global__ void k_phase_tables(const double* __restrict__ th, int nt, const double* __restrict__ ph, int np, int n0,
+                               int n1, int n2, double h, double cx, double cy, double cz, double k0, c32* ez, c32* ey,
+                               c32* ex) {
+    const long long totz = (long long)nt * n2, toty = (long long)nt * np * n1, totx = (long long)nt * np * n0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < totz + toty + totx;
+         i += (long long)gridDim.x * blockDim.x) {
+        double arg;
+        if (i < totz) {
+            const int t = (int)(i / n2), z = (int)(i % n2);
+            arg = -k0 * cos(th[t]) * (cz + z * h);
+            double s, c;
+            sincos(arg, &s, &c);
+            ez[i] = c32{(float)c, (float)s};
+        } else if (i < totz + toty) {
+            const long long q = i - totz;
+            const int y = (int)(q % n1);
+            const int p = (int)((q / n1) % np);
+            const int t = (int)(q / ((long long)n1 * np));
+            arg = -k0 * sin(th[t]) * sin(ph[p]) * (cy + y * h);
+            double s, c;
+            sincos(arg, &s, &c);
+            ey[q] = c32{(float)c, (float)s};
+        } else {
+            const long long q = i - totz - toty;
+            const int x = (int)(q % n0);
+            const int p = (int)((q / n0) % np);
+            const int t = (int)(q / ((long long)n0 * np));
+            arg = -k0 * sin(th[t]) * cos(ph[p]) * (cx + x * h);
+            double s, c;
+            sincos(arg, &s, &c);
+            ex[q] = c32{(float)c, (float)s};
+        }
+    }
+}
+
+// S[rc][t][p] = sum_x B[t][rc*n0 + x][p] ex[t][p][x]; then projection
+__global__ void k_ff_xreduce(const c32* __restrict__ Bt, const c32* __restrict__ ex, int nt, int np, int n0, int RC,
+                             c64* __restrict__ Sraw /* [R][nt*np][3] */) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long tot = (long long)nt * np * RC;
+    if (i >= tot) return;
+    const int p = (int)(i % np);
+    const int rc = (int)((i / np) % RC);
+    const int t = (int)(i / ((long long)np * RC));
+    const c32* e = ex + ((long long)t * np + p) * n0;
+    const c32* b = Bt + ((long long)t * RC * n0 + (long long)rc * n0) * np + p;
+    float ar = 0.f, ai = 0.f;
+    for (int x = 0; x < n0; ++x) {
+        const c32 bv = b[(long long)x * np];
+        const c32 ev = e[x];
+        ar += bv.x * ev.x - bv.y * ev.y;
+        ai += bv.x * ev.y + bv.y * ev.x;
+    }
+    const int r = rc / 3, c = rc % 3;
+    Sraw[(((long long)r * nt + t) * np + p) * 3 + c] = c64{ar, ai};
+}
+
+__global__ void k_grid_dirs(const double* __restrict__ th, int nt, const double* __restrict__ ph, int np,
+                            double* __restrict__ dirs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt * np) return;
+    const int t = i / np, p = i % np;
+    double st, ct, sp, cp;
+    sincos(th[t], &st, &ct);
+    sincos(ph[p], &sp, &cp);
+    dirs[3 * i] = st * cp;
+    dirs[3 * i + 1] = st * sp;
+    dirs[3 * i + 2] = ct;
+}
+
+int farfield_grid(Operator& op, const c64* x, long long n3, int R, const double* dth, int nt, const double* dph,
+                  int np, int basis, c64* dout) {
+    const int n0 = op.n[0], n1 = op.n[1], n2 = op.n[2];
+    const long long N = op.N;
+    const int RC = 3 * R;
+    std::vector<void*> bufs;
+    auto alloc = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        bufs.push_back(p);
+        return p;
+    };
+    auto cleanup = [&]() {
+        for (void* p : bufs) cudaFree(p);
+    };
+    c32* W = (c32*)alloc(sizeof(c32) * N * RC);
+    c32* ez = (c32*)alloc(sizeof(c32) * (size_t)nt * n2);
+    c32* ey = (c32*)alloc(sizeof(c32) * (size_t)nt * np * n1);
+    c32* ex = (c32*)alloc(sizeof(c32) * (size_t)nt * np * n0);
+    c32* A = (c32*)alloc(sizeof(c32) * (size_t)RC * n0 * n1 * nt);
+    c32* Bt = (c32*)alloc(sizeof(c32) * (size_t)nt * RC * n0 * np);
+    c64* Sraw = (c64*)alloc(sizeof(c64) * 3 * (size_t)R * nt * np);
+    double* dirs = (double*)alloc(sizeof(double) * 3 * (size_t)nt * np);
+    if (!W || !ez || !ey || !ex || !A || !Bt || !Sraw || !dirs) {
+        cleanup();
+        return fail(VIE_ENOMEM, "far-field workspace allocation failed");
+    }
+    cudaStream_t s = op.stream;
+    const double cx = op.origin[0] - 0.5 * (n0 - 1) * op.h;
+    const double cy = op.origin[1] - 0.5 * (n1 - 1) * op.h;
+    const double cz = op.origin[2] - 0.5 * (n2 - 1) * op.h;
+    cudaMemsetAsync(W, 0, sizeof(c32) * N * RC, s);
+    k_scatter_full<<<dim3(std::max(1, std::min(2048, ceil_div(op.Nb, 256))), RC), 256, 0, s>>>(x, n3, op.vox, op.Nb,
+                                                                                               N, W);
+    k_phase_tables<<<1024, 256, 0, s>>>(dth, nt, dph, np, n0, n1, n2, op.h, cx, cy, cz, op.k0, ez, ey, ex);
+    // stage A: M = RC*n0*n1, K = n2, N = nt
+    {
+        const int M = RC * n0 * n1;
+        dim3 g(ceil_div(nt, GT), ceil_div(M, GT), 1);
+        k_cgemm<<<g, 256, 0, s>>>(M, nt, n2, W, 0, n2, 1, ez, 0, 1, n2, A, 0, nt, 1);
+    }
+    // stage B: per t: M = RC*n0, K = n1, N = np; A(m,y) = A[(m*n1 + y)*nt + t]
+    {
+        const int M = RC * n0;
+        dim3 g(ceil_div(np, GT), ceil_div(M, GT), nt);
+        k_cgemm<<<g, 256, 0, s>>>(M, np, n1, A, 1, (long long)n1 * nt, nt, ey, (long long)np * n1, 1, n1, Bt,
+                                  (long long)M * np, np, 1);
+    }
+    k_ff_xreduce<<<ceil_div((long long)nt * np * RC, 256), 256, 0, s>>>(Bt, ex, nt, np, n0, RC, Sraw);
+    k_grid_dirs<<<ceil_div(nt * np, 256), 256, 0, s>>>(dth, nt, dph, np, dirs);
+    k_ff_project<<<ceil_div((long long)nt * np * R, 256), 256, 0, s>>>(Sraw, dirs, nt * np, R, ff_constant(op), basis,
+                                                                       dout);
+    count_launch(7);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "far field (grid)");
+    return VIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// two-photon observables
+// ---------------------------------------------------------------------------
+__global__ void k_hom_map(const c64* __restrict__ Ea, int nA, const c64* __restrict__ Eb, int nB, double* g2,
+                          double* vis, double* p2) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)nA * nB) return;
+    const int ia = (int)(i / nB), ib = (int)(i % nB);
+    double E[8];
+    const c64 a1 = Ea[ia], a2 = Ea[nA + ia], b1 = Eb[ib], b2 = Eb[nB + ib];
+    E[0] = a1.x;
+    E[1] = a1.y;
+    E[2] = a2.x;
+    E[3] = a2.y;
+    E[4] = b1.x;
+    E[5] = b1.y;
+    E[6] = b2.x;
+    E[7] = b2.y;
+    HomScalars s = hom_scalars(E, 1.0, 1.0);
+    if (g2) g2[i] = s.g2;
+    if (vis) vis[i] = s.undefined_nc ? nan("") : 1.0 - s.nc0;
+    if (p2) {
+        const double Ia = (a1.x + a2.x) * (a1.x + a2.x) + (a1.y + a2.y) * (a1.y + a2.y);
+        const double Ib = (b1.x + b2.x) * (b1.x + b2.x) + (b1.y + b2.y) * (b1.y + b2.y);
+        p2[i] = Ia * Ib;
+    }
+}
+
+__global__ void k_max(const double* __restrict__ v, long long n, unsigned long long* __restrict__ out) {
+    double m = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, v[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_scale_by(double* __restrict__ v, long long n, const unsigned long long* __restrict__ mx) {
+    const double m = __longlong_as_double((long long)*mx);
+    const double s = m > 0 ? 1.0 / m : 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v[i] *= s;
+}
+
+int hom_map_device(const c64* Ea, int nA, const c64* Eb, int nB, double* g2, double* vis, double* p2,
+                   cudaStream_t s) {
+    const long long n = (long long)nA * nB;
+    k_hom_map<<<ceil_div(n, 256), 256, 0, s>>>(Ea, nA, Eb, nB, g2, vis, p2);
+    count_launch();
+    VIE_CUDA(cudaGetLastError());
+    if (p2) {
+        unsigned long long* mx = nullptr;
+        VIE_CUDA(cudaMalloc(&mx, sizeof(unsigned long long)));
+        cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s);
+        k_max<<<std::max(1, std::min(1024, ceil_div(n, 256))), 256, 0, s>>>(p2, n, mx);
+        k_scale_by<<<std::max(1, std::min(1024, ceil_div(n, 256))), 256, 0, s>>>(p2, n, mx);
+        count_launch(2);
+        cudaError_t e = cudaStreamSynchronize(s);
+        cudaFree(mx);
+        if (e != cudaSuccess) return cuda_fail(e, "hom map");
+    }
+    return VIE_OK;
+}
+
+}  // namespace vie

@@ -1,0 +1,254 @@
+// Shared-memory mixed-radix Stockham FFT engine (radices 16, 8, 4, 2, 3, 5, 7).
+//
+// The zero-padded convolution of Sec. II-C needs many short 1-D transforms
+// (lengths P = smallest 2,3,5,7-smooth size >= 2n-1) along each grid axis.
+// A CTA holds a tile of `nl` lines in shared memory in "column" layout:
+// element p of line l lives at s[p * ld + l].  Each Stockham stage of radix R
+// reads R elements of stride L/R into registers, applies the stage twiddles,
+// performs an R-point DFT in registers and writes the results in autosorted
+// position; two buffers alternate between stages.  Twiddles are precomputed
+// on the host in FP64 (rounded once to the working precision) and staged in
+// shared memory.
+//
+// Forward transforms use exp(-2 pi i j k / L), inverse exp(+2 pi i j k / L),
+// both unnormalised.
+#pragma once
+
+#include "common.cuh"
+
+namespace vie {
+
+constexpr int FFT_MAX_STAGES = 10;
+constexpr int FFT_MAX_L = 1024;
+
+struct FFTPlan {
+    int L;
+    int nst;
+    int R[FFT_MAX_STAGES];
+    int Ns[FFT_MAX_STAGES];
+    int twoff[FFT_MAX_STAGES];
+    int twlen;  // total twiddle entries
+};
+
+// ---- small DFTs in registers ----------------------------------------------
+// multiply by -i (forward) or +i (inverse)
+template <typename T, bool INV> __device__ __forceinline__ cplx<T> mul_mi(cplx<T> a) {
+    return INV ? cplx<T>{-a.y, a.x} : cplx<T>{a.y, -a.x};
+}
+
+template <typename T, bool INV> __device__ __forceinline__ void dft2(cplx<T>& a0, cplx<T>& a1) {
+    cplx<T> t = a0;
+    a0 = t + a1;
+    a1 = t - a1;
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2, cplx<T>& a3) {
+    cplx<T> t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, t3 = mul_mi<T, INV>(a1 - a3);
+    a0 = t0 + t2;
+    a2 = t0 - t2;
+    a1 = t1 + t3;
+    a3 = t1 - t3;
+}
+
+#define VIE_SQRT1_2 0.70710678118654752440
+#define VIE_COS_PI8 0.92387953251128675613
+#define VIE_SIN_PI8 0.38268343236508977173
+
+// twiddle w_N^k = exp(-+ 2 pi i k / N) for the radix-8/16 inner combinations
+template <typename T, bool INV> __device__ __forceinline__ cplx<T> w8(int k) {
+    const T c = (T)VIE_SQRT1_2;
+    cplx<T> w;
+    switch (k & 7) {
+        case 0: w = {1, 0}; break;
+        case 1: w = {c, -c}; break;
+        case 2: w = {0, -1}; break;
+        default: w = {-c, -c}; break;  // k = 3
+    }
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+template <typename T, bool INV> __device__ __forceinline__ void dft8(cplx<T>* a) {
+    // even / odd split: E = DFT4(a0,a2,a4,a6), O = DFT4(a1,a3,a5,a7)
+    cplx<T> e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    cplx<T> o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+    dft4<T, INV>(e0, e1, e2, e3);
+    dft4<T, INV>(o0, o1, o2, o3);
+    cplx<T> E[4] = {e0, e1, e2, e3}, O[4] = {o0, o1, o2, o3};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        cplx<T> t = w8<T, INV>(k) * O[k];
+        a[k] = E[k] + t;
+        a[k + 4] = E[k] - t;
+    }
+}
+
+template <typename T, bool INV> __device__ __forceinline__ cplx<T> w16(int k) {
+    const T c1 = (T)VIE_COS_PI8, s1 = (T)VIE_SIN_PI8, h = (T)VIE_SQRT1_2;
+    cplx<T> w;
+    switch (k) {
+        case 0: w = {1, 0}; break;
+        case 1: w = {c1, -s1}; break;
+        case 2: w = {h, -h}; break;
+        case 3: w = {s1, -c1}; break;
+        case 4: w = {0, -1}; break;
+        case 5: w = {-s1, -c1}; break;
+        case 6: w = {-h, -h}; break;
+        default: w = {-c1, -s1}; break;  // k = 7
+    }
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+template <typename T, bool INV> __device__ __forceinline__ void dft16(cplx<T>* a) {
+    cplx<T> E[8], O[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        E[k] = a[2 * k];
+        O[k] = a[2 * k + 1];
+    }
+    dft8<T, INV>(E);
+    dft8<T, INV>(O);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        cplx<T> t = w16<T, INV>(k) * O[k];
+        a[k] = E[k] + t;
+        a[k + 8] = E[k] - t;
+    }
+}
+
+template <typename T, bool INV> __device__ __forceinline__ void dft3(cplx<T>* a) {
+    const T s3 = (T)0.86602540378443864676;
+    cplx<T> t = a[1] + a[2], d = a[1] - a[2];
+    cplx<T> m = {a[0].x - (T)0.5 * t.x, a[0].y - (T)0.5 * t.y};
+    // forward: y1 = m - i s3 d, y2 = m + i s3 d
+    cplx<T> r = mul_mi<T, INV>(d);
+    a[0] = a[0] + t;
+    a[1] = {m.x + s3 * r.x, m.y + s3 * r.y};
+    a[2] = {m.x - s3 * r.x, m.y - s3 * r.y};
+}
+
+// direct DFT for the odd radices 5 and 7: y_q = sum_t a_t exp(-+ 2 pi i t q / R)
+template <int R> struct OddRoots;
+template <> struct OddRoots<5> {
+    __device__ static double c(int k) {
+        const double v[5] = {1.0, 0.30901699437494742410, -0.80901699437494742410,
+                             -0.80901699437494742410, 0.30901699437494742410};
+        return v[k];
+    }
+    __device__ static double s(int k) {
+        const double v[5] = {0.0, 0.95105651629515357212, 0.58778525229247312917,
+                             -0.58778525229247312917, -0.95105651629515357212};
+        return v[k];
+    }
+};
+template <> struct OddRoots<7> {
+    __device__ static double c(int k) {
+        const double v[7] = {1.0, 0.62348980185873353053, -0.22252093395631440429,
+                             -0.90096886790241912624, -0.90096886790241912624,
+                             -0.22252093395631440429, 0.62348980185873353053};
+        return v[k];
+    }
+    __device__ static double s(int k) {
+        const double v[7] = {0.0, 0.78183148246802980871, 0.97492791218182360702,
+                             0.43388373911755812048, -0.43388373911755812048,
+                             -0.97492791218182360702, -0.78183148246802980871};
+        return v[k];
+    }
+};
+
+template <typename T, int R, bool INV> __device__ __forceinline__ void dft_odd(cplx<T>* a) {
+    cplx<T> y[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        cplx<T> acc = a[0];
+#pragma unroll
+        for (int t = 1; t < R; ++t) {
+            const int k = (t * q) % R;
+            const T c = (T)OddRoots<R>::c(k);
+            const T s = INV ? (T)OddRoots<R>::s(k) : -(T)OddRoots<R>::s(k);
+            acc.x += a[t].x * c - a[t].y * s;
+            acc.y += a[t].x * s + a[t].y * c;
+        }
+        y[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) a[q] = y[q];
+}
+
+template <typename T, int R, bool INV> __device__ __forceinline__ void dft(cplx<T>* a) {
+    if constexpr (R == 2) dft2<T, INV>(a[0], a[1]);
+    else if constexpr (R == 4) dft4<T, INV>(a[0], a[1], a[2], a[3]);
+    else if constexpr (R == 8) dft8<T, INV>(a);
+    else if constexpr (R == 16) dft16<T, INV>(a);
+    else if constexpr (R == 3) dft3<T, INV>(a);
+    else dft_odd<T, R, INV>(a);
+}
+
+// ---- one Stockham stage over nl lines in column layout ---------------------
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out,
+                                               int L, int Ns, int nl, int ld,
+                                               const cplx<T>* __restrict__ tw) {
+    const int nbf = L / R;
+    const int total = nbf * nl;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        const int l = b % nl;
+        const int j = b / nl;
+        cplx<T> a[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) a[t] = in[(j + t * nbf) * ld + l];
+        const int k = j % Ns;
+        if (Ns > 1) {
+            const cplx<T>* w = tw + k * (R - 1);
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                cplx<T> wt = w[t - 1];
+                if (INV) wt.y = -wt.y;
+                a[t] = a[t] * wt;
+            }
+        }
+        dft<T, R, INV>(a);
+        const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int t = 0; t < R; ++t) out[(base + t * Ns) * ld + l] = a[t];
+    }
+}
+
+// Full transform of nl lines; data starts in `a`, `b` is scratch of the same
+// size.  Returns the buffer holding the result.  Must be called by the whole
+// CTA; ends with a __syncthreads().
+template <typename T, bool INV>
+__device__ cplx<T>* fft_tile(cplx<T>* a, cplx<T>* b, const FFTPlan& p, const cplx<T>* tw, int nl, int ld) {
+    cplx<T>* in = a;
+    cplx<T>* out = b;
+    for (int s = 0; s < p.nst; ++s) {
+        const cplx<T>* t = tw + p.twoff[s];
+        switch (p.R[s]) {
+            case 16: stockham_stage<T, 16, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
+            case 8: stockham_stage<T, 8, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
+            case 4: stockham_stage<T, 4, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
+            case 2: stockham_stage<T, 2, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
+            case 3: stockham_stage<T, 3, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
+            case 5: stockham_stage<T, 5, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
+            default: stockham_stage<T, 7, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
+        }
+        __syncthreads();
+        cplx<T>* tmp = in;
+        in = out;
+        out = tmp;
+    }
+    return in;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cplx<T>* dst, const cplx<T>* __restrict__ src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// host side: plan construction and twiddle table (FP64, rounded to T on copy)
+bool make_plan(int L, FFTPlan* p);
+void plan_twiddles(const FFTPlan& p, double* re_im /* [2*twlen] */);
+
+}  // namespace vie

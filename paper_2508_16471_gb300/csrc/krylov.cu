@@ -1,0 +1,589 @@
+// Batched restarted GMRES with iterative refinement (solve of Eq. 24 for every
+// incident channel at once).
+//
+// Precision layout:
+//   * outer loop in FP64: x (solution), b, the true residual r = b - A64 x and
+//     its norm (the convergence test);
+//   * inner GMRES cycle of at most m steps on A_T d = r with the Krylov basis
+//     stored in T (float in mixed mode, double in plain FP64 mode); the
+//     Arnoldi inner products and the update w -= V h accumulate in FP64
+//     (classical Gram-Schmidt, two passes), the Hessenberg matrix, the Givens
+//     rotations and the least-squares solve are FP64;
+//   * after each cycle x += V y in FP64 and the FP64 residual is recomputed.
+// Each RHS stops on its own; converged RHS drop out of the launch lists.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "krylov.cuh"
+
+namespace vie {
+
+constexpr int KB = 256;   // threads per block for vector kernels
+constexpr int KE = 4;     // elements per thread
+constexpr int KCH = KB * KE;
+
+template <typename T> __device__ __forceinline__ c64 ld64(const cplx<T>* p, long long i) {
+    const cplx<T> v = p[i];
+    return c64{(double)v.x, (double)v.y};
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// partial[(r*mp1 + i)*nblk + b] = sum over block b of conj(V_i) . V_{j+1}
+template <typename T>
+__global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long long vstride, int j,
+                       const int* __restrict__ list, c64* __restrict__ partial, int mp1, long long n, int nblk) {
+    __shared__ double sre[KB / 32][64], sim[KB / 32][64];
+    const int r = list[blockIdx.y];
+    const cplx<T>* Vr = V + r * rstride;
+    const cplx<T>* w = Vr + (long long)(j + 1) * vstride;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+    c64 wv[KE];
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        wv[k] = e < n ? ld64(w, e) : c64{0, 0};
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = 0; i <= j; ++i) {
+        const cplx<T>* vi = Vr + (long long)i * vstride;
+        double ar = 0, ai = 0;
+#pragma unroll
+        for (int k = 0; k < KE; ++k) {
+            const long long e = e0 + k * KB;
+            if (e < n) {
+                const c64 a = ld64(vi, e);
+                ar += a.x * wv[k].x + a.y * wv[k].y;
+                ai += a.x * wv[k].y - a.y * wv[k].x;
+            }
+        }
+        ar = warp_sum(ar);
+        ai = warp_sum(ai);
+        if (lane == 0) {
+            sre[wid][i] = ar;
+            sim[wid][i] = ai;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j; i += KB) {
+        double ar = 0, ai = 0;
+        for (int q = 0; q < KB / 32; ++q) {
+            ar += sre[q][i];
+            ai += sim[q][i];
+        }
+        partial[((long long)r * mp1 + i) * nblk + blockIdx.x] = c64{ar, ai};
+    }
+}
+
+// coef[r][i] = sum_b partial; H[r][i, j] (+)= coef
+__global__ void k_reduce_dots(const c64* __restrict__ partial, c64* __restrict__ coef, c64* __restrict__ H, int j,
+                              const int* __restrict__ list, int mp1, int nblk, int accumulate) {
+    __shared__ double sre[KB / 32], sim[KB / 32];
+    const int r = list[blockIdx.y];
+    const int i = blockIdx.x;
+    const c64* p = partial + ((long long)r * mp1 + i) * nblk;
+    double ar = 0, ai = 0;
+    for (int b = threadIdx.x; b < nblk; b += KB) {
+        ar += p[b].x;
+        ai += p[b].y;
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if ((threadIdx.x & 31) == 0) {
+        sre[threadIdx.x >> 5] = ar;
+        sim[threadIdx.x >> 5] = ai;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0, ti = 0;
+        for (int q = 0; q < KB / 32; ++q) {
+            tr += sre[q];
+            ti += sim[q];
+        }
+        coef[(long long)r * mp1 + i] = c64{tr, ti};
+        c64* h = H + (long long)r * mp1 * (mp1 - 1) + (long long)j * mp1 + i;  // column-major (m+1) x m
+        if (accumulate) *h = c64{h->x + tr, h->y + ti};
+        else *h = c64{tr, ti};
+    }
+}
+
+// w = V_{j+1} -= sum_{i<=j} coef_i V_i ; normpart[r][b] = ||w||^2 over block
+template <typename T>
+__global__ void k_update(cplx<T>* __restrict__ V, long long rstride, long long vstride, int j,
+                         const int* __restrict__ list, const c64* __restrict__ coef, double* __restrict__ normpart,
+                         int mp1, long long n, int nblk) {
+    __shared__ c64 cf[64];
+    __shared__ double ws[KB / 32];
+    const int r = list[blockIdx.y];
+    for (int i = threadIdx.x; i <= j; i += KB) cf[i] = coef[(long long)r * mp1 + i];
+    __syncthreads();
+    cplx<T>* Vr = V + r * rstride;
+    cplx<T>* w = Vr + (long long)(j + 1) * vstride;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+    c64 acc[KE];
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        acc[k] = e < n ? ld64(w, e) : c64{0, 0};
+    }
+    for (int i = 0; i <= j; ++i) {
+        const cplx<T>* vi = Vr + (long long)i * vstride;
+        const c64 c = cf[i];
+#pragma unroll
+        for (int k = 0; k < KE; ++k) {
+            const long long e = e0 + k * KB;
+            if (e < n) {
+                const c64 a = ld64(vi, e);
+                acc[k].x -= c.x * a.x - c.y * a.y;
+                acc[k].y -= c.x * a.y + c.y * a.x;
+            }
+        }
+    }
+    double nrm = 0;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) {
+            const cplx<T> o = cplx<T>{(T)acc[k].x, (T)acc[k].y};
+            w[e] = o;
+            nrm += (double)o.x * o.x + (double)o.y * o.y;
+        }
+    }
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < KB / 32; ++q) t += ws[q];
+        normpart[(long long)r * nblk + blockIdx.x] = t;
+    }
+}
+
+// One thread per listed RHS: finish step j (Givens rotations, residual estimate).
+__global__ void k_finish(const double* __restrict__ normpart, int nblk, c64* __restrict__ H, double* __restrict__ cs,
+                         c64* __restrict__ sn, c64* __restrict__ g, double* __restrict__ inv, int* __restrict__ kcount,
+                         int* __restrict__ flag, const double* __restrict__ target, int j, const int* __restrict__ list,
+                         int nr, int m) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nr) return;
+    const int r = list[s];
+    const int mp1 = m + 1;
+    double t = 0;
+    for (int b = 0; b < nblk; ++b) t += normpart[(long long)r * nblk + b];
+    const double hn = sqrt(t);
+    c64* Hc = H + (long long)r * mp1 * m + (long long)j * mp1;  // column j
+    Hc[j + 1] = c64{hn, 0};
+    double* c = cs + (long long)r * m;
+    c64* sr = sn + (long long)r * m;
+    c64* gr = g + (long long)r * mp1;
+    for (int i = 0; i < j; ++i) {
+        const c64 a = Hc[i], b = Hc[i + 1];
+        const c64 sv = sr[i];
+        // [c s; -conj(s) c] [a; b]
+        const c64 t0 = {c[i] * a.x + (sv.x * b.x - sv.y * b.y), c[i] * a.y + (sv.x * b.y + sv.y * b.x)};
+        const c64 t1 = {-(sv.x * a.x + sv.y * a.y) + c[i] * b.x, -(sv.x * a.y - sv.y * a.x) + c[i] * b.y};
+        Hc[i] = t0;
+        Hc[i + 1] = t1;
+    }
+    const c64 a = Hc[j], b = Hc[j + 1];
+    const double aa = sqrt(a.x * a.x + a.y * a.y), bb = sqrt(b.x * b.x + b.y * b.y);
+    const double den = sqrt(aa * aa + bb * bb);
+    double cj;
+    c64 sj;
+    if (den == 0.0) {
+        cj = 1.0;
+        sj = c64{0, 0};
+    } else if (aa == 0.0) {
+        cj = 0.0;
+        sj = c64{b.x / bb, -b.y / bb};  // conj(b)/|b| so that s b = |b|
+    } else {
+        cj = aa / den;
+        const c64 ph = {a.x / aa, a.y / aa};
+        // s = (a/|a|) conj(b) / den
+        sj = c64{(ph.x * b.x + ph.y * b.y) / den, (ph.y * b.x - ph.x * b.y) / den};
+    }
+    c[j] = cj;
+    sr[j] = sj;
+    Hc[j] = c64{cj * a.x + (sj.x * b.x - sj.y * b.y), cj * a.y + (sj.x * b.y + sj.y * b.x)};
+    Hc[j + 1] = c64{0, 0};
+    const c64 gj = gr[j];
+    gr[j + 1] = c64{-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x)};  // -conj(s) g_j
+    gr[j] = c64{cj * gj.x, cj * gj.y};
+    const double est = sqrt(gr[j + 1].x * gr[j + 1].x + gr[j + 1].y * gr[j + 1].y);
+    kcount[r] = j + 1;
+    inv[r] = hn > 0 ? 1.0 / hn : 0.0;
+    const bool breakdown = !(hn > 1e-300);
+    flag[r] = (est <= target[r] || breakdown || !isfinite(est)) ? 1 : 0;
+}
+
+template <typename T>
+__global__ void k_scale(cplx<T>* __restrict__ V, long long rstride, long long vstride, int j,
+                        const int* __restrict__ list, const double* __restrict__ inv, long long n) {
+    const int r = list[blockIdx.y];
+    cplx<T>* w = V + r * rstride + (long long)(j + 1) * vstride;
+    const double s = inv[r];
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) {
+            const cplx<T> v = w[e];
+            w[e] = cplx<T>{(T)(v.x * s), (T)(v.y * s)};
+        }
+    }
+}
+
+// back substitution: y = R^{-1} g over the first kcount[r] rows (one thread / RHS)
+__global__ void k_lsq(const c64* __restrict__ H, const c64* __restrict__ g, c64* __restrict__ y,
+                      const int* __restrict__ kcount, const int* __restrict__ list, int nr, int m) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nr) return;
+    const int r = list[s];
+    const int mp1 = m + 1;
+    const int k = kcount[r];
+    const c64* Hr = H + (long long)r * mp1 * m;
+    const c64* gr = g + (long long)r * mp1;
+    c64* yr = y + (long long)r * m;
+    for (int i = k - 1; i >= 0; --i) {
+        c64 acc = gr[i];
+        for (int q = i + 1; q < k; ++q) {
+            const c64 h = Hr[(long long)q * mp1 + i];
+            acc.x -= h.x * yr[q].x - h.y * yr[q].y;
+            acc.y -= h.x * yr[q].y + h.y * yr[q].x;
+        }
+        const c64 d = Hr[(long long)i * mp1 + i];
+        const double dd = d.x * d.x + d.y * d.y;
+        yr[i] = dd > 0 ? c64{(acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd} : c64{0, 0};
+    }
+}
+
+// x += sum_{i<k} y_i V_i  (x in FP64)
+template <typename T>
+__global__ void k_xupdate(c64* __restrict__ x, long long xstride, const cplx<T>* __restrict__ V, long long rstride,
+                          long long vstride, const c64* __restrict__ y, const int* __restrict__ kcount,
+                          const int* __restrict__ list, int m, long long n) {
+    __shared__ c64 ys[256];
+    const int r = list[blockIdx.y];
+    const int k = kcount[r];
+    for (int i = threadIdx.x; i < k; i += KB) ys[i] = y[(long long)r * m + i];
+    __syncthreads();
+    const cplx<T>* Vr = V + r * rstride;
+    c64* xr = x + r * xstride;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < KE; ++q) {
+        const long long e = e0 + q * KB;
+        if (e >= n) continue;
+        c64 acc = xr[e];
+        for (int i = 0; i < k; ++i) {
+            const c64 a = ld64(Vr + (long long)i * vstride, e);
+            acc.x += ys[i].x * a.x - ys[i].y * a.y;
+            acc.y += ys[i].x * a.y + ys[i].y * a.x;
+        }
+        xr[e] = acc;
+    }
+}
+
+// r = b - r (r holds A x on entry); normpart = ||r||^2 per block
+__global__ void k_residual(const c64* __restrict__ b, c64* __restrict__ r, long long stride,
+                           const int* __restrict__ list, double* __restrict__ normpart, long long n, int nblk,
+                           int copy_b) {
+    __shared__ double ws[KB / 32];
+    const int rr = list[blockIdx.y];
+    const c64* br = b + rr * stride;
+    c64* res = r + rr * stride;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+    double nrm = 0;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) {
+            const c64 bv = br[e];
+            c64 v;
+            if (copy_b) v = bv;
+            else {
+                const c64 ax = res[e];
+                v = c64{bv.x - ax.x, bv.y - ax.y};
+            }
+            res[e] = v;
+            nrm += v.x * v.x + v.y * v.y;
+        }
+    }
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < KB / 32; ++q) t += ws[q];
+        normpart[(long long)rr * nblk + blockIdx.x] = t;
+    }
+}
+
+__global__ void k_norm_finish(const double* __restrict__ normpart, int nblk, double* __restrict__ out,
+                              const int* __restrict__ list, int nr) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nr) return;
+    const int r = list[s];
+    double t = 0;
+    for (int b = 0; b < nblk; ++b) t += normpart[(long long)r * nblk + b];
+    out[r] = sqrt(t);
+}
+
+// V_0 = r / ||r|| (cast to T); g = (||r||, 0, ...)
+template <typename T>
+__global__ void k_start_cycle(const c64* __restrict__ res, long long rs, cplx<T>* __restrict__ V, long long vrs,
+                              const double* __restrict__ rnorm, c64* __restrict__ g, const int* __restrict__ list,
+                              int m, long long n) {
+    const int r = list[blockIdx.y];
+    const double nr = rnorm[r];
+    const double s = nr > 0 ? 1.0 / nr : 0.0;
+    const c64* a = res + r * rs;
+    cplx<T>* v = V + r * vrs;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) v[e] = cplx<T>{(T)(a[e].x * s), (T)(a[e].y * s)};
+    }
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i <= m; i += KB) g[(long long)r * (m + 1) + i] = i == 0 ? c64{nr, 0} : c64{0, 0};
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+int Solver::alloc(Operator& op, int R_, int m_, int prec_) {
+    const long long n = 3 * op.Nb;
+    if (R_ == R && m_ == m && prec_ == prec && n == n3 && x) return VIE_OK;
+    release(op);
+    R = R_;
+    m = m_;
+    prec = prec_;
+    n3 = n;
+    nblk = ceil_div(n, KCH);
+    const size_t tsz = prec ? sizeof(c64) : sizeof(c32);
+    VIE_TRY(dev_alloc(op, (void**)&x, sizeof(c64) * n * R));
+    VIE_TRY(dev_alloc(op, (void**)&b, sizeof(c64) * n * R));
+    VIE_TRY(dev_alloc(op, (void**)&res, sizeof(c64) * n * R));
+    VIE_TRY(dev_alloc(op, &V, tsz * n * R * (m + 1)));
+    VIE_TRY(dev_alloc(op, (void**)&H, sizeof(c64) * R * (m + 1) * m));
+    VIE_TRY(dev_alloc(op, (void**)&cs, sizeof(double) * R * m));
+    VIE_TRY(dev_alloc(op, (void**)&sn, sizeof(c64) * R * m));
+    VIE_TRY(dev_alloc(op, (void**)&g, sizeof(c64) * R * (m + 1)));
+    VIE_TRY(dev_alloc(op, (void**)&y, sizeof(c64) * R * m));
+    VIE_TRY(dev_alloc(op, (void**)&coef, sizeof(c64) * R * (m + 1)));
+    VIE_TRY(dev_alloc(op, (void**)&partial, sizeof(c64) * (size_t)R * (m + 1) * nblk));
+    VIE_TRY(dev_alloc(op, (void**)&normpart, sizeof(double) * (size_t)R * nblk));
+    VIE_TRY(dev_alloc(op, (void**)&inv, sizeof(double) * R));
+    VIE_TRY(dev_alloc(op, (void**)&target, sizeof(double) * R));
+    VIE_TRY(dev_alloc(op, (void**)&bnorm, sizeof(double) * R));
+    VIE_TRY(dev_alloc(op, (void**)&rnorm, sizeof(double) * R));
+    VIE_TRY(dev_alloc(op, (void**)&kcount, sizeof(int) * R));
+    VIE_TRY(dev_alloc(op, (void**)&flag, sizeof(int) * R));
+    return VIE_OK;
+}
+
+void Solver::release(Operator& op) {
+    const size_t tsz = prec ? sizeof(c64) : sizeof(c32);
+    if (x) {
+        dev_free(op, x, sizeof(c64) * n3 * R);
+        dev_free(op, b, sizeof(c64) * n3 * R);
+        dev_free(op, res, sizeof(c64) * n3 * R);
+        dev_free(op, V, tsz * n3 * R * (m + 1));
+        dev_free(op, H, sizeof(c64) * R * (m + 1) * m);
+        dev_free(op, cs, sizeof(double) * R * m);
+        dev_free(op, sn, sizeof(c64) * R * m);
+        dev_free(op, g, sizeof(c64) * R * (m + 1));
+        dev_free(op, y, sizeof(c64) * R * m);
+        dev_free(op, coef, sizeof(c64) * R * (m + 1));
+        dev_free(op, partial, sizeof(c64) * (size_t)R * (m + 1) * nblk);
+        dev_free(op, normpart, sizeof(double) * (size_t)R * nblk);
+        dev_free(op, inv, sizeof(double) * R);
+        dev_free(op, target, sizeof(double) * R);
+        dev_free(op, bnorm, sizeof(double) * R);
+        dev_free(op, rnorm, sizeof(double) * R);
+        dev_free(op, kcount, sizeof(int) * R);
+        dev_free(op, flag, sizeof(int) * R);
+    }
+    x = b = res = nullptr;
+    V = nullptr;
+    H = sn = g = y = coef = partial = nullptr;
+    cs = normpart = inv = target = bnorm = rnorm = nullptr;
+    kcount = flag = nullptr;
+    R = 0;
+}
+
+#define LAUNCH_CHECK()                               \
+    do {                                             \
+        count_launch();                              \
+        VIE_CUDA(cudaGetLastError());                \
+    } while (0)
+
+template <typename T>
+static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult& out) {
+    const long long n = S.n3;
+    const int R = S.R, m = S.m, mp1 = m + 1, nblk = S.nblk;
+    const long long vrs = n * mp1;  // per-RHS stride in V
+    cplx<T>* V = (cplx<T>*)S.V;
+    cudaStream_t st = op.stream;
+    const int prec_in = sizeof(T) == 8 ? VIE_PREC_FP64 : VIE_PREC_MIXED;
+    const double ET = sizeof(cplx<T>);
+
+    std::vector<int> outer_active(R), it(R, 0), outer(R, 0);
+    for (int r = 0; r < R; ++r) outer_active[r] = r;
+    std::vector<double> hb(R), hr(R), htarget(R);
+    std::vector<int> hflag(R), hk(R);
+
+    // b norms
+    VIE_TRY(op_set_list(op, outer_active.data(), R));
+    dim3 gv(nblk, R);
+    tmr_begin(TMR_RESIDUAL, st);
+    k_residual<<<gv, KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 1);
+    tmr_end(TMR_RESIDUAL, st, 2.0 * R * n * 16.0);
+    LAUNCH_CHECK();
+    tmr_begin(TMR_OTHER, st);
+    k_norm_finish<<<ceil_div(R, 128), 128, 0, st>>>(S.normpart, nblk, S.bnorm, op.d_list, R);
+    tmr_end(TMR_OTHER, st);
+    LAUNCH_CHECK();
+    VIE_CUDA(cudaMemcpyAsync(hb.data(), S.bnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; ++r)
+        if (!(hb[r] > 0) || !std::isfinite(hb[r])) return fail(VIE_EINVAL, "right-hand side is zero or not finite");
+
+    bool first = !o.use_x0;
+    std::vector<int> done(R, 0);
+    out.matvecs32 = out.matvecs64 = 0;
+    while (true) {
+        std::vector<int> act;
+        for (int r = 0; r < R; ++r)
+            if (!done[r]) act.push_back(r);
+        if (act.empty()) break;
+        const int na = (int)act.size();
+        VIE_TRY(op_set_list(op, act.data(), na));
+        dim3 ga(nblk, na);
+        // FP64 residual r = b - A64 x
+        if (first) {
+            tmr_begin(TMR_RESIDUAL, st);
+            k_residual<<<ga, KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 1);
+            tmr_end(TMR_RESIDUAL, st, 2.0 * na * n * 16.0);
+            LAUNCH_CHECK();
+        } else {
+            VIE_TRY(op_apply(op, VIE_PREC_FP64, S.x, n, S.res, n, op.d_list, na));
+            out.matvecs64 += na;
+            tmr_begin(TMR_RESIDUAL, st);
+            k_residual<<<ga, KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 0);
+            tmr_end(TMR_RESIDUAL, st, 3.0 * na * n * 16.0);
+            LAUNCH_CHECK();
+        }
+        first = false;
+        tmr_begin(TMR_OTHER, st);
+        k_norm_finish<<<ceil_div(na, 128), 128, 0, st>>>(S.normpart, nblk, S.rnorm, op.d_list, na);
+        tmr_end(TMR_OTHER, st);
+        LAUNCH_CHECK();
+        VIE_CUDA(cudaMemcpyAsync(hr.data(), S.rnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        VIE_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> cyc;
+        for (int r : act) {
+            const double rel = hr[r] / hb[r];
+            out.relres[r] = rel;
+            if (rel <= o.tol || !std::isfinite(rel)) done[r] = 1;
+            else if (it[r] >= o.max_iter) done[r] = 2;
+            else cyc.push_back(r);
+        }
+        if (cyc.empty()) break;
+        for (int r : cyc) {
+            outer[r]++;
+            double t = 0.99 * o.tol * hb[r];
+            if (prec_in == VIE_PREC_MIXED) t = std::max(o.inner_tol * hr[r], 0.3 * o.tol * hb[r]);
+            htarget[r] = t;
+        }
+        VIE_CUDA(cudaMemcpyAsync(S.target, htarget.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+        int nc = (int)cyc.size();
+        VIE_TRY(op_set_list(op, cyc.data(), nc));
+        tmr_begin(TMR_START, st);
+        k_start_cycle<T><<<dim3(nblk, nc), KB, 0, st>>>(S.res, n, V, vrs, S.rnorm, S.g, op.d_list, m, n);
+        tmr_end(TMR_START, st, (double)nc * n * (16.0 + ET));
+        LAUNCH_CHECK();
+        std::vector<int> inner = cyc;  // RHS still iterating in this cycle
+        std::vector<int> all_cyc = cyc;
+        long long steps_sum = 0;       // Krylov steps taken in this cycle, summed over RHS
+        for (int j = 0; j < m && !inner.empty(); ++j) {
+            const int ni = (int)inner.size();
+            VIE_TRY(op_set_list(op, inner.data(), ni));
+            // V_{j+1} = A_T V_j
+            VIE_TRY(op_apply(op, prec_in, V + (long long)j * n, vrs, V + (long long)(j + 1) * n, vrs, op.d_list, ni));
+            if (prec_in == VIE_PREC_FP64) out.matvecs64 += ni;
+            else out.matvecs32 += ni;
+            dim3 gi(nblk, ni);
+            for (int pass = 0; pass < 2; ++pass) {
+                tmr_begin(TMR_DOTS, st);
+                k_dots<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.partial, mp1, n, nblk);
+                tmr_end(TMR_DOTS, st, (double)ni * (j + 2) * n * ET);
+                LAUNCH_CHECK();
+                tmr_begin(TMR_REDUCE, st);
+                k_reduce_dots<<<dim3(j + 1, ni), KB, 0, st>>>(S.partial, S.coef, S.H, j, op.d_list, mp1, nblk, pass);
+                tmr_end(TMR_REDUCE, st, (double)ni * (j + 1) * nblk * 16.0);
+                LAUNCH_CHECK();
+                tmr_begin(TMR_UPDATE, st);
+                k_update<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.coef, S.normpart, mp1, n, nblk);
+                tmr_end(TMR_UPDATE, st, (double)ni * (j + 3) * n * ET);
+                LAUNCH_CHECK();
+            }
+            tmr_begin(TMR_FINISH, st);
+            k_finish<<<ceil_div(ni, 64), 64, 0, st>>>(S.normpart, nblk, S.H, S.cs, S.sn, S.g, S.inv, S.kcount, S.flag,
+                                                      S.target, j, op.d_list, ni, m);
+            tmr_end(TMR_FINISH, st, (double)ni * nblk * 8.0);
+            LAUNCH_CHECK();
+            tmr_begin(TMR_SCALE, st);
+            k_scale<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.inv, n);
+            tmr_end(TMR_SCALE, st, 2.0 * ni * n * ET);
+            LAUNCH_CHECK();
+            VIE_CUDA(cudaMemcpyAsync(hflag.data(), S.flag, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+            VIE_CUDA(cudaStreamSynchronize(st));
+            std::vector<int> nxt;
+            steps_sum += ni;
+            for (int r : inner) {
+                it[r]++;
+                if (!hflag[r] && it[r] < o.max_iter) nxt.push_back(r);
+            }
+            inner.swap(nxt);
+        }
+        // x += V y
+        VIE_TRY(op_set_list(op, all_cyc.data(), nc));
+        tmr_begin(TMR_OTHER, st);
+        k_lsq<<<ceil_div(nc, 64), 64, 0, st>>>(S.H, S.g, S.y, S.kcount, op.d_list, nc, m);
+        tmr_end(TMR_OTHER, st);
+        LAUNCH_CHECK();
+        tmr_begin(TMR_XUPDATE, st);
+        k_xupdate<T><<<dim3(nblk, nc), KB, 0, st>>>(S.x, n, V, vrs, n, S.y, S.kcount, op.d_list, m, n);
+        tmr_end(TMR_XUPDATE, st, (double)steps_sum * n * ET + 2.0 * nc * n * 16.0);
+        LAUNCH_CHECK();
+    }
+    out.converged = 0;
+    out.iters_max = 0;
+    out.outer_max = 0;
+    out.relres_max = 0;
+    for (int r = 0; r < R; ++r) {
+        out.iters[r] = it[r];
+        out.converged += done[r] == 1;
+        out.iters_max = std::max(out.iters_max, it[r]);
+        out.outer_max = std::max(out.outer_max, outer[r]);
+        out.relres_max = std::max(out.relres_max, out.relres[r]);
+    }
+    return VIE_OK;
+}
+
+int solver_run(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult& out) {
+    out.iters.assign(S.R, 0);
+    out.relres.assign(S.R, 0.0);
+    if (!o.use_x0) VIE_CUDA(cudaMemsetAsync(S.x, 0, sizeof(c64) * S.n3 * S.R, op.stream));
+    if (S.prec == VIE_PREC_FP64) return gmres_t<double>(op, S, o, out);
+    return gmres_t<float>(op, S, o, out);
+}
+
+}  // namespace vie

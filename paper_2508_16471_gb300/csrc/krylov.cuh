@@ -1,0 +1,51 @@
+// Batched GMRES state and driver (see krylov.cu).
+#pragma once
+
+#include <vector>
+
+#include "vie_internal.cuh"
+
+namespace vie {
+
+constexpr int MAX_RESTART = 64;
+
+struct Solver {
+    int R = 0, m = 0, prec = 0, nblk = 0;
+    long long n3 = 0;          // vector length 3 * Nb
+    c64* x = nullptr;          // [R][n3] solution (FP64)
+    c64* b = nullptr;          // [R][n3] right-hand sides
+    c64* res = nullptr;        // [R][n3] residual / A x scratch
+    void* V = nullptr;         // [R][m+1][n3] Krylov basis (float2 or double2)
+    c64* H = nullptr;          // [R][m][m+1] Hessenberg, column-major
+    double* cs = nullptr;      // [R][m] Givens cosines
+    c64* sn = nullptr;         // [R][m] Givens sines
+    c64* g = nullptr;          // [R][m+1] rotated residual vector
+    c64* y = nullptr;          // [R][m] least-squares solution
+    c64* coef = nullptr;       // [R][m+1] current projection coefficients
+    c64* partial = nullptr;    // [R][m+1][nblk] block partial dot products
+    double* normpart = nullptr;  // [R][nblk]
+    double* inv = nullptr;     // [R] 1 / h_{j+1,j}
+    double* target = nullptr;  // [R] inner-cycle stopping threshold
+    double* bnorm = nullptr;   // [R]
+    double* rnorm = nullptr;   // [R]
+    int* kcount = nullptr;     // [R] steps taken in the current cycle
+    int* flag = nullptr;       // [R] 1 = stop the current cycle
+
+    int alloc(Operator& op, int R, int m, int prec);
+    void release(Operator& op);
+};
+
+struct SolveResult {
+    std::vector<int> iters;
+    std::vector<double> relres;
+    int converged = 0, iters_max = 0, outer_max = 0;
+    long long matvecs32 = 0, matvecs64 = 0;
+    double relres_max = 0;
+};
+
+int solver_run(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult& out);
+
+// right-hand sides b[r][c][v] = chi_v pol_rc exp(i k0 khat_r . r_v) (FP64)
+int build_rhs(Operator& op, Solver& S, const vie_channel* ch, int n_rhs);
+
+}  // namespace vie

@@ -1,0 +1,823 @@
+// FFT-accelerated operator y = w - chi (K * w) on the compact body-voxel
+// layout (Sec. II-C: uniform voxels give a Toeplitz/convolution structure, so
+// the matrix-vector product is a zero-padded FFT convolution, O(N log N)).
+//
+// Data flow for a batch of RHS (grid n0 x n1 x n2 = x, y, z; padded P):
+//   pass 1  k_zfwd    gather w from the body list, pad z: n2 -> P2, FFT z
+//                     -> A [slot][3][n0][n1][P2]
+//   pass 2  k_axis    FFT y, pad n1 -> P1              -> B [slot][3][n0][P1][P2]
+//   pass 3  k_xfused  FFT x (pad n0 -> P0), 3x3 spectral multiply with the
+//                     kernel octant, inverse FFT x, keep n0 rows (in place on B)
+//   pass 4  k_axis    inverse FFT y, keep n1 rows      -> A
+//   pass 5  k_zinv    inverse FFT z, keep n2, epilogue y = w - chi * u scattered
+//                     to the body list
+// The 1/(P0 P1 P2) normalisation is folded into the kernel spectrum.
+//
+// Kernel spectrum: K(m) (Eq. dyadicG sampled on voxel offsets, ball-averaged,
+// plus the self term) is embedded in a periodic P0 x P1 x P2 array, transformed
+// once in FP64 with the same FFT engine, and one octant (P/2+1 per axis) per
+// tensor component is kept: K_ij(m) is even or odd in each axis, so its
+// transform is too, and the other octants follow by sign flips.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "vie_internal.cuh"
+
+namespace vie {
+
+// ---------------------------------------------------------------------------
+// plans
+// ---------------------------------------------------------------------------
+bool make_plan(int L, FFTPlan* p) {
+    if (L < 1 || L > FFT_MAX_L) return false;
+    std::memset(p, 0, sizeof(*p));
+    p->L = L;
+    int r = L, Ns = 1, off = 0;
+    const int order[] = {16, 8, 4, 2, 3, 5, 7};
+    for (int R : order) {
+        while (r % R == 0) {
+            if (p->nst >= FFT_MAX_STAGES) return false;
+            p->R[p->nst] = R;
+            p->Ns[p->nst] = Ns;
+            p->twoff[p->nst] = off;
+            off += Ns * (R - 1);
+            Ns *= R;
+            r /= R;
+            p->nst++;
+        }
+    }
+    if (r != 1) return false;
+    p->twlen = off;
+    return true;
+}
+
+void plan_twiddles(const FFTPlan& p, double* reim) {
+    for (int s = 0; s < p.nst; ++s) {
+        const int R = p.R[s], Ns = p.Ns[s];
+        for (int k = 0; k < Ns; ++k)
+            for (int t = 1; t < R; ++t) {
+                const double ang = -2.0 * M_PI * (double)(t * k) / (double)(Ns * R);
+                const int i = p.twoff[s] + k * (R - 1) + (t - 1);
+                reim[2 * i] = std::cos(ang);
+                reim[2 * i + 1] = std::sin(ang);
+            }
+    }
+}
+
+int smooth_size(int m) {
+    int v = std::max(1, m);
+    for (;; ++v) {
+        int r = v;
+        for (int q : {2, 3, 5, 7})
+            while (r % q == 0) r /= q;
+        if (r == 1) return v;
+    }
+}
+
+static int upload_twiddles(Operator& op, AxisFFT& a) {
+    const int n = std::max(1, a.plan.twlen);
+    std::vector<double> t(2 * n, 0.0);
+    plan_twiddles(a.plan, t.data());
+    std::vector<float> tf(2 * n);
+    for (int i = 0; i < 2 * n; ++i) tf[i] = (float)t[i];
+    VIE_TRY(dev_alloc(op, (void**)&a.tw64, sizeof(c64) * n));
+    VIE_TRY(dev_alloc(op, (void**)&a.tw32, sizeof(c32) * n));
+    VIE_CUDA(cudaMemcpy(a.tw64, t.data(), sizeof(c64) * n, cudaMemcpyHostToDevice));
+    VIE_CUDA(cudaMemcpy(a.tw32, tf.data(), sizeof(c32) * n, cudaMemcpyHostToDevice));
+    return VIE_OK;
+}
+
+int op_init_axes(Operator& op) {
+    for (int a = 0; a < 3; ++a) {
+        op.P[a] = smooth_size(2 * op.n[a] - 1);
+        op.H[a] = op.P[a] / 2 + 1;
+        if (!make_plan(op.P[a], &op.ax[a].plan))
+            return fail(VIE_EINVAL, "padded FFT size " + std::to_string(op.P[a]) + " exceeds the engine limit (1024)");
+        VIE_TRY(upload_twiddles(op, op.ax[a]));
+    }
+    return VIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ cplx<T> czero() { return cplx<T>{(T)0, (T)0}; }
+
+// Generic contiguous lines: in [count][n_in] -> out [count][n_out], length L.
+template <typename T, bool INV>
+__global__ void k_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_in,
+                        int n_out, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+    const int L = plan.L;
+    const int ld = NL + 1;
+    cplx<T>* bA = tw + ((plan.twlen + 1) & ~1);
+    cplx<T>* bB = bA + L * ld;
+    load_twiddles(tw, twg, plan.twlen);
+    const long long line0 = (long long)blockIdx.x * NL;
+    for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
+        const int l = e / L, p = e - (e / L) * L;
+        const long long line = line0 + l;
+        cplx<T> v = czero<T>();
+        if (line < count && p < n_in) v = in[line * n_in + p];
+        bA[p * ld + l] = v;
+    }
+    __syncthreads();
+    cplx<T>* r = fft_tile<T, INV>(bA, bB, plan, tw, NL, ld);
+    for (int e = threadIdx.x; e < NL * n_out; e += blockDim.x) {
+        const int l = e / n_out, p = e - l * n_out;
+        const long long line = line0 + l;
+        if (line < count) out[line * n_out + p] = r[p * ld + l];
+    }
+}
+
+// Middle-axis transform: in [outer][n_in][inner] -> out [outer][n_out][inner].
+template <typename T, bool INV>
+__global__ void k_axis(const cplx<T>* in, cplx<T>* out, long long inner, int n_in,
+                       int n_out, FFTPlan plan, const cplx<T>* __restrict__ twg, int TW) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+    const int L = plan.L;
+    cplx<T>* bA = tw + ((plan.twlen + 1) & ~1);
+    cplx<T>* bB = bA + L * TW;
+    load_twiddles(tw, twg, plan.twlen);
+    const long long ntile = (inner + TW - 1) / TW;
+    const long long o = blockIdx.x / ntile;
+    const long long i0 = (blockIdx.x - o * ntile) * TW;
+    for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
+        const int p = e / TW, t = e - (e / TW) * TW;
+        cplx<T> v = czero<T>();
+        if (p < n_in && i0 + t < inner) v = in[(o * n_in + p) * inner + i0 + t];
+        bA[p * TW + t] = v;
+    }
+    __syncthreads();
+    cplx<T>* r = fft_tile<T, INV>(bA, bB, plan, tw, TW, TW);
+    for (int e = threadIdx.x; e < n_out * TW; e += blockDim.x) {
+        const int p = e / TW, t = e - (e / TW) * TW;
+        if (i0 + t < inner) out[(o * n_out + p) * inner + i0 + t] = r[p * TW + t];
+    }
+}
+
+// Pass 1: gather compact w, zero-pad z, forward FFT along z.
+template <typename T>
+__global__ void k_zfwd(const cplx<T>* __restrict__ w, long long w_rstride, const int* __restrict__ list,
+                       const int* __restrict__ idx_map, cplx<T>* __restrict__ A, int n0, int n1, int n2,
+                       long long Nb, long long nlines, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+    const int L = plan.L;
+    const int ld = NL + 1;
+    cplx<T>* bA = tw + ((plan.twlen + 1) & ~1);
+    cplx<T>* bB = bA + L * ld;
+    load_twiddles(tw, twg, plan.twlen);
+    const long long line0 = (long long)blockIdx.x * NL;
+    const long long plane = (long long)n0 * n1;
+    for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
+        const int l = e / L, p = e - (e / L) * L;
+        const long long line = line0 + l;
+        cplx<T> v = czero<T>();
+        if (line < nlines && p < n2) {
+            const long long sc = line / plane;
+            const long long xy = line - sc * plane;
+            const int slot = (int)(sc / 3), c = (int)(sc - (sc / 3) * 3);
+            const int vi = idx_map[xy * n2 + p];
+            if (vi >= 0) v = w[(long long)list[slot] * w_rstride + c * Nb + vi];
+        }
+        bA[p * ld + l] = v;
+    }
+    __syncthreads();
+    cplx<T>* r = fft_tile<T, false>(bA, bB, plan, tw, NL, ld);
+    for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
+        const int l = e / L, p = e - l * L;
+        const long long line = line0 + l;
+        if (line < nlines) A[line * L + p] = r[p * ld + l];
+    }
+}
+
+// Pass 5: inverse FFT along z, crop, epilogue y = w - chi u on body voxels.
+template <typename T>
+__global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict__ w, long long w_rstride,
+                       cplx<T>* __restrict__ y, long long y_rstride, const int* __restrict__ list,
+                       const int* __restrict__ idx_map, const T* __restrict__ chi, int n0, int n1, int n2,
+                       long long Nb, long long nlines, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+    const int L = plan.L;
+    const int ld = NL + 1;
+    cplx<T>* bA = tw + ((plan.twlen + 1) & ~1);
+    cplx<T>* bB = bA + L * ld;
+    load_twiddles(tw, twg, plan.twlen);
+    const long long line0 = (long long)blockIdx.x * NL;
+    const long long plane = (long long)n0 * n1;
+    for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
+        const int l = e / L, p = e - (e / L) * L;
+        const long long line = line0 + l;
+        cplx<T> v = czero<T>();
+        if (line < nlines) v = A[line * L + p];
+        bA[p * ld + l] = v;
+    }
+    __syncthreads();
+    cplx<T>* r = fft_tile<T, true>(bA, bB, plan, tw, NL, ld);
+    for (int e = threadIdx.x; e < NL * n2; e += blockDim.x) {
+        const int l = e / n2, p = e - l * n2;
+        const long long line = line0 + l;
+        if (line >= nlines) continue;
+        const long long sc = line / plane;
+        const long long xy = line - sc * plane;
+        const int vi = idx_map[xy * n2 + p];
+        if (vi < 0) continue;
+        const int slot = (int)(sc / 3), c = (int)(sc - (sc / 3) * 3);
+        const long long rr = list[slot];
+        const cplx<T> u = r[p * ld + l];
+        const cplx<T> wv = w[rr * w_rstride + c * Nb + vi];
+        const T ch = chi[vi];
+        y[rr * y_rstride + c * Nb + vi] = cplx<T>{wv.x - ch * u.x, wv.y - ch * u.y};
+    }
+}
+
+// Pass 3: FFT x, spectral multiply by the 3x3 symmetric kernel, inverse FFT x.
+// B [slot][3][n0][inner], inner = P1 * P2; updated in place for x < n0.
+template <typename T>
+__global__ void k_xfused(cplx<T>* __restrict__ B, int n0, long long inner, int P0, int P1, int P2,
+                         const cplx<T>* __restrict__ khat, int H0, int H1, int H2, FFTPlan plan,
+                         const cplx<T>* __restrict__ twg, int TW) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+    const int L = plan.L;  // == P0
+    cplx<T>* D[4];
+    D[0] = tw + ((plan.twlen + 1) & ~1);
+    for (int i = 1; i < 4; ++i) D[i] = D[i - 1] + L * TW;
+    load_twiddles(tw, twg, plan.twlen);
+    const long long ntile = (inner + TW - 1) / TW;
+    const long long slot = blockIdx.x / ntile;
+    const long long i0 = (blockIdx.x - slot * ntile) * TW;
+    cplx<T>* base = B + slot * 3 * (long long)n0 * inner;
+    for (int e = threadIdx.x; e < 3 * L * TW; e += blockDim.x) {
+        const int c = e / (L * TW);
+        const int q = e - c * (L * TW);
+        const int p = q / TW, t = q - (q / TW) * TW;
+        cplx<T> v = czero<T>();
+        if (p < n0 && i0 + t < inner) v = base[((long long)c * n0 + p) * inner + i0 + t];
+        D[c][p * TW + t] = v;
+    }
+    __syncthreads();
+    cplx<T>* cur[3] = {D[0], D[1], D[2]};
+    cplx<T>* scr = D[3];
+    for (int c = 0; c < 3; ++c) {
+        cplx<T>* r = fft_tile<T, false>(cur[c], scr, plan, tw, TW, TW);
+        if (r != cur[c]) {
+            scr = cur[c];
+            cur[c] = r;
+        }
+    }
+    // spectral multiply
+    const long long HH = (long long)H0 * H1 * H2;
+    for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
+        const int p = e / TW, t = e - (e / TW) * TW;
+        const long long ii = i0 + t;
+        if (ii >= inner) continue;
+        const int ky = (int)(ii / P2), kz = (int)(ii - (ii / P2) * P2);
+        const int kx = p;
+        const bool flx = 2 * kx > P0, fly = 2 * ky > P1, flz = 2 * kz > P2;
+        const int fx = flx ? P0 - kx : kx, fy = fly ? P1 - ky : ky, fz = flz ? P2 - kz : kz;
+        const long long o = ((long long)fx * H1 + fy) * H2 + fz;
+        cplx<T> kxx = khat[o], kxy = khat[HH + o], kxz = khat[2 * HH + o];
+        cplx<T> kyy = khat[3 * HH + o], kyz = khat[4 * HH + o], kzz = khat[5 * HH + o];
+        if (flx ^ fly) kxy = cplx<T>{-kxy.x, -kxy.y};
+        if (flx ^ flz) kxz = cplx<T>{-kxz.x, -kxz.y};
+        if (fly ^ flz) kyz = cplx<T>{-kyz.x, -kyz.y};
+        const cplx<T> a = cur[0][e], b = cur[1][e], cc = cur[2][e];
+        cur[0][e] = kxx * a + kxy * b + kxz * cc;
+        cur[1][e] = kxy * a + kyy * b + kyz * cc;
+        cur[2][e] = kxz * a + kyz * b + kzz * cc;
+    }
+    __syncthreads();
+    for (int c = 0; c < 3; ++c) {
+        cplx<T>* r = fft_tile<T, true>(cur[c], scr, plan, tw, TW, TW);
+        if (r != cur[c]) {
+            scr = cur[c];
+            cur[c] = r;
+        }
+    }
+    for (int e = threadIdx.x; e < 3 * n0 * TW; e += blockDim.x) {
+        const int c = e / (n0 * TW);
+        const int q = e - c * (n0 * TW);
+        const int p = q / TW, t = q - (q / TW) * TW;
+        if (i0 + t < inner) base[((long long)c * n0 + p) * inner + i0 + t] = cur[c][p * TW + t];
+    }
+}
+
+// Periodic embedding of the discrete kernel K(m) (six components, FP64).
+__global__ void k_kernel_circulant(c64* __restrict__ Kc, int n0, int n1, int n2, int P0, int P1, int P2, double h,
+                                   double k0, double coef, double self_re, double self_im) {
+    const long long tot = (long long)P0 * P1 * P2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int p2 = (int)(i % P2);
+        const long long r0 = i / P2;
+        const int p1 = (int)(r0 % P1);
+        const int p0 = (int)(r0 / P1);
+        int m[3];
+        bool ok = true;
+        const int pp[3] = {p0, p1, p2}, nn[3] = {n0, n1, n2}, PP[3] = {P0, P1, P2};
+        for (int a = 0; a < 3; ++a) {
+            if (pp[a] <= nn[a] - 1) m[a] = pp[a];
+            else if (pp[a] >= PP[a] - nn[a] + 1) m[a] = pp[a] - PP[a];
+            else ok = false;
+        }
+        c64 out[6] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        if (ok) {
+            if (m[0] == 0 && m[1] == 0 && m[2] == 0) {
+                out[0] = out[3] = out[5] = c64{self_re, self_im};
+            } else {
+                const double R[3] = {m[0] * h, m[1] * h, m[2] * h};
+                const double r = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+                const double kr = k0 * r;
+                double s, c;
+                sincos(kr, &s, &c);
+                const double gi = coef / (4.0 * M_PI * r);
+                const c64 g = {gi * c, gi * s};
+                const double ikr = 1.0 / kr, ikr2 = ikr * ikr;
+                const c64 A = {1.0 - ikr2, ikr};
+                const c64 Bc = {-1.0 + 3.0 * ikr2, -3.0 * ikr};
+                const double u[3] = {R[0] / r, R[1] / r, R[2] / r};
+                const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
+                for (int q = 0; q < 6; ++q) {
+                    c64 t = {Bc.x * u[I[q]] * u[J[q]], Bc.y * u[I[q]] * u[J[q]]};
+                    if (I[q] == J[q]) t = t + A;
+                    out[q] = g * t;
+                }
+            }
+        }
+        for (int q = 0; q < 6; ++q) Kc[q * tot + i] = out[q];
+    }
+}
+
+__global__ void k_octant(const c64* __restrict__ Kc, c64* __restrict__ o64, c32* __restrict__ o32, int P0, int P1,
+                         int P2, int H0, int H1, int H2, double scale) {
+    const long long HH = (long long)H0 * H1 * H2;
+    const long long PP = (long long)P0 * P1 * P2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 6 * HH;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(i / HH);
+        const long long r = i - q * HH;
+        const int fz = (int)(r % H2);
+        const int fy = (int)((r / H2) % H1);
+        const int fx = (int)(r / ((long long)H1 * H2));
+        const c64 v = Kc[q * PP + ((long long)fx * P1 + fy) * P2 + fz];
+        const c64 s = {v.x * scale, v.y * scale};
+        o64[i] = s;
+        o32[i] = c32{(float)s.x, (float)s.y};
+    }
+}
+
+// ---------------------------------------------------------------------------
+// body compaction: idx_map, vox, chi from a device eps grid
+// ---------------------------------------------------------------------------
+constexpr int SCAN_B = 1024;
+
+__global__ void k_body_count(const double* __restrict__ eps, long long N, int* __restrict__ bcount,
+                             int* __restrict__ err) {
+    __shared__ int ws[32];
+    const long long i = (long long)blockIdx.x * SCAN_B + threadIdx.x;
+    int f = 0;
+    if (i < N) {
+        const double e = eps[i];
+        if (!(e >= 1.0) || !isfinite(e)) atomicOr(err, 1);
+        f = e > 1.0;
+    }
+    int s = __syncthreads_count(f);
+    (void)ws;
+    if (threadIdx.x == 0) bcount[blockIdx.x] = s;
+}
+
+// single-CTA exclusive scan of the block counts; writes total to *total
+__global__ void k_scan_blocks(int* __restrict__ bcount, int nb, long long* __restrict__ total) {
+    __shared__ int carry;
+    __shared__ int wsum[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        int v = i < nb ? bcount[i] : 0;
+        // inclusive warp scan
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int s = threadIdx.x < (blockDim.x >> 5) ? wsum[threadIdx.x] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (threadIdx.x >= o) s += y;
+            }
+            wsum[threadIdx.x] = s;
+        }
+        __syncthreads();
+        const int wpre = (threadIdx.x >> 5) ? wsum[(threadIdx.x >> 5) - 1] : 0;
+        const int excl = carry + wpre + x - v;
+        if (i < nb) bcount[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_body_write(const double* __restrict__ eps, long long N, const int* __restrict__ boff,
+                             int* __restrict__ idx_map, int* __restrict__ vox, float* __restrict__ chi32,
+                             double* __restrict__ chi64) {
+    __shared__ int wsum[32];
+    const long long i = (long long)blockIdx.x * SCAN_B + threadIdx.x;
+    const double e = i < N ? eps[i] : 1.0;
+    const int f = e > 1.0;
+    int x = f;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int s = wsum[threadIdx.x];
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (threadIdx.x >= o) s += y;
+        }
+        wsum[threadIdx.x] = s;
+    }
+    __syncthreads();
+    const int excl = boff[blockIdx.x] + ((threadIdx.x >> 5) ? wsum[(threadIdx.x >> 5) - 1] : 0) + x - f;
+    if (i < N) {
+        idx_map[i] = f ? excl : -1;
+        if (f) {
+            vox[excl] = (int)i;
+            chi32[excl] = (float)(e - 1.0);
+            chi64[excl] = e - 1.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static const size_t SMEM_CAP = 200 * 1024;
+
+template <typename KernelT> static int allow_smem(KernelT k) {
+    VIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CAP));
+    return VIE_OK;
+}
+
+static int pow2_floor(int v) {
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+template <typename T> static size_t tw_bytes(const FFTPlan& p) {
+    return sizeof(cplx<T>) * (size_t)((p.twlen + 1) & ~1);
+}
+
+// lines per CTA for the contiguous-line kernels (two buffers of L*(NL+1))
+template <typename T> static int lines_per_cta(int L) {
+    const int budget = 48 * 1024;
+    int nl = budget / (2 * (int)sizeof(cplx<T>) * std::max(L, 1)) - 1;
+    return std::max(1, std::min(32, pow2_floor(std::max(1, nl))));
+}
+template <typename T> static size_t lines_smem(const FFTPlan& p, int NL) {
+    return tw_bytes<T>(p) + 2 * sizeof(cplx<T>) * (size_t)p.L * (NL + 1);
+}
+// tile width for the strided-axis kernels (two buffers of L*TW)
+template <typename T> static int axis_tile(int L, long long inner) {
+    const int budget = 64 * 1024;
+    int tw = budget / (2 * (int)sizeof(cplx<T>) * std::max(L, 1));
+    tw = std::max(1, std::min(32, pow2_floor(std::max(1, tw))));
+    while (tw > 1 && tw / 2 >= inner) tw /= 2;
+    return tw;
+}
+template <typename T> static size_t axis_smem(const FFTPlan& p, int TW) {
+    return tw_bytes<T>(p) + 2 * sizeof(cplx<T>) * (size_t)p.L * TW;
+}
+template <typename T> static int xfused_tile(int L, long long inner) {
+    const int budget = 96 * 1024;
+    int tw = budget / (4 * (int)sizeof(cplx<T>) * std::max(L, 1));
+    tw = std::max(1, std::min(32, pow2_floor(std::max(1, tw))));
+    while (tw > 1 && tw / 2 >= inner) tw /= 2;
+    return tw;
+}
+template <typename T> static size_t xfused_smem(const FFTPlan& p, int TW) {
+    return tw_bytes<T>(p) + 4 * sizeof(cplx<T>) * (size_t)p.L * TW;
+}
+
+template <typename T> static const cplx<T>* twp(const AxisFFT& a);
+template <> const c32* twp<float>(const AxisFFT& a) { return a.tw32; }
+template <> const c64* twp<double>(const AxisFFT& a) { return a.tw64; }
+
+template <typename T, bool INV>
+static int launch_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_in, int n_out, const FFTPlan& p,
+                        const cplx<T>* tw, cudaStream_t s) {
+    static bool init = false;
+    if (!init) {
+        VIE_TRY(allow_smem(k_lines<T, INV>));
+        init = true;
+    }
+    const int NL = lines_per_cta<T>(p.L);
+    const size_t sm = lines_smem<T>(p, NL);
+    const long long grid = (count + NL - 1) / NL;
+    if (grid <= 0) return VIE_OK;
+    k_lines<T, INV><<<(unsigned)grid, 256, sm, s>>>(in, out, count, n_in, n_out, p, tw, NL);
+    count_launch();
+    VIE_CUDA(cudaGetLastError());
+    return VIE_OK;
+}
+
+template <typename T, bool INV>
+static int launch_axis(const cplx<T>* in, cplx<T>* out, long long outer, int n_in, int n_out, long long inner,
+                       const FFTPlan& p, const cplx<T>* tw, cudaStream_t s, int tid = TMR_OTHER) {
+    const double bytes = (double)sizeof(cplx<T>) * outer * inner * (double)(n_in + n_out);
+    static bool init = false;
+    if (!init) {
+        VIE_TRY(allow_smem(k_axis<T, INV>));
+        init = true;
+    }
+    const int TW = axis_tile<T>(p.L, inner);
+    const size_t sm = axis_smem<T>(p, TW);
+    const long long grid = outer * ((inner + TW - 1) / TW);
+    if (grid <= 0) return VIE_OK;
+    tmr_begin(tid, s);
+    k_axis<T, INV><<<(unsigned)grid, 256, sm, s>>>(in, out, inner, n_in, n_out, p, tw, TW);
+    tmr_end(tid, s, bytes);
+    count_launch();
+    VIE_CUDA(cudaGetLastError());
+    return VIE_OK;
+}
+
+int fft_lines_device(const void* in, void* out, int L, int count, int inverse, int prec, cudaStream_t s) {
+    FFTPlan p;
+    if (!make_plan(L, &p)) return fail(VIE_EINVAL, "FFT length must be 2,3,5,7-smooth and <= 1024");
+    const int n = std::max(1, p.twlen);
+    std::vector<double> t(2 * n, 0.0);
+    plan_twiddles(p, t.data());
+    void* dtw = nullptr;
+    int st = VIE_OK;
+    if (prec == VIE_PREC_FP64) {
+        VIE_CUDA(cudaMalloc(&dtw, sizeof(c64) * n));
+        VIE_CUDA(cudaMemcpy(dtw, t.data(), sizeof(c64) * n, cudaMemcpyHostToDevice));
+        st = inverse ? launch_lines<double, true>((const c64*)in, (c64*)out, count, L, L, p, (const c64*)dtw, s)
+                     : launch_lines<double, false>((const c64*)in, (c64*)out, count, L, L, p, (const c64*)dtw, s);
+    } else {
+        std::vector<float> tf(2 * n);
+        for (int i = 0; i < 2 * n; ++i) tf[i] = (float)t[i];
+        VIE_CUDA(cudaMalloc(&dtw, sizeof(c32) * n));
+        VIE_CUDA(cudaMemcpy(dtw, tf.data(), sizeof(c32) * n, cudaMemcpyHostToDevice));
+        st = inverse ? launch_lines<float, true>((const c32*)in, (c32*)out, count, L, L, p, (const c32*)dtw, s)
+                     : launch_lines<float, false>((const c32*)in, (c32*)out, count, L, L, p, (const c32*)dtw, s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(dtw);
+    if (st != VIE_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "fft_lines");
+    return VIE_OK;
+}
+
+int op_build_kernel(Operator& op) {
+    const int P0 = op.P[0], P1 = op.P[1], P2 = op.P[2];
+    const long long PP = (long long)P0 * P1 * P2;
+    c64* Kc = nullptr;
+    VIE_TRY(dev_alloc(op, (void**)&Kc, sizeof(c64) * 6 * PP));
+    const double a = op.h * std::cbrt(3.0 / (4.0 * M_PI));
+    const double ka = op.k0 * a;
+    double kap;
+    if (ka < 1e-3) kap = 1.0 - ka * ka / 10.0 + ka * ka * ka * ka / 280.0;
+    else kap = 3.0 * (std::sin(ka) - ka * std::cos(ka)) / (ka * ka * ka);
+    const double coef = kap * op.k0 * op.k0 * op.h * op.h * op.h;
+    // self term: 2/3((1 - i ka) e^{i ka} - 1) - 1/3
+    const double cr = std::cos(ka), sr = std::sin(ka);
+    const double self_re = (2.0 / 3.0) * ((cr + ka * sr) - 1.0) - 1.0 / 3.0;
+    const double self_im = (2.0 / 3.0) * (sr - ka * cr);
+    int st = VIE_OK;
+    k_kernel_circulant<<<1184, 256, 0, op.stream>>>(Kc, op.n[0], op.n[1], op.n[2], P0, P1, P2, op.h, op.k0, coef,
+                                                    self_re, self_im);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) st = fail(VIE_EDEVICE, "kernel build launch failed");
+    // 3-D FFT, in place: z (contiguous lines), y, x
+    if (st == VIE_OK)
+        st = launch_lines<double, false>(Kc, Kc, 6LL * P0 * P1, P2, P2, op.ax[2].plan, op.ax[2].tw64, op.stream);
+    if (st == VIE_OK)
+        st = launch_axis<double, false>(Kc, Kc, 6LL * P0, P1, P1, P2, op.ax[1].plan, op.ax[1].tw64, op.stream);
+    if (st == VIE_OK)
+        st = launch_axis<double, false>(Kc, Kc, 6LL, P0, P0, (long long)P1 * P2, op.ax[0].plan, op.ax[0].tw64,
+                                        op.stream);
+    const long long HH = (long long)op.H[0] * op.H[1] * op.H[2];
+    if (st == VIE_OK) st = dev_alloc(op, (void**)&op.khat64, sizeof(c64) * 6 * HH);
+    if (st == VIE_OK) st = dev_alloc(op, (void**)&op.khat32, sizeof(c32) * 6 * HH);
+    if (st == VIE_OK) {
+        k_octant<<<1184, 256, 0, op.stream>>>(Kc, op.khat64, op.khat32, P0, P1, P2, op.H[0], op.H[1], op.H[2],
+                                              1.0 / (double)PP);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) st = fail(VIE_EDEVICE, "octant launch failed");
+    }
+    cudaError_t e = cudaStreamSynchronize(op.stream);
+    dev_free(op, Kc, sizeof(c64) * 6 * PP);
+    if (st != VIE_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "kernel spectrum build");
+    return VIE_OK;
+}
+
+int op_set_body_device(Operator& op, const double* eps) {
+    const long long N = op.N;
+    const int nb = (int)((N + SCAN_B - 1) / SCAN_B);
+    int* bcount = nullptr;
+    int* err = nullptr;
+    long long* total = nullptr;
+    VIE_CUDA(cudaMalloc(&bcount, sizeof(int) * (nb + 1)));
+    VIE_CUDA(cudaMalloc(&err, sizeof(int)));
+    VIE_CUDA(cudaMalloc(&total, sizeof(long long)));
+    VIE_CUDA(cudaMemsetAsync(err, 0, sizeof(int), op.stream));
+    k_body_count<<<nb, SCAN_B, 0, op.stream>>>(eps, N, bcount, err);
+    k_scan_blocks<<<1, 1024, 0, op.stream>>>(bcount, nb, total);
+    count_launch(2);
+    int herr = 0;
+    long long Nb = 0;
+    VIE_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, op.stream));
+    VIE_CUDA(cudaMemcpyAsync(&Nb, total, sizeof(long long), cudaMemcpyDeviceToHost, op.stream));
+    VIE_CUDA(cudaStreamSynchronize(op.stream));
+    int st = VIE_OK;
+    if (herr) st = fail(VIE_EINVAL, "eps_r must be finite and >= 1 everywhere");
+    else if (Nb == 0) st = fail(VIE_EINVAL, "the body is empty (no voxel with eps_r > 1)");
+    if (st == VIE_OK) {
+        if (op.vox) dev_free(op, op.vox, sizeof(int) * op.Nb);
+        if (op.chi32) dev_free(op, op.chi32, sizeof(float) * op.Nb);
+        if (op.chi64) dev_free(op, op.chi64, sizeof(double) * op.Nb);
+        op.vox = nullptr;
+        op.chi32 = nullptr;
+        op.chi64 = nullptr;
+        if (!op.idx_map) st = dev_alloc(op, (void**)&op.idx_map, sizeof(int) * N);
+        if (st == VIE_OK) st = dev_alloc(op, (void**)&op.vox, sizeof(int) * Nb);
+        if (st == VIE_OK) st = dev_alloc(op, (void**)&op.chi32, sizeof(float) * Nb);
+        if (st == VIE_OK) st = dev_alloc(op, (void**)&op.chi64, sizeof(double) * Nb);
+        if (st == VIE_OK) {
+            op.Nb = Nb;
+            k_body_write<<<nb, SCAN_B, 0, op.stream>>>(eps, N, bcount, op.idx_map, op.vox, op.chi32, op.chi64);
+            count_launch();
+            cudaError_t e = cudaStreamSynchronize(op.stream);
+            if (e != cudaSuccess) st = cuda_fail(e, "body compaction");
+        }
+    }
+    cudaFree(bcount);
+    cudaFree(err);
+    cudaFree(total);
+    return st;
+}
+
+int op_reserve(Operator& op, int prec, int nrhs) {
+    MatvecWork& W = op.work[prec];
+    const size_t esz = prec ? sizeof(c64) : sizeof(c32);
+    const long long perA = 3LL * op.n[0] * op.n[1] * op.P[2];
+    const long long perB = 3LL * op.n[0] * op.P[1] * op.P[2];
+    // cap the workspace at ~8 GB per precision; larger batches run in chunks
+    const double limit = 8e9;
+    int cap = std::max(1, std::min(nrhs, (int)(limit / ((perA + perB) * (double)esz))));
+    if (W.cap >= cap) return VIE_OK;
+    if (W.A) dev_free(op, W.A, esz * perA * W.cap);
+    if (W.B) dev_free(op, W.B, esz * perB * W.cap);
+    W.A = W.B = nullptr;
+    W.cap = 0;
+    VIE_TRY(dev_alloc(op, &W.A, esz * perA * cap));
+    VIE_TRY(dev_alloc(op, &W.B, esz * perB * cap));
+    W.cap = cap;
+    return VIE_OK;
+}
+
+int op_set_list(Operator& op, const int* host_list, int nr) {
+    if (nr > op.list_cap) {
+        if (op.d_list) dev_free(op, op.d_list, sizeof(int) * op.list_cap);
+        op.d_list = nullptr;
+        const int cap = std::max(nr, 64);
+        VIE_TRY(dev_alloc(op, (void**)&op.d_list, sizeof(int) * cap));
+        op.list_cap = cap;
+    }
+    VIE_CUDA(cudaMemcpyAsync(op.d_list, host_list, sizeof(int) * nr, cudaMemcpyHostToDevice, op.stream));
+    return VIE_OK;
+}
+
+template <typename T>
+static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, long long yr, const int* d_list,
+                   int nr) {
+    const int pi = sizeof(T) == 8 ? 1 : 0;
+    VIE_TRY(op_reserve(op, pi, nr));
+    MatvecWork& W = op.work[pi];
+    static bool init = false;
+    if (!init) {
+        VIE_TRY(allow_smem(k_zfwd<T>));
+        VIE_TRY(allow_smem(k_zinv<T>));
+        VIE_TRY(allow_smem(k_xfused<T>));
+        init = true;
+    }
+    const int n0 = op.n[0], n1 = op.n[1], n2 = op.n[2];
+    const int P0 = op.P[0], P1 = op.P[1], P2 = op.P[2];
+    cplx<T>* A = (cplx<T>*)W.A;
+    cplx<T>* B = (cplx<T>*)W.B;
+    const cplx<T>* kh;
+    const T* chi;
+    if constexpr (sizeof(T) == 8) {
+        kh = (const cplx<T>*)op.khat64;
+        chi = (const T*)op.chi64;
+    } else {
+        kh = (const cplx<T>*)op.khat32;
+        chi = (const T*)op.chi32;
+    }
+    const double E = sizeof(cplx<T>);
+    const double lineA = 3.0 * n0 * n1 * P2 * E;  // one slot of A
+    const double lineB = 3.0 * n0 * P1 * P2 * E;  // one slot of B
+    const double vec = 3.0 * op.Nb * E;           // one compact vector
+    for (int s0 = 0; s0 < nr; s0 += W.cap) {
+        const int ns = std::min(W.cap, nr - s0);
+        const int* list = d_list + s0;
+        // pass 1
+        {
+            const FFTPlan& p = op.ax[2].plan;
+            const int NL = lines_per_cta<T>(p.L);
+            const long long nlines = (long long)ns * 3 * n0 * n1;
+            tmr_begin(TMR_ZFWD, op.stream);
+            k_zfwd<T><<<(unsigned)((nlines + NL - 1) / NL), 256, lines_smem<T>(p, NL), op.stream>>>(
+                w, wr, list, op.idx_map, A, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), NL);
+            tmr_end(TMR_ZFWD, op.stream, ns * (vec + lineA) + 4.0 * op.N);
+            count_launch();
+            VIE_CUDA(cudaGetLastError());
+        }
+        // pass 2
+        VIE_TRY((launch_axis<T, false>(A, B, (long long)ns * 3 * n0, n1, P1, P2, op.ax[1].plan, twp<T>(op.ax[1]),
+                                       op.stream, TMR_YFWD)));
+        // pass 3
+        {
+            const FFTPlan& p = op.ax[0].plan;
+            const long long inner = (long long)P1 * P2;
+            const int TW = xfused_tile<T>(p.L, inner);
+            const long long grid = (long long)ns * ((inner + TW - 1) / TW);
+            tmr_begin(TMR_XFUSED, op.stream);
+            k_xfused<T><<<(unsigned)grid, 256, xfused_smem<T>(p, TW), op.stream>>>(
+                B, n0, inner, P0, P1, P2, kh, op.H[0], op.H[1], op.H[2], p, twp<T>(op.ax[0]), TW);
+            tmr_end(TMR_XFUSED, op.stream, 2.0 * ns * lineB + 6.0 * op.H[0] * op.H[1] * op.H[2] * E);
+            count_launch();
+            VIE_CUDA(cudaGetLastError());
+        }
+        // pass 4
+        VIE_TRY((launch_axis<T, true>(B, A, (long long)ns * 3 * n0, P1, n1, P2, op.ax[1].plan, twp<T>(op.ax[1]),
+                                      op.stream, TMR_YINV)));
+        // pass 5
+        {
+            const FFTPlan& p = op.ax[2].plan;
+            const int NL = lines_per_cta<T>(p.L);
+            const long long nlines = (long long)ns * 3 * n0 * n1;
+            tmr_begin(TMR_ZINV, op.stream);
+            k_zinv<T><<<(unsigned)((nlines + NL - 1) / NL), 256, lines_smem<T>(p, NL), op.stream>>>(
+                A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), NL);
+            tmr_end(TMR_ZINV, op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
+            count_launch();
+            VIE_CUDA(cudaGetLastError());
+        }
+    }
+    return VIE_OK;
+}
+
+int op_apply(Operator& op, int prec, const void* w, long long wr, void* y, long long yr, const int* d_list, int nr) {
+    if (nr <= 0) return VIE_OK;
+    if (prec == VIE_PREC_FP64) return apply_t<double>(op, (const c64*)w, wr, (c64*)y, yr, d_list, nr);
+    return apply_t<float>(op, (const c32*)w, wr, (c32*)y, yr, d_list, nr);
+}
+
+void op_free(Operator& op) {
+    for (int a = 0; a < 3; ++a) {
+        cudaFree(op.ax[a].tw32);
+        cudaFree(op.ax[a].tw64);
+        op.ax[a].tw32 = nullptr;
+        op.ax[a].tw64 = nullptr;
+    }
+    cudaFree(op.khat32);
+    cudaFree(op.khat64);
+    cudaFree(op.idx_map);
+    cudaFree(op.vox);
+    cudaFree(op.chi32);
+    cudaFree(op.chi64);
+    for (int p = 0; p < 2; ++p) {
+        cudaFree(op.work[p].A);
+        cudaFree(op.work[p].B);
+        op.work[p] = MatvecWork();
+    }
+    cudaFree(op.d_list);
+    op.khat32 = nullptr;
+    op.khat64 = nullptr;
+    op.idx_map = nullptr;
+    op.vox = nullptr;
+    op.chi32 = nullptr;
+    op.chi64 = nullptr;
+    op.d_list = nullptr;
+    op.bytes = 0;
+}
+
+}  // namespace vie

@@ -1,0 +1,68 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace vie {
+
+// device twiddle tables of one axis, in both precisions
+struct AxisFFT {
+    FFTPlan plan;
+    c32* tw32 = nullptr;
+    c64* tw64 = nullptr;
+};
+
+// matvec workspace of one precision
+struct MatvecWork {
+    void* A = nullptr;  // [cap][3][n0][n1][P2]   after the z pass
+    void* B = nullptr;  // [cap][3][n0][P1][P2]   after the y pass (x pass in place)
+    int cap = 0;        // RHS slots
+};
+
+// The discrete operator A w = w - chi (K * w) on one grid.
+struct Operator {
+    int n[3] = {0, 0, 0};
+    int P[3] = {0, 0, 0};
+    int H[3] = {0, 0, 0};  // octant extents P/2 + 1
+    long long N = 0, Nb = 0;
+    double h = 0, k0 = 0, origin[3] = {0, 0, 0};
+    AxisFFT ax[3];
+    c32* khat32 = nullptr;  // [6][H0][H1][H2], scaled by 1/(P0 P1 P2)
+    c64* khat64 = nullptr;
+    int* idx_map = nullptr;  // [N] compact index or -1
+    int* vox = nullptr;      // [Nb] linear voxel index of body voxel
+    float* chi32 = nullptr;  // [Nb]
+    double* chi64 = nullptr; // [Nb]
+    MatvecWork work[2];      // 0: FP32, 1: FP64
+    int* d_list = nullptr;   // RHS index list for batched launches
+    int list_cap = 0;
+    cudaStream_t stream = nullptr;
+    double bytes = 0;        // device bytes held
+};
+
+// device allocation helpers (track bytes)
+int dev_alloc(Operator& op, void** p, size_t bytes);
+void dev_free(Operator& op, void* p, size_t bytes);
+
+// smooth padded size >= m (factors 2, 3, 5, 7)
+int smooth_size(int m);
+
+// ---- operator (matvec.cu) ---------------------------------------------------
+int op_init_axes(Operator& op);
+int op_build_kernel(Operator& op);                 // K-hat octants (FP64 build)
+int op_set_body_device(Operator& op, const double* eps_dev);  // chi, idx_map, vox
+int op_reserve(Operator& op, int prec, int nrhs);  // matvec workspace
+int op_set_list(Operator& op, const int* host_list, int nr);  // uploads d_list
+// y[list[s]] = A w[list[s]] for s < nr.  w, y on the compact layout with RHS
+// stride `rstride` elements; prec 0 = float, 1 = double.
+int op_apply(Operator& op, int prec, const void* w, long long w_rstride, void* y, long long y_rstride,
+             const int* d_list, int nr);
+void op_free(Operator& op);
+
+// standalone batched line FFT (vie_fft_lines)
+int fft_lines_device(const void* in, void* out, int L, int count, int inverse, int prec, cudaStream_t s);
+
+}  // namespace vie

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of libvie.so (names follow include/vie.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  There is no fallback: if ``libvie.so`` is missing or
+no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libvie.so")
+
+VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_ENOCONV = 0, -1, -2, -3
+VIE_ETIMEOUT, VIE_EUNDEF, VIE_EDEVICE, VIE_ESTATE = -4, -5, -6, -7
+PREC_MIXED, PREC_FP64 = 0, 1
+BASIS_CART, BASIS_SPH, BASIS_CIRC = 0, 1, 2
+
+EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device", "vie_solve",
+           "vie_farfield", "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer",
+           "vie_hom_map", "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines",
+           "vie_get_info", "vie_kernel_launches", "vie_stream", "vie_destroy", "vie_last_error",
+           "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
+
+
+class VieError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class _Grid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("h", C.c_double), ("origin", C.c_double * 3)]
+
+
+class _Channel(C.Structure):
+    _fields_ = [("khat", C.c_double * 3), ("pol", C.c_double * 6)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iter", C.c_int),
+                ("precision", C.c_int), ("inner_tol", C.c_double), ("use_x0", C.c_int),
+                ("reserved", C.c_int * 3)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("n_rhs", C.c_int), ("converged", C.c_int), ("iters_max", C.c_int),
+                ("outer_max", C.c_int), ("matvecs32", C.c_longlong), ("matvecs64", C.c_longlong),
+                ("relres_max", C.c_double), ("seconds", C.c_double),
+                ("iters", C.POINTER(C.c_int)), ("relres", C.POINTER(C.c_double))]
+
+
+class _Info(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("P", C.c_int * 3), ("n_body", C.c_longlong),
+                ("n_rhs", C.c_int), ("device", C.c_int), ("device_bytes", C.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load libvie.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2508_16471_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    L.vie_default_opts.argtypes = [C.POINTER(_Opts)]
+    L.vie_setup.argtypes = [C.POINTER(_Grid), dp, C.c_double, C.POINTER(P)]
+    L.vie_set_eps.argtypes = [P, dp]
+    L.vie_set_eps_device.argtypes = [P, P]
+    L.vie_solve.argtypes = [P, C.POINTER(_Channel), C.c_int, C.POINTER(_Opts), C.POINTER(_Stats)]
+    L.vie_farfield.argtypes = [P, dp, C.c_int, dp, C.c_int, C.c_int, dp]
+    L.vie_farfield_dirs.argtypes = [P, dp, C.c_int, C.c_int, dp]
+    L.vie_farfield_dirs_device.argtypes = [P, P, C.c_int, C.c_int, P]
+    L.hom_transfer.argtypes = [dp, dp, C.c_double, dp, C.c_int, dp, dp, dp]
+    L.vie_hom_map.argtypes = [dp, C.c_int, dp, C.c_int, C.c_double, dp, dp, dp]
+    L.vie_get_current.argtypes = [P, C.c_int, dp]
+    L.vie_apply.argtypes = [P, dp, dp, C.c_int, C.c_int]
+    L.vie_apply_device.argtypes = [P, P, P, C.c_int, C.c_int]
+    L.vie_fft_lines.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int]
+    L.vie_get_info.argtypes = [P, C.POINTER(_Info)]
+    L.vie_kernel_launches.restype = C.c_longlong
+    L.vie_stream.argtypes = [P]
+    L.vie_stream.restype = P
+    L.vie_destroy.argtypes = [P]
+    L.vie_destroy.restype = None
+    L.vie_last_error.restype = C.c_char_p
+    L.vie_timer_enable.argtypes = [C.c_int]
+    L.vie_timer_enable.restype = None
+    L.vie_timer_reset.restype = None
+    L.vie_timer_read.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                 C.POINTER(C.c_double)]
+    L.vie_timer_read.restype = C.c_int
+    L.vie_timer_name.argtypes = [C.c_int]
+    L.vie_timer_name.restype = C.c_char_p
+    L.vie_timer_count.restype = C.c_int
+    for f in ["vie_setup", "vie_set_eps", "vie_set_eps_device", "vie_solve", "vie_farfield",
+              "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer", "vie_hom_map",
+              "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines", "vie_get_info"]:
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(code, allow=()):
+    if code != VIE_OK and code not in allow:
+        raise VieError(code, load().vie_last_error().decode())
+    return code
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def kernel_launches() -> int:
+    return int(load().vie_kernel_launches())
+
+
+def timer_enable(on=True):
+    load().vie_timer_enable(int(bool(on)))
+
+
+def timer_reset():
+    load().vie_timer_reset()
+
+
+def timer_read():
+    """{kernel name: (total ms, launches, algorithmic bytes)} since the last reset."""
+    L = load()
+    out = {}
+    for i in range(L.vie_timer_count()):
+        ms, n, b = C.c_double(), C.c_longlong(), C.c_double()
+        L.vie_timer_read(i, C.byref(ms), C.byref(n), C.byref(b))
+        out[L.vie_timer_name(i).decode()] = (ms.value, n.value, b.value)
+    return out
+
+
+def default_opts(**kw):
+    o = _Opts()
+    load().vie_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _channels(chs):
+    arr = (_Channel * len(chs))()
+    for i, c in enumerate(chs):
+        if hasattr(c, "khat"):
+            k, p = c.khat, c.pol
+        else:
+            k, p = c
+        p = np.asarray(p, dtype=np.complex128)
+        for q in range(3):
+            arr[i].khat[q] = float(k[q])
+            arr[i].pol[2 * q] = float(p[q].real)
+            arr[i].pol[2 * q + 1] = float(p[q].imag)
+    return arr
+
+
+class Handle:
+    """One grid + body on the current CUDA device (vie_setup ... vie_destroy)."""
+
+    def __init__(self, n, h, eps_r, k0=2.0 * np.pi, origin=(0.0, 0.0, 0.0)):
+        L = load()
+        g = _Grid()
+        for a in range(3):
+            g.n[a] = int(n[a])
+            g.origin[a] = float(origin[a])
+        g.h = float(h)
+        self.n = tuple(int(v) for v in n)
+        eps = np.ascontiguousarray(eps_r, dtype=np.float64).reshape(self.n)
+        hp = C.c_void_p()
+        _check(L.vie_setup(C.byref(g), _dptr(eps), float(k0), C.byref(hp)))
+        self._h = hp
+        self.n_rhs = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vie_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def info(self):
+        i = _Info()
+        _check(load().vie_get_info(self._h, C.byref(i)))
+        return dict(n=tuple(i.n), P=tuple(i.P), n_body=int(i.n_body), n_rhs=int(i.n_rhs),
+                    device=int(i.device), device_bytes=float(i.device_bytes))
+
+    def stream(self):
+        return load().vie_stream(self._h)
+
+    def set_eps(self, eps_r):
+        eps = np.ascontiguousarray(eps_r, dtype=np.float64).reshape(self.n)
+        _check(load().vie_set_eps(self._h, _dptr(eps)))
+        self.n_rhs = 0
+
+    def set_eps_device(self, ptr: int):
+        _check(load().vie_set_eps_device(self._h, C.c_void_p(ptr)))
+        self.n_rhs = 0
+
+    def solve(self, channels, allow_noconv=False, **opts):
+        o = default_opts(**opts)
+        R = len(channels)
+        iters = np.zeros(R, dtype=np.int32)
+        rel = np.zeros(R, dtype=np.float64)
+        st = _Stats()
+        st.iters = iters.ctypes.data_as(C.POINTER(C.c_int))
+        st.relres = rel.ctypes.data_as(C.POINTER(C.c_double))
+        code = load().vie_solve(self._h, _channels(channels), R, C.byref(o), C.byref(st))
+        _check(code, allow=(VIE_ENOCONV,) if allow_noconv else ())
+        self.n_rhs = R
+        return dict(code=code, converged=st.converged, iters_max=st.iters_max, outer_max=st.outer_max,
+                    matvecs32=st.matvecs32, matvecs64=st.matvecs64, relres_max=st.relres_max,
+                    seconds=st.seconds, iters=iters, relres=rel)
+
+    def farfield(self, theta, phi, basis=BASIS_CART):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        ph = np.ascontiguousarray(phi, dtype=np.float64)
+        out = np.zeros((self.n_rhs, len(th), len(ph), 3), dtype=np.complex128)
+        _check(load().vie_farfield(self._h, _dptr(th), len(th), _dptr(ph), len(ph), int(basis),
+                                   out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def farfield_dirs(self, dirs, basis=BASIS_CART):
+        d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+        out = np.zeros((self.n_rhs, len(d), 3), dtype=np.complex128)
+        _check(load().vie_farfield_dirs(self._h, _dptr(d), len(d), int(basis),
+                                        out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def farfield_dirs_device(self, dirs_ptr: int, D: int, out_ptr: int, basis=BASIS_CART):
+        _check(load().vie_farfield_dirs_device(self._h, C.c_void_p(dirs_ptr), int(D), int(basis),
+                                               C.c_void_p(out_ptr)))
+
+    def get_current(self, rhs):
+        out = np.zeros((3,) + self.n, dtype=np.complex128)
+        _check(load().vie_get_current(self._h, int(rhs), out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def apply(self, w, precision=PREC_FP64):
+        w = _c128(w)
+        R = w.shape[0]
+        y = np.zeros_like(w)
+        _check(load().vie_apply(self._h, _dptr(w.view(np.float64)), y.ctypes.data_as(C.POINTER(C.c_double)),
+                                R, int(precision)))
+        return y
+
+    def apply_device(self, w_ptr: int, y_ptr: int, n_rhs: int, precision=PREC_MIXED):
+        _check(load().vie_apply_device(self._h, C.c_void_p(w_ptr), C.c_void_p(y_ptr), int(n_rhs),
+                                       int(precision)))
+
+
+def hom_transfer(E, omega=None, sigma=1.2, dtau=()):
+    """g2, N~c(dtau), visibility for E[2 det][2 ch] complex."""
+    e = _c128(np.asarray(E).reshape(2, 2)).view(np.float64).reshape(-1).copy()
+    dt = np.ascontiguousarray(dtau, dtype=np.float64)
+    nc = np.zeros(len(dt))
+    g2 = np.zeros(1)
+    vis = np.zeros(1)
+    om = None if omega is None else np.ascontiguousarray(omega, dtype=np.float64)
+    code = load().hom_transfer(_dptr(e), None if om is None else _dptr(om), float(sigma),
+                               _dptr(dt) if len(dt) else None, len(dt), _dptr(g2),
+                               _dptr(nc) if len(dt) else None, _dptr(vis))
+    _check(code, allow=(VIE_EUNDEF,))
+    return float(g2[0]), nc, float(vis[0]), code
+
+
+def hom_map(Ea, Eb, sigma=1.2):
+    """g2, visibility and normalised classical P2 over all pairs (a in A, b in B).
+    Ea: [2][nA] complex (channels 1, 2), Eb: [2][nB]."""
+    a = _c128(Ea)
+    b = _c128(Eb)
+    nA, nB = a.shape[1], b.shape[1]
+    g2 = np.zeros((nA, nB))
+    vis = np.zeros((nA, nB))
+    p2 = np.zeros((nA, nB))
+    _check(load().vie_hom_map(_dptr(a.view(np.float64)), nA, _dptr(b.view(np.float64)), nB, float(sigma),
+                              _dptr(g2), _dptr(vis), _dptr(p2)))
+    return g2, vis, p2
+
+
+def fft_lines(x, inverse=False, precision=PREC_FP64):
+    x = _c128(np.atleast_2d(x))
+    out = np.zeros_like(x)
+    _check(load().vie_fft_lines(_dptr(x.view(np.float64)), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                x.shape[1], x.shape[0], int(bool(inverse)), int(precision)))
+    return out

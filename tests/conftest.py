@@ -17,3 +17,12 @@ def pytest_configure(config):
 def k0():
     import math
     return 2.0 * math.pi
+
+
+@pytest.fixture(scope="session")
+def vielib():
+    """Build (if stale) and load libvie.so."""
+    from paper_2508_16471_gb300 import build
+    build.build()
+    from paper_2508_16471_gb300 import vie
+    return vie

@@ -1,0 +1,126 @@
+"""GPU parity of the FFT engine and the FFT-VIE operator against the oracle.
+
+The operator y = w - chi (K * w) (Sec. II-C, Eq. 24 in the w unknown) from the
+CUDA path is compared element by element with the oracle's direct-sum
+convolution on the same seeded inputs.  FP64 path: 1e-11 relative to max|y|
+(FFT round-off over ~log2(P^3) stages); FP32 path: 2e-5 (single-precision
+FFT round-off, ~10 eps32 * log2 P per pass).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import vie as ovie
+from paper_2508_16471_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+K0 = 2.0 * math.pi
+TOL64 = 1e-11
+TOL32 = 2e-5
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 7, 16, 32, 75, 96, 125, 128, 192, 256, 343, 512, 1024])
+def test_fft_lines_vs_numpy(vielib, L):
+    rng = np.random.default_rng(L)
+    x = rng.standard_normal((5, L)) + 1j * rng.standard_normal((5, L))
+    ref = np.fft.fft(x, axis=1)
+    refi = np.fft.ifft(x, axis=1) * L
+    s = np.abs(ref).max()
+    assert np.abs(vielib.fft_lines(x, precision=vielib.PREC_FP64) - ref).max() <= 1e-13 * s * max(1, math.log2(L))
+    assert np.abs(vielib.fft_lines(x, inverse=True, precision=vielib.PREC_FP64) - refi).max() <= 1e-13 * s * max(1, math.log2(L))
+    assert np.abs(vielib.fft_lines(x, precision=vielib.PREC_MIXED) - ref).max() <= 2e-6 * s * max(1, math.log2(L))
+
+
+def _case_random(n, seed, fill=0.6):
+    rng = np.random.default_rng(seed)
+    eps = 1.0 + rng.uniform(0.2, 4.0, n) * (rng.uniform(size=n) < fill)
+    if not np.any(eps > 1):
+        eps.flat[0] = 2.0
+    return eps
+
+
+def _check_apply(vielib, n, h, eps, R=2, seed=0):
+    mask = eps > 1.0
+    g = inputs.Grid(n, h)
+    w = inputs.random_field(g, R, seed, mask)
+    chi = ovie.contrast(eps)
+    T = ovie.kernel_table(n, h, K0)
+    ref = np.stack([ovie.apply_direct(T, n, chi, w[r]) for r in range(R)])
+    with vielib.Handle(n, h, eps, K0) as hd:
+        y64 = hd.apply(w, precision=vielib.PREC_FP64)
+        y32 = hd.apply(w, precision=vielib.PREC_MIXED)
+    s = np.abs(ref).max()
+    e64 = np.abs(y64 - ref).max() / s
+    e32 = np.abs(y32 - ref).max() / s
+    assert e64 <= TOL64, e64
+    assert e32 <= TOL32, e32
+
+
+@pytest.mark.parametrize("n", [(1, 1, 1), (2, 3, 1), (5, 6, 4), (7, 5, 9), (12, 10, 7)])
+def test_apply_small_ragged_grids(vielib, n):
+    _check_apply(vielib, n, 0.07, _case_random(n, sum(n)))
+
+
+def test_apply_sphere16(vielib):
+    wl = inputs.sphere_config1()
+    _check_apply(vielib, wl.grid.n, wl.grid.h, wl.eps, R=3)
+
+
+def test_apply_full_body_and_single_voxel_body(vielib):
+    n = (6, 6, 6)
+    _check_apply(vielib, n, 0.05, np.full(n, 3.0))
+    eps = np.ones(n)
+    eps[2, 3, 4] = 2.5
+    _check_apply(vielib, n, 0.05, eps)
+
+
+def test_apply_nonsmooth_sizes(vielib):
+    # 2n-1 = 73 -> P = 75 (radix 3, 5), 2n-1 = 21 -> P = 21
+    n = (37, 11, 6)
+    eps = _case_random(n, 5, fill=0.3)
+    mask = eps > 1.0
+    g = inputs.Grid(n, 0.04)
+    w = inputs.random_field(g, 1, 3, mask)
+    chi = ovie.contrast(eps)
+    ref = ovie.apply_direct(ovie.kernel_table(n, 0.04, K0), n, chi, w[0])[None]
+    with vielib.Handle(n, 0.04, eps, K0) as hd:
+        assert hd.info()["P"] == (75, 21, 12)
+        y64 = hd.apply(w, precision=vielib.PREC_FP64)
+    assert np.abs(y64 - ref).max() <= TOL64 * np.abs(ref).max()
+
+
+def _sampled_parity(vielib, n, h, eps, R, seed, nsamp, prec_list):
+    g = inputs.Grid(n, h)
+    mask = eps > 1.0
+    w = inputs.random_field(g, R, seed, mask)
+    body = np.argwhere(mask)
+    rng = np.random.default_rng(seed + 1)
+    pts = body[rng.choice(len(body), size=min(nsamp, len(body)), replace=False)]
+    chi = ovie.contrast(eps)
+    out = {}
+    with vielib.Handle(n, h, eps, K0) as hd:
+        for p in prec_list:
+            out[p] = hd.apply(w, precision=p)
+    convs = ovie.convolve_direct_points_multi(n, h, K0, w, pts)
+    for r in range(R):
+        conv = convs[r]
+        ref = np.stack([w[r][:, a, b, c] - chi[a, b, c] * conv[:, i] for i, (a, b, c) in enumerate(pts)], 1)
+        s = np.abs(ref).max()
+        for p, tol in ((vielib.PREC_FP64, TOL64), (vielib.PREC_MIXED, TOL32)):
+            if p not in out:
+                continue
+            got = np.stack([out[p][r][:, a, b, c] for (a, b, c) in pts], 1)
+            assert np.abs(got - ref).max() <= tol * s, (p, np.abs(got - ref).max() / s)
+
+
+def test_apply_sphere64_sampled(vielib):
+    wl = inputs.sphere_config2()
+    _sampled_parity(vielib, wl.grid.n, wl.grid.h, wl.eps, 2, 11, 24,
+                    (vielib.PREC_FP64, vielib.PREC_MIXED))
+
+
+def test_apply_bench_size_sampled(vielib):
+    """The 128^3 random-body workload the bench times, 4 RHS, sampled voxels."""
+    wl = inputs.random_body_workload(20000, n_axis=128, h=1.0 / 40.0)
+    _sampled_parity(vielib, wl.grid.n, wl.grid.h, wl.eps, 4, 12, 6, (vielib.PREC_MIXED, vielib.PREC_FP64))

@@ -1,0 +1,179 @@
+"""GPU parity of the full path (right-hand side -> GMRES -> far field -> g2 /
+N~c) against the oracle.
+
+Tolerances: far-field amplitudes <= 1e-5 relative (l2 over all directions and
+channels, and max |dF| / max |F|); g2 <= 1e-6 absolute (g2 is in [0, 1] and
+vanishes at the HOM dips).  Parity solves run the GPU to an FP64 residual of
+1e-10 so that the solver tolerance does not dominate.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import hom as ohom
+from oracle import vie as ovie
+from paper_2508_16471_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+K0 = 2.0 * math.pi
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _maxrel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.fixture(scope="module")
+def config1():
+    wl = inputs.sphere_config1()
+    g = wl.grid
+    chs = [(c.khat, c.pol) for c in wl.channels]
+    w_or, infos = ovie.solve_channels(g.n, g.h, wl.k0, wl.eps, chs, tol=1e-12)
+    assert all(i["converged"] for i in infos)
+    return wl, chs, w_or
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_config1_currents_and_farfield(vielib, config1, prec):
+    wl, chs, w_or = config1
+    g = wl.grid
+    th, ph = inputs.angle_grid(wl.extra["theta_deg"], wl.extra["phi_deg"])
+    dirs = inputs.directions_from_angles(th, ph)
+    with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
+        st = hd.solve(chs, tol=1e-10, restart=40, precision=prec)
+        assert st["converged"] == 2 and st["relres_max"] <= 1e-10
+        w = np.stack([hd.get_current(r) for r in range(2)])
+        Fg = hd.farfield(th, ph)  # product grid (FP32 chain)
+        Fd = hd.farfield_dirs(dirs)  # direction list (FP64)
+    assert _maxrel(w, w_or) < 1e-8
+    F_or = np.stack([ovie.farfield(w_or[j], g.n, g.h, wl.k0, dirs) for j in range(2)])
+    Fg = Fg.reshape(F_or.shape)
+    assert _rel(Fd, F_or) < 1e-8 and _maxrel(Fd, F_or) < 1e-8
+    assert _rel(Fg, F_or) < 1e-5 and _maxrel(Fg, F_or) < 1e-5
+
+
+def test_config1_g2_and_coincidences(vielib, config1):
+    wl, chs, w_or = config1
+    g = wl.grid
+    dets = np.stack([inputs.spherical_basis(math.radians(t), math.radians(p))[0]
+                     for t, p in wl.extra["detectors_deg"]])
+    with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
+        hd.solve(chs, tol=1e-10, restart=40, precision=vielib.PREC_MIXED)
+        F = hd.farfield_dirs(dets)
+    F_or = np.stack([ovie.farfield(w_or[j], g.n, g.h, wl.k0, dets) for j in range(2)])
+    # E[det][ch] = z components (a = b = z)
+    E = F[:, :, 2].T
+    E_or = F_or[:, :, 2].T
+    dtau = wl.extra["dtau"]
+    g2, nc, vis, code = vielib.hom_transfer(E, sigma=1.2, dtau=dtau)
+    assert code == 0
+    assert abs(g2 - ohom.g2_degenerate(E_or)) < 1e-6
+    assert np.abs(nc - ohom.coincidence_closed(E_or, dtau, 1.2)).max() < 1e-6
+    assert abs(vis - ohom.visibility(E_or)) < 1e-6
+
+
+def test_config1_y_polarised_variant_gives_trivial_zero(vielib):
+    """y-pol along +x has no z far field on the y = 0 plane (mirror symmetry):
+    g2 = 0 with N~c undefined (single-path zero, Sec. III-A)."""
+    wl = inputs.sphere_config1()
+    g = wl.grid
+    chs = [((0, 0, 1.0), (1.0, 0, 0)), ((1.0, 0, 0), (0, 1.0, 0))]
+    dets = np.stack([inputs.spherical_basis(math.radians(t), math.radians(p))[0]
+                     for t, p in wl.extra["detectors_deg"]])
+    with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
+        hd.solve(chs, tol=1e-10, restart=40)
+        F = hd.farfield_dirs(dets)
+    E = F[:, :, 2].T
+    assert np.abs(E[:, 1]).max() < 1e-9 * np.abs(E[:, 0]).max()
+    g2, nc, vis, code = vielib.hom_transfer(np.where(np.abs(E) < 1e-9 * np.abs(E).max(), 0, E),
+                                            sigma=1.2, dtau=[0.0, 1.0])
+    assert g2 == 0.0 and np.all(np.isnan(nc)) and code == vielib.VIE_EUNDEF
+
+
+def test_mixed_and_fp64_agree_random_body(vielib):
+    rng = np.random.default_rng(3)
+    n = (14, 11, 9)
+    eps = 1.0 + rng.uniform(0.5, 3.0, n) * (rng.uniform(size=n) < 0.5)
+    chs = [(c.khat, c.pol) for c in inputs.channels_fibonacci(2)]
+    with vielib.Handle(n, 0.05, eps, K0) as hd:
+        s64 = hd.solve(chs, tol=1e-9, restart=30, precision=vielib.PREC_FP64)
+        w64 = np.stack([hd.get_current(r) for r in range(len(chs))])
+        s32 = hd.solve(chs, tol=1e-9, restart=30, precision=vielib.PREC_MIXED)
+        w32 = np.stack([hd.get_current(r) for r in range(len(chs))])
+    assert s64["converged"] == len(chs) and s32["converged"] == len(chs)
+    assert s32["matvecs32"] > 0 and s64["matvecs32"] == 0
+    assert _maxrel(w32, w64) < 1e-7
+    # oracle check on one channel
+    x, info = ovie.gmres(ovie.FFTOperator(n, 0.05, K0, ovie.contrast(eps)),
+                         ovie.rhs(ovie.contrast(eps), ovie.incident_field(n, 0.05, K0, *chs[0])), tol=1e-12)
+    assert _maxrel(w64[0], x) < 1e-8
+
+
+def test_config2_against_stored_oracle(vielib):
+    """64^3 sphere (R = 1 lambda, eps_r = 4): mixed-precision batch of all 8
+    channels; channels 0 and 5 against far fields stored by
+    tests/golden/make_golden.py (oracle GMRES to 1e-9)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "sphere64_farfield.npz")
+    gold = np.load(path)
+    wl = inputs.sphere_config2()
+    g = wl.grid
+    chs = [(c.khat, c.pol) for c in wl.channels]
+    th, ph = gold["theta"], gold["phi"]
+    with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
+        st = hd.solve(chs, tol=1e-9, restart=64, precision=vielib.PREC_MIXED, max_iter=50000)
+        assert st["converged"] == 8
+        F = hd.farfield(th, ph).reshape(8, -1, 3)
+    for j, r in enumerate(gold["channels"]):
+        assert _rel(F[r], gold["F"][j]) < 1e-5, _rel(F[r], gold["F"][j])
+
+
+def test_optical_theorem_on_gpu_solution(vielib):
+    """Energy balance of the GPU solution of a random lossless body (property
+    of the exact discrete solution at any size; residual 1e-9 here)."""
+    wl = inputs.random_body_workload(7, n_axis=32, h=1.0 / 20.0)
+    g = wl.grid
+    chs = [(c.khat, c.pol) for c in wl.channels[:2]]
+    Rb = g.h * math.sqrt(3.0) * g.n[0] / 2.0
+    d, wq = ovie.sphere_quadrature(int(K0 * Rb) + 12)
+    with vielib.Handle(g.n, g.h, wl.eps, K0) as hd:
+        hd.solve(chs, tol=1e-9, restart=50)
+        F = hd.farfield_dirs(d)
+        Ff = hd.farfield_dirs(np.stack([c[0] for c in chs]))
+    for j, (k, p) in enumerate(chs):
+        ext = 4 * math.pi / K0 * np.imag(np.conj(p) @ Ff[j, j])
+        sca = float(np.sum(wq * np.sum(np.abs(F[j]) ** 2, axis=1)))
+        assert abs(ext - sca) <= 1e-6 * sca
+
+
+def test_errors_and_states(vielib):
+    n = (4, 4, 4)
+    eps = np.full(n, 2.0)
+    with pytest.raises(vielib.VieError) as e:
+        vielib.Handle(n, 0.1, np.full(n, 0.5), K0)
+    assert e.value.code == vielib.VIE_EINVAL
+    bad = eps.copy()
+    bad[0, 0, 0] = np.nan
+    with pytest.raises(vielib.VieError):
+        vielib.Handle(n, 0.1, bad, K0)
+    with pytest.raises(vielib.VieError):
+        vielib.Handle(n, 0.1, eps, -1.0)
+    with pytest.raises(vielib.VieError):
+        vielib.Handle(n, 0.1, np.ones(n), K0)
+    with vielib.Handle(n, 0.1, eps, K0) as hd:
+        with pytest.raises(vielib.VieError) as e:
+            hd.farfield_dirs([[0, 0, 1.0]])
+        assert e.value.code == vielib.VIE_ESTATE
+        with pytest.raises(vielib.VieError) as e:
+            hd.solve([((0, 0, 1.0), (0, 0, 1.0))])  # longitudinal polarisation
+        assert e.value.code == vielib.VIE_EINVAL
+        st = hd.solve([((0, 0, 1.0), (1.0, 0, 0))], allow_noconv=True, max_iter=1, restart=1, tol=1e-14)
+        assert st["code"] == vielib.VIE_ENOCONV and st["converged"] == 0
+        assert st["relres_max"] > 1e-14
+        # the stored current is still usable
+        F = hd.farfield_dirs([[1.0, 0, 0]])
+        assert np.all(np.isfinite(F))

@@ -87,3 +87,15 @@ def test_smooth_size():
     assert vie.smooth_size(73) == 75
     assert vie.smooth_size(121) == 125
     assert vie.smooth_size(191) == 192
+
+
+def test_multi_point_direct_sum_matches_single():
+    n = (6, 5, 4)
+    h = 0.08
+    rng = np.random.default_rng(8)
+    W = rng.standard_normal((2, 3) + n) + 1j * rng.standard_normal((2, 3) + n)
+    pts = np.array([[0, 0, 0], [5, 4, 3], [2, 1, 2]])
+    multi = vie.convolve_direct_points_multi(n, h, K0, W, pts)
+    for r in range(2):
+        single = vie.convolve_direct_points(n, h, K0, W[r], pts)
+        assert np.abs(multi[r] - single).max() <= 1e-13 * np.abs(single).max()
