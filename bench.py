@@ -2,7 +2,7 @@
 """Benchmark: VIE solves/sec to an FP64 residual of 1e-6 on 128^3 random bodies.
 
 One step = one body of the 128^3 evaluation set (random unions of ellipsoids /
-cuboids, eps_r in [1.5, 6], h = lambda/40) solved for 32 incident channels (16
+cuboids, eps_r in [1.5, 6], h = lambda/128, a 1-lambda box) solved for 32 incident channels (16
 Fibonacci directions x 2 polarisations) in one batched call: right-hand-side
 build, mixed-precision GMRES (FP32 FFT matvec, FP64 Arnoldi / Givens, FP64
 iterative refinement) down to the FP64 residual check.  The kernel spectrum of
@@ -41,7 +41,7 @@ sys.path.insert(0, ROOT)
 METRIC = "VIE solves/sec to FP64 residual 1e-6 (128^3 random bodies, 32 RHS/body)"
 UNIT = "solves/s"
 N_AXIS = 128
-H = 1.0 / 40.0
+H = 1.0 / 128.0
 N_DIRS = 16  # x 2 polarisations = 32 RHS
 SEED0 = 20000
 
@@ -175,7 +175,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"random bodies {N_AXIS}^3, h=lambda/40, {2 * N_DIRS} RHS/body",
+            "config": {"workload": f"random bodies {N_AXIS}^3, h=lambda/128 (1 lambda box), {2 * N_DIRS} RHS/body",
                        "l2": "inputs larger than L2"},
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": det["cores"],
                              "sample": (f"FP64 oracle (NumPy/SciPy FFT operator, GMRES) on body seed {SEED0}: "
@@ -372,7 +372,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded random bodies)",
-        "config": {"workload": f"random bodies {N_AXIS}^3, h=lambda/40, eps_r in [1.5,6], "
+        "config": {"workload": f"random bodies {N_AXIS}^3, h=lambda/128 (1 lambda box), eps_r in [1.5,6], "
                                f"{R} RHS/body ({N_DIRS} Fibonacci directions x 2 pol), tol 1e-6",
                    "solver": f"mixed FP32 matvec / FP64 Arnoldi GMRES({args.restart}) + FP64 refinement",
                    "bodies_per_rank": args.bodies, "parallelism": f"replicas x{world}",

@@ -230,6 +230,13 @@ int vie_fft_lines(const double* in, double* out, int L, int count, int inverse, 
 
 int vie_get_info(const vie_handle* hd, vie_info* info);
 
+/* FFT kernel family of the FP32 operator passes: 0 (default) uses the
+ * register four-step kernels on every axis whose padded length is a power of
+ * two in 16..512 and the generic shared-memory Stockham kernels elsewhere;
+ * 1 forces the generic kernels everywhere.  Results agree to FP32 round-off;
+ * used for A/B timing.  Errors: VIE_EINVAL. */
+int vie_set_fft_path(vie_handle* hd, int path);
+
 /* Launch statistics: number of library kernels launched by this process. */
 long long vie_kernel_launches(void);
 

@@ -473,6 +473,12 @@ int vie_get_info(const vie_handle* hd, vie_info* info) {
     return VIE_OK;
 }
 
+int vie_set_fft_path(vie_handle* hd, int path) {
+    if (!hd || (path != 0 && path != 1)) return fail(VIE_EINVAL, "fft path must be 0 or 1");
+    hd->op.fft_path = path;
+    return VIE_OK;
+}
+
 void* vie_stream(vie_handle* hd) { return hd ? (void*)hd->op.stream : nullptr; }
 
 void vie_destroy(vie_handle* hd) {

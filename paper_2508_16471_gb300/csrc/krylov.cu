@@ -21,7 +21,7 @@
 namespace vie {
 
 constexpr int KB = 256;   // threads per block for vector kernels
-constexpr int KE = 4;     // elements per thread
+constexpr int KE = 8;     // elements per thread
 constexpr int KCH = KB * KE;
 
 template <typename T> __device__ __forceinline__ c64 ld64(const cplx<T>* p, long long i) {
@@ -34,43 +34,59 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// partial[(r*mp1 + i)*nblk + b] = sum over block b of conj(V_i) . V_{j+1}
+// partial[(r*mp1 + i)*nblk + b] = sum over block b of conj(V_i) . V_{j+1}.
+// Each thread forms its KE products in the basis precision T (the stored
+// vectors carry no more than that); every sum across threads, warps and
+// blocks is FP64.
 template <typename T>
 __global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long long vstride, int j,
-                       const int* __restrict__ list, c64* __restrict__ partial, int mp1, long long n, int nblk) {
-    __shared__ double sre[KB / 32][64], sim[KB / 32][64];
+                       const int* __restrict__ list, c64* __restrict__ partial, int mp1, long long n, int nblk,
+                       const int* __restrict__ gate) {
+    __shared__ double sre[KB / 32][MAX_RESTART + 1], sim[KB / 32][MAX_RESTART + 1];
     const int r = list[blockIdx.y];
+    if (gate && !gate[r]) return;
     const cplx<T>* Vr = V + r * rstride;
     const cplx<T>* w = Vr + (long long)(j + 1) * vstride;
     const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
-    c64 wv[KE];
+    cplx<T> wv[KE];
 #pragma unroll
     for (int k = 0; k < KE; ++k) {
         const long long e = e0 + k * KB;
-        wv[k] = e < n ? ld64(w, e) : c64{0, 0};
+        wv[k] = e < n ? w[e] : cplx<T>{(T)0, (T)0};
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = 0; i <= j; ++i) {
         const cplx<T>* vi = Vr + (long long)i * vstride;
-        double ar = 0, ai = 0;
+        T ar = 0, ai = 0;
 #pragma unroll
         for (int k = 0; k < KE; ++k) {
             const long long e = e0 + k * KB;
             if (e < n) {
-                const c64 a = ld64(vi, e);
+                const cplx<T> a = vi[e];
                 ar += a.x * wv[k].x + a.y * wv[k].y;
                 ai += a.x * wv[k].y - a.y * wv[k].x;
             }
         }
-        ar = warp_sum(ar);
-        ai = warp_sum(ai);
+        double dr = warp_sum((double)ar);
+        double di = warp_sum((double)ai);
         if (lane == 0) {
-            sre[wid][i] = ar;
-            sim[wid][i] = ai;
+            sre[wid][i] = dr;
+            sim[wid][i] = di;
+        }
+    }
+    {
+        // ||w||^2 before the projection (entry j+1), for the reorthogonalisation test
+        T ww = 0;
+#pragma unroll
+        for (int k = 0; k < KE; ++k) ww += wv[k].x * wv[k].x + wv[k].y * wv[k].y;
+        const double dw = warp_sum((double)ww);
+        if (lane == 0) {
+            sre[wid][j + 1] = dw;
+            sim[wid][j + 1] = 0.0;
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i <= j; i += KB) {
+    for (int i = threadIdx.x; i <= j + 1; i += KB) {
         double ar = 0, ai = 0;
         for (int q = 0; q < KB / 32; ++q) {
             ar += sre[q][i];
@@ -82,11 +98,13 @@ __global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long lo
 
 // coef[r][i] = sum_b partial; H[r][i, j] (+)= coef
 __global__ void k_reduce_dots(const c64* __restrict__ partial, c64* __restrict__ coef, c64* __restrict__ H, int j,
-                              const int* __restrict__ list, int mp1, int nblk, int accumulate) {
+                              const int* __restrict__ list, int mp1, int nblk, int accumulate,
+                              const int* __restrict__ gate) {
     __shared__ double sre[KB / 32], sim[KB / 32];
     const int r = list[blockIdx.y];
+    if (gate && !gate[r]) return;
     const int i = blockIdx.x;
-    const c64* p = partial + ((long long)r * mp1 + i) * nblk;
+    const c64* p = partial + ((long long)r * (mp1 + 1) + i) * nblk;
     double ar = 0, ai = 0;
     for (int b = threadIdx.x; b < nblk; b += KB) {
         ar += p[b].x;
@@ -105,63 +123,86 @@ __global__ void k_reduce_dots(const c64* __restrict__ partial, c64* __restrict__
             tr += sre[q];
             ti += sim[q];
         }
-        coef[(long long)r * mp1 + i] = c64{tr, ti};
+        if (i > j) {  // ||w||^2 before projection
+            coef[(long long)r * (mp1 + 1) + i] = c64{tr, ti};
+            return;
+        }
+        coef[(long long)r * (mp1 + 1) + i] = c64{tr, ti};
         c64* h = H + (long long)r * mp1 * (mp1 - 1) + (long long)j * mp1 + i;  // column-major (m+1) x m
         if (accumulate) *h = c64{h->x + tr, h->y + ti};
         else *h = c64{tr, ti};
     }
 }
 
-// w = V_{j+1} -= sum_{i<=j} coef_i V_i ; normpart[r][b] = ||w||^2 over block
+// w = V_{j+1} -= sum_{i<=j} coef_i V_i ; normpart[r][b] = ||w||^2 over block.
+// The projection is applied in the basis precision T (coefficients rounded
+// from FP64 once per block); the norm is reduced in FP64.
 template <typename T>
 __global__ void k_update(cplx<T>* __restrict__ V, long long rstride, long long vstride, int j,
                          const int* __restrict__ list, const c64* __restrict__ coef, double* __restrict__ normpart,
-                         int mp1, long long n, int nblk) {
-    __shared__ c64 cf[64];
+                         int mp1, long long n, int nblk, const int* __restrict__ gate) {
+    __shared__ cplx<T> cf[MAX_RESTART];
     __shared__ double ws[KB / 32];
     const int r = list[blockIdx.y];
-    for (int i = threadIdx.x; i <= j; i += KB) cf[i] = coef[(long long)r * mp1 + i];
+    if (gate && !gate[r]) return;
+    for (int i = threadIdx.x; i <= j; i += KB) {
+        const c64 c = coef[(long long)r * (mp1 + 1) + i];
+        cf[i] = cplx<T>{(T)c.x, (T)c.y};
+    }
     __syncthreads();
     cplx<T>* Vr = V + r * rstride;
     cplx<T>* w = Vr + (long long)(j + 1) * vstride;
     const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
-    c64 acc[KE];
+    cplx<T> acc[KE];
 #pragma unroll
     for (int k = 0; k < KE; ++k) {
         const long long e = e0 + k * KB;
-        acc[k] = e < n ? ld64(w, e) : c64{0, 0};
+        acc[k] = e < n ? w[e] : cplx<T>{(T)0, (T)0};
     }
     for (int i = 0; i <= j; ++i) {
         const cplx<T>* vi = Vr + (long long)i * vstride;
-        const c64 c = cf[i];
+        const cplx<T> c = cf[i];
 #pragma unroll
         for (int k = 0; k < KE; ++k) {
             const long long e = e0 + k * KB;
             if (e < n) {
-                const c64 a = ld64(vi, e);
+                const cplx<T> a = vi[e];
                 acc[k].x -= c.x * a.x - c.y * a.y;
                 acc[k].y -= c.x * a.y + c.y * a.x;
             }
         }
     }
-    double nrm = 0;
+    T nrm = 0;
 #pragma unroll
     for (int k = 0; k < KE; ++k) {
         const long long e = e0 + k * KB;
         if (e < n) {
-            const cplx<T> o = cplx<T>{(T)acc[k].x, (T)acc[k].y};
-            w[e] = o;
-            nrm += (double)o.x * o.x + (double)o.y * o.y;
+            w[e] = acc[k];
+            nrm += acc[k].x * acc[k].x + acc[k].y * acc[k].y;
         }
     }
-    nrm = warp_sum(nrm);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = nrm;
+    const double dn = warp_sum((double)nrm);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = dn;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0;
         for (int q = 0; q < KB / 32; ++q) t += ws[q];
         normpart[(long long)r * nblk + blockIdx.x] = t;
     }
+}
+
+// Selective reorthogonalisation test (Daniel-Gragg-Kaufman-Stewart): a second
+// Gram-Schmidt pass is needed when the projection cancelled most of w,
+// ||w'|| < ||w|| / sqrt(2).  One thread per listed RHS.
+__global__ void k_reorth_check(const double* __restrict__ normpart, int nblk, const c64* __restrict__ coef, int j,
+                               const int* __restrict__ list, int nr, int mp1, int* __restrict__ gate) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nr) return;
+    const int r = list[s];
+    double t = 0;
+    for (int b = 0; b < nblk; ++b) t += normpart[(long long)r * nblk + b];
+    const double before = coef[(long long)r * (mp1 + 1) + j + 1].x;
+    gate[r] = (t < 0.5 * before) ? 1 : 0;
 }
 
 // One thread per listed RHS: finish step j (Givens rotations, residual estimate).
@@ -226,14 +267,14 @@ __global__ void k_scale(cplx<T>* __restrict__ V, long long rstride, long long vs
                         const int* __restrict__ list, const double* __restrict__ inv, long long n) {
     const int r = list[blockIdx.y];
     cplx<T>* w = V + r * rstride + (long long)(j + 1) * vstride;
-    const double s = inv[r];
+    const T s = (T)inv[r];
     const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
 #pragma unroll
     for (int k = 0; k < KE; ++k) {
         const long long e = e0 + k * KB;
         if (e < n) {
             const cplx<T> v = w[e];
-            w[e] = cplx<T>{(T)(v.x * s), (T)(v.y * s)};
+            w[e] = cplx<T>{v.x * s, v.y * s};
         }
     }
 }
@@ -262,15 +303,18 @@ __global__ void k_lsq(const c64* __restrict__ H, const c64* __restrict__ g, c64*
     }
 }
 
-// x += sum_{i<k} y_i V_i  (x in FP64)
+// x += sum_{i<k} y_i V_i  (x in FP64; the combination is formed in T)
 template <typename T>
 __global__ void k_xupdate(c64* __restrict__ x, long long xstride, const cplx<T>* __restrict__ V, long long rstride,
                           long long vstride, const c64* __restrict__ y, const int* __restrict__ kcount,
                           const int* __restrict__ list, int m, long long n) {
-    __shared__ c64 ys[256];
+    __shared__ cplx<T> ys[MAX_RESTART];
     const int r = list[blockIdx.y];
     const int k = kcount[r];
-    for (int i = threadIdx.x; i < k; i += KB) ys[i] = y[(long long)r * m + i];
+    for (int i = threadIdx.x; i < k; i += KB) {
+        const c64 v = y[(long long)r * m + i];
+        ys[i] = cplx<T>{(T)v.x, (T)v.y};
+    }
     __syncthreads();
     const cplx<T>* Vr = V + r * rstride;
     c64* xr = x + r * xstride;
@@ -279,13 +323,14 @@ __global__ void k_xupdate(c64* __restrict__ x, long long xstride, const cplx<T>*
     for (int q = 0; q < KE; ++q) {
         const long long e = e0 + q * KB;
         if (e >= n) continue;
-        c64 acc = xr[e];
+        cplx<T> acc = {(T)0, (T)0};
         for (int i = 0; i < k; ++i) {
-            const c64 a = ld64(Vr + (long long)i * vstride, e);
+            const cplx<T> a = Vr[(long long)i * vstride + e];
             acc.x += ys[i].x * a.x - ys[i].y * a.y;
             acc.y += ys[i].x * a.y + ys[i].y * a.x;
         }
-        xr[e] = acc;
+        const c64 xv = xr[e];
+        xr[e] = c64{xv.x + (double)acc.x, xv.y + (double)acc.y};
     }
 }
 
@@ -376,8 +421,9 @@ int Solver::alloc(Operator& op, int R_, int m_, int prec_) {
     VIE_TRY(dev_alloc(op, (void**)&sn, sizeof(c64) * R * m));
     VIE_TRY(dev_alloc(op, (void**)&g, sizeof(c64) * R * (m + 1)));
     VIE_TRY(dev_alloc(op, (void**)&y, sizeof(c64) * R * m));
-    VIE_TRY(dev_alloc(op, (void**)&coef, sizeof(c64) * R * (m + 1)));
-    VIE_TRY(dev_alloc(op, (void**)&partial, sizeof(c64) * (size_t)R * (m + 1) * nblk));
+    VIE_TRY(dev_alloc(op, (void**)&coef, sizeof(c64) * R * (m + 2)));
+    VIE_TRY(dev_alloc(op, (void**)&partial, sizeof(c64) * (size_t)R * (m + 2) * nblk));
+    VIE_TRY(dev_alloc(op, (void**)&reorth, sizeof(int) * R));
     VIE_TRY(dev_alloc(op, (void**)&normpart, sizeof(double) * (size_t)R * nblk));
     VIE_TRY(dev_alloc(op, (void**)&inv, sizeof(double) * R));
     VIE_TRY(dev_alloc(op, (void**)&target, sizeof(double) * R));
@@ -400,8 +446,9 @@ void Solver::release(Operator& op) {
         dev_free(op, sn, sizeof(c64) * R * m);
         dev_free(op, g, sizeof(c64) * R * (m + 1));
         dev_free(op, y, sizeof(c64) * R * m);
-        dev_free(op, coef, sizeof(c64) * R * (m + 1));
-        dev_free(op, partial, sizeof(c64) * (size_t)R * (m + 1) * nblk);
+        dev_free(op, coef, sizeof(c64) * R * (m + 2));
+        dev_free(op, partial, sizeof(c64) * (size_t)R * (m + 2) * nblk);
+        dev_free(op, reorth, sizeof(int) * R);
         dev_free(op, normpart, sizeof(double) * (size_t)R * nblk);
         dev_free(op, inv, sizeof(double) * R);
         dev_free(op, target, sizeof(double) * R);
@@ -414,7 +461,7 @@ void Solver::release(Operator& op) {
     V = nullptr;
     H = sn = g = y = coef = partial = nullptr;
     cs = normpart = inv = target = bnorm = rnorm = nullptr;
-    kcount = flag = nullptr;
+    kcount = flag = reorth = nullptr;
     R = 0;
 }
 
@@ -521,17 +568,24 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
             else out.matvecs32 += ni;
             dim3 gi(nblk, ni);
             for (int pass = 0; pass < 2; ++pass) {
+                const int* gate = pass ? S.reorth : nullptr;
                 tmr_begin(TMR_DOTS, st);
-                k_dots<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.partial, mp1, n, nblk);
+                k_dots<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.partial, mp1 + 1, n, nblk, gate);
                 tmr_end(TMR_DOTS, st, (double)ni * (j + 2) * n * ET);
                 LAUNCH_CHECK();
                 tmr_begin(TMR_REDUCE, st);
-                k_reduce_dots<<<dim3(j + 1, ni), KB, 0, st>>>(S.partial, S.coef, S.H, j, op.d_list, mp1, nblk, pass);
+                k_reduce_dots<<<dim3(j + 2, ni), KB, 0, st>>>(S.partial, S.coef, S.H, j, op.d_list, mp1, nblk, pass,
+                                                               gate);
                 tmr_end(TMR_REDUCE, st, (double)ni * (j + 1) * nblk * 16.0);
                 LAUNCH_CHECK();
                 tmr_begin(TMR_UPDATE, st);
-                k_update<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.coef, S.normpart, mp1, n, nblk);
+                k_update<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.coef, S.normpart, mp1, n, nblk, gate);
                 tmr_end(TMR_UPDATE, st, (double)ni * (j + 3) * n * ET);
+                if (pass == 0) {
+                    k_reorth_check<<<ceil_div(ni, 64), 64, 0, st>>>(S.normpart, nblk, S.coef, j, op.d_list, ni, mp1,
+                                                                   S.reorth);
+                    LAUNCH_CHECK();
+                }
                 LAUNCH_CHECK();
             }
             tmr_begin(TMR_FINISH, st);

@@ -21,8 +21,8 @@ struct Solver {
     c64* sn = nullptr;         // [R][m] Givens sines
     c64* g = nullptr;          // [R][m+1] rotated residual vector
     c64* y = nullptr;          // [R][m] least-squares solution
-    c64* coef = nullptr;       // [R][m+1] current projection coefficients
-    c64* partial = nullptr;    // [R][m+1][nblk] block partial dot products
+    c64* coef = nullptr;       // [R][m+2] projection coefficients (+ ||w||^2 before projection)
+    c64* partial = nullptr;    // [R][m+2][nblk] block partial dot products
     double* normpart = nullptr;  // [R][nblk]
     double* inv = nullptr;     // [R] 1 / h_{j+1,j}
     double* target = nullptr;  // [R] inner-cycle stopping threshold
@@ -30,6 +30,7 @@ struct Solver {
     double* rnorm = nullptr;   // [R]
     int* kcount = nullptr;     // [R] steps taken in the current cycle
     int* flag = nullptr;       // [R] 1 = stop the current cycle
+    int* reorth = nullptr;     // [R] 1 = second Gram-Schmidt pass needed this step
 
     int alloc(Operator& op, int R, int m, int prec);
     void release(Operator& op);

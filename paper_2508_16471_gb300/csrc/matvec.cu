@@ -85,6 +85,24 @@ static int upload_twiddles(Operator& op, AxisFFT& a) {
     VIE_TRY(dev_alloc(op, (void**)&a.tw32, sizeof(c32) * n));
     VIE_CUDA(cudaMemcpy(a.tw64, t.data(), sizeof(c64) * n, cudaMemcpyHostToDevice));
     VIE_CUDA(cudaMemcpy(a.tw32, tf.data(), sizeof(c32) * n, cudaMemcpyHostToDevice));
+    if (fast_length(a.plan.L)) {
+        // four-step twiddles w_L^{k1 n2} in two orders: TA[k1][n2] then TB[n2][k1]
+        const int L = a.plan.L;
+        int R1 = 0, R2 = 0;
+        fast_factors(L, &R1, &R2);
+        std::vector<float> r(4 * L);
+        for (int k1 = 0; k1 < R1; ++k1)
+            for (int n2 = 0; n2 < R2; ++n2) {
+                const double ang = -2.0 * M_PI * (double)((k1 * n2) % L) / (double)L;
+                const float c = (float)std::cos(ang), sn = (float)std::sin(ang);
+                r[2 * (k1 * R2 + n2)] = c;
+                r[2 * (k1 * R2 + n2) + 1] = sn;
+                r[2 * (L + n2 * R1 + k1)] = c;
+                r[2 * (L + n2 * R1 + k1) + 1] = sn;
+            }
+        VIE_TRY(dev_alloc(op, (void**)&a.roots32, sizeof(c32) * 2 * L));
+        VIE_CUDA(cudaMemcpy(a.roots32, r.data(), sizeof(c32) * 2 * L, cudaMemcpyHostToDevice));
+    }
     return VIE_OK;
 }
 
@@ -679,8 +697,8 @@ int op_reserve(Operator& op, int prec, int nrhs) {
     const size_t esz = prec ? sizeof(c64) : sizeof(c32);
     const long long perA = 3LL * op.n[0] * op.n[1] * op.P[2];
     const long long perB = 3LL * op.n[0] * op.P[1] * op.P[2];
-    // cap the workspace at ~8 GB per precision; larger batches run in chunks
-    const double limit = 8e9;
+    // cap the workspace at ~24 GB per precision; larger batches run in chunks
+    const double limit = 24e9;
     int cap = std::max(1, std::min(nrhs, (int)(limit / ((perA + perB) * (double)esz))));
     if (W.cap >= cap) return VIE_OK;
     if (W.A) dev_free(op, W.A, esz * perA * W.cap);
@@ -738,8 +756,19 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
     for (int s0 = 0; s0 < nr; s0 += W.cap) {
         const int ns = std::min(W.cap, nr - s0);
         const int* list = d_list + s0;
+        const bool fz = sizeof(T) == 4 && op.fft_path == 0 && fast_length(P2);
+        const bool fy = sizeof(T) == 4 && op.fft_path == 0 && fast_length(P1);
+        const bool fx = sizeof(T) == 4 && op.fft_path == 0 && fast_length(P0);
         // pass 1
-        {
+        if (fz) {
+            const long long nlines = (long long)ns * 3 * n0 * n1;
+            tmr_begin(TMR_ZFWD, op.stream);
+            VIE_TRY(fast_zfwd((const c32*)w, wr, list, op.idx_map, (c32*)A, n0, n1, n2, op.Nb, nlines, P2,
+                              op.ax[2].roots32, op.stream));
+            tmr_end(TMR_ZFWD, op.stream, ns * (vec + lineA) + 4.0 * op.N);
+            count_launch();
+            VIE_CUDA(cudaGetLastError());
+        } else {
             const FFTPlan& p = op.ax[2].plan;
             const int NL = lines_per_cta<T>(p.L);
             const long long nlines = (long long)ns * 3 * n0 * n1;
@@ -751,10 +780,26 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             VIE_CUDA(cudaGetLastError());
         }
         // pass 2
-        VIE_TRY((launch_axis<T, false>(A, B, (long long)ns * 3 * n0, n1, P1, P2, op.ax[1].plan, twp<T>(op.ax[1]),
-                                       op.stream, TMR_YFWD)));
+        if (fy) {
+            tmr_begin(TMR_YFWD, op.stream);
+            VIE_TRY(fast_axis((const c32*)A, (c32*)B, (long long)ns * 3 * n0, n1, P1, P2, P1, op.ax[1].roots32, false,
+                              op.stream));
+            tmr_end(TMR_YFWD, op.stream, (double)ns * (lineA + lineB));
+            count_launch();
+            VIE_CUDA(cudaGetLastError());
+        } else {
+            VIE_TRY((launch_axis<T, false>(A, B, (long long)ns * 3 * n0, n1, P1, P2, op.ax[1].plan, twp<T>(op.ax[1]),
+                                           op.stream, TMR_YFWD)));
+        }
         // pass 3
-        {
+        if (fx) {
+            tmr_begin(TMR_XFUSED, op.stream);
+            VIE_TRY(fast_xfused((c32*)B, n0, (long long)P1 * P2, P0, P1, P2, (const c32*)kh, op.H, op.ax[0].roots32, ns,
+                                op.stream));
+            tmr_end(TMR_XFUSED, op.stream, 2.0 * ns * lineB + 6.0 * op.H[0] * op.H[1] * op.H[2] * E);
+            count_launch();
+            VIE_CUDA(cudaGetLastError());
+        } else {
             const FFTPlan& p = op.ax[0].plan;
             const long long inner = (long long)P1 * P2;
             const int TW = xfused_tile<T>(p.L, inner);
@@ -767,10 +812,27 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             VIE_CUDA(cudaGetLastError());
         }
         // pass 4
-        VIE_TRY((launch_axis<T, true>(B, A, (long long)ns * 3 * n0, P1, n1, P2, op.ax[1].plan, twp<T>(op.ax[1]),
-                                      op.stream, TMR_YINV)));
+        if (fy) {
+            tmr_begin(TMR_YINV, op.stream);
+            VIE_TRY(fast_axis((const c32*)B, (c32*)A, (long long)ns * 3 * n0, P1, n1, P2, P1, op.ax[1].roots32, true,
+                              op.stream));
+            tmr_end(TMR_YINV, op.stream, (double)ns * (lineA + lineB));
+            count_launch();
+            VIE_CUDA(cudaGetLastError());
+        } else {
+            VIE_TRY((launch_axis<T, true>(B, A, (long long)ns * 3 * n0, P1, n1, P2, op.ax[1].plan, twp<T>(op.ax[1]),
+                                          op.stream, TMR_YINV)));
+        }
         // pass 5
-        {
+        if (fz) {
+            const long long nlines = (long long)ns * 3 * n0 * n1;
+            tmr_begin(TMR_ZINV, op.stream);
+            VIE_TRY(fast_zinv((const c32*)A, (const c32*)w, wr, (c32*)y, yr, list, op.idx_map, (const float*)chi, n0, n1,
+                              n2, op.Nb, nlines, P2, op.ax[2].roots32, op.stream));
+            tmr_end(TMR_ZINV, op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
+            count_launch();
+            VIE_CUDA(cudaGetLastError());
+        } else {
             const FFTPlan& p = op.ax[2].plan;
             const int NL = lines_per_cta<T>(p.L);
             const long long nlines = (long long)ns * 3 * n0 * n1;
@@ -795,8 +857,10 @@ void op_free(Operator& op) {
     for (int a = 0; a < 3; ++a) {
         cudaFree(op.ax[a].tw32);
         cudaFree(op.ax[a].tw64);
+        cudaFree(op.ax[a].roots32);
         op.ax[a].tw32 = nullptr;
         op.ax[a].tw64 = nullptr;
+        op.ax[a].roots32 = nullptr;
     }
     cudaFree(op.khat32);
     cudaFree(op.khat64);

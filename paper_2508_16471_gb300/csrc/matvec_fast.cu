@@ -1,0 +1,449 @@
+// FP32 fast path of the operator passes for power-of-two padded lengths
+// (16 .. 512): register-resident four-step FFTs (fft4.cuh) with a single
+// shared-memory exchange per transform, loads and stores straight between
+// registers and global memory.  Same data layouts and semantics as the
+// generic passes in matvec.cu, which remain the path for other lengths and
+// for FP64.
+//
+// Twiddles w_L^{k1 n2} come from two tables of L entries staged in shared
+// memory, TA[k1][n2] for the forward step (threads indexed by n2) and
+// TB[n2][k1] for the inverse step (threads indexed by k1), so that lanes of a
+// warp read consecutive words.
+#include "fft4.cuh"
+#include "vie_internal.cuh"
+
+namespace vie {
+
+bool fast_length(int L) { return L == 16 || L == 32 || L == 64 || L == 128 || L == 256 || L == 512; }
+
+void fast_factors(int L, int* R1, int* R2) {
+    switch (L) {
+        case 16: *R1 = Fac<16>::R1; *R2 = Fac<16>::R2; break;
+        case 32: *R1 = Fac<32>::R1; *R2 = Fac<32>::R2; break;
+        case 64: *R1 = Fac<64>::R1; *R2 = Fac<64>::R2; break;
+        case 128: *R1 = Fac<128>::R1; *R2 = Fac<128>::R2; break;
+        case 256: *R1 = Fac<256>::R1; *R2 = Fac<256>::R2; break;
+        default: *R1 = Fac<512>::R1; *R2 = Fac<512>::R2; break;
+    }
+}
+
+namespace {
+
+constexpr int AX_TW = 16;  // columns per CTA, strided-axis passes
+constexpr int XF_TW = 8;   // columns per CTA, fused x pass (3 components)
+
+__device__ __forceinline__ c32 z32() { return c32{0.f, 0.f}; }
+
+__device__ __forceinline__ void stage_table(c32* dst, const c32* __restrict__ g, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = g[i];
+}
+
+template <bool INV> __device__ __forceinline__ c32 tw(const c32* t, int i) {
+    c32 w = t[i];
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+// ---- strided axis: in [outer][n_in][inner] -> out [outer][n_out][inner] ------
+template <int L, bool INV>
+__global__ void __launch_bounds__(Fac<L>::R2 * AX_TW) k_axis_r(const c32* __restrict__ in, c32* __restrict__ out,
+                                                               long long inner, int n_in, int n_out,
+                                                               const c32* __restrict__ tw4) {
+    constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2, TW = AX_TW, NT = R2 * TW;
+    constexpr int SR = R2 * TW;  // row stride of the R1 x R2 x TW exchange
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c32* T = reinterpret_cast<c32*>(smraw);  // TA (forward) or TB (inverse)
+    c32* S = T + L;
+    stage_table(T, tw4 + (INV ? L : 0), L);
+    const long long ntile = (inner + TW - 1) / TW;
+    const long long o = blockIdx.x / ntile;
+    const long long i0 = (blockIdx.x - o * ntile) * TW;
+    const int t = threadIdx.x % TW, n2 = threadIdx.x / TW;
+    __syncthreads();
+    if (!INV) {
+        c32 a[R1];
+        const bool ok = i0 + t < inner;
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) {
+            const int p = n1 * R2 + n2;
+            a[n1] = (ok && p < n_in) ? in[(o * n_in + p) * inner + i0 + t] : z32();
+        }
+        dftp2<float, R1, false>(a);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) a[k1] = a[k1] * tw<false>(T, k1 * R2 + n2);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) S[k1 * SR + n2 * TW + t] = a[k1];
+        __syncthreads();
+        for (int it = threadIdx.x; it < R1 * TW; it += NT) {
+            const int k1 = it / TW, tt = it % TW;
+            c32 b[R2];
+#pragma unroll
+            for (int q = 0; q < R2; ++q) b[q] = S[k1 * SR + q * TW + tt];
+            dftp2<float, R2, false>(b);
+            if (i0 + tt < inner) {
+#pragma unroll
+                for (int k2 = 0; k2 < R2; ++k2) {
+                    const int p = k1 + R1 * k2;
+                    if (p < n_out) out[(o * n_out + p) * inner + i0 + tt] = b[k2];
+                }
+            }
+        }
+    } else {
+        for (int it = threadIdx.x; it < R1 * TW; it += NT) {
+            const int k1 = it / TW, tt = it % TW;
+            const bool ok = i0 + tt < inner;
+            c32 b[R2];
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) {
+                const int p = k1 + R1 * k2;
+                b[k2] = (ok && p < n_in) ? in[(o * n_in + p) * inner + i0 + tt] : z32();
+            }
+            dftp2<float, R2, true>(b);
+#pragma unroll
+            for (int q = 0; q < R2; ++q) S[k1 * SR + q * TW + tt] = b[q] * tw<true>(T, q * R1 + k1);
+        }
+        __syncthreads();
+        c32 a[R1];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) a[k1] = S[k1 * SR + n2 * TW + t];
+        dftp2<float, R1, true>(a);
+        if (i0 + t < inner) {
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) {
+                const int p = n1 * R2 + n2;
+                if (p < n_out) out[(o * n_out + p) * inner + i0 + t] = a[n1];
+            }
+        }
+    }
+}
+
+// ---- fused x pass: forward FFT x, 3x3 spectral multiply, inverse FFT x ------
+// One CTA per tile of XF_TW (y, z)-frequency columns; it stages the kernel
+// octant rows of its columns in shared memory once (x-folded, y/z signs
+// applied) and loops over all RHS slots.
+template <int L> struct XF {
+    static constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2, TW = XF_TW, NT = R2 * TW;
+    static constexpr int SR = R2 * TW + 8;  // padded exchange row (conflict-free half-warps)
+    static constexpr int SC = R1 * SR;      // one component
+    static constexpr int HX = L / 2 + 1;    // folded x rows of the kernel tile
+    static constexpr size_t smem = sizeof(c32) * (2 * L + 6 * (size_t)HX * TW + 3 * (size_t)SC);
+};
+
+template <int L>
+__global__ void __launch_bounds__(XF<L>::NT) k_xfused_r(c32* __restrict__ B, int n0, long long inner, int P1,
+                                                       int P2, const c32* __restrict__ khat, int H0, int H1, int H2,
+                                                       const c32* __restrict__ tw4, int nslots) {
+    constexpr int R1 = XF<L>::R1, R2 = XF<L>::R2, TW = XF<L>::TW, NT = XF<L>::NT;
+    constexpr int SR = XF<L>::SR, SC = XF<L>::SC, HX = XF<L>::HX;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c32* TA = reinterpret_cast<c32*>(smraw);
+    c32* TB = TA + L;
+    c32* Kt = TB + L;          // [6][HX][TW]
+    c32* S = Kt + 6 * HX * TW;  // [3][R1][SR]
+    stage_table(TA, tw4, 2 * L);
+    const long long i0 = (long long)blockIdx.x * TW;
+    const long long HH = (long long)H0 * H1 * H2;
+    // kernel tile: rows fx = 0..L/2 of the 6 components for this CTA's columns
+    for (int e = threadIdx.x; e < 6 * HX * TW; e += NT) {
+        const int tt = e % TW;
+        const int fx = (e / TW) % HX;
+        const int q = e / (TW * HX);
+        const long long ii = i0 + tt;
+        c32 v = z32();
+        if (ii < inner) {
+            const int ky = (int)(ii / P2), kz = (int)(ii - (ii / P2) * P2);
+            const bool fly = 2 * ky > P1, flz = 2 * kz > P2;
+            const int fy = fly ? P1 - ky : ky, fz = flz ? P2 - kz : kz;
+            v = khat[q * HH + ((long long)fx * H1 + fy) * H2 + fz];
+            // y/z parity of the off-diagonal components: xy odd in y, xz odd in z, yz odd in y and z
+            const bool neg = (q == 1 && fly) || (q == 2 && flz) || (q == 4 && (fly ^ flz));
+            if (neg) v = c32{-v.x, -v.y};
+        }
+        Kt[e] = v;
+    }
+    const int t = threadIdx.x % TW, n2 = threadIdx.x / TW;
+    const bool okt = i0 + t < inner;
+    __syncthreads();
+    for (int slot = 0; slot < nslots; ++slot) {
+        c32* base = B + (long long)slot * 3 * n0 * inner;
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            c32 a[R1];
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) {
+                const int p = n1 * R2 + n2;
+                a[n1] = (okt && p < n0) ? base[((long long)c * n0 + p) * inner + i0 + t] : z32();
+            }
+            dftp2<float, R1, false>(a);
+#pragma unroll
+            for (int k1 = 1; k1 < R1; ++k1) a[k1] = a[k1] * tw<false>(TA, k1 * R2 + n2);
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) S[c * SC + k1 * SR + n2 * TW + t] = a[k1];
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < R1 * TW; it += NT) {
+            const int k1 = it / TW, tt = it % TW;
+            c32 bx[R2], by[R2], bz[R2];
+#pragma unroll
+            for (int q = 0; q < R2; ++q) {
+                bx[q] = S[0 * SC + k1 * SR + q * TW + tt];
+                by[q] = S[1 * SC + k1 * SR + q * TW + tt];
+                bz[q] = S[2 * SC + k1 * SR + q * TW + tt];
+            }
+            dftp2<float, R2, false>(bx);
+            dftp2<float, R2, false>(by);
+            dftp2<float, R2, false>(bz);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) {
+                const int kx = k1 + R1 * k2;
+                const bool flx = 2 * kx > L;
+                const int fx = flx ? L - kx : kx;
+                const c32* kt = Kt + fx * TW + tt;
+                c32 kxx = kt[0], kxy = kt[HX * TW], kxz = kt[2 * HX * TW];
+                const c32 kyy = kt[3 * HX * TW], kyz = kt[4 * HX * TW], kzz = kt[5 * HX * TW];
+                if (flx) {
+                    kxy = c32{-kxy.x, -kxy.y};
+                    kxz = c32{-kxz.x, -kxz.y};
+                }
+                const c32 a = bx[k2], b = by[k2], cc = bz[k2];
+                bx[k2] = kxx * a + kxy * b + kxz * cc;
+                by[k2] = kxy * a + kyy * b + kyz * cc;
+                bz[k2] = kxz * a + kyz * b + kzz * cc;
+            }
+            dftp2<float, R2, true>(bx);
+            dftp2<float, R2, true>(by);
+            dftp2<float, R2, true>(bz);
+#pragma unroll
+            for (int q = 0; q < R2; ++q) {
+                const c32 w = tw<true>(TB, q * R1 + k1);
+                S[0 * SC + k1 * SR + q * TW + tt] = bx[q] * w;
+                S[1 * SC + k1 * SR + q * TW + tt] = by[q] * w;
+                S[2 * SC + k1 * SR + q * TW + tt] = bz[q] * w;
+            }
+        }
+        __syncthreads();
+        if (okt) {
+#pragma unroll 1
+            for (int c = 0; c < 3; ++c) {
+                c32 a[R1];
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1) a[k1] = S[c * SC + k1 * SR + n2 * TW + t];
+                dftp2<float, R1, true>(a);
+#pragma unroll
+                for (int n1 = 0; n1 < R1; ++n1) {
+                    const int p = n1 * R2 + n2;
+                    if (p < n0) base[((long long)c * n0 + p) * inner + i0 + t] = a[n1];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- z passes on contiguous lines (gather from / scatter to the body list) ---
+constexpr int Z_THREADS = 256;
+
+template <int L>
+__global__ void __launch_bounds__(Z_THREADS) k_zfwd_r(const c32* __restrict__ w, long long w_rstride,
+                                                      const int* __restrict__ list, const int* __restrict__ idx_map,
+                                                      c32* __restrict__ A, int n0, int n1, int n2, long long Nb,
+                                                      long long nlines, const c32* __restrict__ tw4) {
+    constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2;
+    constexpr int NL = Z_THREADS / R2;
+    constexpr int RS = R2 + 1;  // padded row
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c32* TA = reinterpret_cast<c32*>(smraw);
+    c32* S = TA + L;
+    stage_table(TA, tw4, L);
+    const long long line0 = (long long)blockIdx.x * NL;
+    const long long plane = (long long)n0 * n1;
+    const int q2 = threadIdx.x % R2, l = threadIdx.x / R2;
+    const long long line = line0 + l;
+    c32 a[R1];
+    if (line < nlines) {
+        const long long sc = line / plane;
+        const long long xy = line - sc * plane;
+        const int slot = (int)(sc / 3), c = (int)(sc - (sc / 3) * 3);
+        const c32* wr = w + (long long)list[slot] * w_rstride + c * Nb;
+        const int* im = idx_map + xy * n2;
+#pragma unroll
+        for (int n1i = 0; n1i < R1; ++n1i) {
+            const int z = n1i * R2 + q2;
+            c32 v = z32();
+            if (z < n2) {
+                const int vi = im[z];
+                if (vi >= 0) v = wr[vi];
+            }
+            a[n1i] = v;
+        }
+    } else {
+#pragma unroll
+        for (int n1i = 0; n1i < R1; ++n1i) a[n1i] = z32();
+    }
+    __syncthreads();
+    dftp2<float, R1, false>(a);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) a[k1] = a[k1] * tw<false>(TA, k1 * R2 + q2);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) S[(l * R1 + k1) * RS + q2] = a[k1];
+    __syncthreads();
+    for (int it = threadIdx.x; it < NL * R1; it += Z_THREADS) {
+        const int k1 = it % R1, ll = it / R1;
+        c32 b[R2];
+#pragma unroll
+        for (int q = 0; q < R2; ++q) b[q] = S[(ll * R1 + k1) * RS + q];
+        dftp2<float, R2, false>(b);
+        const long long ln = line0 + ll;
+        if (ln < nlines) {
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) A[ln * L + k1 + R1 * k2] = b[k2];
+        }
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(Z_THREADS) k_zinv_r(const c32* __restrict__ A, const c32* __restrict__ w,
+                                                      long long w_rstride, c32* __restrict__ y, long long y_rstride,
+                                                      const int* __restrict__ list, const int* __restrict__ idx_map,
+                                                      const float* __restrict__ chi, int n0, int n1, int n2,
+                                                      long long Nb, long long nlines, const c32* __restrict__ tw4) {
+    constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2;
+    constexpr int NL = Z_THREADS / R2;
+    constexpr int RS = R2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c32* TB = reinterpret_cast<c32*>(smraw);
+    c32* S = TB + L;
+    stage_table(TB, tw4 + L, L);
+    const long long line0 = (long long)blockIdx.x * NL;
+    __syncthreads();
+    for (int it = threadIdx.x; it < NL * R1; it += Z_THREADS) {
+        const int k1 = it % R1, ll = it / R1;
+        const long long ln = line0 + ll;
+        c32 b[R2];
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) b[k2] = ln < nlines ? A[ln * L + k1 + R1 * k2] : z32();
+        dftp2<float, R2, true>(b);
+#pragma unroll
+        for (int q = 0; q < R2; ++q) S[(ll * R1 + k1) * RS + q] = b[q] * tw<true>(TB, q * R1 + k1);
+    }
+    __syncthreads();
+    const int q2 = threadIdx.x % R2, l = threadIdx.x / R2;
+    const long long line = line0 + l;
+    if (line >= nlines) return;
+    c32 a[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) a[k1] = S[(l * R1 + k1) * RS + q2];
+    dftp2<float, R1, true>(a);
+    const long long plane = (long long)n0 * n1;
+    const long long sc = line / plane;
+    const long long xy = line - sc * plane;
+    const int slot = (int)(sc / 3), c = (int)(sc - (sc / 3) * 3);
+    const long long rr = list[slot];
+    const c32* wr = w + rr * w_rstride + c * Nb;
+    c32* yr = y + rr * y_rstride + c * Nb;
+    const int* im = idx_map + xy * n2;
+#pragma unroll
+    for (int n1i = 0; n1i < R1; ++n1i) {
+        const int z = n1i * R2 + q2;
+        if (z < n2) {
+            const int vi = im[z];
+            if (vi >= 0) {
+                const c32 u = a[n1i];
+                const c32 wv = wr[vi];
+                const float ch = chi[vi];
+                yr[vi] = c32{wv.x - ch * u.x, wv.y - ch * u.y};
+            }
+        }
+    }
+}
+
+template <typename K> int set_smem(K k, size_t bytes) {
+    if (bytes > 48 * 1024) VIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return VIE_OK;
+}
+
+template <int L> int launch_axis_r(const c32* in, c32* out, long long outer, int n_in, int n_out, long long inner,
+                                   const c32* tw4, bool inv, cudaStream_t s) {
+    constexpr int NT = Fac<L>::R2 * AX_TW;
+    const size_t sm = sizeof(c32) * (L + (size_t)L * AX_TW);
+    const long long grid = outer * ((inner + AX_TW - 1) / AX_TW);
+    if (inv) {
+        VIE_TRY(set_smem(k_axis_r<L, true>, sm));
+        k_axis_r<L, true><<<(unsigned)grid, NT, sm, s>>>(in, out, inner, n_in, n_out, tw4);
+    } else {
+        VIE_TRY(set_smem(k_axis_r<L, false>, sm));
+        k_axis_r<L, false><<<(unsigned)grid, NT, sm, s>>>(in, out, inner, n_in, n_out, tw4);
+    }
+    return VIE_OK;
+}
+
+template <int L> int launch_xfused_r(c32* B, int n0, long long inner, int P1, int P2, const c32* kh, const int* H,
+                                     const c32* tw4, int ns, cudaStream_t s) {
+    const size_t sm = XF<L>::smem;
+    if (sm > 227 * 1024) return fail(VIE_EINVAL, "fused x pass does not fit in shared memory");
+    VIE_TRY(set_smem(k_xfused_r<L>, sm));
+    const long long grid = (inner + XF_TW - 1) / XF_TW;
+    k_xfused_r<L><<<(unsigned)grid, XF<L>::NT, sm, s>>>(B, n0, inner, P1, P2, kh, H[0], H[1], H[2], tw4, ns);
+    return VIE_OK;
+}
+
+template <int L> int launch_zfwd_r(const c32* w, long long wr, const int* list, const int* idx, c32* A, int n0,
+                                   int n1, int n2, long long Nb, long long nlines, const c32* tw4, cudaStream_t s) {
+    constexpr int NL = Z_THREADS / Fac<L>::R2;
+    const size_t sm = sizeof(c32) * (L + (size_t)NL * Fac<L>::R1 * (Fac<L>::R2 + 1));
+    VIE_TRY(set_smem(k_zfwd_r<L>, sm));
+    k_zfwd_r<L><<<(unsigned)((nlines + NL - 1) / NL), Z_THREADS, sm, s>>>(w, wr, list, idx, A, n0, n1, n2, Nb, nlines,
+                                                                         tw4);
+    return VIE_OK;
+}
+
+template <int L> int launch_zinv_r(const c32* A, const c32* w, long long wr, c32* y, long long yr, const int* list,
+                                   const int* idx, const float* chi, int n0, int n1, int n2, long long Nb,
+                                   long long nlines, const c32* tw4, cudaStream_t s) {
+    constexpr int NL = Z_THREADS / Fac<L>::R2;
+    const size_t sm = sizeof(c32) * (L + (size_t)NL * Fac<L>::R1 * (Fac<L>::R2 + 1));
+    VIE_TRY(set_smem(k_zinv_r<L>, sm));
+    k_zinv_r<L><<<(unsigned)((nlines + NL - 1) / NL), Z_THREADS, sm, s>>>(A, w, wr, y, yr, list, idx, chi, n0, n1,
+                                                                         n2, Nb, nlines, tw4);
+    return VIE_OK;
+}
+
+#define VIE_DISPATCH_L(Lv, CALL) \
+    switch (Lv) {                \
+        case 16: { constexpr int LL = 16; CALL; } break; \
+        case 32: { constexpr int LL = 32; CALL; } break; \
+        case 64: { constexpr int LL = 64; CALL; } break; \
+        case 128: { constexpr int LL = 128; CALL; } break; \
+        case 256: { constexpr int LL = 256; CALL; } break; \
+        case 512: { constexpr int LL = 512; CALL; } break; \
+        default: return fail(VIE_EINVAL, "fast FFT length not supported"); \
+    }
+
+}  // namespace
+
+int fast_axis(const c32* in, c32* out, long long outer, int n_in, int n_out, long long inner, int L,
+              const c32* tw4, bool inv, cudaStream_t s) {
+    VIE_DISPATCH_L(L, VIE_TRY(launch_axis_r<LL>(in, out, outer, n_in, n_out, inner, tw4, inv, s)));
+    return VIE_OK;
+}
+
+int fast_xfused(c32* B, int n0, long long inner, int L, int P1, int P2, const c32* kh, const int* H,
+                const c32* tw4, int ns, cudaStream_t s) {
+    VIE_DISPATCH_L(L, VIE_TRY(launch_xfused_r<LL>(B, n0, inner, P1, P2, kh, H, tw4, ns, s)));
+    return VIE_OK;
+}
+
+int fast_zfwd(const c32* w, long long wr, const int* list, const int* idx, c32* A, int n0, int n1, int n2,
+              long long Nb, long long nlines, int L, const c32* tw4, cudaStream_t s) {
+    VIE_DISPATCH_L(L, VIE_TRY(launch_zfwd_r<LL>(w, wr, list, idx, A, n0, n1, n2, Nb, nlines, tw4, s)));
+    return VIE_OK;
+}
+
+int fast_zinv(const c32* A, const c32* w, long long wr, c32* y, long long yr, const int* list, const int* idx,
+              const float* chi, int n0, int n1, int n2, long long Nb, long long nlines, int L, const c32* tw4,
+              cudaStream_t s) {
+    VIE_DISPATCH_L(L, VIE_TRY(launch_zinv_r<LL>(A, w, wr, y, yr, list, idx, chi, n0, n1, n2, Nb, nlines, tw4, s)));
+    return VIE_OK;
+}
+
+}  // namespace vie

@@ -13,6 +13,7 @@ struct AxisFFT {
     FFTPlan plan;
     c32* tw32 = nullptr;
     c64* tw64 = nullptr;
+    c32* roots32 = nullptr;  // fast path: w_P^{k1 n2} as [k1][n2] then [n2][k1] (2P entries)
 };
 
 // matvec workspace of one precision
@@ -41,6 +42,7 @@ struct Operator {
     int list_cap = 0;
     cudaStream_t stream = nullptr;
     double bytes = 0;        // device bytes held
+    int fft_path = 0;        // 0: register four-step where the length allows, 1: generic only
 };
 
 // device allocation helpers (track bytes)
@@ -61,6 +63,19 @@ int op_set_list(Operator& op, const int* host_list, int nr);  // uploads d_list
 int op_apply(Operator& op, int prec, const void* w, long long w_rstride, void* y, long long y_rstride,
              const int* d_list, int nr);
 void op_free(Operator& op);
+
+// FP32 fast passes (matvec_fast.cu), power-of-two lengths 16..512
+bool fast_length(int L);
+void fast_factors(int L, int* R1, int* R2);
+int fast_axis(const c32* in, c32* out, long long outer, int n_in, int n_out, long long inner, int L,
+              const c32* roots, bool inv, cudaStream_t s);
+int fast_xfused(c32* B, int n0, long long inner, int L, int P1, int P2, const c32* kh, const int* H,
+                const c32* roots, int ns, cudaStream_t s);
+int fast_zfwd(const c32* w, long long wr, const int* list, const int* idx, c32* A, int n0, int n1, int n2,
+              long long Nb, long long nlines, int L, const c32* roots, cudaStream_t s);
+int fast_zinv(const c32* A, const c32* w, long long wr, c32* y, long long yr, const int* list, const int* idx,
+              const float* chi, int n0, int n1, int n2, long long Nb, long long nlines, int L, const c32* roots,
+              cudaStream_t s);
 
 // standalone batched line FFT (vie_fft_lines)
 int fft_lines_device(const void* in, void* out, int L, int count, int inverse, int prec, cudaStream_t s);

@@ -23,7 +23,7 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_farfield", "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer",
            "vie_hom_map", "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines",
            "vie_get_info", "vie_kernel_launches", "vie_stream", "vie_destroy", "vie_last_error",
-           "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
+           "vie_set_fft_path", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
 
 
 class VieError(RuntimeError):
@@ -86,6 +86,7 @@ def load():
     L.vie_apply_device.argtypes = [P, P, P, C.c_int, C.c_int]
     L.vie_fft_lines.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int]
     L.vie_get_info.argtypes = [P, C.POINTER(_Info)]
+    L.vie_set_fft_path.argtypes = [P, C.c_int]
     L.vie_kernel_launches.restype = C.c_longlong
     L.vie_stream.argtypes = [P]
     L.vie_stream.restype = P
@@ -103,7 +104,8 @@ def load():
     L.vie_timer_count.restype = C.c_int
     for f in ["vie_setup", "vie_set_eps", "vie_set_eps_device", "vie_solve", "vie_farfield",
               "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer", "vie_hom_map",
-              "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines", "vie_get_info"]:
+              "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines", "vie_get_info",
+              "vie_set_fft_path"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -215,6 +217,9 @@ class Handle:
 
     def stream(self):
         return load().vie_stream(self._h)
+
+    def set_fft_path(self, path: int):
+        _check(load().vie_set_fft_path(self._h, int(path)))
 
     def set_eps(self, eps_r):
         eps = np.ascontiguousarray(eps_r, dtype=np.float64).reshape(self.n)

@@ -122,5 +122,23 @@ def test_apply_sphere64_sampled(vielib):
 
 def test_apply_bench_size_sampled(vielib):
     """The 128^3 random-body workload the bench times, 4 RHS, sampled voxels."""
-    wl = inputs.random_body_workload(20000, n_axis=128, h=1.0 / 40.0)
+    wl = inputs.random_body_workload(20000, n_axis=128, h=1.0 / 128.0)
     _sampled_parity(vielib, wl.grid.n, wl.grid.h, wl.eps, 4, 12, 6, (vielib.PREC_MIXED, vielib.PREC_FP64))
+
+
+@pytest.mark.parametrize("n", [(16, 16, 16), (32, 24, 20), (64, 64, 64)])
+def test_fast_and_generic_fft_paths_agree(vielib, n):
+    """Register four-step kernels (power-of-two padded axes) vs the generic
+    shared-memory Stockham kernels, FP32, on the same vectors."""
+    rng = np.random.default_rng(7)
+    eps = 1.0 + rng.uniform(0.3, 3.0, n) * (rng.uniform(size=n) < 0.5)
+    g = inputs.Grid(n, 0.03)
+    w = inputs.random_field(g, 3, 9, eps > 1.0)
+    with vielib.Handle(n, 0.03, eps, K0) as hd:
+        y_fast = hd.apply(w, precision=vielib.PREC_MIXED)
+        hd.set_fft_path(1)
+        y_gen = hd.apply(w, precision=vielib.PREC_MIXED)
+        y64 = hd.apply(w, precision=vielib.PREC_FP64)
+    s = np.abs(y64).max()
+    assert np.abs(y_fast - y64).max() <= TOL32 * s
+    assert np.abs(y_gen - y64).max() <= TOL32 * s
