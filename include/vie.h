@@ -230,6 +230,19 @@ int vie_fft_lines(const double* in, double* out, int L, int count, int inverse, 
 
 int vie_get_info(const vie_handle* hd, vie_info* info);
 
+/* Engine of the far-field contractions on (theta, phi) grids (vie_farfield):
+ * 0 (default) tensor cores (tcgen05, TF32 split three ways: hi*hi + hi*lo +
+ * lo*hi, FP32 accumulation in tensor memory), 1 CUDA-core FP32.
+ * Errors: VIE_EINVAL. */
+int vie_set_farfield_engine(vie_handle* hd, int engine);
+
+/* Kernel-level check of the far-field GEMM engines: C = A B for complex
+ * matrices (host, row-major, interleaved doubles): A [M][K], B [K][N],
+ * C [M][N]; computed on the device in complex64 by the engine named as in
+ * vie_set_farfield_engine.  Errors: VIE_EINVAL, VIE_ENOMEM, VIE_ETIMEOUT,
+ * VIE_EDEVICE. */
+int vie_cgemm(int M, int N, int K, const double* A, const double* B, double* C, int engine);
+
 /* FFT kernel family of the FP32 operator passes: 0 (default) uses the
  * register four-step kernels on every axis whose padded length is a power of
  * two in 16..512 and the generic shared-memory Stockham kernels elsewhere;

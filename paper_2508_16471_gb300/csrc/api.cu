@@ -473,6 +473,52 @@ int vie_get_info(const vie_handle* hd, vie_info* info) {
     return VIE_OK;
 }
 
+int vie_set_farfield_engine(vie_handle* hd, int engine) {
+    if (!hd || (engine != 0 && engine != 1)) return fail(VIE_EINVAL, "far-field engine must be 0 or 1");
+    hd->op.ff_engine = engine;
+    return VIE_OK;
+}
+
+int vie_cgemm(int M, int N, int K, const double* A, const double* B, double* C, int engine) {
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || (engine != 0 && engine != 1))
+        return fail(VIE_EINVAL, "bad arguments");
+    std::vector<c32> a((size_t)M * K), b((size_t)K * N), c((size_t)M * N);
+    for (size_t i = 0; i < a.size(); ++i) a[i] = c32{(float)A[2 * i], (float)A[2 * i + 1]};
+    for (size_t i = 0; i < b.size(); ++i) b[i] = c32{(float)B[2 * i], (float)B[2 * i + 1]};
+    c32 *da = nullptr, *db = nullptr, *dc = nullptr;
+    int* derr = nullptr;
+    int st = VIE_OK;
+    cudaError_t e = cudaMalloc(&da, sizeof(c32) * a.size());
+    if (e == cudaSuccess) e = cudaMalloc(&db, sizeof(c32) * b.size());
+    if (e == cudaSuccess) e = cudaMalloc(&dc, sizeof(c32) * c.size());
+    if (e == cudaSuccess) e = cudaMalloc(&derr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(da, a.data(), sizeof(c32) * a.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(db, b.data(), sizeof(c32) * b.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(derr, 0, sizeof(int));
+    if (e != cudaSuccess) st = cuda_fail(e, "gemm buffers");
+    if (st == VIE_OK)
+        st = engine == 0 ? tc_cgemm(M, N, K, 1, da, 0, K, 1, db, 0, N, 1, dc, 0, N, 1, derr, 0)
+                         : cc_cgemm(M, N, K, 1, da, 0, K, 1, db, 0, N, 1, dc, 0, N, 1, 0);
+    int herr = 0;
+    if (st == VIE_OK) {
+        e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(c.data(), dc, sizeof(c32) * c.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "gemm");
+    }
+    cudaFree(da);
+    cudaFree(db);
+    cudaFree(dc);
+    cudaFree(derr);
+    if (st != VIE_OK) return st;
+    if (herr) return fail(VIE_ETIMEOUT, "tensor-core GEMM: a bounded wait on the MMA barrier gave up");
+    for (size_t i = 0; i < c.size(); ++i) {
+        C[2 * i] = c[i].x;
+        C[2 * i + 1] = c[i].y;
+    }
+    return VIE_OK;
+}
+
 int vie_set_fft_path(vie_handle* hd, int path) {
     if (!hd || (path != 0 && path != 1)) return fail(VIE_EINVAL, "fft path must be 0 or 1");
     hd->op.fft_path = path;

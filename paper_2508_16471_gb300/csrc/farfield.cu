@@ -285,6 +285,17 @@ __global__ void k_cgemm(int M, int N, int K, const c32* __restrict__ A, long lon
         }
 }
 
+int cc_cgemm(int M, int N, int K, int batch, const c32* A, long long sAb, long long sAm, long long sAk, const c32* B,
+             long long sBb, long long sBk, long long sBn, c32* C, long long sCb, long long sCm, long long sCn,
+             cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return VIE_OK;
+    dim3 g(ceil_div(N, GT), ceil_div(M, GT), batch);
+    k_cgemm<<<g, 256, 0, s>>>(M, N, K, A, sAb, sAm, sAk, B, sBb, sBk, sBn, C, sCb, sCm, sCn);
+    count_launch();
+    VIE_CUDA(cudaGetLastError());
+    return VIE_OK;
+}
+
 // phase tables: ez[t][z] = e^{-i k0 cos(th_t) z}, ey[t][p][y] = e^{-i k0 sin th sin ph y},
 // ex[t][p][x] = e^{-i k0 sin th cos ph x}
 __global__ void k_phase_tables(const double* __restrict__ th, int nt, const double* __restrict__ ph, int np, int n0,
@@ -392,28 +403,44 @@ int farfield_grid(Operator& op, const c64* x, long long n3, int R, const double*
     k_scatter_full<<<dim3(std::max(1, std::min(2048, ceil_div(op.Nb, 256))), RC), 256, 0, s>>>(x, n3, op.vox, op.Nb,
                                                                                                N, W);
     k_phase_tables<<<1024, 256, 0, s>>>(dth, nt, dph, np, n0, n1, n2, op.h, cx, cy, cz, op.k0, ez, ey, ex);
+    int* derr = (int*)alloc(sizeof(int));
+    if (!derr) {
+        cleanup();
+        return fail(VIE_ENOMEM, "far-field workspace allocation failed");
+    }
+    cudaMemsetAsync(derr, 0, sizeof(int), s);
+    int st = VIE_OK;
     // stage A: M = RC*n0*n1, K = n2, N = nt
     {
         const int M = RC * n0 * n1;
-        dim3 g(ceil_div(nt, GT), ceil_div(M, GT), 1);
-        k_cgemm<<<g, 256, 0, s>>>(M, nt, n2, W, 0, n2, 1, ez, 0, 1, n2, A, 0, nt, 1);
+        st = op.ff_engine == 0 ? tc_cgemm(M, nt, n2, 1, W, 0, n2, 1, ez, 0, 1, n2, A, 0, nt, 1, derr, s)
+                               : cc_cgemm(M, nt, n2, 1, W, 0, n2, 1, ez, 0, 1, n2, A, 0, nt, 1, s);
     }
     // stage B: per t: M = RC*n0, K = n1, N = np; A(m,y) = A[(m*n1 + y)*nt + t]
-    {
+    if (st == VIE_OK) {
         const int M = RC * n0;
-        dim3 g(ceil_div(np, GT), ceil_div(M, GT), nt);
-        k_cgemm<<<g, 256, 0, s>>>(M, np, n1, A, 1, (long long)n1 * nt, nt, ey, (long long)np * n1, 1, n1, Bt,
-                                  (long long)M * np, np, 1);
+        st = op.ff_engine == 0
+                 ? tc_cgemm(M, np, n1, nt, A, 1, (long long)n1 * nt, nt, ey, (long long)np * n1, 1, n1, Bt,
+                            (long long)M * np, np, 1, derr, s)
+                 : cc_cgemm(M, np, n1, nt, A, 1, (long long)n1 * nt, nt, ey, (long long)np * n1, 1, n1, Bt,
+                            (long long)M * np, np, 1, s);
+    }
+    if (st != VIE_OK) {
+        cleanup();
+        return st;
     }
     k_ff_xreduce<<<ceil_div((long long)nt * np * RC, 256), 256, 0, s>>>(Bt, ex, nt, np, n0, RC, Sraw);
     k_grid_dirs<<<ceil_div(nt * np, 256), 256, 0, s>>>(dth, nt, dph, np, dirs);
     k_ff_project<<<ceil_div((long long)nt * np * R, 256), 256, 0, s>>>(Sraw, dirs, nt * np, R, ff_constant(op), basis,
                                                                        dout);
-    count_launch(7);
+    count_launch(5);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "far field (grid)");
+    if (herr) return fail(VIE_ETIMEOUT, "tensor-core GEMM: a bounded wait on the MMA barrier gave up");
     return VIE_OK;
 }
 

@@ -34,6 +34,25 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Warp sum of FP32 values with error-free TwoSum accumulation (Knuth): the
+// running (sum, correction) pair carries about twice the FP32 precision, so
+// the result equals an FP64 sum of the lane values up to O(eps32^2); it costs
+// a few FP32 operations per level instead of FP64 additions.
+__device__ __forceinline__ double warp_sum_comp(float v) {
+    float s = v, c = 0.f;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, o);
+        const float co = __shfl_xor_sync(0xffffffffu, c, o);
+        const float t = s + so;
+        const float bb = t - s;
+        const float err = (s - (t - bb)) + (so - bb);
+        c = c + co + err;
+        s = t;
+    }
+    return (double)s + (double)c;
+}
+__device__ __forceinline__ double warp_sum_comp(double v) { return warp_sum(v); }
+
 // partial[(r*mp1 + i)*nblk + b] = sum over block b of conj(V_i) . V_{j+1}.
 // Each thread forms its KE products in the basis precision T (the stored
 // vectors carry no more than that); every sum across threads, warps and
@@ -55,6 +74,7 @@ __global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long lo
         wv[k] = e < n ? w[e] : cplx<T>{(T)0, (T)0};
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll 2
     for (int i = 0; i <= j; ++i) {
         const cplx<T>* vi = Vr + (long long)i * vstride;
         T ar = 0, ai = 0;
@@ -67,8 +87,8 @@ __global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long lo
                 ai += a.x * wv[k].y - a.y * wv[k].x;
             }
         }
-        double dr = warp_sum((double)ar);
-        double di = warp_sum((double)ai);
+        const double dr = warp_sum_comp(ar);
+        const double di = warp_sum_comp(ai);
         if (lane == 0) {
             sre[wid][i] = dr;
             sim[wid][i] = di;
@@ -79,7 +99,7 @@ __global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long lo
         T ww = 0;
 #pragma unroll
         for (int k = 0; k < KE; ++k) ww += wv[k].x * wv[k].x + wv[k].y * wv[k].y;
-        const double dw = warp_sum((double)ww);
+        const double dw = warp_sum_comp(ww);
         if (lane == 0) {
             sre[wid][j + 1] = dw;
             sim[wid][j + 1] = 0.0;
@@ -159,6 +179,7 @@ __global__ void k_update(cplx<T>* __restrict__ V, long long rstride, long long v
         const long long e = e0 + k * KB;
         acc[k] = e < n ? w[e] : cplx<T>{(T)0, (T)0};
     }
+#pragma unroll 4
     for (int i = 0; i <= j; ++i) {
         const cplx<T>* vi = Vr + (long long)i * vstride;
         const cplx<T> c = cf[i];
@@ -181,7 +202,7 @@ __global__ void k_update(cplx<T>* __restrict__ V, long long rstride, long long v
             nrm += acc[k].x * acc[k].x + acc[k].y * acc[k].y;
         }
     }
-    const double dn = warp_sum((double)nrm);
+    const double dn = warp_sum_comp(nrm);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = dn;
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -166,19 +166,22 @@ __global__ void __launch_bounds__(XF<L>::NT) k_xfused_r(c32* __restrict__ B, int
     __syncthreads();
     for (int slot = 0; slot < nslots; ++slot) {
         c32* base = B + (long long)slot * 3 * n0 * inner;
-#pragma unroll 1
-        for (int c = 0; c < 3; ++c) {
-            c32 a[R1];
+        // issue the loads of all three components before any arithmetic
+        c32 a[3][R1];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int n1 = 0; n1 < R1; ++n1) {
                 const int p = n1 * R2 + n2;
-                a[n1] = (okt && p < n0) ? base[((long long)c * n0 + p) * inner + i0 + t] : z32();
+                a[c][n1] = (okt && p < n0) ? base[((long long)c * n0 + p) * inner + i0 + t] : z32();
             }
-            dftp2<float, R1, false>(a);
 #pragma unroll
-            for (int k1 = 1; k1 < R1; ++k1) a[k1] = a[k1] * tw<false>(TA, k1 * R2 + n2);
+        for (int c = 0; c < 3; ++c) {
+            dftp2<float, R1, false>(a[c]);
 #pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) S[c * SC + k1 * SR + n2 * TW + t] = a[k1];
+            for (int k1 = 1; k1 < R1; ++k1) a[c][k1] = a[c][k1] * tw<false>(TA, k1 * R2 + n2);
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) S[c * SC + k1 * SR + n2 * TW + t] = a[c][k1];
         }
         __syncthreads();
         for (int it = threadIdx.x; it < R1 * TW; it += NT) {

@@ -43,6 +43,7 @@ struct Operator {
     cudaStream_t stream = nullptr;
     double bytes = 0;        // device bytes held
     int fft_path = 0;        // 0: register four-step where the length allows, 1: generic only
+    int ff_engine = 0;       // far-field contractions: 0 tcgen05 3xTF32, 1 CUDA-core FP32
 };
 
 // device allocation helpers (track bytes)
@@ -76,6 +77,15 @@ int fast_zfwd(const c32* w, long long wr, const int* list, const int* idx, c32* 
 int fast_zinv(const c32* A, const c32* w, long long wr, c32* y, long long yr, const int* list, const int* idx,
               const float* chi, int n0, int n1, int n2, long long Nb, long long nlines, int L, const c32* roots,
               cudaStream_t s);
+
+// tensor-core batched complex GEMM (tc_gemm.cu): C = A B, complex64, strided
+int tc_cgemm(int M, int N, int K, int batch, const c32* A, long long sAb, long long sAm, long long sAk, const c32* B,
+             long long sBb, long long sBk, long long sBn, c32* C, long long sCb, long long sCm, long long sCn,
+             int* d_err, cudaStream_t s);
+// CUDA-core FP32 batched complex GEMM (farfield.cu), same contract
+int cc_cgemm(int M, int N, int K, int batch, const c32* A, long long sAb, long long sAm, long long sAk, const c32* B,
+             long long sBb, long long sBk, long long sBn, c32* C, long long sCb, long long sCm, long long sCn,
+             cudaStream_t s);
 
 // standalone batched line FFT (vie_fft_lines)
 int fft_lines_device(const void* in, void* out, int L, int count, int inverse, int prec, cudaStream_t s);

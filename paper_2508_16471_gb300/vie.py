@@ -23,7 +23,7 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_farfield", "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer",
            "vie_hom_map", "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines",
            "vie_get_info", "vie_kernel_launches", "vie_stream", "vie_destroy", "vie_last_error",
-           "vie_set_fft_path", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
+           "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
 
 
 class VieError(RuntimeError):
@@ -87,6 +87,8 @@ def load():
     L.vie_fft_lines.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int]
     L.vie_get_info.argtypes = [P, C.POINTER(_Info)]
     L.vie_set_fft_path.argtypes = [P, C.c_int]
+    L.vie_set_farfield_engine.argtypes = [P, C.c_int]
+    L.vie_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int]
     L.vie_kernel_launches.restype = C.c_longlong
     L.vie_stream.argtypes = [P]
     L.vie_stream.restype = P
@@ -105,7 +107,7 @@ def load():
     for f in ["vie_setup", "vie_set_eps", "vie_set_eps_device", "vie_solve", "vie_farfield",
               "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer", "vie_hom_map",
               "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines", "vie_get_info",
-              "vie_set_fft_path"]:
+              "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -221,6 +223,9 @@ class Handle:
     def set_fft_path(self, path: int):
         _check(load().vie_set_fft_path(self._h, int(path)))
 
+    def set_farfield_engine(self, engine: int):
+        _check(load().vie_set_farfield_engine(self._h, int(engine)))
+
     def set_eps(self, eps_r):
         eps = np.ascontiguousarray(eps_r, dtype=np.float64).reshape(self.n)
         _check(load().vie_set_eps(self._h, _dptr(eps)))
@@ -309,6 +314,19 @@ def hom_map(Ea, Eb, sigma=1.2):
     _check(load().vie_hom_map(_dptr(a.view(np.float64)), nA, _dptr(b.view(np.float64)), nB, float(sigma),
                               _dptr(g2), _dptr(vis), _dptr(p2)))
     return g2, vis, p2
+
+
+def cgemm(A, B, engine=0):
+    """C = A B (complex) on the device: engine 0 tensor cores (3xTF32), 1 CUDA cores."""
+    a = _c128(A)
+    b = _c128(B)
+    M, K = a.shape
+    K2, N = b.shape
+    assert K == K2
+    c = np.zeros((M, N), dtype=np.complex128)
+    _check(load().vie_cgemm(M, N, K, _dptr(a.view(np.float64)), _dptr(b.view(np.float64)),
+                            c.ctypes.data_as(C.POINTER(C.c_double)), int(engine)))
+    return c
 
 
 def fft_lines(x, inverse=False, precision=PREC_FP64):
