@@ -64,13 +64,18 @@ def build(verbose: bool = False, extra_flags=None) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
+    stamp = os.path.join(BUILD, "objects.txt")
+    listing = "\n".join(objs)
+    same_set = os.path.exists(stamp) and open(stamp).read() == listing
+    if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest or not same_set:
         cmd = [exe] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        with open(stamp, "w") as f:
+            f.write(listing)
     return LIB
 
 
