@@ -77,7 +77,7 @@ typedef struct vie_channel {
 
 typedef struct vie_solve_opts {
     double tol;        /* target ||b - A64 x||_2 / ||b||_2 per RHS (default 1e-6) */
-    int restart;       /* GMRES restart length m (default 30, 1..64)             */
+    int restart;       /* GMRES restart length m (default 30, 1..512)            */
     int max_iter;      /* cap on inner iterations per RHS (default 5000)         */
     int precision;     /* VIE_PREC_MIXED (default) or VIE_PREC_FP64              */
     double inner_tol;  /* mixed mode: relative reduction asked of each FP32 inner
@@ -102,7 +102,8 @@ typedef struct vie_solve_stats {
 
 typedef struct vie_info {
     int n[3];          /* grid                                                   */
-    int P[3];          /* padded FFT sizes (smallest 2,3,5,7-smooth >= 2n-1)     */
+    int P[3];          /* padded FFT sizes: next power of two >= 2n-1 if within
+                          15 % of the smallest 2,3,5,7-smooth size, else that   */
     long long n_body;  /* voxels with eps_r > 1 (unknowns / 3)                   */
     int n_rhs;         /* RHS held by the handle (last solve)                    */
     int device;        /* CUDA device ordinal                                    */

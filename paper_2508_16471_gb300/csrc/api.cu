@@ -176,7 +176,7 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
     else vie_default_opts(&o);
     if (!(o.tol > 0) || o.restart < 1 || o.restart > MAX_RESTART || o.max_iter < 1 ||
         (o.precision != VIE_PREC_MIXED && o.precision != VIE_PREC_FP64) || !(o.inner_tol > 0))
-        return fail(VIE_EINVAL, "invalid solve options (tol > 0, restart 1..64, max_iter >= 1, precision 0/1)");
+        return fail(VIE_EINVAL, "invalid solve options (tol > 0, restart 1..512, max_iter >= 1, precision 0/1)");
     for (int r = 0; r < n_rhs; ++r) {
         const double* k = ch[r].khat;
         const double* p = ch[r].pol;

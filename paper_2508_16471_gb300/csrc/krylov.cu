@@ -61,7 +61,11 @@ template <typename T>
 __global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long long vstride, int j,
                        const int* __restrict__ list, c64* __restrict__ partial, int mp1, long long n, int nblk,
                        const int* __restrict__ gate) {
-    __shared__ double sre[KB / 32][MAX_RESTART + 1], sim[KB / 32][MAX_RESTART + 1];
+    // per-warp partial sums of the j+2 inner products: [KB/32][j+2] (re, im)
+    extern __shared__ double dsm[];
+    const int J2 = j + 2;
+    double* sre = dsm;
+    double* sim = dsm + (KB / 32) * J2;
     const int r = list[blockIdx.y];
     if (gate && !gate[r]) return;
     const cplx<T>* Vr = V + r * rstride;
@@ -90,8 +94,8 @@ __global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long lo
         const double dr = warp_sum_comp(ar);
         const double di = warp_sum_comp(ai);
         if (lane == 0) {
-            sre[wid][i] = dr;
-            sim[wid][i] = di;
+            sre[wid * J2 + i] = dr;
+            sim[wid * J2 + i] = di;
         }
     }
     {
@@ -101,16 +105,16 @@ __global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long lo
         for (int k = 0; k < KE; ++k) ww += wv[k].x * wv[k].x + wv[k].y * wv[k].y;
         const double dw = warp_sum_comp(ww);
         if (lane == 0) {
-            sre[wid][j + 1] = dw;
-            sim[wid][j + 1] = 0.0;
+            sre[wid * J2 + j + 1] = dw;
+            sim[wid * J2 + j + 1] = 0.0;
         }
     }
     __syncthreads();
     for (int i = threadIdx.x; i <= j + 1; i += KB) {
         double ar = 0, ai = 0;
         for (int q = 0; q < KB / 32; ++q) {
-            ar += sre[q][i];
-            ai += sim[q][i];
+            ar += sre[q * J2 + i];
+            ai += sim[q * J2 + i];
         }
         partial[((long long)r * mp1 + i) * nblk + blockIdx.x] = c64{ar, ai};
     }
@@ -501,6 +505,12 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
     cudaStream_t st = op.stream;
     const int prec_in = sizeof(T) == 8 ? VIE_PREC_FP64 : VIE_PREC_MIXED;
     const double ET = sizeof(cplx<T>);
+    static bool smem_set = false;
+    if (!smem_set) {
+        VIE_CUDA(cudaFuncSetAttribute(k_dots<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(double) * 2 * (KB / 32) * (MAX_RESTART + 2))));
+        smem_set = true;
+    }
 
     std::vector<int> outer_active(R), it(R, 0), outer(R, 0);
     for (int r = 0; r < R; ++r) outer_active[r] = r;
@@ -591,7 +601,8 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
             for (int pass = 0; pass < 2; ++pass) {
                 const int* gate = pass ? S.reorth : nullptr;
                 tmr_begin(TMR_DOTS, st);
-                k_dots<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.partial, mp1 + 1, n, nblk, gate);
+                k_dots<T><<<gi, KB, sizeof(double) * 2 * (KB / 32) * (j + 2), st>>>(V, vrs, n, j, op.d_list, S.partial,
+                                                                                  mp1 + 1, n, nblk, gate);
                 tmr_end(TMR_DOTS, st, (double)ni * (j + 2) * n * ET);
                 LAUNCH_CHECK();
                 tmr_begin(TMR_REDUCE, st);

@@ -7,7 +7,7 @@
 
 namespace vie {
 
-constexpr int MAX_RESTART = 64;
+constexpr int MAX_RESTART = 512;
 
 struct Solver {
     int R = 0, m = 0, prec = 0, nblk = 0;

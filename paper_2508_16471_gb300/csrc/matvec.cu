@@ -106,9 +106,19 @@ static int upload_twiddles(Operator& op, AxisFFT& a) {
     return VIE_OK;
 }
 
+// Padded length of one axis: the next power of two >= 2n-1 when it costs at
+// most 15 % more points than the smallest 2,3,5,7-smooth length (the power of
+// two runs on the register four-step kernels), else the smooth length.
+int padded_size(int n) {
+    const int sm = smooth_size(2 * n - 1);
+    int p2 = 1;
+    while (p2 < 2 * n - 1) p2 *= 2;
+    return (p2 <= 512 && p2 * 100 <= sm * 115) ? p2 : sm;
+}
+
 int op_init_axes(Operator& op) {
     for (int a = 0; a < 3; ++a) {
-        op.P[a] = smooth_size(2 * op.n[a] - 1);
+        op.P[a] = padded_size(op.n[a]);
         op.H[a] = op.P[a] / 2 + 1;
         if (!make_plan(op.P[a], &op.ax[a].plan))
             return fail(VIE_EINVAL, "padded FFT size " + std::to_string(op.P[a]) + " exceeds the engine limit (1024)");

@@ -52,6 +52,8 @@ void dev_free(Operator& op, void* p, size_t bytes);
 
 // smooth padded size >= m (factors 2, 3, 5, 7)
 int smooth_size(int m);
+// padded FFT length used for a grid axis of n voxels
+int padded_size(int n);
 
 // ---- operator (matvec.cu) ---------------------------------------------------
 int op_init_axes(Operator& op);
