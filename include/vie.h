@@ -223,6 +223,27 @@ int vie_apply(vie_handle* hd, const double* w, double* y, int n_rhs, int precisi
  * not synchronised. */
 int vie_apply_device(vie_handle* hd, const void* w_dev, void* y_dev, int n_rhs, int precision);
 
+/*
+ * vie_apply_noalloc -- the FP32 operator of vie_apply_device for callers that
+ * cannot let the library allocate device memory: their device memory belongs
+ * to a framework's caching allocator or to a pool sized at start-up, or their
+ * loop must not stall on cudaMalloc/cudaFree.  The paper has no counterpart;
+ * this is a deployment variant of vie_apply_device that allocates nothing.
+ * Its FFT workspace is a fixed 64 MiB file-scope device array, held by every
+ * GPU that loads the library until the process exits.
+ *   w_dev, y_dev : device [n_rhs][3][n_body] complex64 (float2), layout as in
+ *                  vie_apply_device; 1 <= n_rhs <= 1024.
+ * Limits: every padded size must be a power of two (16..512), and the
+ * workspace of one RHS (3 n0 n1 P2 + 3 n0 P1 P2 complex64 words) must fit in
+ * the array (grids up to 64^3 do); otherwise VIE_EINVAL, with the sizes in
+ * vie_last_error().  The first call on each device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture.  All calls share the array and leave their data in it: calls that
+ * can overlap on the GPU (other streams, unordered handles) race; calls on one
+ * stream run in order.  Enqueued on the handle's stream; not synchronised.
+ */
+int vie_apply_noalloc(vie_handle* hd, const void* w_dev, void* y_dev, int n_rhs);
+
 /* Kernel-level check: batched 1-D complex DFT of `count` contiguous lines of
  * length L (2,3,5,7-smooth, <= 1024) by the library's FFT engine, host
  * in/out [count][L] complex doubles, forward (sign -1) when inverse == 0,

@@ -51,6 +51,8 @@ void dev_free(Operator& op, void* p, size_t bytes) {
     op.bytes -= (double)bytes;
 }
 
+Operator* handle_operator(vie_handle* hd) { return &hd->op; }
+
 }  // namespace vie
 
 using namespace vie;

@@ -23,7 +23,7 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_farfield", "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer",
            "vie_hom_map", "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines",
            "vie_get_info", "vie_kernel_launches", "vie_stream", "vie_destroy", "vie_last_error",
-           "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
+           "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_apply_noalloc", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
 
 
 class VieError(RuntimeError):
