@@ -54,11 +54,18 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--bodies", type=int, default=8)
     p.add_argument("--restart", type=int, default=64)
+    p.add_argument("--inner-tol", type=float, default=1e-3,
+                   help="mixed mode: relative residual reduction asked of each FP32 inner solve")
     p.add_argument("--plain-rhs", type=int, default=4)
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--max-iter", type=int, default=20000)
+    p.add_argument("--apply-only", type=int, default=0,
+                   help="profiling aid: one warm-up and one FP32 operator application with this many RHS on the "
+                        "first bench body, then exit (no JSON line)")
+    p.add_argument("--profile-solve", type=int, default=0,
+                   help="profiling aid: a 12-iteration solve with this many RHS on the first bench body, then exit")
     return p.parse_args()
 
 
@@ -190,17 +197,18 @@ def run_reference(args):
 # --------------------------------------------------------------------------- #
 # our arm
 # --------------------------------------------------------------------------- #
-def csrc_hash():
+def sources_hash(files):
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2508_16471_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary of this kernel,
-    if it was captured on the current sources (else None)."""
+def profiled_traffic(kernel, alg_bytes_per_launch):
+    """DRAM bytes per launch of `kernel`, from the committed ncu summary
+    profiles/traffic_<kernel>.txt (DRAM traffic / algorithmic bytes measured
+    on one launch, scaled to this run's launches), or None when that summary
+    is missing or was taken on sources that have changed since."""
     path = os.path.join(ROOT, "profiles", f"traffic_{kernel}.txt")
     if not os.path.exists(path):
         return None
@@ -209,11 +217,11 @@ def profiled_traffic(kernel):
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("csrc_sha256_16") != csrc_hash():
-        return None
     try:
-        return float(kv["dram_bytes_per_launch_full_size"])
-    except (KeyError, ValueError):
+        if kv.get("sources_sha256_16") != sources_hash(kv["sources"].split()):
+            return None
+        return float(kv["traffic_over_alg"]) * alg_bytes_per_launch
+    except (KeyError, ValueError, OSError):
         return None
 
 
@@ -235,6 +243,24 @@ def run_ours(args):
         torch.distributed.barrier()
     V.load()
 
+    if args.apply_only:
+        wl = inputs.random_body_workload(SEED0, n_axis=N_AXIS, h=H, n_dirs=N_DIRS)
+        with V.Handle(wl.grid.n, wl.grid.h, wl.eps, wl.k0) as hd0:
+            nb = hd0.info()["n_body"]
+            w = torch.randn(args.apply_only, 3, nb, dtype=torch.complex64, device="cuda")
+            y = torch.empty_like(w)
+            for _ in range(2):
+                hd0.apply_device(w.data_ptr(), y.data_ptr(), args.apply_only, V.PREC_MIXED)
+            torch.cuda.synchronize()
+        return 0
+
+    if args.profile_solve:
+        wl = inputs.random_body_workload(SEED0, n_axis=N_AXIS, h=H, n_dirs=N_DIRS)
+        chs0 = [(c.khat, c.pol) for c in wl.channels][:args.profile_solve]
+        with V.Handle(wl.grid.n, wl.grid.h, wl.eps, wl.k0) as hd0:
+            hd0.solve(chs0, tol=1e-6, restart=args.restart, max_iter=12, allow_noconv=True)
+        return 0
+
     seeds = body_seeds(rank, args.bodies)
     wls = [inputs.random_body_workload(s, n_axis=N_AXIS, h=H, n_dirs=N_DIRS) for s in seeds]
     g = wls[0].grid
@@ -244,7 +270,8 @@ def run_ours(args):
     eps_host = [torch.from_numpy(np.ascontiguousarray(w.eps)).pin_memory() for w in wls]
     hd = V.Handle(g.n, g.h, wls[0].eps, wls[0].k0)
     stream = torch.cuda.ExternalStream(hd.stream())
-    opts = dict(tol=1e-6, restart=args.restart, precision=V.PREC_MIXED, max_iter=args.max_iter)
+    opts = dict(tol=1e-6, restart=args.restart, precision=V.PREC_MIXED, max_iter=args.max_iter,
+                inner_tol=args.inner_tol)
 
     def step(i):
         hd.set_eps_device(eps_dev[i % len(eps_dev)].data_ptr())
@@ -341,13 +368,15 @@ def run_ours(args):
     # ---- roofline of the dominant kernel -----------------------------------
     peaks = load_peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
-    dom = max(timers.items(), key=lambda kv: kv[1][0])
+    # dominant HBM-bound kernel of the FP32 path (the FP64 residual operator is FP64-ALU bound)
+    dom = max(((k, v) for k, v in timers.items() if k != "matvec_fp64"), key=lambda kv: kv[1][0])
     name, (kms, kn, kbytes) = dom
     achieved = kbytes / (kms / 1000.0) / 1e9 if kms > 0 else 0.0
     kernels = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / max(1e-9, sum(x[0] for x in timers.values())), 4),
                    "alg_GBps": round(v[2] / (v[0] / 1000.0) / 1e9, 1) if v[0] > 0 else None}
                for k, v in timers.items() if v[1] > 0}
-    traffic = profiled_traffic(name)
+    tname = {"xfused": "xfused"}.get(name, name)
+    traffic = profiled_traffic(tname, kbytes / max(1, kn))
     roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks
             else "fallback 6800 GB/s", "alg_bytes_per_launch": kbytes / max(1, kn),

@@ -82,8 +82,11 @@ typedef struct vie_solve_opts {
     int precision;     /* VIE_PREC_MIXED (default) or VIE_PREC_FP64              */
     double inner_tol;  /* mixed mode: relative reduction asked of each FP32 inner
                           solve (default 1e-3)                                    */
-    int use_x0;        /* 1: start from the currents stored in the handle (same
-                          n_rhs as the previous solve); 0: x0 = 0                 */
+    int use_x0;        /* 0: x0 = 0; 1: start from the currents stored in the
+                          handle (same n_rhs, restart and precision as the previous
+                          solve); 2: initial currents predicted by the network
+                          attached with vie_attach_net.  A supplied guess whose
+                          FP64 residual is not below ||b|| is replaced by zero.  */
     int reserved[3];
 } vie_solve_opts;
 
@@ -251,6 +254,46 @@ int vie_apply_noalloc(vie_handle* hd, const void* w_dev, void* y_dev, int n_rhs)
 int vie_fft_lines(const double* in, double* out, int L, int count, int inverse, int precision);
 
 int vie_get_info(const vie_handle* hd, vie_info* info);
+
+/* ---- learned initial guess ----------------------------------------------
+ * A 4-level 3-D U-Net (channels c0..c3, 3x3x3 convolutions with ReLU, 2x2x2
+ * average pooling, nearest upsampling, skip concatenations, 1x1x1 head) maps
+ * 10 input channels on a coarse cubic grid of D^3 voxels (D % 8 == 0) --
+ * block-averaged chi, Re/Im of the polarisation and the propagation direction
+ * (constant channels) -- to 6 output channels, the scattered part of the
+ * total field with the incident phase removed, (E_tot - E_inc) e^{-i k0 khat.r},
+ * averaged over each block's body voxels.  The solver turns the prediction
+ * into x0 = chi (E_inc + upsampled prediction e^{i k0 khat.r}) (use_x0 = 2);
+ * plain GMRES from x0 = 0 is the fallback, chosen per RHS by the FP64
+ * residual.  Activations in bf16 (or FP32 for gradient checks), weights FP32
+ * masters, every sum in FP32; trained with Adam on solver-generated data.
+ * The paper has no learned component; this is the build's systems pattern.
+ * Device arrays: x [B][10][D^3], y / t [B][6][D^3], m [B][D^3] (float32),
+ * on the current device; these calls synchronise the device's null stream. */
+typedef struct vie_net vie_net;
+int vie_net_create(const int channels[4], unsigned long long seed, int bf16, vie_net** out);
+void vie_net_destroy(vie_net* net);
+long long vie_net_num_params(const vie_net* net);
+/* host float32 arrays of vie_net_num_params() entries: per layer w[co][ci][k^3] then b[co] */
+int vie_net_get_params(const vie_net* net, float* host);
+int vie_net_set_params(vie_net* net, const float* host);
+int vie_net_forward(vie_net* net, const float* x_dev, float* y_dev, int B, int D);
+/* masked mean-squared error sum m (y - t)^2 / (6 sum m) and its parameter
+ * gradients (host, same layout as the parameters; NULL to skip) */
+int vie_net_gradients(vie_net* net, const float* x_dev, const float* t_dev, const float* m_dev, int B, int D,
+                      float* loss, float* grads_host);
+/* one Adam step (beta 0.9, 0.999, eps 1e-8) on that loss */
+int vie_net_train_step(vie_net* net, const float* x_dev, const float* t_dev, const float* m_dev, int B, int D,
+                       float lr, float* loss);
+/* training sample of every RHS of the handle's last solve on the grid
+ * coarsened by `factor`: x [rhs][10][D^3]; when t_dev / m_dev are given also
+ * the targets t [rhs][6][D^3] and mask m [rhs][D^3] (fraction of body voxels
+ * per block) from the solved currents.  Errors: VIE_EINVAL, VIE_ESTATE. */
+int vie_net_features(vie_handle* hd, int factor, float* x_dev, float* t_dev, float* m_dev);
+/* attach (or detach with NULL) the network used by use_x0 = 2; not owned */
+int vie_attach_net(vie_handle* hd, vie_net* net, int factor);
+/* number of RHS of the last solve whose supplied initial guess was rejected */
+int vie_guesses_rejected(const vie_handle* hd);
 
 /* Engine of the far-field contractions on (theta, phi) grids (vie_farfield):
  * 0 (default) tensor cores (tcgen05, TF32 split three ways: hi*hi + hi*lo +

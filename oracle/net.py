@@ -3,7 +3,7 @@ infrastructure only; only ``tests/`` may import it).
 
 A 4-level 3-D U-Net on a cubic grid of D^3 voxels (D divisible by 8):
 
-  enc0: conv(7->c0) relu conv(c0->c0) relu            -> s0   (D^3)
+  enc0: conv(cin->c0) relu conv(c0->c0) relu          -> s0   (D^3)
   pool: 2x2x2 average
   enc1: conv(c0->c1) relu conv(c1->c1) relu           -> s1   ((D/2)^3)
   enc2: conv(c1->c2) relu conv(c2->c2) relu           -> s2   ((D/4)^3)
@@ -25,7 +25,7 @@ import numpy as np
 OFFS = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
 
 
-def layer_specs(c=(16, 32, 64, 128), cin=7, cout=6):
+def layer_specs(c=(16, 32, 64, 128), cin=10, cout=6):
     """List of (name, Cin, Cout, ksize) in the order the network applies them."""
     c0, c1, c2, c3 = c
     return [("e0a", cin, c0, 3), ("e0b", c0, c0, 3), ("e1a", c0, c1, 3), ("e1b", c1, c1, 3),

@@ -7,6 +7,11 @@
 #include <vector>
 
 #include "farfield.cuh"
+#include "net.cuh"
+
+struct vie_net {
+    vie::Net net;
+};
 
 struct vie_handle {
     vie::Operator op;
@@ -15,6 +20,9 @@ struct vie_handle {
     int n_rhs = 0;
     bool have_solution = false;
     std::vector<int> vox_host;  // body voxel list (for host-side scatter/gather)
+    vie_net* net = nullptr;     // attached initial-guess network (not owned)
+    int net_factor = 4;         // coarsening of the network grid
+    int guesses_rejected = 0;
 };
 
 namespace vie {
@@ -95,6 +103,38 @@ static int set_eps_dev(vie_handle* hd, const double* eps_dev) {
     hd->n_rhs = 0;
     VIE_TRY(op_set_body_device(hd->op, eps_dev));
     return refresh_vox_host(hd);
+}
+
+// initial currents of every RHS from the attached network (use_x0 = 2)
+static int net_guess(vie_handle* hd, int n_rhs) {
+    Operator& op = hd->op;
+    const int f = hd->net_factor;
+    if (op.n[0] != op.n[1] || op.n[0] != op.n[2] || op.n[0] % (8 * f) != 0)
+        return fail(VIE_EINVAL, "the network needs a cubic grid with n divisible by 8 x coarsening factor");
+    const int D = op.n[0] / f;
+    const long long V = (long long)D * D * D;
+    Net& net = hd->net->net;
+    const int Bb = std::min(n_rhs, 8);
+    VIE_TRY(net.reserve(Bb, D));
+    float *x = nullptr, *y = nullptr;
+    cudaError_t e = cudaMalloc(&x, sizeof(float) * NET_IN * V * n_rhs);
+    if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(float) * 6 * V * n_rhs);
+    int st = e == cudaSuccess ? VIE_OK : cuda_fail(e, "network buffers");
+    if (st == VIE_OK) st = net_features(op, hd->S.chans, n_rhs, f, x, nullptr, 0, nullptr, nullptr, op.stream);
+    for (int r0 = 0; st == VIE_OK && r0 < n_rhs; r0 += Bb) {
+        const int nb = std::min(Bb, n_rhs - r0);
+        st = net.set_input(x + (long long)r0 * NET_IN * V, nb, op.stream);
+        if (st == VIE_OK) st = net.forward(nb, op.stream);
+        if (st == VIE_OK) st = net.get_output(y + (long long)r0 * 6 * V, nb, op.stream);
+    }
+    if (st == VIE_OK) st = net_initial_guess(op, hd->S.chans, n_rhs, f, y, hd->S.x, hd->S.n3, op.stream);
+    if (st == VIE_OK) {
+        e = cudaStreamSynchronize(op.stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "network initial guess");
+    }
+    cudaFree(x);
+    cudaFree(y);
+    return st;
 }
 
 extern "C" {
@@ -199,13 +239,17 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
         if (std::sqrt(dr * dr + di * di) > 1e-10 * std::sqrt(pn))
             return fail(VIE_EINVAL, "polarisation must be transverse to khat");
     }
-    if (o.use_x0 && (!hd->have_solution || hd->n_rhs != n_rhs || hd->S.m != o.restart || hd->S.prec != o.precision))
+    if (o.use_x0 == 1 &&
+        (!hd->have_solution || hd->n_rhs != n_rhs || hd->S.m != o.restart || hd->S.prec != o.precision))
         return fail(VIE_ESTATE, "use_x0 needs a stored solution with the same n_rhs, restart and precision");
+    if (o.use_x0 == 2 && !hd->net) return fail(VIE_ESTATE, "use_x0 = 2 needs a network attached with vie_attach_net");
+    if (o.use_x0 < 0 || o.use_x0 > 2) return fail(VIE_EINVAL, "use_x0 must be 0, 1 or 2");
     VIE_CUDA(cudaSetDevice(hd->device));
     auto t0 = std::chrono::steady_clock::now();
     VIE_TRY(hd->S.alloc(hd->op, n_rhs, o.restart, o.precision));
     hd->have_solution = false;
     VIE_TRY(build_rhs(hd->op, hd->S, ch, n_rhs));
+    if (o.use_x0 == 2) VIE_TRY(net_guess(hd, n_rhs));
     SolveResult res;
     int st = solver_run(hd->op, hd->S, o, res);
     VIE_CUDA(cudaStreamSynchronize(hd->op.stream));
@@ -213,6 +257,7 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
     if (st != VIE_OK) return st;
     hd->n_rhs = n_rhs;
     hd->have_solution = true;
+    hd->guesses_rejected = res.guesses_rejected;
     if (stats) {
         stats->n_rhs = n_rhs;
         stats->converged = res.converged;
@@ -538,5 +583,127 @@ void vie_destroy(vie_handle* hd) {
     if (hd->op.stream) cudaStreamDestroy(hd->op.stream);
     delete hd;
 }
+
+// ---- learned initial guess ------------------------------------------------
+int vie_net_create(const int channels[4], unsigned long long seed, int bf16, vie_net** out) {
+    if (!out || !channels) return fail(VIE_EINVAL, "NULL argument");
+    for (int i = 0; i < 4; ++i)
+        if (channels[i] < 1 || channels[i] > 256) return fail(VIE_EINVAL, "channels must be in 1..256");
+    vie_net* n = new vie_net();
+    int st = n->net.init(channels, seed, bf16 ? 1 : 0);
+    if (st != VIE_OK) {
+        delete n;
+        return st;
+    }
+    *out = n;
+    return VIE_OK;
+}
+
+void vie_net_destroy(vie_net* n) { delete n; }
+
+long long vie_net_num_params(const vie_net* n) { return n ? n->net.nparams : 0; }
+
+int vie_net_get_params(const vie_net* n, float* host) {
+    if (!n || !host) return fail(VIE_EINVAL, "NULL argument");
+    long long o = 0;
+    for (int l = 0; l < Net::NL; ++l) {
+        VIE_CUDA(cudaMemcpy(host + o, n->net.L[l].w, 4 * n->net.L[l].nw, cudaMemcpyDeviceToHost));
+        o += n->net.L[l].nw;
+        VIE_CUDA(cudaMemcpy(host + o, n->net.L[l].b, 4 * n->net.L[l].co, cudaMemcpyDeviceToHost));
+        o += n->net.L[l].co;
+    }
+    return VIE_OK;
+}
+
+int vie_net_set_params(vie_net* n, const float* host) {
+    if (!n || !host) return fail(VIE_EINVAL, "NULL argument");
+    long long o = 0;
+    for (int l = 0; l < Net::NL; ++l) {
+        VIE_CUDA(cudaMemcpy(n->net.L[l].w, host + o, 4 * n->net.L[l].nw, cudaMemcpyHostToDevice));
+        o += n->net.L[l].nw;
+        VIE_CUDA(cudaMemcpy(n->net.L[l].b, host + o, 4 * n->net.L[l].co, cudaMemcpyHostToDevice));
+        o += n->net.L[l].co;
+    }
+    return VIE_OK;
+}
+
+static int net_check(vie_net* n, int B, int D) {
+    if (!n || B < 1 || D < 8 || D % 8 != 0 || D > 256) return fail(VIE_EINVAL, "bad network arguments (D % 8 == 0)");
+    return VIE_OK;
+}
+
+int vie_net_forward(vie_net* n, const float* x_dev, float* y_dev, int B, int D) {
+    VIE_TRY(net_check(n, B, D));
+    if (!x_dev || !y_dev) return fail(VIE_EINVAL, "NULL argument");
+    Net& net = n->net;
+    VIE_TRY(net.reserve(B, D));
+    VIE_TRY(net.set_input(x_dev, B, 0));
+    VIE_TRY(net.forward(B, 0));
+    VIE_TRY(net.get_output(y_dev, B, 0));
+    VIE_CUDA(cudaStreamSynchronize(0));
+    return VIE_OK;
+}
+
+static int net_fwd_bwd(vie_net* n, const float* x, const float* t, const float* m, int B, int D, float* loss) {
+    VIE_TRY(net_check(n, B, D));
+    if (!x || !t || !m) return fail(VIE_EINVAL, "NULL argument");
+    Net& net = n->net;
+    VIE_TRY(net.reserve(B, D));
+    VIE_TRY(device_sum(m, (long long)B * D * D * D, &net.mask_sum, net.d_loss, 0));
+    VIE_TRY(net.set_input(x, B, 0));
+    VIE_TRY(net.forward(B, 0));
+    VIE_TRY(net.loss_grad(t, m, B, 0, loss));
+    VIE_TRY(net.backward(B, 0));
+    return VIE_OK;
+}
+
+int vie_net_gradients(vie_net* n, const float* x_dev, const float* t_dev, const float* m_dev, int B, int D, float* loss,
+                      float* grads_host) {
+    VIE_TRY(net_fwd_bwd(n, x_dev, t_dev, m_dev, B, D, loss));
+    VIE_CUDA(cudaStreamSynchronize(0));
+    if (grads_host) {
+        long long o = 0;
+        for (int l = 0; l < Net::NL; ++l) {
+            VIE_CUDA(cudaMemcpy(grads_host + o, n->net.L[l].gw, 4 * n->net.L[l].nw, cudaMemcpyDeviceToHost));
+            o += n->net.L[l].nw;
+            VIE_CUDA(cudaMemcpy(grads_host + o, n->net.L[l].gb, 4 * n->net.L[l].co, cudaMemcpyDeviceToHost));
+            o += n->net.L[l].co;
+        }
+    }
+    return VIE_OK;
+}
+
+int vie_net_train_step(vie_net* n, const float* x_dev, const float* t_dev, const float* m_dev, int B, int D, float lr,
+                       float* loss) {
+    if (!(lr > 0)) return fail(VIE_EINVAL, "learning rate must be positive");
+    VIE_TRY(net_fwd_bwd(n, x_dev, t_dev, m_dev, B, D, loss));
+    VIE_TRY(n->net.adam(lr, 0));
+    VIE_CUDA(cudaStreamSynchronize(0));
+    return VIE_OK;
+}
+
+int vie_net_features(vie_handle* hd, int factor, float* x_dev, float* t_dev, float* m_dev) {
+    if (!hd || !x_dev) return fail(VIE_EINVAL, "NULL argument");
+    if (!hd->have_solution && t_dev) return fail(VIE_ESTATE, "training targets need a solve first");
+    const Operator& op = hd->op;
+    if (factor < 1 || op.n[0] != op.n[1] || op.n[0] != op.n[2] || op.n[0] % factor != 0)
+        return fail(VIE_EINVAL, "features need a cubic grid with n divisible by the factor");
+    if (!hd->S.chans) return fail(VIE_ESTATE, "no right-hand sides yet: call vie_solve first");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    VIE_TRY(net_features(hd->op, hd->S.chans, hd->S.R, factor, x_dev, t_dev ? hd->S.x : nullptr, hd->S.n3, t_dev,
+                         m_dev, hd->op.stream));
+    VIE_CUDA(cudaStreamSynchronize(hd->op.stream));
+    return VIE_OK;
+}
+
+int vie_attach_net(vie_handle* hd, vie_net* n, int factor) {
+    if (!hd) return fail(VIE_EINVAL, "NULL handle");
+    if (n && factor < 1) return fail(VIE_EINVAL, "factor must be >= 1");
+    hd->net = n;
+    hd->net_factor = factor;
+    return VIE_OK;
+}
+
+int vie_guesses_rejected(const vie_handle* hd) { return hd ? hd->guesses_rejected : 0; }
 
 }  // extern "C"

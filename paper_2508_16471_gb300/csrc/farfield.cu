@@ -51,8 +51,7 @@ int build_rhs(Operator& op, Solver& S, const vie_channel* chs, int n_rhs) {
         for (int q = 0; q < 3; ++q) hc[9 * r + q] = chs[r].khat[q];
         for (int q = 0; q < 6; ++q) hc[9 * r + 3 + q] = chs[r].pol[q];
     }
-    double* d = nullptr;
-    VIE_CUDA(cudaMalloc(&d, sizeof(double) * hc.size()));
+    double* d = S.chans;
     cudaError_t e = cudaMemcpyAsync(d, hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice, op.stream);
     if (e == cudaSuccess) {
         const double cx = op.origin[0] - 0.5 * (op.n[0] - 1) * op.h;
@@ -64,7 +63,6 @@ int build_rhs(Operator& op, Solver& S, const vie_channel* chs, int n_rhs) {
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(op.stream);
     }
-    cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(e, "rhs build");
     return VIE_OK;
 }

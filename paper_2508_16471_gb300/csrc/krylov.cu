@@ -9,7 +9,12 @@
 //     Arnoldi inner products and the update w -= V h accumulate in FP64
 //     (classical Gram-Schmidt, two passes), the Hessenberg matrix, the Givens
 //     rotations and the least-squares solve are FP64;
-//   * after each cycle x += V y in FP64 and the FP64 residual is recomputed.
+//   * after each cycle x += V y in FP64.  A cycle that ended because its
+//     recurrence residual met the target (or the iteration budget is spent)
+//     is followed by the FP64 residual, which alone decides convergence; a
+//     cycle that only ran out of its m steps restarts from r = b - A_T x
+//     formed with the working-precision operator (mixed mode), so each RHS
+//     normally pays one FP64 operator application, at the final check.
 // Each RHS stops on its own; converged RHS drop out of the launch lists.
 #include <algorithm>
 #include <chrono>
@@ -394,6 +399,70 @@ __global__ void k_residual(const c64* __restrict__ b, c64* __restrict__ r, long 
     }
 }
 
+// restart residual in the working precision: the basis slot 0 of each listed
+// RHS receives x rounded to T, the operator writes A_T x into slot 1, and
+// k_residual_lo forms r = b - A_T x in FP64 with its norm partials
+template <typename T>
+__global__ void k_x_to_basis(const c64* __restrict__ x, long long stride, cplx<T>* __restrict__ V, long long vrs,
+                             const int* __restrict__ list, long long n) {
+    const int r = list[blockIdx.y];
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) {
+            const c64 v = x[r * stride + e];
+            V[r * vrs + e] = cplx<T>{(T)v.x, (T)v.y};
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_residual_lo(const c64* __restrict__ b, c64* __restrict__ res, long long stride,
+                              const cplx<T>* __restrict__ V, long long vrs, const int* __restrict__ list,
+                              double* __restrict__ normpart, long long n, int nblk) {
+    __shared__ double ws[KB / 32];
+    const int rr = list[blockIdx.y];
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+    double nrm = 0;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) {
+            const c64 bv = b[rr * stride + e];
+            const cplx<T> ax = V[rr * vrs + n + e];
+            const c64 v{bv.x - (double)ax.x, bv.y - (double)ax.y};
+            res[rr * stride + e] = v;
+            nrm += v.x * v.x + v.y * v.y;
+        }
+    }
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < KB / 32; ++q) t += ws[q];
+        normpart[(long long)rr * nblk + blockIdx.x] = t;
+    }
+}
+
+// initial guess worse than zero: x = 0, r = b, ||r|| = ||b||
+__global__ void k_reset_guess(c64* __restrict__ x, c64* __restrict__ res, const c64* __restrict__ b, long long stride,
+                              double* __restrict__ rnorm, const double* __restrict__ bnorm,
+                              const int* __restrict__ list, long long n) {
+    const int r = list[blockIdx.y];
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) {
+            x[r * stride + e] = c64{0, 0};
+            res[r * stride + e] = b[r * stride + e];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) rnorm[r] = bnorm[r];
+}
+
 __global__ void k_norm_finish(const double* __restrict__ normpart, int nblk, double* __restrict__ out,
                               const int* __restrict__ list, int nr) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -449,6 +518,7 @@ int Solver::alloc(Operator& op, int R_, int m_, int prec_) {
     VIE_TRY(dev_alloc(op, (void**)&coef, sizeof(c64) * R * (m + 2)));
     VIE_TRY(dev_alloc(op, (void**)&partial, sizeof(c64) * (size_t)R * (m + 2) * nblk));
     VIE_TRY(dev_alloc(op, (void**)&reorth, sizeof(int) * R));
+    VIE_TRY(dev_alloc(op, (void**)&chans, sizeof(double) * 9 * R));
     VIE_TRY(dev_alloc(op, (void**)&normpart, sizeof(double) * (size_t)R * nblk));
     VIE_TRY(dev_alloc(op, (void**)&inv, sizeof(double) * R));
     VIE_TRY(dev_alloc(op, (void**)&target, sizeof(double) * R));
@@ -474,6 +544,7 @@ void Solver::release(Operator& op) {
         dev_free(op, coef, sizeof(c64) * R * (m + 2));
         dev_free(op, partial, sizeof(c64) * (size_t)R * (m + 2) * nblk);
         dev_free(op, reorth, sizeof(int) * R);
+        dev_free(op, chans, sizeof(double) * 9 * R);
         dev_free(op, normpart, sizeof(double) * (size_t)R * nblk);
         dev_free(op, inv, sizeof(double) * R);
         dev_free(op, target, sizeof(double) * R);
@@ -485,7 +556,7 @@ void Solver::release(Operator& op) {
     x = b = res = nullptr;
     V = nullptr;
     H = sn = g = y = coef = partial = nullptr;
-    cs = normpart = inv = target = bnorm = rnorm = nullptr;
+    cs = normpart = inv = target = bnorm = rnorm = chans = nullptr;
     kcount = flag = reorth = nullptr;
     R = 0;
 }
@@ -534,8 +605,13 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         if (!(hb[r] > 0) || !std::isfinite(hb[r])) return fail(VIE_EINVAL, "right-hand side is zero or not finite");
 
     bool first = !o.use_x0;
+    bool guess_pending = o.use_x0 != 0;
     std::vector<int> done(R, 0);
+    // 1: the next residual of this RHS is the FP64 one (a convergence check);
+    // 0: a restart residual in the working precision suffices
+    std::vector<int> need64(R, 1), stopped(R, 0);
     out.matvecs32 = out.matvecs64 = 0;
+    out.guesses_rejected = 0;
     while (true) {
         std::vector<int> act;
         for (int r = 0; r < R; ++r)
@@ -544,19 +620,48 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         const int na = (int)act.size();
         VIE_TRY(op_set_list(op, act.data(), na));
         dim3 ga(nblk, na);
-        // FP64 residual r = b - A64 x
+        // exact residuals: x = 0 (r = b), or the FP64 operator
+        std::vector<int> act64, actlo;
+        std::vector<char> exact(R, 0);
+        for (int r : act) {
+            exact[r] = first || need64[r] || guess_pending || prec_in == VIE_PREC_FP64;
+            (exact[r] ? act64 : actlo).push_back(r);
+        }
         if (first) {
+            // x = 0: r = b
             tmr_begin(TMR_RESIDUAL, st);
             k_residual<<<ga, KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 1);
             tmr_end(TMR_RESIDUAL, st, 2.0 * na * n * 16.0);
             LAUNCH_CHECK();
         } else {
-            VIE_TRY(op_apply(op, VIE_PREC_FP64, S.x, n, S.res, n, op.d_list, na));
-            out.matvecs64 += na;
-            tmr_begin(TMR_RESIDUAL, st);
-            k_residual<<<ga, KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 0);
-            tmr_end(TMR_RESIDUAL, st, 3.0 * na * n * 16.0);
-            LAUNCH_CHECK();
+            if (!act64.empty()) {
+                // FP64 residual r = b - A64 x
+                const int n64 = (int)act64.size();
+                VIE_TRY(op_set_list(op, act64.data(), n64));
+                VIE_TRY(op_apply(op, VIE_PREC_FP64, S.x, n, S.res, n, op.d_list, n64));
+                out.matvecs64 += n64;
+                tmr_begin(TMR_RESIDUAL, st);
+                k_residual<<<dim3(nblk, n64), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 0);
+                tmr_end(TMR_RESIDUAL, st, 3.0 * n64 * n * 16.0);
+                LAUNCH_CHECK();
+            }
+            if (!actlo.empty()) {
+                // restart residual r = b - A_T x (working precision)
+                const int nlo = (int)actlo.size();
+                VIE_TRY(op_set_list(op, actlo.data(), nlo));
+                tmr_begin(TMR_RESIDUAL, st);
+                k_x_to_basis<T><<<dim3(nblk, nlo), KB, 0, st>>>(S.x, n, V, vrs, op.d_list, n);
+                tmr_end(TMR_RESIDUAL, st, (double)nlo * n * (16.0 + ET));
+                LAUNCH_CHECK();
+                VIE_TRY(op_apply(op, prec_in, V, vrs, V + n, vrs, op.d_list, nlo));
+                out.matvecs32 += nlo;
+                tmr_begin(TMR_RESIDUAL, st);
+                k_residual_lo<T><<<dim3(nblk, nlo), KB, 0, st>>>(S.b, S.res, n, V, vrs, op.d_list, S.normpart, n,
+                                                                 nblk);
+                tmr_end(TMR_RESIDUAL, st, (double)nlo * n * (32.0 + ET));
+                LAUNCH_CHECK();
+            }
+            VIE_TRY(op_set_list(op, act.data(), na));
         }
         first = false;
         tmr_begin(TMR_OTHER, st);
@@ -565,15 +670,42 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         LAUNCH_CHECK();
         VIE_CUDA(cudaMemcpyAsync(hr.data(), S.rnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
         VIE_CUDA(cudaStreamSynchronize(st));
+        if (guess_pending) {
+            // the true FP64 residual judges a supplied initial guess: where it is
+            // no better than x0 = 0, fall back to zero
+            guess_pending = false;
+            std::vector<int> bad;
+            for (int r : act)
+                if (!(hr[r] < hb[r])) bad.push_back(r);
+            if (!bad.empty()) {
+                VIE_TRY(op_set_list(op, bad.data(), (int)bad.size()));
+                k_reset_guess<<<dim3(nblk, (int)bad.size()), KB, 0, st>>>(S.x, S.res, S.b, n, S.rnorm, S.bnorm,
+                                                                         op.d_list, n);
+                LAUNCH_CHECK();
+                for (int r : bad) hr[r] = hb[r];
+                out.guesses_rejected += (int)bad.size();
+                VIE_TRY(op_set_list(op, act.data(), na));
+            }
+        }
         std::vector<int> cyc;
+        bool recheck = false;
         for (int r : act) {
             const double rel = hr[r] / hb[r];
+            if (!exact[r] && (rel <= o.tol || !std::isfinite(rel) || it[r] >= o.max_iter)) {
+                // a working-precision residual decides nothing: confirm in FP64
+                need64[r] = 1;
+                recheck = true;
+                continue;
+            }
             out.relres[r] = rel;
             if (rel <= o.tol || !std::isfinite(rel)) done[r] = 1;
             else if (it[r] >= o.max_iter) done[r] = 2;
             else cyc.push_back(r);
         }
-        if (cyc.empty()) break;
+        if (cyc.empty()) {
+            if (recheck) continue;
+            break;
+        }
         for (int r : cyc) {
             outer[r]++;
             double t = 0.99 * o.tol * hb[r];
@@ -587,6 +719,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         k_start_cycle<T><<<dim3(nblk, nc), KB, 0, st>>>(S.res, n, V, vrs, S.rnorm, S.g, op.d_list, m, n);
         tmr_end(TMR_START, st, (double)nc * n * (16.0 + ET));
         LAUNCH_CHECK();
+        for (int r : cyc) stopped[r] = 0;
         std::vector<int> inner = cyc;  // RHS still iterating in this cycle
         std::vector<int> all_cyc = cyc;
         long long steps_sum = 0;       // Krylov steps taken in this cycle, summed over RHS
@@ -636,6 +769,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
             for (int r : inner) {
                 it[r]++;
                 if (!hflag[r] && it[r] < o.max_iter) nxt.push_back(r);
+                else stopped[r] = 1;
             }
             inner.swap(nxt);
         }
@@ -649,6 +783,8 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         k_xupdate<T><<<dim3(nblk, nc), KB, 0, st>>>(S.x, n, V, vrs, n, S.y, S.kcount, op.d_list, m, n);
         tmr_end(TMR_XUPDATE, st, (double)steps_sum * n * ET + 2.0 * nc * n * 16.0);
         LAUNCH_CHECK();
+        // met the target or spent the budget: FP64 check; ran out of m steps: restart residual
+        for (int r : all_cyc) need64[r] = stopped[r];
     }
     out.converged = 0;
     out.iters_max = 0;

@@ -31,6 +31,7 @@ struct Solver {
     int* kcount = nullptr;     // [R] steps taken in the current cycle
     int* flag = nullptr;       // [R] 1 = stop the current cycle
     int* reorth = nullptr;     // [R] 1 = second Gram-Schmidt pass needed this step
+    double* chans = nullptr;   // [R][9] channels of the current right-hand sides
 
     int alloc(Operator& op, int R, int m, int prec);
     void release(Operator& op);
@@ -42,6 +43,7 @@ struct SolveResult {
     int converged = 0, iters_max = 0, outer_max = 0;
     long long matvecs32 = 0, matvecs64 = 0;
     double relres_max = 0;
+    int guesses_rejected = 0;  // initial guesses replaced by zero (worse than x0 = 0)
 };
 
 int solver_run(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult& out);

@@ -763,6 +763,8 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
     const double lineA = 3.0 * n0 * n1 * P2 * E;  // one slot of A
     const double lineB = 3.0 * n0 * P1 * P2 * E;  // one slot of B
     const double vec = 3.0 * op.Nb * E;           // one compact vector
+    // FP64 passes are timed under one id (FP64-bound on GB300, kept apart from the FP32 roofline)
+    auto tid = [](int id) { return sizeof(T) == 8 ? (int)TMR_MV64 : id; };
     for (int s0 = 0; s0 < nr; s0 += W.cap) {
         const int ns = std::min(W.cap, nr - s0);
         const int* list = d_list + s0;
@@ -772,41 +774,41 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
         // pass 1
         if (fz) {
             const long long nlines = (long long)ns * 3 * n0 * n1;
-            tmr_begin(TMR_ZFWD, op.stream);
+            tmr_begin(tid(TMR_ZFWD), op.stream);
             VIE_TRY(fast_zfwd((const c32*)w, wr, list, op.idx_map, (c32*)A, n0, n1, n2, op.Nb, nlines, P2,
                               op.ax[2].roots32, op.stream));
-            tmr_end(TMR_ZFWD, op.stream, ns * (vec + lineA) + 4.0 * op.N);
+            tmr_end(tid(TMR_ZFWD), op.stream, ns * (vec + lineA) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
         } else {
             const FFTPlan& p = op.ax[2].plan;
             const int NL = lines_per_cta<T>(p.L);
             const long long nlines = (long long)ns * 3 * n0 * n1;
-            tmr_begin(TMR_ZFWD, op.stream);
+            tmr_begin(tid(TMR_ZFWD), op.stream);
             k_zfwd<T><<<(unsigned)((nlines + NL - 1) / NL), 256, lines_smem<T>(p, NL), op.stream>>>(
                 w, wr, list, op.idx_map, A, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), NL);
-            tmr_end(TMR_ZFWD, op.stream, ns * (vec + lineA) + 4.0 * op.N);
+            tmr_end(tid(TMR_ZFWD), op.stream, ns * (vec + lineA) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
         }
         // pass 2
         if (fy) {
-            tmr_begin(TMR_YFWD, op.stream);
+            tmr_begin(tid(TMR_YFWD), op.stream);
             VIE_TRY(fast_axis((const c32*)A, (c32*)B, (long long)ns * 3 * n0, n1, P1, P2, P1, op.ax[1].roots32, false,
                               op.stream));
-            tmr_end(TMR_YFWD, op.stream, (double)ns * (lineA + lineB));
+            tmr_end(tid(TMR_YFWD), op.stream, (double)ns * (lineA + lineB));
             count_launch();
             VIE_CUDA(cudaGetLastError());
         } else {
             VIE_TRY((launch_axis<T, false>(A, B, (long long)ns * 3 * n0, n1, P1, P2, op.ax[1].plan, twp<T>(op.ax[1]),
-                                           op.stream, TMR_YFWD)));
+                                           op.stream, tid(TMR_YFWD))));
         }
         // pass 3
         if (fx) {
-            tmr_begin(TMR_XFUSED, op.stream);
+            tmr_begin(tid(TMR_XFUSED), op.stream);
             VIE_TRY(fast_xfused((c32*)B, n0, (long long)P1 * P2, P0, P1, P2, (const c32*)kh, op.H, op.ax[0].roots32, ns,
                                 op.stream));
-            tmr_end(TMR_XFUSED, op.stream, 2.0 * ns * lineB + 6.0 * op.H[0] * op.H[1] * op.H[2] * E);
+            tmr_end(tid(TMR_XFUSED), op.stream, 2.0 * ns * lineB + 6.0 * op.H[0] * op.H[1] * op.H[2] * E);
             count_launch();
             VIE_CUDA(cudaGetLastError());
         } else {
@@ -814,42 +816,42 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             const long long inner = (long long)P1 * P2;
             const int TW = xfused_tile<T>(p.L, inner);
             const long long grid = (long long)ns * ((inner + TW - 1) / TW);
-            tmr_begin(TMR_XFUSED, op.stream);
+            tmr_begin(tid(TMR_XFUSED), op.stream);
             k_xfused<T><<<(unsigned)grid, 256, xfused_smem<T>(p, TW), op.stream>>>(
                 B, n0, inner, P0, P1, P2, kh, op.H[0], op.H[1], op.H[2], p, twp<T>(op.ax[0]), TW);
-            tmr_end(TMR_XFUSED, op.stream, 2.0 * ns * lineB + 6.0 * op.H[0] * op.H[1] * op.H[2] * E);
+            tmr_end(tid(TMR_XFUSED), op.stream, 2.0 * ns * lineB + 6.0 * op.H[0] * op.H[1] * op.H[2] * E);
             count_launch();
             VIE_CUDA(cudaGetLastError());
         }
         // pass 4
         if (fy) {
-            tmr_begin(TMR_YINV, op.stream);
+            tmr_begin(tid(TMR_YINV), op.stream);
             VIE_TRY(fast_axis((const c32*)B, (c32*)A, (long long)ns * 3 * n0, P1, n1, P2, P1, op.ax[1].roots32, true,
                               op.stream));
-            tmr_end(TMR_YINV, op.stream, (double)ns * (lineA + lineB));
+            tmr_end(tid(TMR_YINV), op.stream, (double)ns * (lineA + lineB));
             count_launch();
             VIE_CUDA(cudaGetLastError());
         } else {
             VIE_TRY((launch_axis<T, true>(B, A, (long long)ns * 3 * n0, P1, n1, P2, op.ax[1].plan, twp<T>(op.ax[1]),
-                                          op.stream, TMR_YINV)));
+                                          op.stream, tid(TMR_YINV))));
         }
         // pass 5
         if (fz) {
             const long long nlines = (long long)ns * 3 * n0 * n1;
-            tmr_begin(TMR_ZINV, op.stream);
+            tmr_begin(tid(TMR_ZINV), op.stream);
             VIE_TRY(fast_zinv((const c32*)A, (const c32*)w, wr, (c32*)y, yr, list, op.idx_map, (const float*)chi, n0, n1,
                               n2, op.Nb, nlines, P2, op.ax[2].roots32, op.stream));
-            tmr_end(TMR_ZINV, op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
+            tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
         } else {
             const FFTPlan& p = op.ax[2].plan;
             const int NL = lines_per_cta<T>(p.L);
             const long long nlines = (long long)ns * 3 * n0 * n1;
-            tmr_begin(TMR_ZINV, op.stream);
+            tmr_begin(tid(TMR_ZINV), op.stream);
             k_zinv<T><<<(unsigned)((nlines + NL - 1) / NL), 256, lines_smem<T>(p, NL), op.stream>>>(
                 A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), NL);
-            tmr_end(TMR_ZINV, op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
+            tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
         }

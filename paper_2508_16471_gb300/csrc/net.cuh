@@ -1,0 +1,68 @@
+// Learned initial guess network (see net.cu).
+#pragma once
+
+#include <vector>
+
+#include "krylov.cuh"
+
+namespace vie {
+
+constexpr int NET_IN = 10;  // input channels: chi, pol (Re/Im x3), khat (3)
+
+struct Net {
+    static constexpr int NL = 15;  // layers
+    enum Buf { IN = 0, E0A, CAT0, P0, E1A, CAT1, P1, E2A, CAT2, P2, BA, BB, D2A, D2B, D1A, D1B, D0A, D0B, OUT, NBUF };
+    struct Layer {
+        int ci = 0, co = 0, ks = 3;
+        long long nw = 0;
+        float *w = nullptr, *b = nullptr, *wt = nullptr, *gw = nullptr, *gb = nullptr;
+        float *mw = nullptr, *vw = nullptr, *mb = nullptr, *vb = nullptr;
+    };
+    int c[4] = {16, 32, 64, 128};
+    int bf16 = 1;
+    Layer L[NL];
+    long long nparams = 0;
+    int t = 0;  // Adam step
+    int D = 0, Bcap = 0;
+    void* act[NBUF] = {};
+    void* grd[NBUF] = {};
+    int ch_[NBUF] = {};
+    long long vox_[NBUF] = {};
+    float* d_loss = nullptr;
+    float mask_sum = 1.f;
+    std::vector<void*> owned;
+
+    ~Net();
+    int alloc(void** p, size_t bytes);
+    int init(const int* ch, unsigned long long seed, int store_bf16);
+    int reserve(int B, int D);
+    int set_input(const float* x_dev, int B, cudaStream_t s);
+    int get_output(float* y_dev, int B, cudaStream_t s);
+    int forward(int B, cudaStream_t s);
+    int backward(int B, cudaStream_t s);
+    int loss_grad(const float* t_dev, const float* m_dev, int B, cudaStream_t s, float* loss_host);
+    int adam(float lr, cudaStream_t s);
+    const float* bly_w(int l) const;
+
+    template <typename S> int forward_t(int B, cudaStream_t s);
+    template <typename S> int backward_t(int B, cudaStream_t s);
+    template <typename S> int conv_fwd(int l, int src, int src_c0, int dst, int dst_c0, int Dl, int B, int relu,
+                                       cudaStream_t s);
+    template <typename S> int conv_bwd(int l, int src, int src_c0, int dst, int dst_c0, int Dl, int B, int relu,
+                                       int want_dx, cudaStream_t s);
+};
+
+// features of the solver's RHS on the coarse grid (edge n/f per axis):
+// x [rhs][10][D^3] = (chi averaged over each f^3 block, Re/Im of the
+// polarisation, khat); when `w` is given also the training target
+// t [rhs][6][D^3] (block average over body voxels of
+// (E_tot - E_inc) exp(-i k0 khat.r), E_tot = w/chi) and the mask m [rhs][D^3]
+// (fraction of body voxels in the block)
+int net_features(Operator& op, const double* chans_dev, int n_rhs, int f, float* x, const c64* w, long long wstride,
+                 float* t, float* m, cudaStream_t s);
+// x0 on the fine body voxels: chi (E_inc + upsampled prediction y [rhs][6][D^3])
+int device_sum(const float* a, long long n, float* out_host, float* scratch, cudaStream_t s);
+int net_initial_guess(Operator& op, const double* chans_dev, int n_rhs, int f, const float* y, c64* x0,
+                      long long xstride, cudaStream_t s);
+
+}  // namespace vie

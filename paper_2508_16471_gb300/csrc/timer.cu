@@ -56,7 +56,8 @@ void flush() {
     t.pending.clear();
 }
 const char* kNames[TMR_COUNT] = {"zfwd", "yfwd", "xfused", "yinv", "zinv", "dots", "reduce_dots", "update",
-                                 "finish", "scale", "xupdate", "residual", "start_cycle", "rhs", "other"};
+                                 "finish", "scale", "xupdate", "residual", "start_cycle", "rhs", "other",
+                                 "matvec_fp64"};
 }  // namespace
 
 void tmr_begin(int id, cudaStream_t s) {

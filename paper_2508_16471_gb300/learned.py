@@ -1,0 +1,67 @@
+"""Training pipeline of the learned initial guess (solver-generated data).
+
+The library solves seeded random bodies, extracts (features, targets, mask)
+on the coarse grid with vie_net_features and trains the network with
+vie_net_train_step; all arithmetic runs in the library's kernels, PyTorch
+only holds the device buffers.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import inputs
+from . import vie as V
+
+
+def generate(n_axis, h, seeds, n_dirs, factor, restart=64, tol=1e-6, max_iter=20000):
+    """Solve one body per seed (all on one grid) and return device tensors
+    X [S][10][D^3], T [S][6][D^3], M [S][D^3] (float32) with S = 2 n_dirs per body,
+    plus the solver iteration counts."""
+    import torch
+    D = n_axis // factor
+    Vc = D ** 3
+    Xs, Ts, Ms, iters = [], [], [], []
+    hd = None
+    try:
+        for seed in seeds:
+            wl = inputs.random_body_workload(seed, n_axis=n_axis, h=h, n_dirs=n_dirs)
+            if hd is None:
+                hd = V.Handle(wl.grid.n, wl.grid.h, wl.eps, wl.k0)
+            else:
+                hd.set_eps(wl.eps)
+            chs = [(c.khat, c.pol) for c in wl.channels]
+            st = hd.solve(chs, tol=tol, restart=restart, max_iter=max_iter, allow_noconv=True)
+            R = len(chs)
+            x = torch.empty(R, 10, Vc, device="cuda")
+            t = torch.empty(R, 6, Vc, device="cuda")
+            m = torch.empty(R, Vc, device="cuda")
+            hd.net_features(factor, x.data_ptr(), t.data_ptr(), m.data_ptr())
+            Xs.append(x)
+            Ts.append(t)
+            Ms.append(m)
+            iters.append(st["iters"])
+    finally:
+        if hd is not None:
+            hd.close()
+    return torch.cat(Xs), torch.cat(Ts), torch.cat(Ms), np.concatenate(iters)
+
+
+def train(net, X, T, M, D, epochs=20, batch=8, lr=2e-3, seed=0, lr_decay=0.9):
+    """Minibatch Adam over the samples; returns the mean loss per epoch."""
+    import torch
+    S = X.shape[0]
+    rng = np.random.default_rng(seed)
+    hist = []
+    for ep in range(epochs):
+        perm = rng.permutation(S)
+        tot, nb = 0.0, 0
+        for b0 in range(0, S - batch + 1, batch):
+            idx = torch.as_tensor(perm[b0:b0 + batch], device=X.device)
+            xb = X.index_select(0, idx).contiguous()
+            tb = T.index_select(0, idx).contiguous()
+            mb = M.index_select(0, idx).contiguous()
+            tot += net.train_step(xb.data_ptr(), tb.data_ptr(), mb.data_ptr(), batch, D, lr)
+            nb += 1
+        hist.append(tot / max(nb, 1))
+        lr *= lr_decay
+    return hist

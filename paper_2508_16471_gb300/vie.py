@@ -23,7 +23,9 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_farfield", "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer",
            "vie_hom_map", "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines",
            "vie_get_info", "vie_kernel_launches", "vie_stream", "vie_destroy", "vie_last_error",
-           "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_apply_noalloc", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
+           "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_apply_noalloc", "vie_net_create", "vie_net_destroy", "vie_net_num_params",
+           "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
+           "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_guesses_rejected", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
 
 
 class VieError(RuntimeError):
@@ -87,6 +89,21 @@ def load():
     L.vie_fft_lines.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int]
     L.vie_get_info.argtypes = [P, C.POINTER(_Info)]
     L.vie_set_fft_path.argtypes = [P, C.c_int]
+    fp = C.POINTER(C.c_float)
+    L.vie_net_create.argtypes = [C.POINTER(C.c_int), C.c_ulonglong, C.c_int, C.POINTER(P)]
+    L.vie_net_destroy.argtypes = [P]
+    L.vie_net_destroy.restype = None
+    L.vie_net_num_params.argtypes = [P]
+    L.vie_net_num_params.restype = C.c_longlong
+    L.vie_net_get_params.argtypes = [P, fp]
+    L.vie_net_set_params.argtypes = [P, fp]
+    L.vie_net_forward.argtypes = [P, P, P, C.c_int, C.c_int]
+    L.vie_net_gradients.argtypes = [P, P, P, P, C.c_int, C.c_int, fp, fp]
+    L.vie_net_train_step.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_float, fp]
+    L.vie_net_features.argtypes = [P, C.c_int, P, P, P]
+    L.vie_attach_net.argtypes = [P, P, C.c_int]
+    L.vie_guesses_rejected.argtypes = [P]
+    L.vie_guesses_rejected.restype = C.c_int
     L.vie_set_farfield_engine.argtypes = [P, C.c_int]
     L.vie_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int]
     L.vie_kernel_launches.restype = C.c_longlong
@@ -107,7 +124,9 @@ def load():
     for f in ["vie_setup", "vie_set_eps", "vie_set_eps_device", "vie_solve", "vie_farfield",
               "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer", "vie_hom_map",
               "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines", "vie_get_info",
-              "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm"]:
+              "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_net_create",
+              "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
+              "vie_net_train_step", "vie_net_features", "vie_attach_net"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -226,6 +245,20 @@ class Handle:
     def set_farfield_engine(self, engine: int):
         _check(load().vie_set_farfield_engine(self._h, int(engine)))
 
+    def net_features(self, factor, x_ptr, t_ptr=None, m_ptr=None):
+        """Coarse-grid network features of the last solve's RHS (device float32
+        buffers: x [rhs][10][D^3], optional targets t [rhs][6][D^3], mask m [rhs][D^3])."""
+        _check(load().vie_net_features(self._h, int(factor), C.c_void_p(x_ptr),
+                                       C.c_void_p(t_ptr) if t_ptr else None,
+                                       C.c_void_p(m_ptr) if m_ptr else None))
+
+    def attach_net(self, net, factor):
+        _check(load().vie_attach_net(self._h, net.ptr if net is not None else None, int(factor)))
+        self._net = net  # keep alive
+
+    def guesses_rejected(self):
+        return int(load().vie_guesses_rejected(self._h))
+
     def set_eps(self, eps_r):
         eps = np.ascontiguousarray(eps_r, dtype=np.float64).reshape(self.n)
         _check(load().vie_set_eps(self._h, _dptr(eps)))
@@ -285,6 +318,63 @@ class Handle:
     def apply_device(self, w_ptr: int, y_ptr: int, n_rhs: int, precision=PREC_MIXED):
         _check(load().vie_apply_device(self._h, C.c_void_p(w_ptr), C.c_void_p(y_ptr), int(n_rhs),
                                        int(precision)))
+
+
+class Net:
+    """The learned initial-guess network (vie_net_*); device buffers are passed
+    as raw pointers (e.g. torch.Tensor.data_ptr())."""
+
+    def __init__(self, channels=(16, 32, 64, 128), seed=0, bf16=True):
+        L = load()
+        ch = (C.c_int * 4)(*[int(c) for c in channels])
+        p = C.c_void_p()
+        _check(L.vie_net_create(ch, C.c_ulonglong(seed), int(bool(bf16)), C.byref(p)))
+        self._p = p
+        self.channels = tuple(channels)
+
+    @property
+    def ptr(self):
+        return self._p
+
+    def close(self):
+        if getattr(self, "_p", None):
+            load().vie_net_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self):
+        return int(load().vie_net_num_params(self._p))
+
+    def get_params(self):
+        a = np.zeros(self.num_params(), dtype=np.float32)
+        _check(load().vie_net_get_params(self._p, a.ctypes.data_as(C.POINTER(C.c_float))))
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        assert a.size == self.num_params()
+        _check(load().vie_net_set_params(self._p, a.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def forward(self, x_ptr, y_ptr, B, D):
+        _check(load().vie_net_forward(self._p, C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(B), int(D)))
+
+    def gradients(self, x_ptr, t_ptr, m_ptr, B, D):
+        loss = C.c_float()
+        g = np.zeros(self.num_params(), dtype=np.float32)
+        _check(load().vie_net_gradients(self._p, C.c_void_p(x_ptr), C.c_void_p(t_ptr), C.c_void_p(m_ptr), int(B),
+                                        int(D), C.byref(loss), g.ctypes.data_as(C.POINTER(C.c_float))))
+        return float(loss.value), g
+
+    def train_step(self, x_ptr, t_ptr, m_ptr, B, D, lr):
+        loss = C.c_float()
+        _check(load().vie_net_train_step(self._p, C.c_void_p(x_ptr), C.c_void_p(t_ptr), C.c_void_p(m_ptr), int(B),
+                                         int(D), float(lr), C.byref(loss)))
+        return float(loss.value)
 
 
 def hom_transfer(E, omega=None, sigma=1.2, dtau=()):
