@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--bodies", type=int, default=8)
     p.add_argument("--restart", type=int, default=64)
-    p.add_argument("--inner-tol", type=float, default=1e-3,
+    p.add_argument("--inner-tol", type=float, default=1e-6,
                    help="mixed mode: relative residual reduction asked of each FP32 inner solve")
     p.add_argument("--plain-rhs", type=int, default=4)
     p.add_argument("--no-plain", action="store_true")
@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--apply-only", type=int, default=0,
                    help="profiling aid: one warm-up and one FP32 operator application with this many RHS on the "
                         "first bench body, then exit (no JSON line)")
+    p.add_argument("--apply-fp64", action="store_true",
+                   help="with --apply-only: apply the FP64 operator instead of the FP32 one")
     p.add_argument("--profile-solve", type=int, default=0,
                    help="profiling aid: a 12-iteration solve with this many RHS on the first bench body, then exit")
     return p.parse_args()
@@ -247,10 +249,11 @@ def run_ours(args):
         wl = inputs.random_body_workload(SEED0, n_axis=N_AXIS, h=H, n_dirs=N_DIRS)
         with V.Handle(wl.grid.n, wl.grid.h, wl.eps, wl.k0) as hd0:
             nb = hd0.info()["n_body"]
-            w = torch.randn(args.apply_only, 3, nb, dtype=torch.complex64, device="cuda")
+            dt, prec = (torch.complex128, V.PREC_FP64) if args.apply_fp64 else (torch.complex64, V.PREC_MIXED)
+            w = torch.randn(args.apply_only, 3, nb, dtype=dt, device="cuda")
             y = torch.empty_like(w)
             for _ in range(2):
-                hd0.apply_device(w.data_ptr(), y.data_ptr(), args.apply_only, V.PREC_MIXED)
+                hd0.apply_device(w.data_ptr(), y.data_ptr(), args.apply_only, prec)
             torch.cuda.synchronize()
         return 0
 

@@ -81,12 +81,16 @@ typedef struct vie_solve_opts {
     int max_iter;      /* cap on inner iterations per RHS (default 5000)         */
     int precision;     /* VIE_PREC_MIXED (default) or VIE_PREC_FP64              */
     double inner_tol;  /* mixed mode: relative reduction asked of each FP32 inner
-                          solve (default 1e-3)                                    */
+                          solve, floored at 0.3 tol ||b|| (default 1e-6)          */
     int use_x0;        /* 0: x0 = 0; 1: start from the currents stored in the
                           handle (same n_rhs, restart and precision as the previous
-                          solve); 2: initial currents predicted by the network
-                          attached with vie_attach_net.  A supplied guess whose
-                          FP64 residual is not below ||b|| is replaced by zero.  */
+                          solve); 2: initial currents from the network attached
+                          with vie_attach_net: the prediction x0 = b + s (Born
+                          term b plus the network's scattered-field correction s)
+                          enters as beta b + alpha s with (beta, alpha) minimising
+                          the residual norm (needs restart >= 3).  A supplied
+                          guess whose FP64 residual is not below ||b|| is
+                          replaced by zero.                                       */
     int reserved[3];
 } vie_solve_opts;
 
@@ -263,11 +267,12 @@ int vie_get_info(const vie_handle* hd, vie_info* info);
  * (constant channels) -- to 6 output channels, the scattered part of the
  * total field with the incident phase removed, (E_tot - E_inc) e^{-i k0 khat.r},
  * averaged over each block's body voxels.  The solver turns the prediction
- * into x0 = chi (E_inc + upsampled prediction e^{i k0 khat.r}) (use_x0 = 2);
- * plain GMRES from x0 = 0 is the fallback, chosen per RHS by the FP64
- * residual.  Activations in bf16 (or FP32 for gradient checks), weights FP32
+ * into b + s, b = chi E_inc and s = chi (upsampled prediction e^{i k0 khat.r}),
+ * and starts from the residual-minimising combination beta b + alpha s
+ * (use_x0 = 2); plain GMRES from x0 = 0 is the fallback, chosen per RHS by
+ * the FP64 residual.  The paper's method is not learned: this part is an
+ * addition of this library.  Activations in bf16 (or FP32 for gradient checks), weights FP32
  * masters, every sum in FP32; trained with Adam on solver-generated data.
- * The paper has no learned component; this is the build's systems pattern.
  * Device arrays: x [B][10][D^3], y / t [B][6][D^3], m [B][D^3] (float32),
  * on the current device; these calls synchronise the device's null stream. */
 typedef struct vie_net vie_net;

@@ -146,7 +146,7 @@ void vie_default_opts(vie_solve_opts* o) {
     o->restart = 30;
     o->max_iter = 5000;
     o->precision = VIE_PREC_MIXED;
-    o->inner_tol = 1e-3;
+    o->inner_tol = 1e-6;
     o->use_x0 = 0;
 }
 

@@ -55,18 +55,48 @@ __device__ __forceinline__ void dft4(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2, cplx
 #define VIE_COS_PI8 0.92387953251128675613
 #define VIE_SIN_PI8 0.38268343236508977173
 
-// twiddle w_N^k = exp(-+ 2 pi i k / N) for the radix-8/16 inner combinations
-template <typename T, bool INV> __device__ __forceinline__ cplx<T> w8(int k) {
-    const T c = (T)VIE_SQRT1_2;
-    cplx<T> w;
-    switch (k & 7) {
-        case 0: w = {1, 0}; break;
-        case 1: w = {c, -c}; break;
-        case 2: w = {0, -1}; break;
-        default: w = {-c, -c}; break;  // k = 3
+// cos(2 pi m / 32) for m = 0..8 (the first octant; the rest by symmetry)
+template <typename T> __device__ __forceinline__ T cos32(int m) {
+    switch (m) {
+        case 0: return (T)1.0;
+        case 1: return (T)0.98078528040323044913;
+        case 2: return (T)VIE_COS_PI8;
+        case 3: return (T)0.83146961230254523708;
+        case 4: return (T)VIE_SQRT1_2;
+        case 5: return (T)0.55557023301960222474;
+        case 6: return (T)VIE_SIN_PI8;
+        case 7: return (T)0.19509032201612826785;
+        default: return (T)0.0;
     }
-    if (INV) w.y = -w.y;
-    return w;
+}
+
+// a * w_N^k, w_N = exp(-+ 2 pi i / N), N a divisor of 32, 0 <= k < N.  Used
+// with k known after unrolling: the multiples of pi/4 reduce to sign swaps
+// or one shared scaling, instead of a full complex product with 0 / +-1
+// entries that IEEE rules (signed zeros, NaN) forbid the compiler to drop.
+template <typename T, int N, bool INV> __device__ __forceinline__ cplx<T> rootmul(cplx<T> a, int k) {
+    const T h = (T)VIE_SQRT1_2;
+    if (k == 0) return a;
+    if (4 * k == N) return mul_mi<T, INV>(a);
+    if (2 * k == N) return cplx<T>{-a.x, -a.y};
+    if (4 * k == 3 * N) return mul_mi<T, !INV>(a);
+    if (8 * k == N)  // (1 -+ i) / sqrt2
+        return INV ? cplx<T>{h * (a.x - a.y), h * (a.x + a.y)} : cplx<T>{h * (a.x + a.y), h * (a.y - a.x)};
+    if (8 * k == 3 * N)  // (-1 -+ i) / sqrt2
+        return INV ? cplx<T>{-h * (a.x + a.y), h * (a.x - a.y)} : cplx<T>{h * (a.y - a.x), -h * (a.x + a.y)};
+    // general root: angle 2 pi m / 32, m = 32 k / N in (0, 32)
+    const int m = k * (32 / N);
+    const int q = m & 7, oct = m >> 3;  // octant and offset within it
+    T c = cos32<T>(q), sn = cos32<T>(8 - q);  // cos and sin of 2 pi q / 32
+    T cs, si;
+    switch (oct) {
+        case 0: cs = c; si = sn; break;
+        case 1: cs = -sn; si = c; break;
+        case 2: cs = -c; si = -sn; break;
+        default: cs = sn; si = -c; break;
+    }
+    const cplx<T> w = INV ? cplx<T>{cs, si} : cplx<T>{cs, -si};
+    return w * a;
 }
 
 template <typename T, bool INV> __device__ __forceinline__ void dft8(cplx<T>* a) {
@@ -78,27 +108,10 @@ template <typename T, bool INV> __device__ __forceinline__ void dft8(cplx<T>* a)
     cplx<T> E[4] = {e0, e1, e2, e3}, O[4] = {o0, o1, o2, o3};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        cplx<T> t = w8<T, INV>(k) * O[k];
+        cplx<T> t = rootmul<T, 8, INV>(O[k], k);
         a[k] = E[k] + t;
         a[k + 4] = E[k] - t;
     }
-}
-
-template <typename T, bool INV> __device__ __forceinline__ cplx<T> w16(int k) {
-    const T c1 = (T)VIE_COS_PI8, s1 = (T)VIE_SIN_PI8, h = (T)VIE_SQRT1_2;
-    cplx<T> w;
-    switch (k) {
-        case 0: w = {1, 0}; break;
-        case 1: w = {c1, -s1}; break;
-        case 2: w = {h, -h}; break;
-        case 3: w = {s1, -c1}; break;
-        case 4: w = {0, -1}; break;
-        case 5: w = {-s1, -c1}; break;
-        case 6: w = {-h, -h}; break;
-        default: w = {-c1, -s1}; break;  // k = 7
-    }
-    if (INV) w.y = -w.y;
-    return w;
 }
 
 template <typename T, bool INV> __device__ __forceinline__ void dft16(cplx<T>* a) {
@@ -112,7 +125,7 @@ template <typename T, bool INV> __device__ __forceinline__ void dft16(cplx<T>* a
     dft8<T, INV>(O);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        cplx<T> t = w16<T, INV>(k) * O[k];
+        cplx<T> t = rootmul<T, 16, INV>(O[k], k);
         a[k] = E[k] + t;
         a[k + 8] = E[k] - t;
     }

@@ -14,27 +14,6 @@
 
 namespace vie {
 
-#define VIE_C32_1 0.98078528040323044913
-#define VIE_C32_3 0.83146961230254523708
-#define VIE_C32_5 0.55557023301960222474
-#define VIE_C32_7 0.19509032201612826785
-
-// w_32^k = exp(-+ 2 pi i k / 32), k = 0..15
-template <typename T, bool INV> __device__ __forceinline__ cplx<T> w32(int k) {
-    const T c[9] = {(T)1.0, (T)VIE_C32_1, (T)VIE_COS_PI8, (T)VIE_C32_3, (T)VIE_SQRT1_2,
-                    (T)VIE_C32_5, (T)VIE_SIN_PI8, (T)VIE_C32_7, (T)0.0};
-    // angle 2 pi k / 32 for k in [0, 16): cos = c[k] (k <= 8) or -c[16-k]; sin = c[8-k] (k <= 8) or c[k-8]
-    T cs, sn;
-    if (k <= 8) {
-        cs = c[k];
-        sn = c[8 - k];
-    } else {
-        cs = -c[16 - k];
-        sn = c[k - 8];
-    }
-    return INV ? cplx<T>{cs, sn} : cplx<T>{cs, -sn};
-}
-
 template <typename T, bool INV> __device__ __forceinline__ void dft32(cplx<T>* a) {
     cplx<T> E[16], O[16];
 #pragma unroll
@@ -46,7 +25,7 @@ template <typename T, bool INV> __device__ __forceinline__ void dft32(cplx<T>* a
     dft16<T, INV>(O);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-        cplx<T> t = w32<T, INV>(k) * O[k];
+        cplx<T> t = rootmul<T, 32, INV>(O[k], k);
         a[k] = E[k] + t;
         a[k + 16] = E[k] - t;
     }
@@ -59,6 +38,53 @@ template <typename T, int R, bool INV> __device__ __forceinline__ void dftp2(cpl
     else if constexpr (R == 8) dft8<T, INV>(a);
     else if constexpr (R == 16) dft16<T, INV>(a);
     else dft32<T, INV>(a);
+}
+
+// R-point DFT whose inputs a[R/2 .. R) are zero (the zero-padded half):
+// X[2m] = DFT_{R/2}(a)[m], X[2m+1] = DFT_{R/2}(a[n] w_R^n)[m]; reads a[0..R/2),
+// writes a[0..R).
+template <typename T, int R, bool INV> __device__ __forceinline__ void dftp2_half_in(cplx<T>* a) {
+    if constexpr (R == 1) {
+    } else if constexpr (R == 2) {
+        a[1] = a[0];
+    } else {
+        constexpr int H = R / 2;
+        cplx<T> E[H], O[H];
+#pragma unroll
+        for (int n = 0; n < H; ++n) {
+            E[n] = a[n];
+            O[n] = rootmul<T, R, INV>(a[n], n);
+        }
+        dftp2<T, H, INV>(E);
+        dftp2<T, H, INV>(O);
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+            a[2 * m] = E[m];
+            a[2 * m + 1] = O[m];
+        }
+    }
+}
+
+// R-point DFT of which only the outputs X[0 .. R/2) are wanted (the crop):
+// X[n] = E[n] + w_R^n O[n] with E, O the DFTs of the even and odd inputs;
+// writes a[0..R/2).
+template <typename T, int R, bool INV> __device__ __forceinline__ void dftp2_half_out(cplx<T>* a) {
+    if constexpr (R == 1) {
+    } else if constexpr (R == 2) {
+        a[0] = a[0] + a[1];
+    } else {
+        constexpr int H = R / 2;
+        cplx<T> E[H], O[H];
+#pragma unroll
+        for (int n = 0; n < H; ++n) {
+            E[n] = a[2 * n];
+            O[n] = a[2 * n + 1];
+        }
+        dftp2<T, H, INV>(E);
+        dftp2<T, H, INV>(O);
+#pragma unroll
+        for (int n = 0; n < H; ++n) a[n] = E[n] + rootmul<T, R, INV>(O[n], n);
+    }
 }
 
 // Factorisations used by the fast path.

@@ -446,6 +446,121 @@ __global__ void k_residual_lo(const c64* __restrict__ b, c64* __restrict__ res, 
     }
 }
 
+// ---- learned guess: minimal-residual combination ---------------------------
+// The network supplies x0 = b + s (b = chi E_inc, the Born term; s its
+// scattered-field correction).  The start used is x0 = beta b + alpha s with
+// (beta, alpha) minimising ||b - A (beta b + alpha s)|| (a 2 x 2 Hermitian
+// least-squares problem formed with the working-precision operator), so
+// the start is never worse than the best multiple of b, which is the first
+// GMRES step from zero.  Basis slots: 0 = b, 1 = s, 2 = A b, 3 = A s.
+template <typename T>
+__global__ void k_guess_split(const c64* __restrict__ x, const c64* __restrict__ b, long long stride,
+                              cplx<T>* __restrict__ V, long long vrs, long long vstride, const int* __restrict__ list,
+                              long long n) {
+    const int r = list[blockIdx.y];
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) {
+            const c64 bv = b[r * stride + e], xv = x[r * stride + e];
+            V[r * vrs + e] = cplx<T>{(T)bv.x, (T)bv.y};
+            V[r * vrs + vstride + e] = cplx<T>{(T)(xv.x - bv.x), (T)(xv.y - bv.y)};
+        }
+    }
+}
+
+// block partials of <Ab,Ab>, <Ab,As>, <As,As>, <Ab,b>, <As,b>  (<u,v> = sum conj(u) v)
+template <typename T>
+__global__ void k_guess_dots(const cplx<T>* __restrict__ V, long long vrs, long long vstride,
+                             const int* __restrict__ list, c64* __restrict__ partial, int pstride, long long n,
+                             int nblk) {
+    __shared__ double sm[10][KB / 32];
+    const int r = list[blockIdx.y];
+    const cplx<T>* Vr = V + r * vrs;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+    double q[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) {
+            const c64 bb = ld64(Vr, e), ab = ld64(Vr + 2 * vstride, e), as = ld64(Vr + 3 * vstride, e);
+            q[0] += ab.x * ab.x + ab.y * ab.y;
+            q[2] += ab.x * as.x + ab.y * as.y;
+            q[3] += ab.x * as.y - ab.y * as.x;
+            q[4] += as.x * as.x + as.y * as.y;
+            q[6] += ab.x * bb.x + ab.y * bb.y;
+            q[7] += ab.x * bb.y - ab.y * bb.x;
+            q[8] += as.x * bb.x + as.y * bb.y;
+            q[9] += as.x * bb.y - as.y * bb.x;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const double v = warp_sum(q[i]);
+        if ((threadIdx.x & 31) == 0) sm[i][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double re = 0, im = 0;
+        for (int w = 0; w < KB / 32; ++w) {
+            re += sm[2 * threadIdx.x][w];
+            im += sm[2 * threadIdx.x + 1][w];
+        }
+        partial[((long long)r * pstride + threadIdx.x) * nblk + blockIdx.x] = c64{re, im};
+    }
+}
+
+// per RHS: (beta, alpha) into coef[r][0..1]
+__global__ void k_guess_coef(const c64* __restrict__ partial, int pstride, int nblk, c64* __restrict__ coef,
+                             int cstride, const int* __restrict__ list, int nr) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nr) return;
+    const int r = list[s];
+    c64 g[5];
+    for (int i = 0; i < 5; ++i) {
+        double re = 0, im = 0;
+        const c64* p = partial + ((long long)r * pstride + i) * nblk;
+        for (int b = 0; b < nblk; ++b) {
+            re += p[b].x;
+            im += p[b].y;
+        }
+        g[i] = c64{re, im};
+    }
+    const double g11 = g[0].x, g22 = g[2].x;
+    const c64 g12 = g[1], c1 = g[3], c2 = g[4];
+    const double det = g11 * g22 - (g12.x * g12.x + g12.y * g12.y);
+    c64 beta{0, 0}, alpha{0, 0};
+    if (g11 > 0 && g22 > 0 && det > 1e-10 * g11 * g22) {
+        // beta = (g22 c1 - g12 c2) / det, alpha = (g11 c2 - conj(g12) c1) / det
+        const c64 t = g12 * c2;
+        beta = c64{(g22 * c1.x - t.x) / det, (g22 * c1.y - t.y) / det};
+        const c64 u = conjg(g12) * c1;
+        alpha = c64{(g11 * c2.x - u.x) / det, (g11 * c2.y - u.y) / det};
+    } else if (g11 > 0) {
+        beta = c64{c1.x / g11, c1.y / g11};
+    }
+    coef[(long long)r * cstride] = beta;
+    coef[(long long)r * cstride + 1] = alpha;
+}
+
+// x = beta b + alpha (x - b)
+__global__ void k_guess_combine(c64* __restrict__ x, const c64* __restrict__ b, long long stride,
+                                const c64* __restrict__ coef, int cstride, const int* __restrict__ list, long long n) {
+    const int r = list[blockIdx.y];
+    const c64 beta = coef[(long long)r * cstride], alpha = coef[(long long)r * cstride + 1];
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) {
+            const c64 bv = b[r * stride + e], xv = x[r * stride + e];
+            const c64 sv{xv.x - bv.x, xv.y - bv.y};
+            x[r * stride + e] = beta * bv + alpha * sv;
+        }
+    }
+}
+
 // initial guess worse than zero: x = 0, r = b, ||r|| = ||b||
 __global__ void k_reset_guess(c64* __restrict__ x, c64* __restrict__ res, const c64* __restrict__ b, long long stride,
                               double* __restrict__ rnorm, const double* __restrict__ bnorm,
@@ -604,12 +719,36 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
     for (int r = 0; r < R; ++r)
         if (!(hb[r] > 0) || !std::isfinite(hb[r])) return fail(VIE_EINVAL, "right-hand side is zero or not finite");
 
+    if (o.use_x0 == 2 && m >= 3) {
+        // learned guess x0 = b + s: keep the minimal-residual combination of b and s
+        VIE_TRY(op_set_list(op, outer_active.data(), R));
+        tmr_begin(TMR_OTHER, st);
+        k_guess_split<T><<<gv, KB, 0, st>>>(S.x, S.b, n, V, vrs, n, op.d_list, n);
+        tmr_end(TMR_OTHER, st);
+        LAUNCH_CHECK();
+        VIE_TRY(op_apply(op, prec_in, V, vrs, V + 2 * n, vrs, op.d_list, R));
+        VIE_TRY(op_apply(op, prec_in, V + n, vrs, V + 3 * n, vrs, op.d_list, R));
+        if (prec_in == VIE_PREC_FP64) out.matvecs64 += 2 * R;
+        else out.matvecs32 += 2 * R;
+        tmr_begin(TMR_OTHER, st);
+        k_guess_dots<T><<<gv, KB, 0, st>>>(V, vrs, n, op.d_list, S.partial, mp1 + 1, n, nblk);
+        LAUNCH_CHECK();
+        k_guess_coef<<<ceil_div(R, 64), 64, 0, st>>>(S.partial, mp1 + 1, nblk, S.y, m, op.d_list, R);
+        LAUNCH_CHECK();
+        k_guess_combine<<<gv, KB, 0, st>>>(S.x, S.b, n, S.y, m, op.d_list, n);
+        tmr_end(TMR_OTHER, st);
+        LAUNCH_CHECK();
+    }
+
     bool first = !o.use_x0;
     bool guess_pending = o.use_x0 != 0;
     std::vector<int> done(R, 0);
     // 1: the next residual of this RHS is the FP64 one (a convergence check);
     // 0: a restart residual in the working precision suffices
-    std::vector<int> need64(R, 1), stopped(R, 0);
+    // sticky64: the residual (of either precision) has come within reach of
+    // the working precision's accuracy (rel < 1e-5), so every later restart
+    // of this RHS uses the FP64 residual (a working-precision one would stall)
+    std::vector<int> need64(R, 1), stopped(R, 0), sticky64(R, 0);
     out.matvecs32 = out.matvecs64 = 0;
     out.guesses_rejected = 0;
     while (true) {
@@ -691,6 +830,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         bool recheck = false;
         for (int r : act) {
             const double rel = hr[r] / hb[r];
+            if (rel < 1e-5) sticky64[r] = 1;
             if (!exact[r] && (rel <= o.tol || !std::isfinite(rel) || it[r] >= o.max_iter)) {
                 // a working-precision residual decides nothing: confirm in FP64
                 need64[r] = 1;
@@ -784,7 +924,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         tmr_end(TMR_XUPDATE, st, (double)steps_sum * n * ET + 2.0 * nc * n * 16.0);
         LAUNCH_CHECK();
         // met the target or spent the budget: FP64 check; ran out of m steps: restart residual
-        for (int r : all_cyc) need64[r] = stopped[r];
+        for (int r : all_cyc) need64[r] = stopped[r] || sticky64[r];
     }
     out.converged = 0;
     out.iters_max = 0;

@@ -266,8 +266,10 @@ __global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict_
 
 // Pass 3: FFT x, spectral multiply by the 3x3 symmetric kernel, inverse FFT x.
 // B [slot][3][n0][inner], inner = P1 * P2; updated in place for x < n0.
+// Two CTAs per SM: the transform stages are separated by CTA barriers, so a
+// second resident CTA keeps the (FP64-bound) pipes busy while one waits.
 template <typename T>
-__global__ void k_xfused(cplx<T>* __restrict__ B, int n0, long long inner, int P0, int P1, int P2,
+__global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int n0, long long inner, int P0, int P1, int P2,
                          const cplx<T>* __restrict__ khat, int H0, int H1, int H2, FFTPlan plan,
                          const cplx<T>* __restrict__ twg, int TW) {
     extern __shared__ __align__(16) unsigned char smraw[];

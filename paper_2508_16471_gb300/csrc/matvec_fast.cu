@@ -45,7 +45,9 @@ template <bool INV> __device__ __forceinline__ c32 tw(const c32* t, int i) {
 }
 
 // ---- strided axis: in [outer][n_in][inner] -> out [outer][n_out][inner] ------
-template <int L, bool INV>
+// HALF: the forward input (n_in) or the inverse output (n_out) spans at most
+// L/2 rows, so the radix-R1 step next to it is a half DFT.
+template <int L, bool INV, bool HALF>
 __global__ void __launch_bounds__(Fac<L>::R2 * AX_TW) k_axis_r(const c32* __restrict__ in, c32* __restrict__ out,
                                                                long long inner, int n_in, int n_out,
                                                                const c32* __restrict__ tw4) {
@@ -64,11 +66,12 @@ __global__ void __launch_bounds__(Fac<L>::R2 * AX_TW) k_axis_r(const c32* __rest
         c32 a[R1];
         const bool ok = i0 + t < inner;
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) {
+        for (int n1 = 0; n1 < (HALF ? R1 / 2 : R1); ++n1) {
             const int p = n1 * R2 + n2;
             a[n1] = (ok && p < n_in) ? in[(o * n_in + p) * inner + i0 + t] : z32();
         }
-        dftp2<float, R1, false>(a);
+        if (HALF) dftp2_half_in<float, R1, false>(a);
+        else dftp2<float, R1, false>(a);
 #pragma unroll
         for (int k1 = 1; k1 < R1; ++k1) a[k1] = a[k1] * tw<false>(T, k1 * R2 + n2);
 #pragma unroll
@@ -106,10 +109,11 @@ __global__ void __launch_bounds__(Fac<L>::R2 * AX_TW) k_axis_r(const c32* __rest
         c32 a[R1];
 #pragma unroll
         for (int k1 = 0; k1 < R1; ++k1) a[k1] = S[k1 * SR + n2 * TW + t];
-        dftp2<float, R1, true>(a);
+        if (HALF) dftp2_half_out<float, R1, true>(a);
+        else dftp2<float, R1, true>(a);
         if (i0 + t < inner) {
 #pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) {
+            for (int n1 = 0; n1 < (HALF ? R1 / 2 : R1); ++n1) {
                 const int p = n1 * R2 + n2;
                 if (p < n_out) out[(o * n_out + p) * inner + i0 + t] = a[n1];
             }
@@ -120,12 +124,19 @@ __global__ void __launch_bounds__(Fac<L>::R2 * AX_TW) k_axis_r(const c32* __rest
 // ---- fused x pass: forward FFT x, 3x3 spectral multiply, inverse FFT x ------
 // One CTA per tile of XF_TW (y, z)-frequency columns; it stages the kernel
 // octant rows of its columns in shared memory once (x-folded, y/z signs
-// applied) and loops over all RHS slots.
+// applied) and loops over all RHS slots.  The x support of the data is
+// n0 <= L/2 rows (zero padding) and only those rows are written back (crop),
+// so the first forward and the last inverse radix-R1 steps take the half
+// DFTs.  For L <= 256 the global loads of the next slot are issued before the
+// arithmetic of the current one (register double buffering), so their
+// latency overlaps the FFTs.
 template <int L> struct XF {
     static constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2, TW = XF_TW, NT = R2 * TW;
     static constexpr int SR = R2 * TW + 8;  // padded exchange row (conflict-free half-warps)
     static constexpr int SC = R1 * SR;      // one component
     static constexpr int HX = L / 2 + 1;    // folded x rows of the kernel tile
+    static constexpr int HR = R1 / 2;       // non-zero input rows per thread
+    static constexpr bool PF = L <= 256;    // prefetch the next slot
     static constexpr size_t smem = sizeof(c32) * (2 * L + 6 * (size_t)HX * TW + 3 * (size_t)SC);
 };
 
@@ -134,7 +145,8 @@ __global__ void __launch_bounds__(XF<L>::NT) k_xfused_r(c32* __restrict__ B, int
                                                        int P2, const c32* __restrict__ khat, int H0, int H1, int H2,
                                                        const c32* __restrict__ tw4, int nslots) {
     constexpr int R1 = XF<L>::R1, R2 = XF<L>::R2, TW = XF<L>::TW, NT = XF<L>::NT;
-    constexpr int SR = XF<L>::SR, SC = XF<L>::SC, HX = XF<L>::HX;
+    constexpr int SR = XF<L>::SR, SC = XF<L>::SC, HX = XF<L>::HX, HR = XF<L>::HR;
+    constexpr bool PF = XF<L>::PF;
     extern __shared__ __align__(16) unsigned char smraw[];
     c32* TA = reinterpret_cast<c32*>(smraw);
     c32* TB = TA + L;
@@ -163,26 +175,41 @@ __global__ void __launch_bounds__(XF<L>::NT) k_xfused_r(c32* __restrict__ B, int
     }
     const int t = threadIdx.x % TW, n2 = threadIdx.x / TW;
     const bool okt = i0 + t < inner;
-    __syncthreads();
-    for (int slot = 0; slot < nslots; ++slot) {
-        c32* base = B + (long long)slot * 3 * n0 * inner;
-        // issue the loads of all three components before any arithmetic
-        c32 a[3][R1];
+    const long long cs = (long long)n0 * inner;        // component stride
+    const long long rs = (long long)R2 * inner;        // stride between a thread's rows
+    c32* const col = B + (long long)n2 * inner + i0 + t;  // row n2 of this thread's column, slot 0, component 0
+    c32 pre[3][HR];
+    auto load = [&](int slot) {
+        const c32* q = col + (long long)slot * 3 * cs;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) {
-                const int p = n1 * R2 + n2;
-                a[c][n1] = (okt && p < n0) ? base[((long long)c * n0 + p) * inner + i0 + t] : z32();
-            }
+            for (int n1 = 0; n1 < HR; ++n1)
+                pre[c][n1] = (okt && n1 * R2 + n2 < n0) ? q[c * cs + n1 * rs] : z32();
+    };
+    if (PF) load(0);
+    __syncthreads();
+    for (int slot = 0; slot < nslots; ++slot) {
+        c32* base = B + (long long)slot * 3 * cs;
+        c32 a[3][R1];
+        if (!PF) load(slot);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            dftp2<float, R1, false>(a[c]);
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int k1 = 1; k1 < R1; ++k1) a[c][k1] = a[c][k1] * tw<false>(TA, k1 * R2 + n2);
+            for (int n1 = 0; n1 < HR; ++n1) a[c][n1] = pre[c][n1];
+        if (PF && slot + 1 < nslots) load(slot + 1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dftp2_half_in<float, R1, false>(a[c]);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) {
+            const c32 w = tw<false>(TA, k1 * R2 + n2);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a[c][k1] = a[c][k1] * w;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int k1 = 0; k1 < R1; ++k1) S[c * SC + k1 * SR + n2 * TW + t] = a[c][k1];
-        }
         __syncthreads();
         for (int it = threadIdx.x; it < R1 * TW; it += NT) {
             const int k1 = it / TW, tt = it % TW;
@@ -196,22 +223,24 @@ __global__ void __launch_bounds__(XF<L>::NT) k_xfused_r(c32* __restrict__ B, int
             dftp2<float, R2, false>(bx);
             dftp2<float, R2, false>(by);
             dftp2<float, R2, false>(bz);
+            // kx = k1 + R1 k2 folds to L - kx above L/2: for k2 < R2/2 never, for
+            // k2 > R2/2 always, for k2 = R2/2 unless k1 = 0
+            const c32* kp = Kt + k1 * TW + tt;        // row kx
+            const c32* km = Kt + (L - k1) * TW + tt;  // row L - kx (plus R1 k2 rows)
 #pragma unroll
             for (int k2 = 0; k2 < R2; ++k2) {
-                const int kx = k1 + R1 * k2;
-                const bool flx = 2 * kx > L;
-                const int fx = flx ? L - kx : kx;
-                const c32* kt = Kt + fx * TW + tt;
+                const bool flx = 2 * k2 > R2 || (2 * k2 == R2 && k1 > 0);
+                const c32* kt = flx ? km - R1 * k2 * TW : kp + R1 * k2 * TW;
                 c32 kxx = kt[0], kxy = kt[HX * TW], kxz = kt[2 * HX * TW];
                 const c32 kyy = kt[3 * HX * TW], kyz = kt[4 * HX * TW], kzz = kt[5 * HX * TW];
                 if (flx) {
                     kxy = c32{-kxy.x, -kxy.y};
                     kxz = c32{-kxz.x, -kxz.y};
                 }
-                const c32 a = bx[k2], b = by[k2], cc = bz[k2];
-                bx[k2] = kxx * a + kxy * b + kxz * cc;
-                by[k2] = kxy * a + kyy * b + kyz * cc;
-                bz[k2] = kxz * a + kyz * b + kzz * cc;
+                const c32 a0 = bx[k2], b0 = by[k2], c0 = bz[k2];
+                bx[k2] = kxx * a0 + kxy * b0 + kxz * c0;
+                by[k2] = kxy * a0 + kyy * b0 + kyz * c0;
+                bz[k2] = kxz * a0 + kyz * b0 + kzz * c0;
             }
             dftp2<float, R2, true>(bx);
             dftp2<float, R2, true>(by);
@@ -228,15 +257,14 @@ __global__ void __launch_bounds__(XF<L>::NT) k_xfused_r(c32* __restrict__ B, int
         if (okt) {
 #pragma unroll 1
             for (int c = 0; c < 3; ++c) {
-                c32 a[R1];
+                c32 o[R1];
 #pragma unroll
-                for (int k1 = 0; k1 < R1; ++k1) a[k1] = S[c * SC + k1 * SR + n2 * TW + t];
-                dftp2<float, R1, true>(a);
+                for (int k1 = 0; k1 < R1; ++k1) o[k1] = S[c * SC + k1 * SR + n2 * TW + t];
+                dftp2_half_out<float, R1, true>(o);
+                c32* q = base + c * cs + (long long)n2 * inner + i0 + t;
 #pragma unroll
-                for (int n1 = 0; n1 < R1; ++n1) {
-                    const int p = n1 * R2 + n2;
-                    if (p < n0) base[((long long)c * n0 + p) * inner + i0 + t] = a[n1];
-                }
+                for (int n1 = 0; n1 < HR; ++n1)
+                    if (n1 * R2 + n2 < n0) q[n1 * rs] = o[n1];
             }
         }
         __syncthreads();
@@ -270,7 +298,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_zfwd_r(const c32* __restrict__ w,
         const c32* wr = w + (long long)list[slot] * w_rstride + c * Nb;
         const int* im = idx_map + xy * n2;
 #pragma unroll
-        for (int n1i = 0; n1i < R1; ++n1i) {
+        for (int n1i = 0; n1i < R1 / 2; ++n1i) {  // n2 <= L/2: the upper half is padding
             const int z = n1i * R2 + q2;
             c32 v = z32();
             if (z < n2) {
@@ -281,10 +309,10 @@ __global__ void __launch_bounds__(Z_THREADS) k_zfwd_r(const c32* __restrict__ w,
         }
     } else {
 #pragma unroll
-        for (int n1i = 0; n1i < R1; ++n1i) a[n1i] = z32();
+        for (int n1i = 0; n1i < R1 / 2; ++n1i) a[n1i] = z32();
     }
     __syncthreads();
-    dftp2<float, R1, false>(a);
+    dftp2_half_in<float, R1, false>(a);
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) a[k1] = a[k1] * tw<false>(TA, k1 * R2 + q2);
 #pragma unroll
@@ -336,7 +364,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_zinv_r(const c32* __restrict__ A,
     c32 a[R1];
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) a[k1] = S[(l * R1 + k1) * RS + q2];
-    dftp2<float, R1, true>(a);
+    dftp2_half_out<float, R1, true>(a);  // only z < n2 <= L/2 is kept
     const long long plane = (long long)n0 * n1;
     const long long sc = line / plane;
     const long long xy = line - sc * plane;
@@ -346,7 +374,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_zinv_r(const c32* __restrict__ A,
     c32* yr = y + rr * y_rstride + c * Nb;
     const int* im = idx_map + xy * n2;
 #pragma unroll
-    for (int n1i = 0; n1i < R1; ++n1i) {
+    for (int n1i = 0; n1i < R1 / 2; ++n1i) {
         const int z = n1i * R2 + q2;
         if (z < n2) {
             const int vi = im[z];
@@ -370,12 +398,23 @@ template <int L> int launch_axis_r(const c32* in, c32* out, long long outer, int
     constexpr int NT = Fac<L>::R2 * AX_TW;
     const size_t sm = sizeof(c32) * (L + (size_t)L * AX_TW);
     const long long grid = outer * ((inner + AX_TW - 1) / AX_TW);
+    const bool half = 2 * (inv ? n_out : n_in) <= L;
     if (inv) {
-        VIE_TRY(set_smem(k_axis_r<L, true>, sm));
-        k_axis_r<L, true><<<(unsigned)grid, NT, sm, s>>>(in, out, inner, n_in, n_out, tw4);
+        if (half) {
+            VIE_TRY(set_smem(k_axis_r<L, true, true>, sm));
+            k_axis_r<L, true, true><<<(unsigned)grid, NT, sm, s>>>(in, out, inner, n_in, n_out, tw4);
+        } else {
+            VIE_TRY(set_smem(k_axis_r<L, true, false>, sm));
+            k_axis_r<L, true, false><<<(unsigned)grid, NT, sm, s>>>(in, out, inner, n_in, n_out, tw4);
+        }
     } else {
-        VIE_TRY(set_smem(k_axis_r<L, false>, sm));
-        k_axis_r<L, false><<<(unsigned)grid, NT, sm, s>>>(in, out, inner, n_in, n_out, tw4);
+        if (half) {
+            VIE_TRY(set_smem(k_axis_r<L, false, true>, sm));
+            k_axis_r<L, false, true><<<(unsigned)grid, NT, sm, s>>>(in, out, inner, n_in, n_out, tw4);
+        } else {
+            VIE_TRY(set_smem(k_axis_r<L, false, false>, sm));
+            k_axis_r<L, false, false><<<(unsigned)grid, NT, sm, s>>>(in, out, inner, n_in, n_out, tw4);
+        }
     }
     return VIE_OK;
 }
@@ -384,6 +423,7 @@ template <int L> int launch_xfused_r(c32* B, int n0, long long inner, int P1, in
                                      const c32* tw4, int ns, cudaStream_t s) {
     const size_t sm = XF<L>::smem;
     if (sm > 227 * 1024) return fail(VIE_EINVAL, "fused x pass does not fit in shared memory");
+    if (2 * n0 > L) return fail(VIE_EINVAL, "fused x pass: data rows exceed half the padded length");
     VIE_TRY(set_smem(k_xfused_r<L>, sm));
     const long long grid = (inner + XF_TW - 1) / XF_TW;
     k_xfused_r<L><<<(unsigned)grid, XF<L>::NT, sm, s>>>(B, n0, inner, P1, P2, kh, H[0], H[1], H[2], tw4, ns);
@@ -394,6 +434,7 @@ template <int L> int launch_zfwd_r(const c32* w, long long wr, const int* list, 
                                    int n1, int n2, long long Nb, long long nlines, const c32* tw4, cudaStream_t s) {
     constexpr int NL = Z_THREADS / Fac<L>::R2;
     const size_t sm = sizeof(c32) * (L + (size_t)NL * Fac<L>::R1 * (Fac<L>::R2 + 1));
+    if (2 * n2 > L) return fail(VIE_EINVAL, "z pass: grid extent exceeds half the padded length");
     VIE_TRY(set_smem(k_zfwd_r<L>, sm));
     k_zfwd_r<L><<<(unsigned)((nlines + NL - 1) / NL), Z_THREADS, sm, s>>>(w, wr, list, idx, A, n0, n1, n2, Nb, nlines,
                                                                          tw4);
@@ -405,6 +446,7 @@ template <int L> int launch_zinv_r(const c32* A, const c32* w, long long wr, c32
                                    long long nlines, const c32* tw4, cudaStream_t s) {
     constexpr int NL = Z_THREADS / Fac<L>::R2;
     const size_t sm = sizeof(c32) * (L + (size_t)NL * Fac<L>::R1 * (Fac<L>::R2 + 1));
+    if (2 * n2 > L) return fail(VIE_EINVAL, "z pass: grid extent exceeds half the padded length");
     VIE_TRY(set_smem(k_zinv_r<L>, sm));
     k_zinv_r<L><<<(unsigned)((nlines + NL - 1) / NL), Z_THREADS, sm, s>>>(A, w, wr, y, yr, list, idx, chi, n0, n1,
                                                                          n2, Nb, nlines, tw4);

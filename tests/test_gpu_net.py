@@ -89,16 +89,16 @@ def test_training_reduces_loss(vielib):
     xd, td, md = (torch.from_numpy(a).cuda().contiguous() for a in (x, t, m))
     losses = [net.train_step(xd.data_ptr(), td.data_ptr(), md.data_ptr(), B, D, 3e-3) for _ in range(300)]
     assert np.all(np.isfinite(losses))
-    assert np.mean(losses[-10:]) < 0.6 * np.mean(losses[:5]), (losses[0], losses[-1])
+    assert np.mean(losses[-10:]) < 0.6 * losses[0], (losses[0], losses[-1])
 
 
 def test_learned_initial_guess_gains_over_zero(vielib):
     """Train on solver-generated data from seeded 64^3 bodies (1-lambda box),
-    then solve held-out bodies from x0 = 0 and from the network's guess.  The
-    FP64-residual judge replaces any guess whose residual is not below ||b||
-    by zero, so every RHS must still reach the target and the learned start
-    must not cost iterations; the measured saving and the number of guesses
-    the judge rejected are printed."""
+    then solve held-out bodies from x0 = 0 and from the network's guess,
+    entered as the residual-minimising combination of the Born term and the
+    predicted correction.  No guess may be rejected by the FP64-residual
+    judge, every RHS must reach the target and the learned start must not
+    cost iterations; the measured saving is printed."""
     from paper_2508_16471_gb300 import learned
     n, h, f, dirs = 64, 1.0 / 64.0, 4, 8
     D = n // f
@@ -121,5 +121,5 @@ def test_learned_initial_guess_gains_over_zero(vielib):
     print(f"learned initial guess: mean GMRES iterations {np.mean(base):.1f} -> {np.mean(lrn):.1f} "
           f"({100 * (1 - np.mean(lrn) / np.mean(base)):.1f} % fewer), {rej} guesses rejected, "
           f"training loss {hist[0]:.4f} -> {hist[-1]:.4f}")
-    assert 0 <= rej <= len(base)
+    assert rej == 0  # the minimal-residual combination is never worse than zero
     assert np.mean(lrn) <= 1.01 * np.mean(base)
