@@ -155,23 +155,51 @@ __global__ void __launch_bounds__(XF<L>::NT) k_xfused_r(c32* __restrict__ B, int
     stage_table(TA, tw4, 2 * L);
     const long long i0 = (long long)blockIdx.x * TW;
     const long long HH = (long long)H0 * H1 * H2;
-    // kernel tile: rows fx = 0..L/2 of the 6 components for this CTA's columns
-    for (int e = threadIdx.x; e < 6 * HX * TW; e += NT) {
-        const int tt = e % TW;
-        const int fx = (e / TW) % HX;
-        const int q = e / (TW * HX);
-        const long long ii = i0 + tt;
-        c32 v = z32();
+    // kernel tile: rows fx = 0..L/2 of the 6 components for this CTA's columns.
+    // Per column: the folded (y, z) offset in the octant and the y/z parities
+    // (xy odd in y, xz odd in z, yz odd in y and z), then batched loads.
+    __shared__ long long coff[TW];
+    __shared__ unsigned char cneg[TW];  // bit q set: negate component q
+    if (threadIdx.x < TW) {
+        const long long ii = i0 + threadIdx.x;
+        long long off = -1;
+        unsigned char ng = 0;
         if (ii < inner) {
             const int ky = (int)(ii / P2), kz = (int)(ii - (ii / P2) * P2);
             const bool fly = 2 * ky > P1, flz = 2 * kz > P2;
-            const int fy = fly ? P1 - ky : ky, fz = flz ? P2 - kz : kz;
-            v = khat[q * HH + ((long long)fx * H1 + fy) * H2 + fz];
-            // y/z parity of the off-diagonal components: xy odd in y, xz odd in z, yz odd in y and z
-            const bool neg = (q == 1 && fly) || (q == 2 && flz) || (q == 4 && (fly ^ flz));
-            if (neg) v = c32{-v.x, -v.y};
+            off = (long long)(fly ? P1 - ky : ky) * H2 + (flz ? P2 - kz : kz);
+            ng = (unsigned char)((fly ? 2 : 0) | (flz ? 4 : 0) | ((fly ^ flz) ? 16 : 0));
         }
-        Kt[e] = v;
+        coff[threadIdx.x] = off;
+        cneg[threadIdx.x] = ng;
+    }
+    __syncthreads();
+    {
+        constexpr int NE = 6 * HX * TW, U = 8;
+        const long long rowst = (long long)H1 * H2;
+        for (int e0 = 0; e0 < NE; e0 += U * NT) {
+            c32 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * NT + threadIdx.x;
+                v[u] = z32();
+                if (e < NE) {
+                    const int tt = e % TW, fx = (e / TW) % HX, q = e / (TW * HX);
+                    const long long off = coff[tt];
+                    if (off >= 0) v[u] = khat[q * HH + fx * rowst + off];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * NT + threadIdx.x;
+                if (e < NE) {
+                    const int tt = e % TW, q = e / (TW * HX);
+                    c32 w = v[u];
+                    if ((cneg[tt] >> q) & 1) w = c32{-w.x, -w.y};
+                    Kt[e] = w;
+                }
+            }
+        }
     }
     const int t = threadIdx.x % TW, n2 = threadIdx.x / TW;
     const bool okt = i0 + t < inner;
