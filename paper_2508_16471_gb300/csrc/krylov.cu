@@ -28,6 +28,11 @@ namespace vie {
 constexpr int KB = 256;   // threads per block for vector kernels
 constexpr int KE = 8;     // elements per thread
 constexpr int KCH = KB * KE;
+// the inner-product kernel takes 4x longer chunks per thread: its cost per
+// element is dominated by the compensated warp reductions (one per basis
+// vector per chunk), not by the loads
+constexpr int KE_D = 4 * KE;
+constexpr int KCH_D = KB * KE_D;
 
 template <typename T> __device__ __forceinline__ c64 ld64(const cplx<T>* p, long long i) {
     const cplx<T> v = p[i];
@@ -58,10 +63,10 @@ __device__ __forceinline__ double warp_sum_comp(float v) {
 }
 __device__ __forceinline__ double warp_sum_comp(double v) { return warp_sum(v); }
 
-// partial[(r*mp1 + i)*nblk + b] = sum over block b of conj(V_i) . V_{j+1}.
-// Each thread forms its KE products in the basis precision T (the stored
-// vectors carry no more than that); every sum across threads, warps and
-// blocks is FP64.
+// partial[(r*mp1 + i)*nblk + b] = sum over block b of conj(V_i) . V_{j+1}
+// (blocks of KCH_D elements).  Each thread sums its KE_D products in the basis
+// precision T (the stored vectors carry no more than that); the sums across
+// threads use error-free (TwoSum) pairs, across warps and blocks FP64.
 template <typename T>
 __global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long long vstride, int j,
                        const int* __restrict__ list, c64* __restrict__ partial, int mp1, long long n, int nblk,
@@ -75,20 +80,19 @@ __global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long lo
     if (gate && !gate[r]) return;
     const cplx<T>* Vr = V + r * rstride;
     const cplx<T>* w = Vr + (long long)(j + 1) * vstride;
-    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
-    cplx<T> wv[KE];
+    const long long e0 = (long long)blockIdx.x * KCH_D + threadIdx.x;
+    cplx<T> wv[KE_D];
 #pragma unroll
-    for (int k = 0; k < KE; ++k) {
+    for (int k = 0; k < KE_D; ++k) {
         const long long e = e0 + k * KB;
         wv[k] = e < n ? w[e] : cplx<T>{(T)0, (T)0};
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll 2
     for (int i = 0; i <= j; ++i) {
         const cplx<T>* vi = Vr + (long long)i * vstride;
         T ar = 0, ai = 0;
 #pragma unroll
-        for (int k = 0; k < KE; ++k) {
+        for (int k = 0; k < KE_D; ++k) {
             const long long e = e0 + k * KB;
             if (e < n) {
                 const cplx<T> a = vi[e];
@@ -107,7 +111,7 @@ __global__ void k_dots(const cplx<T>* __restrict__ V, long long rstride, long lo
         // ||w||^2 before the projection (entry j+1), for the reorthogonalisation test
         T ww = 0;
 #pragma unroll
-        for (int k = 0; k < KE; ++k) ww += wv[k].x * wv[k].x + wv[k].y * wv[k].y;
+        for (int k = 0; k < KE_D; ++k) ww += wv[k].x * wv[k].x + wv[k].y * wv[k].y;
         const double dw = warp_sum_comp(ww);
         if (lane == 0) {
             sre[wid * J2 + j + 1] = dw;
@@ -686,6 +690,7 @@ template <typename T>
 static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult& out) {
     const long long n = S.n3;
     const int R = S.R, m = S.m, mp1 = m + 1, nblk = S.nblk;
+    const int nblk_d = (int)ceil_div(S.n3, (long long)KCH_D);  // inner-product blocks (<= nblk)
     const long long vrs = n * mp1;  // per-RHS stride in V
     cplx<T>* V = (cplx<T>*)S.V;
     cudaStream_t st = op.stream;
@@ -874,14 +879,14 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
             for (int pass = 0; pass < 2; ++pass) {
                 const int* gate = pass ? S.reorth : nullptr;
                 tmr_begin(TMR_DOTS, st);
-                k_dots<T><<<gi, KB, sizeof(double) * 2 * (KB / 32) * (j + 2), st>>>(V, vrs, n, j, op.d_list, S.partial,
-                                                                                  mp1 + 1, n, nblk, gate);
+                k_dots<T><<<dim3(nblk_d, ni), KB, sizeof(double) * 2 * (KB / 32) * (j + 2), st>>>(
+                    V, vrs, n, j, op.d_list, S.partial, mp1 + 1, n, nblk_d, gate);
                 tmr_end(TMR_DOTS, st, (double)ni * (j + 2) * n * ET);
                 LAUNCH_CHECK();
                 tmr_begin(TMR_REDUCE, st);
-                k_reduce_dots<<<dim3(j + 2, ni), KB, 0, st>>>(S.partial, S.coef, S.H, j, op.d_list, mp1, nblk, pass,
+                k_reduce_dots<<<dim3(j + 2, ni), KB, 0, st>>>(S.partial, S.coef, S.H, j, op.d_list, mp1, nblk_d, pass,
                                                                gate);
-                tmr_end(TMR_REDUCE, st, (double)ni * (j + 1) * nblk * 16.0);
+                tmr_end(TMR_REDUCE, st, (double)ni * (j + 1) * nblk_d * 16.0);
                 LAUNCH_CHECK();
                 tmr_begin(TMR_UPDATE, st);
                 k_update<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.coef, S.normpart, mp1, n, nblk, gate);

@@ -57,3 +57,53 @@ def test_metasurface_reduced_glr_map(vielib):
             assert abs(vis[i, j] - ohom.visibility(E)) < 1e-12
     assert np.all((g2 >= -1e-14) & (g2 <= 1 + 1e-12))
     assert abs(p2.max() - 1.0) < 1e-14
+
+
+def test_metasurface_full_size(vielib):
+    """The full PB-phase configuration: 8 x 8 fins on the 256 x 256 x 32 grid,
+    32 incidence angles x L/R (64 RHS) in one batched mixed-precision solve to
+    an FP64 residual of 1e-6.  Checked against the oracle: its equation at
+    sampled fin voxels for the two channels at theta_s = +1 deg, the far field
+    of those currents, and the g_LR / visibility map of Eq. 31 (H/V by
+    linearity, Eq. 28) at sampled detector pairs."""
+    grid, eps, _ = inputs.metasurface(seed=0)
+    k0 = 2 * math.pi
+    chs = [(c.khat, c.pol) for c in inputs.channels_metasurface()]
+    assert len(chs) == 64
+    iL, iR = 32, 33  # theta_s = +1 deg
+    deg = np.arange(-30.0, 30.0 + 1e-9, 0.5)
+    d = _dirs(np.abs(deg), np.where(deg < 0, -1.0, 1.0))
+    with vielib.Handle(grid.n, grid.h, eps, k0) as hd:
+        st = hd.solve(chs, tol=1e-6, restart=128, max_iter=20000)
+        assert st["converged"] == 64 and st["relres_max"] <= 1e-6
+        W = np.stack([hd.get_current(r) for r in (iL, iR)])
+        C = hd.farfield_dirs(d, basis=vielib.BASIS_CIRC)[[iL, iR]]  # [2][D][3]
+    # the oracle's equation at sampled fin voxels
+    chi = ovie.contrast(eps)
+    body = np.argwhere(chi > 0)
+    pts = body[np.random.default_rng(3).choice(len(body), size=3, replace=False)]
+    conv = ovie.convolve_direct_points_multi(grid.n, grid.h, k0, W, pts)
+    for q, r in enumerate((iL, iR)):
+        b = ovie.rhs(chi, ovie.incident_field(grid.n, grid.h, k0, *chs[r]))
+        res = np.array([[W[q][c][tuple(p)] - chi[tuple(p)] * conv[q, c, i] - b[c][tuple(p)] for c in range(3)]
+                        for i, p in enumerate(pts)])
+        assert np.abs(res).max() <= 1.05e-6 * np.linalg.norm(b)
+    # far field of the GPU currents at every 10th detector direction
+    sel = np.arange(0, len(deg), 10)
+    for q in range(2):
+        F_or = ovie.project(ovie.farfield(W[q], grid.n, grid.h, k0, d[sel]), d[sel], 2)
+        assert np.linalg.norm(C[q][sel] - F_or) <= 1e-8 * np.linalg.norm(F_or)
+    # Eq. 31 map: channels H = (L + R)/sqrt2, V = (L - R)/(i sqrt2); a = R at r1, b = L at r2
+    s2 = math.sqrt(2.0)
+    H = (C[0] + C[1]) / s2
+    Vv = (C[0] - C[1]) / (1j * s2)
+    Ea = np.stack([H[:, 1], Vv[:, 1]])
+    Eb = np.stack([H[:, 0], Vv[:, 0]])
+    g2, vis, p2 = vielib.hom_map(Ea, Eb)
+    assert g2.shape == (len(deg), len(deg))
+    for i in range(0, len(deg), 17):
+        for j in range(0, len(deg), 13):
+            E = [[Ea[0, i], Ea[1, i]], [Eb[0, j], Eb[1, j]]]
+            assert abs(g2[i, j] - ohom.g2_degenerate(E)) < 1e-12
+            assert abs(vis[i, j] - ohom.visibility(E)) < 1e-12
+    assert np.all((g2 >= -1e-14) & (g2 <= 1 + 1e-12))

@@ -156,6 +156,22 @@ def test_bench_body_solution_satisfies_oracle_equation(vielib):
     _sampled_residual_check(vielib, wl, (0, 17), restart=64, nsamp=3, seed=4)
 
 
+@pytest.mark.parametrize("seed", [27, 30, 14])
+def test_uneven_random_bodies(vielib, seed):
+    """Random-body configuration (lambda/20 cells, 1-3 ellipsoids/cuboids,
+    eps_r up to 6, 16 RHS = 8 Fibonacci directions x 2 polarisations) on three
+    uneven grids, 32^3, 38^3 and 41^3 (the sizes whose 1.6-2 lambda boxes
+    restarted GMRES resolves; 38 and 41 pad to the non-power-of-two smooth
+    sizes 75 and 81 and run on the generic radix-3/5 kernels): sampled oracle
+    residual and far field of the GPU currents."""
+    wl = inputs.random_body_workload(seed, n_dirs=8)
+    assert wl.grid.n[0] == {27: 32, 30: 38, 14: 41}[seed]
+    th = np.radians([0.0, 40.0, 90.0, 150.0])
+    ph = np.radians([0.0, 70.0, 200.0, 300.0])
+    dirs = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], -1)
+    _sampled_residual_check(vielib, wl, (0, 9), restart=128, nsamp=4, seed=seed, ff_dirs=dirs)
+
+
 def test_optical_theorem_on_gpu_solution(vielib):
     """Energy balance of the GPU solution of a random lossless body (property
     of the exact discrete solution at any size; residual 1e-9 here)."""
