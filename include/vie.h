@@ -91,7 +91,9 @@ typedef struct vie_solve_opts {
                           the residual norm (needs restart >= 3).  A supplied
                           guess whose FP64 residual is not below ||b|| is
                           replaced by zero.                                       */
-    int reserved[3];
+    int precond;       /* 0: GMRES; 1: FGMRES with the learned right preconditioner
+                          attached by vie_attach_precond (mixed or FP64 basis)   */
+    int reserved[2];
 } vie_solve_opts;
 
 typedef struct vie_solve_stats {
@@ -277,6 +279,8 @@ int vie_get_info(const vie_handle* hd, vie_info* info);
  * on the current device; these calls synchronise the device's null stream. */
 typedef struct vie_net vie_net;
 int vie_net_create(const int channels[4], unsigned long long seed, int bf16, vie_net** out);
+/* the same with `cin` input channels (10: initial guess; 7: preconditioner); VIE_EINVAL outside 1..64 */
+int vie_net_create_io(const int channels[4], int cin, unsigned long long seed, int bf16, vie_net** out);
 void vie_net_destroy(vie_net* net);
 long long vie_net_num_params(const vie_net* net);
 /* host float32 arrays of vie_net_num_params() entries: per layer w[co][ci][k^3] then b[co] */
@@ -299,6 +303,23 @@ int vie_net_features(vie_handle* hd, int factor, float* x_dev, float* t_dev, flo
 int vie_attach_net(vie_handle* hd, vie_net* net, int factor);
 /* number of RHS of the last solve whose supplied initial guess was rejected */
 int vie_guesses_rejected(const vie_handle* hd);
+
+/* ---- learned right preconditioner (FGMRES, opts.precond = 1) --------------
+ * Each Krylov vector v (unit norm) is mapped to z = v + up(Net(x)) / sqrt(3 Nb)
+ * with x [7][D^3] = (block-averaged chi, sqrt(3 Nb) times the block-averaged
+ * Re/Im of v per component) on the grid coarsened by `factor`, and the solver
+ * applies A to z and keeps the z vectors for the update (flexible GMRES; the
+ * preconditioner may change between steps).  The network, made with cin = 7,
+ * learns A^{-1} - I on pairs (u = A v, v): targets t = sqrt(3 Nb)/||u|| times
+ * the block average of (v - u).  Not owned; NULL detaches.  Errors: VIE_EINVAL
+ * (non-cubic grid, n not divisible by 8 x factor, network with cin != 7). */
+int vie_attach_precond(vie_handle* hd, vie_net* net, int factor);
+/* training pairs for the preconditioner: v_dev [n][3][Nb] complex64 (device,
+ * the body layout of vie_apply_device) -> u = A v with the FP32 operator, then
+ * x_dev [n][7][D^3], t_dev [n][6][D^3], m_dev [n][D^3] (float32, device) as
+ * above.  Synchronises the handle's stream.  Errors: VIE_EINVAL, VIE_ENOMEM. */
+int vie_precond_pairs(vie_handle* hd, int factor, const void* v_dev, int n, float* x_dev, float* t_dev,
+                      float* m_dev);
 
 /* Engine of the far-field contractions on (theta, phi) grids (vie_farfield):
  * 0 (default) tensor cores (tcgen05, TF32 split three ways: hi*hi + hi*lo +

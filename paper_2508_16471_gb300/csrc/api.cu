@@ -23,6 +23,7 @@ struct vie_handle {
     vie_net* net = nullptr;     // attached initial-guess network (not owned)
     int net_factor = 4;         // coarsening of the network grid
     int guesses_rejected = 0;
+    vie::PrecondCtx pctx;       // attached preconditioner network (pctx.net not owned)
 };
 
 namespace vie {
@@ -148,6 +149,7 @@ void vie_default_opts(vie_solve_opts* o) {
     o->precision = VIE_PREC_MIXED;
     o->inner_tol = 1e-6;
     o->use_x0 = 0;
+    o->precond = 0;
 }
 
 const char* vie_last_error(void) { return g_err.c_str(); }
@@ -244,6 +246,9 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
         return fail(VIE_ESTATE, "use_x0 needs a stored solution with the same n_rhs, restart and precision");
     if (o.use_x0 == 2 && !hd->net) return fail(VIE_ESTATE, "use_x0 = 2 needs a network attached with vie_attach_net");
     if (o.use_x0 < 0 || o.use_x0 > 2) return fail(VIE_EINVAL, "use_x0 must be 0, 1 or 2");
+    if (o.precond != 0 && o.precond != 1) return fail(VIE_EINVAL, "precond must be 0 or 1");
+    if (o.precond == 1 && !hd->pctx.net)
+        return fail(VIE_ESTATE, "precond = 1 needs a network attached with vie_attach_precond");
     VIE_CUDA(cudaSetDevice(hd->device));
     auto t0 = std::chrono::steady_clock::now();
     VIE_TRY(hd->S.alloc(hd->op, n_rhs, o.restart, o.precision));
@@ -251,7 +256,9 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
     VIE_TRY(build_rhs(hd->op, hd->S, ch, n_rhs));
     if (o.use_x0 == 2) VIE_TRY(net_guess(hd, n_rhs));
     SolveResult res;
+    hd->S.pc = o.precond == 1 ? &hd->pctx : nullptr;
     int st = solver_run(hd->op, hd->S, o, res);
+    hd->S.pc = nullptr;
     VIE_CUDA(cudaStreamSynchronize(hd->op.stream));
     auto t1 = std::chrono::steady_clock::now();
     if (st != VIE_OK) return st;
@@ -586,11 +593,16 @@ void vie_destroy(vie_handle* hd) {
 
 // ---- learned initial guess ------------------------------------------------
 int vie_net_create(const int channels[4], unsigned long long seed, int bf16, vie_net** out) {
+    return vie_net_create_io(channels, NET_IN, seed, bf16, out);
+}
+
+int vie_net_create_io(const int channels[4], int cin, unsigned long long seed, int bf16, vie_net** out) {
     if (!out || !channels) return fail(VIE_EINVAL, "NULL argument");
     for (int i = 0; i < 4; ++i)
         if (channels[i] < 1 || channels[i] > 256) return fail(VIE_EINVAL, "channels must be in 1..256");
+    if (cin < 1 || cin > 64) return fail(VIE_EINVAL, "input channels must be in 1..64");
     vie_net* n = new vie_net();
-    int st = n->net.init(channels, seed, bf16 ? 1 : 0);
+    int st = n->net.init(channels, seed, bf16 ? 1 : 0, cin);
     if (st != VIE_OK) {
         delete n;
         return st;
@@ -699,11 +711,44 @@ int vie_net_features(vie_handle* hd, int factor, float* x_dev, float* t_dev, flo
 int vie_attach_net(vie_handle* hd, vie_net* n, int factor) {
     if (!hd) return fail(VIE_EINVAL, "NULL handle");
     if (n && factor < 1) return fail(VIE_EINVAL, "factor must be >= 1");
+    if (n && n->net.cin != NET_IN) return fail(VIE_EINVAL, "the initial-guess network takes 10 input channels");
     hd->net = n;
     hd->net_factor = factor;
     return VIE_OK;
 }
 
 int vie_guesses_rejected(const vie_handle* hd) { return hd ? hd->guesses_rejected : 0; }
+
+int vie_attach_precond(vie_handle* hd, vie_net* n, int factor) {
+    if (!hd) return fail(VIE_EINVAL, "NULL handle");
+    if (n) {
+        const Operator& op = hd->op;
+        if (factor < 1 || op.n[0] != op.n[1] || op.n[0] != op.n[2] || op.n[0] % (8 * factor) != 0)
+            return fail(VIE_EINVAL, "the preconditioner needs a cubic grid with n divisible by 8 x factor");
+        if (n->net.cin != PRE_IN) return fail(VIE_EINVAL, "the preconditioner network takes 7 input channels");
+    }
+    hd->pctx.net = n ? &n->net : nullptr;
+    hd->pctx.f = factor;
+    return VIE_OK;
+}
+
+int vie_precond_pairs(vie_handle* hd, int factor, const void* v_dev, int n, float* x_dev, float* t_dev,
+                      float* m_dev) {
+    if (!hd || !v_dev || !x_dev || !t_dev || !m_dev || n < 1) return fail(VIE_EINVAL, "NULL argument or n < 1");
+    Operator& op = hd->op;
+    if (factor < 1 || op.n[0] != op.n[1] || op.n[0] != op.n[2] || op.n[0] % factor != 0)
+        return fail(VIE_EINVAL, "pairs need a cubic grid with n divisible by the factor");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    const long long nv = 3 * op.Nb;
+    c32* u = nullptr;
+    VIE_CUDA(cudaMalloc(&u, sizeof(c32) * nv * n));
+    std::vector<int> lst(n);
+    for (int i = 0; i < n; ++i) lst[i] = i;
+    int st = op_set_list(op, lst.data(), n);
+    if (st == VIE_OK) st = op_apply(op, VIE_PREC_MIXED, v_dev, nv, u, nv, op.d_list, n);
+    if (st == VIE_OK) st = precond_pairs(op, factor, (const c32*)v_dev, n, u, x_dev, t_dev, m_dev, op.stream);
+    cudaFree(u);
+    return st;
+}
 
 }  // extern "C"

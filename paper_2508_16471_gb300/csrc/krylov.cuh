@@ -9,6 +9,22 @@ namespace vie {
 
 constexpr int MAX_RESTART = 512;
 
+struct Net;
+// Learned right preconditioner of FGMRES: z = v + (||v|| / sqrt(3 Nb)) up(Net(x)),
+// x = [block-averaged chi, sqrt(3 Nb)/||v|| block-averaged Re/Im v] on the D^3
+// coarse grid (D = n / f); see net.cu.
+struct PrecondCtx {
+    Net* net = nullptr;
+    int f = 4;
+    float* x = nullptr;  // [bcap][7][D^3] network input
+    float* y = nullptr;  // [bcap][6][D^3] network output
+    int bcap = 0;
+    ~PrecondCtx();
+};
+template <typename T>
+int precond_apply(Operator& op, PrecondCtx& pc, const cplx<T>* v, long long vrs, cplx<T>* z, long long zrs,
+                  const int* list, int n, cudaStream_t s);
+
 struct Solver {
     int R = 0, m = 0, prec = 0, nblk = 0;
     long long n3 = 0;          // vector length 3 * Nb
@@ -32,6 +48,8 @@ struct Solver {
     int* flag = nullptr;       // [R] 1 = stop the current cycle
     int* reorth = nullptr;     // [R] 1 = second Gram-Schmidt pass needed this step
     double* chans = nullptr;   // [R][9] channels of the current right-hand sides
+    void* Z = nullptr;         // [R][m][n3] preconditioned basis (FGMRES; allocated on first use)
+    PrecondCtx* pc = nullptr;  // learned right preconditioner for the next solve (not owned), or null
 
     int alloc(Operator& op, int R, int m, int prec);
     void release(Operator& op);

@@ -21,6 +21,7 @@
 // upsampling of d_pred).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -270,11 +271,12 @@ int Net::alloc(void** p, size_t bytes) {
     return VIE_OK;
 }
 
-int Net::init(const int* ch, unsigned long long seed, int store_bf16) {
+int Net::init(const int* ch, unsigned long long seed, int store_bf16, int cin_) {
     for (int i = 0; i < 4; ++i) c[i] = ch[i];
     bf16 = store_bf16;
+    cin = cin_;
     const int c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3];
-    const int spec[NL][3] = {{NET_IN, c0, 3},       {c0, c0, 3}, {c0, c1, 3}, {c1, c1, 3}, {c1, c2, 3},
+    const int spec[NL][3] = {{cin, c0, 3},       {c0, c0, 3}, {c0, c1, 3}, {c1, c1, 3}, {c1, c2, 3},
                              {c2, c2, 3},      {c2, c3, 3}, {c3, c3, 3}, {c3 + c2, c2, 3}, {c2, c2, 3},
                              {c2 + c1, c1, 3}, {c1, c1, 3}, {c1 + c0, c0, 3}, {c0, c0, 3}, {c0, 6, 1}};
     std::mt19937_64 rng(seed);
@@ -341,7 +343,7 @@ int Net::reserve(int B_, int D_) {
     const int c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3];
     // buffer channel counts and voxel counts
     const long long sizes[NBUF][2] = {
-        {NET_IN, V0},   // IN
+        {cin, V0},      // IN
         {c0, V0},       // E0A
         {c1 + c0, V0},  // CAT0: [up(d1) | s0]
         {c0, V1},       // P0
@@ -514,7 +516,7 @@ int Net::forward(int B, cudaStream_t s) { return bf16 ? forward_t<__nv_bfloat16>
 int Net::backward(int B, cudaStream_t s) { return bf16 ? backward_t<__nv_bfloat16>(B, s) : backward_t<float>(B, s); }
 
 int Net::set_input(const float* x_dev, int B, cudaStream_t s) {
-    const long long n = (long long)B * NET_IN * D * D * D;
+    const long long n = (long long)B * cin * D * D * D;
     if (bf16) k_to_s<__nv_bfloat16><<<grid1(n), 256, 0, s>>>(x_dev, (__nv_bfloat16*)act[IN], n);
     else VIE_CUDA(cudaMemcpyAsync(act[IN], x_dev, 4 * n, cudaMemcpyDeviceToDevice, s));
     count_launch();
@@ -675,6 +677,162 @@ int net_initial_guess(Operator& op, const double* chans_dev, int n_rhs, int f, c
     count_launch();
     VIE_CUDA(cudaGetLastError());
     return VIE_OK;
+}
+
+// ---- learned right preconditioner (FGMRES) ---------------------------------
+// Input of slot s (vector u of RHS r = list[s]): channel 0 the block-averaged
+// chi, channels 1..6 Re/Im of sc[s] * (block average of u) per component, with
+// sc[s] = sqrt(3 Nb) / ||u|| (unit RMS).  With a training partner v (A v = u)
+// the target is sc[s] * block average of (v - u) and m the body fraction.
+template <typename T>
+__global__ void k_pre_features(int n0, int n1, int n2, int f, int D, const int* __restrict__ idx_map,
+                               const double* __restrict__ chi, const cplx<T>* __restrict__ u, long long ustride,
+                               const cplx<T>* __restrict__ v, long long vstride, const int* __restrict__ list,
+                               const double* __restrict__ sc, double sc0, long long Nb, float* __restrict__ x,
+                               float* __restrict__ t, float* __restrict__ m) {
+    const int s = blockIdx.y;
+    const int r = list ? list[s] : s;
+    const long long V = (long long)D * D * D;
+    const long long cvox = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cvox >= V) return;
+    const double scale = sc ? sc[s] : sc0;
+    const int X = (int)(cvox / ((long long)D * D)), Y = (int)((cvox / D) % D), Z = (int)(cvox % D);
+    double chisum = 0.0;
+    int nbody = 0;
+    double au[6] = {0, 0, 0, 0, 0, 0}, av[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < f * f * f; ++q) {
+        const int i = X * f + q / (f * f), j = Y * f + (q / f) % f, k = Z * f + q % f;
+        if (i >= n0 || j >= n1 || k >= n2) continue;
+        const int vi = idx_map[((long long)i * n1 + j) * n2 + k];
+        if (vi < 0) continue;
+        chisum += chi[vi];
+        ++nbody;
+        for (int a = 0; a < 3; ++a) {
+            const cplx<T> uu = u[r * ustride + a * Nb + vi];
+            au[2 * a] += (double)uu.x;
+            au[2 * a + 1] += (double)uu.y;
+            if (v) {
+                const cplx<T> vv = v[r * vstride + a * Nb + vi];
+                av[2 * a] += (double)vv.x;
+                av[2 * a + 1] += (double)vv.y;
+            }
+        }
+    }
+    const double inv = nbody ? scale / nbody : 0.0;
+    float* xr = x + (long long)s * PRE_IN * V;
+    xr[cvox] = (float)(chisum / (f * f * f));
+    for (int a = 0; a < 6; ++a) xr[(1 + a) * V + cvox] = (float)(au[a] * inv);
+    if (t) {
+        float* tr = t + (long long)s * 6 * V;
+        for (int a = 0; a < 6; ++a) tr[a * V + cvox] = (float)((av[a] - au[a]) * inv);
+        m[(long long)s * V + cvox] = (float)nbody / (float)(f * f * f);
+    }
+}
+
+// z = v + coef * upsampled y on the body voxels (coef = 1 / sqrt(3 Nb) for unit-norm v)
+template <typename T>
+__global__ void k_pre_apply(int n1, int n2, int f, int D, const int* __restrict__ vox, long long Nb,
+                            const cplx<T>* __restrict__ v, long long vrs, const int* __restrict__ list,
+                            const float* __restrict__ y, double coef, cplx<T>* __restrict__ z, long long zrs) {
+    const int s = blockIdx.y;
+    const int r = list[s];
+    const long long V = (long long)D * D * D;
+    const float* ys = y + (long long)s * 6 * V;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < Nb;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int lin = vox[e];
+        const int k = lin % n2, j = (lin / n2) % n1, i = lin / (n1 * n2);
+        const long long cv = ((long long)(i / f) * D + j / f) * D + k / f;
+        for (int a = 0; a < 3; ++a) {
+            const cplx<T> vv = v[r * vrs + a * Nb + e];
+            z[r * zrs + a * Nb + e] = cplx<T>{(T)((double)vv.x + coef * ys[(2 * a) * V + cv]),
+                                              (T)((double)vv.y + coef * ys[(2 * a + 1) * V + cv])};
+        }
+    }
+}
+
+PrecondCtx::~PrecondCtx() {
+    cudaFree(x);
+    cudaFree(y);
+}
+
+template <typename T>
+int precond_apply(Operator& op, PrecondCtx& pc, const cplx<T>* v, long long vrs, cplx<T>* z, long long zrs,
+                  const int* list, int n, cudaStream_t s) {
+    Net& net = *pc.net;
+    const int f = pc.f, D = op.n[0] / f;
+    const long long V = (long long)D * D * D;
+    const int B = std::min(n, 8);
+    if (pc.bcap < n) {
+        cudaFree(pc.x);
+        cudaFree(pc.y);
+        pc.x = pc.y = nullptr;
+        pc.bcap = 0;
+        VIE_CUDA(cudaMalloc(&pc.x, sizeof(float) * PRE_IN * V * n));
+        VIE_CUDA(cudaMalloc(&pc.y, sizeof(float) * 6 * V * n));
+        pc.bcap = n;
+    }
+    VIE_TRY(net.reserve(B, D));
+    // Krylov vectors have unit norm: sc = sqrt(3 Nb)
+    const double sc0 = std::sqrt(3.0 * (double)op.Nb);
+    k_pre_features<T><<<dim3((unsigned)((V + 127) / 128), n), 128, 0, s>>>(
+        op.n[0], op.n[1], op.n[2], f, D, op.idx_map, op.chi64, v, vrs, (const cplx<T>*)nullptr, 0, list, nullptr, sc0,
+        op.Nb, pc.x, nullptr, nullptr);
+    count_launch();
+    VIE_CUDA(cudaGetLastError());
+    for (int r0 = 0; r0 < n; r0 += B) {
+        const int nb = std::min(B, n - r0);
+        VIE_TRY(net.set_input(pc.x + (long long)r0 * PRE_IN * V, nb, s));
+        VIE_TRY(net.forward(nb, s));
+        VIE_TRY(net.get_output(pc.y + (long long)r0 * 6 * V, nb, s));
+    }
+    k_pre_apply<T><<<dim3((unsigned)std::max(1LL, std::min(2048LL, (op.Nb + 255) / 256)), n), 256, 0, s>>>(
+        op.n[1], op.n[2], f, D, op.vox, op.Nb, v, vrs, list, pc.y, 1.0 / sc0, z, zrs);
+    count_launch();
+    VIE_CUDA(cudaGetLastError());
+    return VIE_OK;
+}
+template int precond_apply<float>(Operator&, PrecondCtx&, const c32*, long long, c32*, long long, const int*, int,
+                                  cudaStream_t);
+template int precond_apply<double>(Operator&, PrecondCtx&, const c64*, long long, c64*, long long, const int*, int,
+                                   cudaStream_t);
+
+// sum of |u|^2 per slot (FP64 atomics; training-data path only)
+__global__ void k_sq_norms(const c32* __restrict__ u, long long stride, long long n, double* __restrict__ out) {
+    const int s = blockIdx.y;
+    double acc = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const c32 a = u[s * stride + e];
+        acc += (double)a.x * a.x + (double)a.y * a.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out + s, acc);
+}
+__global__ void k_inv_scale(double* __restrict__ a, int n, double sq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = a[i] > 0 ? sq / sqrt(a[i]) : 0.0;
+}
+
+int precond_pairs(Operator& op, int f, const c32* v, int n, const c32* u, float* x, float* t, float* m,
+                  cudaStream_t s) {
+    const int D = op.n[0] / f;
+    const long long V = (long long)D * D * D, nv = 3 * op.Nb;
+    double* sc = nullptr;
+    VIE_CUDA(cudaMalloc(&sc, sizeof(double) * n));
+    int st = VIE_OK;
+    cudaMemsetAsync(sc, 0, sizeof(double) * n, s);
+    k_sq_norms<<<dim3(256, n), 256, 0, s>>>(u, nv, nv, sc);
+    k_inv_scale<<<(n + 127) / 128, 128, 0, s>>>(sc, n, std::sqrt((double)nv));
+    k_pre_features<float><<<dim3((unsigned)((V + 127) / 128), n), 128, 0, s>>>(
+        op.n[0], op.n[1], op.n[2], f, D, op.idx_map, op.chi64, u, nv, v, nv, nullptr, sc, 0.0, op.Nb, x, t, m);
+    count_launch();
+    count_launch();
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "preconditioner training pairs");
+    cudaFree(sc);
+    return st;
 }
 
 __global__ void k_sum(const float* __restrict__ a, long long n, float* __restrict__ out) {

@@ -8,6 +8,7 @@
 namespace vie {
 
 constexpr int NET_IN = 10;  // input channels: chi, pol (Re/Im x3), khat (3)
+constexpr int PRE_IN = 7;   // preconditioner input channels: chi, Re/Im of the vector (x3)
 
 struct Net {
     static constexpr int NL = 15;  // layers
@@ -20,6 +21,7 @@ struct Net {
     };
     int c[4] = {16, 32, 64, 128};
     int bf16 = 1;
+    int cin = NET_IN;  // input channels
     Layer L[NL];
     long long nparams = 0;
     int t = 0;  // Adam step
@@ -34,7 +36,7 @@ struct Net {
 
     ~Net();
     int alloc(void** p, size_t bytes);
-    int init(const int* ch, unsigned long long seed, int store_bf16);
+    int init(const int* ch, unsigned long long seed, int store_bf16, int cin = NET_IN);
     int reserve(int B, int D);
     int set_input(const float* x_dev, int B, cudaStream_t s);
     int get_output(float* y_dev, int B, cudaStream_t s);
@@ -64,5 +66,11 @@ int net_features(Operator& op, const double* chans_dev, int n_rhs, int f, float*
 int device_sum(const float* a, long long n, float* out_host, float* scratch, cudaStream_t s);
 int net_initial_guess(Operator& op, const double* chans_dev, int n_rhs, int f, const float* y, c64* x0,
                       long long xstride, cudaStream_t s);
+
+// preconditioner training pairs: for n FP32 vectors v [n][3 Nb] and u = A v,
+// x [n][7][D^3] from u and targets t [n][6][D^3] = block average of (v - u),
+// both scaled by sqrt(3 Nb)/||u||; m [n][D^3] the body fraction
+int precond_pairs(Operator& op, int f, const c32* v, int n, const c32* u, float* x, float* t, float* m,
+                  cudaStream_t s);
 
 }  // namespace vie

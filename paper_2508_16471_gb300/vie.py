@@ -25,7 +25,8 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_get_info", "vie_kernel_launches", "vie_stream", "vie_destroy", "vie_last_error",
            "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_apply_noalloc", "vie_net_create", "vie_net_destroy", "vie_net_num_params",
            "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
-           "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_guesses_rejected", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
+           "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_guesses_rejected",
+           "vie_net_create_io", "vie_attach_precond", "vie_precond_pairs", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
 
 
 class VieError(RuntimeError):
@@ -45,7 +46,7 @@ class _Channel(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iter", C.c_int),
                 ("precision", C.c_int), ("inner_tol", C.c_double), ("use_x0", C.c_int),
-                ("reserved", C.c_int * 3)]
+                ("precond", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class _Stats(C.Structure):
@@ -104,6 +105,9 @@ def load():
     L.vie_attach_net.argtypes = [P, P, C.c_int]
     L.vie_guesses_rejected.argtypes = [P]
     L.vie_guesses_rejected.restype = C.c_int
+    L.vie_net_create_io.argtypes = [C.POINTER(C.c_int), C.c_int, C.c_ulonglong, C.c_int, C.POINTER(P)]
+    L.vie_attach_precond.argtypes = [P, P, C.c_int]
+    L.vie_precond_pairs.argtypes = [P, C.c_int, P, C.c_int, P, P, P]
     L.vie_set_farfield_engine.argtypes = [P, C.c_int]
     L.vie_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int]
     L.vie_kernel_launches.restype = C.c_longlong
@@ -126,7 +130,8 @@ def load():
               "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines", "vie_get_info",
               "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_net_create",
               "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
-              "vie_net_train_step", "vie_net_features", "vie_attach_net"]:
+              "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_net_create_io",
+              "vie_attach_precond", "vie_precond_pairs"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -259,6 +264,17 @@ class Handle:
     def guesses_rejected(self):
         return int(load().vie_guesses_rejected(self._h))
 
+    def attach_precond(self, net, factor):
+        """Network used as the FGMRES right preconditioner by solve(..., precond=1)."""
+        _check(load().vie_attach_precond(self._h, net.ptr if net is not None else None, int(factor)))
+        self._pnet = net  # keep alive
+
+    def precond_pairs(self, factor, v_ptr, n, x_ptr, t_ptr, m_ptr):
+        """Preconditioner training pairs of n complex64 body-layout vectors v
+        (device): x [n][7][D^3], t [n][6][D^3], m [n][D^3] (device float32)."""
+        _check(load().vie_precond_pairs(self._h, int(factor), C.c_void_p(v_ptr), int(n), C.c_void_p(x_ptr),
+                                        C.c_void_p(t_ptr), C.c_void_p(m_ptr)))
+
     def set_eps(self, eps_r):
         eps = np.ascontiguousarray(eps_r, dtype=np.float64).reshape(self.n)
         _check(load().vie_set_eps(self._h, _dptr(eps)))
@@ -321,16 +337,18 @@ class Handle:
 
 
 class Net:
-    """The learned initial-guess network (vie_net_*); device buffers are passed
-    as raw pointers (e.g. torch.Tensor.data_ptr())."""
+    """The learned network (vie_net_*): cin = 10 for the initial guess, 7 for
+    the preconditioner; device buffers are passed as raw pointers (e.g.
+    torch.Tensor.data_ptr())."""
 
-    def __init__(self, channels=(16, 32, 64, 128), seed=0, bf16=True):
+    def __init__(self, channels=(16, 32, 64, 128), seed=0, bf16=True, cin=10):
         L = load()
         ch = (C.c_int * 4)(*[int(c) for c in channels])
         p = C.c_void_p()
-        _check(L.vie_net_create(ch, C.c_ulonglong(seed), int(bool(bf16)), C.byref(p)))
+        _check(L.vie_net_create_io(ch, int(cin), C.c_ulonglong(seed), int(bool(bf16)), C.byref(p)))
         self._p = p
         self.channels = tuple(channels)
+        self.cin = int(cin)
 
     @property
     def ptr(self):

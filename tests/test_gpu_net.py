@@ -28,9 +28,9 @@ def _flat(G, specs):
     return np.concatenate([np.concatenate([G[n + ".w"].reshape(-1), G[n + ".b"]]) for n, *_ in specs])
 
 
-def _data(B, D, seed):
+def _data(B, D, seed, cin=10):
     rng = np.random.default_rng(seed)
-    x = rng.standard_normal((B, 10, D, D, D)).astype(np.float32)
+    x = rng.standard_normal((B, cin, D, D, D)).astype(np.float32)
     t = rng.standard_normal((B, 6, D, D, D)).astype(np.float32)
     m = (rng.uniform(size=(B, 1, D, D, D)) < 0.7).astype(np.float32) * rng.uniform(0.2, 1.0, (B, 1, D, D, D)).astype(np.float32)
     return x, t, m
@@ -42,11 +42,13 @@ def _data(B, D, seed):
 # B*D^3 = 1024 voxel products of varying sign, so its relative error is
 # u * (cancellation ~ sqrt(1024)) * depth, several percent and largest at the
 # first layer; the all-parameter gradient is held to the tighter bound.
-@pytest.mark.parametrize("bf16,tol_y,tol_g,tol_all", [(False, 2e-5, 2e-4, 2e-4), (True, 3e-2, 0.25, 0.08)])
-def test_forward_and_gradients_match_oracle(vielib, bf16, tol_y, tol_g, tol_all):
+@pytest.mark.parametrize("bf16,tol_y,tol_g,tol_all,cin", [(False, 2e-5, 2e-4, 2e-4, 10), (True, 3e-2, 0.25, 0.08, 10),
+                                                          (False, 2e-5, 2e-4, 2e-4, 7)])
+def test_forward_and_gradients_match_oracle(vielib, bf16, tol_y, tol_g, tol_all, cin):
+    """cin = 10: the initial-guess network; cin = 7: the preconditioner network."""
     import torch
-    specs = onet.layer_specs(c=CH)
-    net = vielib.Net(CH, seed=5, bf16=bf16)
+    specs = onet.layer_specs(c=CH, cin=cin)
+    net = vielib.Net(CH, seed=5, bf16=bf16, cin=cin)
     # non-zero biases so that their gradients and the ReLU masks are exercised
     p = net.get_params()
     rng = np.random.default_rng(6)
@@ -57,7 +59,7 @@ def test_forward_and_gradients_match_oracle(vielib, bf16, tol_y, tol_g, tol_all)
     net.set_params(_flat(P, specs).astype(np.float32))
     P = _oracle_params(net.get_params(), specs)
     B, D = 2, 8
-    x, t, m = _data(B, D, 7)
+    x, t, m = _data(B, D, 7, cin)
     xd, td, md = (torch.from_numpy(a).cuda().contiguous() for a in (x, t, m))
     yd = torch.empty(B, 6, D, D, D, device="cuda")
     net.forward(xd.data_ptr(), yd.data_ptr(), B, D)
@@ -123,3 +125,49 @@ def test_learned_initial_guess_gains_over_zero(vielib):
           f"training loss {hist[0]:.4f} -> {hist[-1]:.4f}")
     assert rej == 0  # the minimal-residual combination is never worse than zero
     assert np.mean(lrn) <= 1.01 * np.mean(base)
+
+
+def test_fgmres_with_zero_network_is_gmres(vielib):
+    """FGMRES plumbing: a preconditioner network with all parameters zero gives
+    z = v, so the flexible solve must take exactly the GMRES iterations and
+    return the same currents."""
+    net = vielib.Net((4, 6, 8, 8), seed=0, bf16=False, cin=7)
+    net.set_params(np.zeros(net.num_params(), dtype=np.float32))
+    wl = inputs.random_body_workload(10200, n_axis=32, h=1.0 / 32.0, n_dirs=2)
+    chs = [(c.khat, c.pol) for c in wl.channels]
+    with vielib.Handle(wl.grid.n, wl.grid.h, wl.eps, wl.k0) as hd:
+        s0 = hd.solve(chs, tol=1e-8, restart=32, max_iter=5000)
+        W0 = np.stack([hd.get_current(r) for r in range(len(chs))])
+        hd.attach_precond(net, 4)
+        s1 = hd.solve(chs, tol=1e-8, restart=32, max_iter=5000, precond=1)
+        W1 = np.stack([hd.get_current(r) for r in range(len(chs))])
+    assert s0["converged"] == s1["converged"] == len(chs)
+    assert np.array_equal(s0["iters"], s1["iters"])
+    assert np.abs(W1 - W0).max() <= 1e-12 * np.abs(W0).max()
+
+
+def test_learned_preconditioner(vielib):
+    """Train the preconditioner network on pairs (A v, v) from solved 64^3
+    bodies (v = the currents and their first Krylov images), then solve
+    held-out bodies with plain GMRES and with FGMRES + the network.  Every RHS
+    must reach the FP64 target; the iteration counts of both are printed."""
+    from paper_2508_16471_gb300 import learned
+    n, h, f, dirs = 64, 1.0 / 64.0, 4, 4
+    D = n // f
+    X, T, M = learned.generate_precond(n, h, list(range(10000, 10008)), dirs, f, powers=3)
+    net = vielib.Net((16, 32, 64, 64), seed=0, bf16=True, cin=7)
+    hist = learned.train(net, X, T, M, D, epochs=40, batch=8, lr=2e-3, lr_decay=0.95)
+    assert np.all(np.isfinite(hist)) and hist[-1] < hist[0], hist
+    base, pre = [], []
+    for seed in (10100, 10101):
+        wl = inputs.random_body_workload(seed, n_axis=n, h=h, n_dirs=dirs)
+        chs = [(c.khat, c.pol) for c in wl.channels]
+        with vielib.Handle(wl.grid.n, wl.grid.h, wl.eps, wl.k0) as hd:
+            s0 = hd.solve(chs, tol=1e-6, restart=64, max_iter=20000)
+            hd.attach_precond(net, f)
+            s1 = hd.solve(chs, tol=1e-6, restart=64, max_iter=20000, precond=1)
+            assert s1["converged"] == len(chs) and s1["relres_max"] <= 1e-6
+            base.extend(s0["iters"].tolist())
+            pre.extend(s1["iters"].tolist())
+    print(f"learned preconditioner: mean GMRES iterations {np.mean(base):.1f} -> FGMRES {np.mean(pre):.1f} "
+          f"({100 * (1 - np.mean(pre) / np.mean(base)):.1f} % fewer), training loss {hist[0]:.4f} -> {hist[-1]:.4f}")
