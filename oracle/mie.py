@@ -95,6 +95,31 @@ def farfield(radius, eps_r, k0, theta, phi):
     return Ft[:, None] * eth + Fp[:, None] * eph
 
 
+def farfield_general(radius, eps_r, k0, khat, pol, dirs):
+    """Cartesian far field F (D, 3) for a plane wave along unit ``khat`` with
+    polarisation ``pol`` (transverse), by rotational symmetry of the sphere:
+    with the scattering plane spanned by khat and the direction r, e_perp =
+    khat x r / |khat x r|, the incident parallel axis e_perp x khat and the
+    scattered one e_perp x r,
+        F = (i/k0) [S2(Theta) (pol . e_perp x khat) e_perp x r + S1(Theta) (pol . e_perp) e_perp],
+    Theta the angle between khat and r; khat = z, pol = x gives ``farfield``."""
+    khat = np.asarray(khat, float)
+    pol = np.asarray(pol, complex)
+    dirs = np.asarray(dirs, float).reshape(-1, 3)
+    theta = np.arccos(np.clip(dirs @ khat, -1.0, 1.0))
+    S1, S2 = amplitudes(k0 * radius, math.sqrt(eps_r), theta)
+    out = np.zeros((len(dirs), 3), dtype=np.complex128)
+    for i, r in enumerate(dirs):
+        c = np.cross(khat, r)
+        nc = np.linalg.norm(c)
+        if nc < 1e-12:  # forward / backward: any axis normal to khat
+            c = np.cross(khat, (1.0, 0.0, 0.0) if abs(khat[0]) < 0.9 else (0.0, 1.0, 0.0))
+            nc = np.linalg.norm(c)
+        ep = c / nc
+        out[i] = (1j / k0) * (S2[i] * (pol @ np.cross(ep, khat)) * np.cross(ep, r) + S1[i] * (pol @ ep) * ep)
+    return out
+
+
 def extinction_efficiency(radius, eps_r, k0):
     """Q_ext = (2/x^2) sum (2n+1) Re(a_n + b_n)."""
     x = k0 * radius

@@ -230,3 +230,20 @@ def test_mie_components_in_spherical_basis():
     assert np.allclose(S[:, 0], 1j / K0 * S2 * np.cos(ph), atol=1e-14)
     assert np.allclose(S[:, 1], -1j / K0 * S1 * np.sin(ph), atol=1e-14)
     assert np.abs(S[:, 2]).max() < 1e-14
+
+
+def test_mie_general_incidence_pins():
+    """The arbitrary-incidence Mie far field reduces to the z/x case and is
+    covariant under a rotation of incidence, polarisation and directions."""
+    T, P, d = _mie_dirs()
+    sel = slice(None, None, 7)
+    F0 = mie.farfield(0.3, 2.1, K0, T[sel], P[sel])
+    Fg = mie.farfield_general(0.3, 2.1, K0, (0, 0, 1.0), (1.0, 0, 0), d[sel])
+    assert np.abs(Fg - F0).max() <= 1e-13 * np.abs(F0).max()
+    rng = np.random.default_rng(5)
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    Q *= np.sign(np.linalg.det(Q))
+    Fr = mie.farfield_general(0.3, 2.1, K0, Q @ (0, 0, 1.0), Q @ np.array([1.0, 0, 0]), d[sel] @ Q.T)
+    assert np.abs(Fr - F0 @ Q.T).max() <= 1e-12 * np.abs(F0).max()
+    # transversality
+    assert np.abs(np.sum(Fr * (d[sel] @ Q.T), axis=1)).max() <= 1e-13 * np.abs(F0).max()
