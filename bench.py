@@ -58,6 +58,8 @@ def parse():
                    help="mixed mode: relative residual reduction asked of each FP32 inner solve")
     p.add_argument("--plain-rhs", type=int, default=4)
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-bicgstab", action="store_true",
+                   help="skip the comparison solve with BiCGStab (the paper's solver) on the first timed body")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--max-iter", type=int, default=20000)
@@ -317,11 +319,12 @@ def run_ours(args):
     e0.record(stream)
     t0 = time.perf_counter()
     solved, iters, outers, relmax, mv32 = 0, [], [], 0.0, 0
-    first_iters = None
+    first_iters = first_all_iters = None
     for i in range(args.steps):
         st = step(args.warmup + i)
         if first_iters is None:
             first_iters = st["iters"][:args.plain_rhs].tolist()
+            first_all_iters = st["iters"].tolist()
         solved += int(st["converged"])
         mv32 += int(st["matvecs32"])
         iters.extend(st["iters"].tolist())
@@ -382,6 +385,21 @@ def run_ours(args):
                  "mixed_iters_mean_same_rhs": float(np.mean(first_iters)) if first_iters else None,
                  "body_seed": seeds[b0]}
 
+    # ---- the paper's solver (BiCGStab) on the same body, same refinement ------
+    bicg = None
+    if not args.no_bicgstab and rank == 0:
+        hd.set_eps_device(eps_dev[b0].data_ptr())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = hd.solve(chs, allow_noconv=True, tol=1e-6, restart=args.restart, precision=V.PREC_MIXED,
+                      max_iter=args.max_iter, inner_tol=args.inner_tol, solver=V.SOLVER_BICGSTAB)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        bicg = {"value": int(st["converged"]) / tb, "unit": UNIT, "rhs": R, "converged": int(st["converged"]),
+                "seconds": tb, "steps_mean": float(np.mean(st["iters"])),
+                "matvecs32_per_rhs": st["matvecs32"] / R, "body_seed": seeds[b0],
+                "gmres_iters_mean_same_body": float(np.mean(first_all_iters)) if first_all_iters else None}
+
     # ---- roofline of the dominant kernel -----------------------------------
     peaks = load_peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
@@ -436,7 +454,7 @@ def run_ours(args):
                    "bodies_per_rank": args.bodies, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (no flush)"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-        "roofline": roof, "matvec_fp32": matvec, "cpu_baseline": cpu, "plain_fp64": plain,
+        "roofline": roof, "matvec_fp32": matvec, "cpu_baseline": cpu, "plain_fp64": plain, "bicgstab": bicg,
         "speedup_vs_plain": (value / plain["value"]) if plain and plain["value"] else None,
         "solver_stats": {"solved": tot_solved, "rhs_total": args.steps * R * world,
                          "iters_mean": float(np.mean(iters)) if iters else None,

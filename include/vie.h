@@ -55,6 +55,10 @@ extern "C" {
                             Givens), iterative refinement on the FP64 residual  */
 #define VIE_PREC_FP64  1 /* plain FP64 GMRES(m): FP64 matvec and basis          */
 
+/* ---- Krylov solvers (vie_solve_opts.solver) ----------------------------- */
+#define VIE_SOLVER_GMRES    0 /* batched restarted GMRES(m), CGS + selective reorth.  */
+#define VIE_SOLVER_BICGSTAB 1 /* batched BiCGStab (van der Vorst), the paper's solver */
+
 /* ---- far-field component bases (vie_farfield*) -------------------------- */
 #define VIE_BASIS_CART 0 /* (F_x, F_y, F_z)                                      */
 #define VIE_BASIS_SPH  1 /* (F_theta, F_phi, F_r)   (F_r = 0 up to rounding)     */
@@ -93,7 +97,11 @@ typedef struct vie_solve_opts {
                           replaced by zero.                                       */
     int precond;       /* 0: GMRES; 1: FGMRES with the learned right preconditioner
                           attached by vie_attach_precond (mixed or FP64 basis)   */
-    int reserved[2];
+    int solver;        /* VIE_SOLVER_GMRES (default) or VIE_SOLVER_BICGSTAB: the
+                          paper's solver (Sec. II-C) inside the same FP64
+                          refinement; needs restart >= 8 (its 7 vectors use the
+                          basis storage), use_x0 0 or 1, precond 0             */
+    int reserved[1];
 } vie_solve_opts;
 
 typedef struct vie_solve_stats {

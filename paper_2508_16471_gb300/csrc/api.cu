@@ -150,6 +150,7 @@ void vie_default_opts(vie_solve_opts* o) {
     o->inner_tol = 1e-6;
     o->use_x0 = 0;
     o->precond = 0;
+    o->solver = VIE_SOLVER_GMRES;
 }
 
 const char* vie_last_error(void) { return g_err.c_str(); }
@@ -247,6 +248,10 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
     if (o.use_x0 == 2 && !hd->net) return fail(VIE_ESTATE, "use_x0 = 2 needs a network attached with vie_attach_net");
     if (o.use_x0 < 0 || o.use_x0 > 2) return fail(VIE_EINVAL, "use_x0 must be 0, 1 or 2");
     if (o.precond != 0 && o.precond != 1) return fail(VIE_EINVAL, "precond must be 0 or 1");
+    if (o.solver != VIE_SOLVER_GMRES && o.solver != VIE_SOLVER_BICGSTAB)
+        return fail(VIE_EINVAL, "solver must be VIE_SOLVER_GMRES or VIE_SOLVER_BICGSTAB");
+    if (o.solver == VIE_SOLVER_BICGSTAB && (o.restart < 8 || o.precond || o.use_x0 == 2))
+        return fail(VIE_EINVAL, "BiCGStab needs restart >= 8, precond 0 and use_x0 0 or 1");
     if (o.precond == 1 && !hd->pctx.net)
         return fail(VIE_ESTATE, "precond = 1 needs a network attached with vie_attach_precond");
     VIE_CUDA(cudaSetDevice(hd->device));

@@ -961,10 +961,371 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
     return VIE_OK;
 }
 
+// ---- BiCGStab (the paper's solver, Sec. II-C) ------------------------------
+// Same outer FP64 refinement as GMRES: each inner solve runs BiCGStab (van der
+// Vorst) on A_T d = r in the working precision T from d = 0 until its own
+// residual meets the target (or a breakdown), then x += d in FP64 and the FP64
+// residual decides.  Vectors in the basis slots of V: 0 rhat, 1 r, 2 p, 3 v,
+// 4 s, 5 t, 6 d.  Per-RHS scalars (FP64 complex) in coef[r][0..9]: rho, alpha,
+// omega, rho_new, beta, <rhat,v>, <t,s>, <t,t>, ||s||^2, ||r||^2.  Inner
+// products as in the Arnoldi kernels: products in T, TwoSum warp sums, FP64
+// across warps and blocks.
+enum { BI_RH = 0, BI_R, BI_P, BI_V, BI_S, BI_T, BI_D, BI_NV };
+enum { SC_RHO = 0, SC_ALPHA, SC_OMEGA, SC_RHON, SC_BETA, SC_RV, SC_TS, SC_TT, SC_SS, SC_RR, SC_N };
+
+// partial[(r*ps + q)*nblk + b] = block sum of conj(V_a[q]) . V_b[q], q < np (<= 3)
+template <typename T>
+__global__ void k_bi_dots(const cplx<T>* __restrict__ V, long long vrs, long long n, const int* __restrict__ list,
+                          int np, int a0, int b0, int a1, int b1, int a2, int b2, c64* __restrict__ partial, int ps,
+                          int nblk) {
+    __shared__ double sre[3][KB / 32], sim[3][KB / 32];
+    const int r = list[blockIdx.y];
+    const cplx<T>* Vr = V + r * vrs;
+    const int av[3] = {a0, a1, a2}, bv[3] = {b0, b1, b2};
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = 0; q < np; ++q) {
+        const cplx<T>* x = Vr + (long long)av[q] * n;
+        const cplx<T>* y = Vr + (long long)bv[q] * n;
+        T ar = 0, ai = 0;
+#pragma unroll
+        for (int k = 0; k < KE; ++k) {
+            const long long e = e0 + k * KB;
+            if (e < n) {
+                const cplx<T> u = x[e], w = y[e];
+                ar += u.x * w.x + u.y * w.y;
+                ai += u.x * w.y - u.y * w.x;
+            }
+        }
+        const double dr = warp_sum_comp(ar), di = warp_sum_comp(ai);
+        if (lane == 0) {
+            sre[q][wid] = dr;
+            sim[q][wid] = di;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < np) {
+        double tr = 0, ti = 0;
+        for (int w = 0; w < KB / 32; ++w) {
+            tr += sre[threadIdx.x][w];
+            ti += sim[threadIdx.x][w];
+        }
+        partial[((long long)r * ps + threadIdx.x) * nblk + blockIdx.x] = c64{tr, ti};
+    }
+}
+
+// coef[r][slot_q] = sum over blocks of partial q (one block per (q, RHS))
+__global__ void k_bi_reduce(const c64* __restrict__ partial, int ps, int nblk, c64* __restrict__ coef, int cs,
+                            const int* __restrict__ list, int s0, int s1, int s2) {
+    __shared__ double sre[KB / 32], sim[KB / 32];
+    const int r = list[blockIdx.y], q = blockIdx.x;
+    const c64* p = partial + ((long long)r * ps + q) * nblk;
+    double ar = 0, ai = 0;
+    for (int b = threadIdx.x; b < nblk; b += KB) {
+        ar += p[b].x;
+        ai += p[b].y;
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if ((threadIdx.x & 31) == 0) {
+        sre[threadIdx.x >> 5] = ar;
+        sim[threadIdx.x >> 5] = ai;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0, ti = 0;
+        for (int w = 0; w < KB / 32; ++w) {
+            tr += sre[w];
+            ti += sim[w];
+        }
+        const int slot = q == 0 ? s0 : (q == 1 ? s1 : s2);
+        coef[(long long)r * cs + slot] = c64{tr, ti};
+    }
+}
+
+__device__ __forceinline__ c64 cdiv(c64 a, c64 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return c64{(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+__device__ __forceinline__ bool tiny(c64 a) { return !(a.x * a.x + a.y * a.y > 1e-300); }
+
+// per-RHS scalar steps; stage 0: beta = (rho_new/rho)(alpha/omega), rho = rho_new;
+// stage 1: alpha = rho / <rhat,v>; stage 2: omega = <t,s>/<t,t>.  A vanishing
+// denominator stops the RHS (flag 2 = breakdown) with the scalars zeroed so that
+// the remaining vector updates of the step change nothing.
+__global__ void k_bi_scalars(c64* __restrict__ coef, int cs, const int* __restrict__ list, int nr, int stage,
+                             int* __restrict__ flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    const int r = list[i];
+    c64* c = coef + (long long)r * cs;
+    if (stage == 0) {
+        if (tiny(c[SC_RHO]) || tiny(c[SC_OMEGA]) || tiny(c[SC_RHON])) {
+            c[SC_BETA] = c64{0, 0};
+            flag[r] = 2;
+        } else {
+            c[SC_BETA] = cdiv(c[SC_RHON], c[SC_RHO]) * cdiv(c[SC_ALPHA], c[SC_OMEGA]);
+        }
+        c[SC_RHO] = c[SC_RHON];
+    } else if (stage == 1) {
+        if (tiny(c[SC_RV])) {
+            c[SC_ALPHA] = c64{0, 0};
+            flag[r] = 2;
+        } else {
+            c[SC_ALPHA] = cdiv(c[SC_RHO], c[SC_RV]);
+        }
+    } else {
+        c[SC_OMEGA] = tiny(c[SC_TT]) ? c64{0, 0} : cdiv(c[SC_TS], c[SC_TT]);
+        if (tiny(c[SC_TT])) flag[r] = 2;
+    }
+}
+
+// vector steps: stage 0  p = r + beta (p - omega v);
+//               stage 1  s = r - alpha v;
+//               stage 2  d += alpha p + omega s, r = s - omega t
+template <typename T>
+__global__ void k_bi_update(cplx<T>* __restrict__ V, long long vrs, long long n, const int* __restrict__ list,
+                            const c64* __restrict__ coef, int cs, int stage) {
+    const int r = list[blockIdx.y];
+    cplx<T>* Vr = V + r * vrs;
+    const c64* c = coef + (long long)r * cs;
+    const cplx<T> beta = {(T)c[SC_BETA].x, (T)c[SC_BETA].y};
+    const cplx<T> alpha = {(T)c[SC_ALPHA].x, (T)c[SC_ALPHA].y};
+    const cplx<T> omega = {(T)c[SC_OMEGA].x, (T)c[SC_OMEGA].y};
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e >= n) continue;
+        if (stage == 0) {
+            const cplx<T> rr = Vr[BI_R * n + e], pp = Vr[BI_P * n + e], vv = Vr[BI_V * n + e];
+            Vr[BI_P * n + e] = rr + beta * (pp - omega * vv);
+        } else if (stage == 1) {
+            const cplx<T> rr = Vr[BI_R * n + e], vv = Vr[BI_V * n + e];
+            Vr[BI_S * n + e] = rr - alpha * vv;
+        } else {
+            const cplx<T> pp = Vr[BI_P * n + e], ss = Vr[BI_S * n + e], tt = Vr[BI_T * n + e];
+            Vr[BI_D * n + e] = Vr[BI_D * n + e] + alpha * pp + omega * ss;
+            Vr[BI_R * n + e] = ss - omega * tt;
+        }
+    }
+}
+
+// start of an inner solve: r = rhat = (T) res, p = v = d = 0; rho = alpha = omega = 1
+template <typename T>
+__global__ void k_bi_start(const c64* __restrict__ res, long long rs, cplx<T>* __restrict__ V, long long vrs,
+                           const int* __restrict__ list, c64* __restrict__ coef, int cs, long long n) {
+    const int r = list[blockIdx.y];
+    cplx<T>* Vr = V + r * vrs;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+    const cplx<T> z = {(T)0, (T)0};
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e >= n) continue;
+        const c64 v = res[r * rs + e];
+        const cplx<T> t = {(T)v.x, (T)v.y};
+        Vr[BI_RH * n + e] = t;
+        Vr[BI_R * n + e] = t;
+        Vr[BI_P * n + e] = z;
+        Vr[BI_V * n + e] = z;
+        Vr[BI_D * n + e] = z;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c64* c = coef + (long long)r * cs;
+        c[SC_RHO] = c64{1, 0};
+        c[SC_ALPHA] = c64{1, 0};
+        c[SC_OMEGA] = c64{1, 0};
+    }
+}
+
+// inner convergence: flag 1 when ||r|| <= target (or ||s|| <= target after the
+// half step, in which case the second half is skipped through omega = 0)
+__global__ void k_bi_check(c64* __restrict__ coef, int cs, const double* __restrict__ target,
+                           const int* __restrict__ list, int nr, int which, int* __restrict__ flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    const int r = list[i];
+    c64* c = coef + (long long)r * cs;
+    const double nrm = sqrt(fmax(0.0, c[which].x));
+    if (!(nrm > target[r])) {
+        if (flag[r] == 0) flag[r] = 1;
+    }
+}
+
+// x += (double) d
+template <typename T>
+__global__ void k_bi_xupdate(c64* __restrict__ x, long long xs, const cplx<T>* __restrict__ V, long long vrs,
+                             const int* __restrict__ list, long long n) {
+    const int r = list[blockIdx.y];
+    const cplx<T>* d = V + r * vrs + BI_D * n;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e >= n) continue;
+        const c64 xv = x[r * xs + e];
+        x[r * xs + e] = c64{xv.x + (double)d[e].x, xv.y + (double)d[e].y};
+    }
+}
+
+template <typename T>
+static int bicgstab_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult& out) {
+    const long long n = S.n3;
+    const int R = S.R, m = S.m, nblk = S.nblk;
+    const int cs = m + 2;     // coef stride
+    const int ps = m + 2;     // partial stride (entries per RHS)
+    if (m + 1 < BI_NV || cs < SC_N) return fail(VIE_EINVAL, "BiCGStab needs restart >= 8 (vector slots)");
+    const long long vrs = n * (m + 1);
+    cplx<T>* V = (cplx<T>*)S.V;
+    cudaStream_t st = op.stream;
+    const int prec_in = sizeof(T) == 8 ? VIE_PREC_FP64 : VIE_PREC_MIXED;
+    const double ET = sizeof(cplx<T>);
+
+    std::vector<int> all(R), it(R, 0), outer(R, 0), done(R, 0), hflag(R);
+    for (int r = 0; r < R; ++r) all[r] = r;
+    std::vector<double> hb(R), hr(R), htarget(R);
+    VIE_TRY(op_set_list(op, all.data(), R));
+    k_residual<<<dim3(nblk, R), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 1);
+    LAUNCH_CHECK();
+    k_norm_finish<<<ceil_div(R, 128), 128, 0, st>>>(S.normpart, nblk, S.bnorm, op.d_list, R);
+    LAUNCH_CHECK();
+    VIE_CUDA(cudaMemcpyAsync(hb.data(), S.bnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; ++r)
+        if (!(hb[r] > 0) || !std::isfinite(hb[r])) return fail(VIE_EINVAL, "right-hand side is zero or not finite");
+    out.matvecs32 = out.matvecs64 = 0;
+    out.guesses_rejected = 0;
+    bool first = !o.use_x0;  // x = 0: r = b without an operator application
+    auto dots = [&](int ni, int np, int a0, int b0, int a1, int b1, int a2, int b2, int s0, int s1, int s2) -> int {
+        tmr_begin(TMR_DOTS, st);
+        k_bi_dots<T><<<dim3(nblk, ni), KB, 0, st>>>(V, vrs, n, op.d_list, np, a0, b0, a1, b1, a2, b2, S.partial, ps,
+                                                     nblk);
+        tmr_end(TMR_DOTS, st, (double)ni * np * 2.0 * n * ET);
+        LAUNCH_CHECK();
+        tmr_begin(TMR_REDUCE, st);
+        k_bi_reduce<<<dim3(np, ni), KB, 0, st>>>(S.partial, ps, nblk, S.coef, cs, op.d_list, s0, s1, s2);
+        tmr_end(TMR_REDUCE, st, (double)ni * np * nblk * 16.0);
+        LAUNCH_CHECK();
+        return VIE_OK;
+    };
+    while (true) {
+        std::vector<int> act;
+        for (int r = 0; r < R; ++r)
+            if (!done[r]) act.push_back(r);
+        if (act.empty()) break;
+        const int na = (int)act.size();
+        VIE_TRY(op_set_list(op, act.data(), na));
+        if (first) {
+            k_residual<<<dim3(nblk, na), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 1);
+        } else {
+            VIE_TRY(op_apply(op, VIE_PREC_FP64, S.x, n, S.res, n, op.d_list, na));
+            out.matvecs64 += na;
+            k_residual<<<dim3(nblk, na), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 0);
+        }
+        LAUNCH_CHECK();
+        first = false;
+        k_norm_finish<<<ceil_div(na, 128), 128, 0, st>>>(S.normpart, nblk, S.rnorm, op.d_list, na);
+        LAUNCH_CHECK();
+        VIE_CUDA(cudaMemcpyAsync(hr.data(), S.rnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        VIE_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> cyc;
+        for (int r : act) {
+            const double rel = hr[r] / hb[r];
+            out.relres[r] = rel;
+            if (rel <= o.tol || !std::isfinite(rel)) done[r] = 1;
+            else if (it[r] >= o.max_iter) done[r] = 2;
+            else cyc.push_back(r);
+        }
+        if (cyc.empty()) break;
+        for (int r : cyc) {
+            outer[r]++;
+            double t = 0.99 * o.tol * hb[r];
+            if (prec_in == VIE_PREC_MIXED) t = std::max(o.inner_tol * hr[r], 0.3 * o.tol * hb[r]);
+            htarget[r] = t;
+        }
+        VIE_CUDA(cudaMemcpyAsync(S.target, htarget.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+        VIE_CUDA(cudaMemsetAsync(S.flag, 0, sizeof(int) * R, st));
+        const int nc = (int)cyc.size();
+        VIE_TRY(op_set_list(op, cyc.data(), nc));
+        k_bi_start<T><<<dim3(nblk, nc), KB, 0, st>>>(S.res, n, V, vrs, op.d_list, S.coef, cs, n);
+        LAUNCH_CHECK();
+        std::vector<int> inner = cyc;
+        int steps = 0;
+        while (!inner.empty()) {
+            const int ni = (int)inner.size();
+            VIE_TRY(op_set_list(op, inner.data(), ni));
+            dim3 gi(nblk, ni);
+            // rho_new = <rhat, r>; beta; p = r + beta (p - omega v)
+            VIE_TRY(dots(ni, 1, BI_RH, BI_R, 0, 0, 0, 0, SC_RHON, 0, 0));
+            k_bi_scalars<<<ceil_div(ni, 64), 64, 0, st>>>(S.coef, cs, op.d_list, ni, 0, S.flag);
+            LAUNCH_CHECK();
+            tmr_begin(TMR_UPDATE, st);
+            k_bi_update<T><<<gi, KB, 0, st>>>(V, vrs, n, op.d_list, S.coef, cs, 0);
+            tmr_end(TMR_UPDATE, st, 4.0 * ni * n * ET);
+            LAUNCH_CHECK();
+            // v = A p; alpha = rho / <rhat, v>; s = r - alpha v
+            VIE_TRY(op_apply(op, prec_in, V + BI_P * n, vrs, V + BI_V * n, vrs, op.d_list, ni));
+            VIE_TRY(dots(ni, 1, BI_RH, BI_V, 0, 0, 0, 0, SC_RV, 0, 0));
+            k_bi_scalars<<<ceil_div(ni, 64), 64, 0, st>>>(S.coef, cs, op.d_list, ni, 1, S.flag);
+            LAUNCH_CHECK();
+            tmr_begin(TMR_UPDATE, st);
+            k_bi_update<T><<<gi, KB, 0, st>>>(V, vrs, n, op.d_list, S.coef, cs, 1);
+            tmr_end(TMR_UPDATE, st, 3.0 * ni * n * ET);
+            LAUNCH_CHECK();
+            // t = A s; omega = <t,s>/<t,t>; d += alpha p + omega s; r = s - omega t
+            VIE_TRY(op_apply(op, prec_in, V + BI_S * n, vrs, V + BI_T * n, vrs, op.d_list, ni));
+            VIE_TRY(dots(ni, 2, BI_T, BI_S, BI_T, BI_T, 0, 0, SC_TS, SC_TT, 0));
+            k_bi_scalars<<<ceil_div(ni, 64), 64, 0, st>>>(S.coef, cs, op.d_list, ni, 2, S.flag);
+            LAUNCH_CHECK();
+            tmr_begin(TMR_UPDATE, st);
+            k_bi_update<T><<<gi, KB, 0, st>>>(V, vrs, n, op.d_list, S.coef, cs, 2);
+            tmr_end(TMR_UPDATE, st, 7.0 * ni * n * ET);
+            LAUNCH_CHECK();
+            if (prec_in == VIE_PREC_FP64) out.matvecs64 += 2 * ni;
+            else out.matvecs32 += 2 * ni;
+            // ||r||^2 against the target
+            VIE_TRY(dots(ni, 1, BI_R, BI_R, 0, 0, 0, 0, SC_RR, 0, 0));
+            k_bi_check<<<ceil_div(ni, 64), 64, 0, st>>>(S.coef, cs, S.target, op.d_list, ni, SC_RR, S.flag);
+            LAUNCH_CHECK();
+            VIE_CUDA(cudaMemcpyAsync(hflag.data(), S.flag, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+            VIE_CUDA(cudaStreamSynchronize(st));
+            ++steps;
+            std::vector<int> nxt;
+            for (int r : inner) {
+                it[r]++;
+                if (!hflag[r] && it[r] < o.max_iter) nxt.push_back(r);
+            }
+            inner.swap(nxt);
+        }
+        VIE_TRY(op_set_list(op, cyc.data(), nc));
+        tmr_begin(TMR_XUPDATE, st);
+        k_bi_xupdate<T><<<dim3(nblk, nc), KB, 0, st>>>(S.x, n, V, vrs, op.d_list, n);
+        tmr_end(TMR_XUPDATE, st, (double)nc * n * (ET + 32.0));
+        LAUNCH_CHECK();
+    }
+    out.converged = 0;
+    out.iters_max = 0;
+    out.outer_max = 0;
+    out.relres_max = 0;
+    for (int r = 0; r < R; ++r) {
+        out.iters[r] = it[r];
+        out.converged += done[r] == 1;
+        out.iters_max = std::max(out.iters_max, it[r]);
+        out.outer_max = std::max(out.outer_max, outer[r]);
+        out.relres_max = std::max(out.relres_max, out.relres[r]);
+    }
+    return VIE_OK;
+}
+
 int solver_run(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult& out) {
     out.iters.assign(S.R, 0);
     out.relres.assign(S.R, 0.0);
     if (!o.use_x0) VIE_CUDA(cudaMemsetAsync(S.x, 0, sizeof(c64) * S.n3 * S.R, op.stream));
+    if (o.solver == VIE_SOLVER_BICGSTAB) {
+        if (S.prec == VIE_PREC_FP64) return bicgstab_t<double>(op, S, o, out);
+        return bicgstab_t<float>(op, S, o, out);
+    }
     if (S.prec == VIE_PREC_FP64) return gmres_t<double>(op, S, o, out);
     return gmres_t<float>(op, S, o, out);
 }

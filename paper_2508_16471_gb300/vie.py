@@ -18,6 +18,7 @@ VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_ENOCONV = 0, -1, -2, -3
 VIE_ETIMEOUT, VIE_EUNDEF, VIE_EDEVICE, VIE_ESTATE = -4, -5, -6, -7
 PREC_MIXED, PREC_FP64 = 0, 1
 BASIS_CART, BASIS_SPH, BASIS_CIRC = 0, 1, 2
+SOLVER_GMRES, SOLVER_BICGSTAB = 0, 1
 
 EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device", "vie_solve",
            "vie_farfield", "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer",
@@ -46,7 +47,7 @@ class _Channel(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iter", C.c_int),
                 ("precision", C.c_int), ("inner_tol", C.c_double), ("use_x0", C.c_int),
-                ("precond", C.c_int), ("reserved", C.c_int * 2)]
+                ("precond", C.c_int), ("solver", C.c_int), ("reserved", C.c_int * 1)]
 
 
 class _Stats(C.Structure):

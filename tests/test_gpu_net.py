@@ -121,7 +121,7 @@ def test_learned_initial_guess_gains_over_zero(vielib):
             base.extend(s0["iters"].tolist())
             lrn.extend(s1["iters"].tolist())
     print(f"learned initial guess: mean GMRES iterations {np.mean(base):.1f} -> {np.mean(lrn):.1f} "
-          f"({100 * (1 - np.mean(lrn) / np.mean(base)):.1f} % fewer), {rej} guesses rejected, "
+          f"({100 * (np.mean(lrn) / np.mean(base) - 1):+.1f} % iterations), {rej} guesses rejected, "
           f"training loss {hist[0]:.4f} -> {hist[-1]:.4f}")
     assert rej == 0  # the minimal-residual combination is never worse than zero
     assert np.mean(lrn) <= 1.01 * np.mean(base)
@@ -170,4 +170,5 @@ def test_learned_preconditioner(vielib):
             base.extend(s0["iters"].tolist())
             pre.extend(s1["iters"].tolist())
     print(f"learned preconditioner: mean GMRES iterations {np.mean(base):.1f} -> FGMRES {np.mean(pre):.1f} "
-          f"({100 * (1 - np.mean(pre) / np.mean(base)):.1f} % fewer), training loss {hist[0]:.4f} -> {hist[-1]:.4f}")
+          f"({100 * (np.mean(pre) / np.mean(base) - 1):+.1f} % iterations), "
+          f"training loss {hist[0]:.4f} -> {hist[-1]:.4f}")

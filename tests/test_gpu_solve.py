@@ -56,6 +56,19 @@ def test_config1_currents_and_farfield(vielib, config1, prec):
     assert _rel(Fg, F_or) < 1e-5 and _maxrel(Fg, F_or) < 1e-5
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bicgstab_config1_currents(vielib, config1, prec):
+    """The paper's solver (BiCGStab, Sec. II-C) inside the same FP64 refinement
+    reaches the oracle's currents of the 16^3 sphere."""
+    wl, chs, w_or = config1
+    g = wl.grid
+    with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
+        st = hd.solve(chs, tol=1e-10, restart=40, precision=prec, solver=vielib.SOLVER_BICGSTAB)
+        assert st["converged"] == 2 and st["relres_max"] <= 1e-10
+        w = np.stack([hd.get_current(r) for r in range(2)])
+    assert _maxrel(w, w_or) < 1e-8
+
+
 def test_config1_g2_and_coincidences(vielib, config1):
     wl, chs, w_or = config1
     g = wl.grid
@@ -113,14 +126,14 @@ def test_mixed_and_fp64_agree_random_body(vielib):
     assert _maxrel(w64[0], x) < 1e-8
 
 
-def _sampled_residual_check(vielib, wl, chs_idx, restart, nsamp, seed, ff_dirs=None):
+def _sampled_residual_check(vielib, wl, chs_idx, restart, nsamp, seed, ff_dirs=None, solver=0, n_rhs=None):
     """Solve on the GPU, then evaluate the oracle's equation w - chi (K * w) = chi E_inc
     on the GPU's currents at sampled body voxels.  A global FP64 relative residual
     rho bounds every entry: |r_t| <= ||r||_2 <= rho ||b||_2."""
     g = wl.grid
-    chs = [(c.khat, c.pol) for c in wl.channels]
+    chs = [(c.khat, c.pol) for c in wl.channels][:n_rhs]
     with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
-        st = hd.solve(chs, tol=1e-6, restart=restart, precision=vielib.PREC_MIXED, max_iter=50000)
+        st = hd.solve(chs, tol=1e-6, restart=restart, precision=vielib.PREC_MIXED, max_iter=50000, solver=solver)
         assert st["converged"] == len(chs) and st["relres_max"] <= 1e-6
         W = np.stack([hd.get_current(r) for r in chs_idx])
         F = hd.farfield_dirs(ff_dirs)[list(chs_idx)] if ff_dirs is not None else None
@@ -170,6 +183,12 @@ def test_uneven_random_bodies(vielib, seed):
     ph = np.radians([0.0, 70.0, 200.0, 300.0])
     dirs = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], -1)
     _sampled_residual_check(vielib, wl, (0, 9), restart=128, nsamp=4, seed=seed, ff_dirs=dirs)
+
+
+def test_bicgstab_bench_body_solution_satisfies_oracle_equation(vielib):
+    """BiCGStab on the 128^3 bench body (8 of its RHS), sampled oracle residual."""
+    wl = inputs.random_body_workload(20001, n_axis=128, h=1.0 / 128.0, n_dirs=16)
+    _sampled_residual_check(vielib, wl, (0, 5), restart=64, nsamp=3, seed=6, solver=1, n_rhs=8)
 
 
 def test_optical_theorem_on_gpu_solution(vielib):
