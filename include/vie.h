@@ -165,6 +165,20 @@ int vie_set_eps_device(vie_handle* hd, const double* eps_r_dev);
  */
 int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_opts* opts,
               vie_solve_stats* stats);
+/* Solves of independent bodies (handles, each with its own grid and stream)
+ * run concurrently: up to max_threads host threads (<= 0: 8) each drive one
+ * handle's vie_solve, so the kernels of different bodies share the GPU --
+ * bodies of uneven grid sizes whose single solves would leave most SMs idle.
+ * ch[i] / n_rhs[i]: the channels of body i; opts shared (NULL: defaults);
+ * stats: optional array [n_bodies].  Every handle must be distinct (a handle
+ * is not thread-safe) and the kernel timer off.  Returns VIE_OK, or the code
+ * of the first body that failed (hard errors before VIE_ENOCONV) with its
+ * message prefixed by the body index; the other bodies' results stand.
+ * Batching of independent problems is this library's addition; the paper
+ * solves one scatterer at a time. */
+int vie_solve_many(vie_handle* const* hds, const vie_channel* const* ch, const int* n_rhs, int n_bodies,
+                   const vie_solve_opts* opts, vie_solve_stats* stats, int max_threads);
+
 
 /*
  * vie_farfield -- far-field amplitudes of every stored current on a product

@@ -1,4 +1,6 @@
 // C ABI of libvie.so (declarations and contracts in include/vie.h).
+#include <algorithm>
+#include <thread>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -723,6 +725,38 @@ int vie_attach_net(vie_handle* hd, vie_net* n, int factor) {
 }
 
 int vie_guesses_rejected(const vie_handle* hd) { return hd ? hd->guesses_rejected : 0; }
+
+int vie_solve_many(vie_handle* const* hds, const vie_channel* const* ch, const int* n_rhs, int n_bodies,
+                   const vie_solve_opts* opts, vie_solve_stats* stats, int max_threads) {
+    if (!hds || !ch || !n_rhs || n_bodies < 1) return fail(VIE_EINVAL, "NULL argument or n_bodies < 1");
+    if (tmr_enabled()) return fail(VIE_EINVAL, "disable the kernel timer for concurrent solves");
+    for (int i = 0; i < n_bodies; ++i) {
+        if (!hds[i] || !ch[i]) return fail(VIE_EINVAL, "NULL handle or channel list");
+        for (int j = 0; j < i; ++j)
+            if (hds[j] == hds[i]) return fail(VIE_EINVAL, "a handle appears twice (handles are not thread-safe)");
+    }
+    const int nt = std::max(1, std::min(max_threads > 0 ? max_threads : 8, n_bodies));
+    std::vector<int> codes(n_bodies, VIE_OK);
+    std::vector<std::string> msgs(n_bodies);
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        for (int i = next++; i < n_bodies; i = next++) {
+            codes[i] = vie_solve(hds[i], ch[i], n_rhs[i], opts, stats ? &stats[i] : nullptr);
+            if (codes[i] != VIE_OK) msgs[i] = vie_last_error();
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+    for (std::thread& t : pool) t.join();
+    // first hard error, else the first non-convergence
+    int first = -1;
+    for (int i = 0; i < n_bodies && first < 0; ++i)
+        if (codes[i] != VIE_OK && codes[i] != VIE_ENOCONV) first = i;
+    for (int i = 0; i < n_bodies && first < 0; ++i)
+        if (codes[i] != VIE_OK) first = i;
+    if (first < 0) return VIE_OK;
+    return fail(codes[first], "body " + std::to_string(first) + ": " + msgs[first]);
+}
 
 int vie_attach_precond(vie_handle* hd, vie_net* n, int factor) {
     if (!hd) return fail(VIE_EINVAL, "NULL handle");

@@ -66,6 +66,7 @@ enum TimerId {
     TMR_ZFWD = 0, TMR_YFWD, TMR_XFUSED, TMR_YINV, TMR_ZINV, TMR_DOTS, TMR_REDUCE, TMR_UPDATE,
     TMR_FINISH, TMR_SCALE, TMR_XUPDATE, TMR_RESIDUAL, TMR_START, TMR_RHS, TMR_OTHER, TMR_MV64, TMR_COUNT
 };
+bool tmr_enabled();
 void tmr_begin(int id, cudaStream_t s);
 void tmr_end(int id, cudaStream_t s, double bytes = 0.0);
 

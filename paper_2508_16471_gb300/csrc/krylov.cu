@@ -16,6 +16,7 @@
 //     formed with the working-precision operator (mixed mode), so each RHS
 //     normally pays one FP64 operator application, at the final check.
 // Each RHS stops on its own; converged RHS drop out of the launch lists.
+#include <atomic>
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -701,7 +702,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
     cudaStream_t st = op.stream;
     const int prec_in = sizeof(T) == 8 ? VIE_PREC_FP64 : VIE_PREC_MIXED;
     const double ET = sizeof(cplx<T>);
-    static bool smem_set = false;
+    static std::atomic<bool> smem_set{false};
     if (!smem_set) {
         VIE_CUDA(cudaFuncSetAttribute(k_dots<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(double) * 2 * (KB / 32) * (MAX_RESTART + 2))));

@@ -18,6 +18,7 @@
 // once in FP64 with the same FFT engine, and one octant (P/2+1 per axis) per
 // tensor component is kept: K_ij(m) is even or odd in each axis, so its
 // transform is too, and the other octants follow by sign flips.
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -550,7 +551,7 @@ template <> const c64* twp<double>(const AxisFFT& a) { return a.tw64; }
 template <typename T, bool INV>
 static int launch_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_in, int n_out, const FFTPlan& p,
                         const cplx<T>* tw, cudaStream_t s) {
-    static bool init = false;
+    static std::atomic<bool> init{false};  // repeated attribute calls from racing threads are harmless
     if (!init) {
         VIE_TRY(allow_smem(k_lines<T, INV>));
         init = true;
@@ -569,7 +570,7 @@ template <typename T, bool INV>
 static int launch_axis(const cplx<T>* in, cplx<T>* out, long long outer, int n_in, int n_out, long long inner,
                        const FFTPlan& p, const cplx<T>* tw, cudaStream_t s, int tid = TMR_OTHER) {
     const double bytes = (double)sizeof(cplx<T>) * outer * inner * (double)(n_in + n_out);
-    static bool init = false;
+    static std::atomic<bool> init{false};  // repeated attribute calls from racing threads are harmless
     if (!init) {
         VIE_TRY(allow_smem(k_axis<T, INV>));
         init = true;
@@ -741,7 +742,7 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
     const int pi = sizeof(T) == 8 ? 1 : 0;
     VIE_TRY(op_reserve(op, pi, nr));
     MatvecWork& W = op.work[pi];
-    static bool init = false;
+    static std::atomic<bool> init{false};  // repeated attribute calls from racing threads are harmless
     if (!init) {
         VIE_TRY(allow_smem(k_zfwd<T>));
         VIE_TRY(allow_smem(k_zinv<T>));

@@ -19,6 +19,7 @@
 // tcgen05.commit, and the epilogue reads the accumulator with tcgen05.ld.
 // Every wait is bounded; on timeout the kernel records an error flag, frees
 // its tensor memory and returns.
+#include <atomic>
 #include <cstdint>
 
 #include "vie_internal.cuh"
@@ -227,7 +228,7 @@ int tc_cgemm(int M, int N, int K, int batch, const c32* A, long long sAb, long l
     dim3 g((2 * N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
     if (g.y > 65535 || g.z > 65535) return fail(VIE_EINVAL, "tensor-core GEMM grid too large");
     const size_t sm = (size_t)(2 * TC_BM + 2 * TC_BN) * TC_BK * 4;
-    static bool init = false;
+    static std::atomic<bool> init{false};  // repeated attribute calls from racing threads are harmless
     if (!init) {
         VIE_CUDA(cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         init = true;

@@ -60,6 +60,8 @@ const char* kNames[TMR_COUNT] = {"zfwd", "yfwd", "xfused", "yinv", "zinv", "dots
                                  "matvec_fp64"};
 }  // namespace
 
+bool tmr_enabled() { return T().on; }
+
 void tmr_begin(int id, cudaStream_t s) {
     TimerState& t = T();
     if (!t.on) return;

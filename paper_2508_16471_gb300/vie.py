@@ -27,7 +27,7 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_apply_noalloc", "vie_net_create", "vie_net_destroy", "vie_net_num_params",
            "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
            "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_guesses_rejected",
-           "vie_net_create_io", "vie_attach_precond", "vie_precond_pairs", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
+           "vie_net_create_io", "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
 
 
 class VieError(RuntimeError):
@@ -109,6 +109,7 @@ def load():
     L.vie_net_create_io.argtypes = [C.POINTER(C.c_int), C.c_int, C.c_ulonglong, C.c_int, C.POINTER(P)]
     L.vie_attach_precond.argtypes = [P, P, C.c_int]
     L.vie_precond_pairs.argtypes = [P, C.c_int, P, C.c_int, P, P, P]
+    L.vie_solve_many.argtypes = [P, P, P, C.c_int, C.POINTER(_Opts), P, C.c_int]
     L.vie_set_farfield_engine.argtypes = [P, C.c_int]
     L.vie_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int]
     L.vie_kernel_launches.restype = C.c_longlong
@@ -132,7 +133,7 @@ def load():
               "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_net_create",
               "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
               "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_net_create_io",
-              "vie_attach_precond", "vie_precond_pairs"]:
+              "vie_attach_precond", "vie_precond_pairs", "vie_solve_many"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -409,6 +410,34 @@ def hom_transfer(E, omega=None, sigma=1.2, dtau=()):
                                _dptr(nc) if len(dt) else None, _dptr(vis))
     _check(code, allow=(VIE_EUNDEF,))
     return float(g2[0]), nc, float(vis[0]), code
+
+
+def solve_many(handles, channel_lists, allow_noconv=False, max_threads=0, **opts):
+    """vie_solve_many: the solves of several handles (bodies) run concurrently;
+    returns one stats dict per handle (as Handle.solve)."""
+    n = len(handles)
+    assert len(channel_lists) == n and n > 0
+    o = default_opts(**opts)
+    chs = [_channels(c) for c in channel_lists]
+    ch_ptrs = (C.POINTER(_Channel) * n)(*[C.cast(c, C.POINTER(_Channel)) for c in chs])
+    hs = (C.c_void_p * n)(*[h._h for h in handles])
+    nr = (C.c_int * n)(*[len(c) for c in channel_lists])
+    stats = (_Stats * n)()
+    its = [np.zeros(len(c), dtype=np.int32) for c in channel_lists]
+    rels = [np.zeros(len(c), dtype=np.float64) for c in channel_lists]
+    for i in range(n):
+        stats[i].iters = its[i].ctypes.data_as(C.POINTER(C.c_int))
+        stats[i].relres = rels[i].ctypes.data_as(C.POINTER(C.c_double))
+    code = load().vie_solve_many(hs, ch_ptrs, nr, n, C.byref(o), stats, int(max_threads))
+    _check(code, allow=(VIE_ENOCONV,) if allow_noconv else ())
+    out = []
+    for i, h in enumerate(handles):
+        h.n_rhs = len(channel_lists[i])
+        st = stats[i]
+        out.append(dict(converged=st.converged, iters_max=st.iters_max, outer_max=st.outer_max,
+                        matvecs32=st.matvecs32, matvecs64=st.matvecs64, relres_max=st.relres_max,
+                        seconds=st.seconds, iters=its[i], relres=rels[i]))
+    return out
 
 
 def hom_map(Ea, Eb, sigma=1.2):
