@@ -362,6 +362,18 @@ int vie_cgemm(int M, int N, int K, const double* A, const double* B, double* C, 
  * 1 forces the generic kernels everywhere.  Results agree to FP32 round-off;
  * used for A/B timing.  Errors: VIE_EINVAL. */
 int vie_set_fft_path(vie_handle* hd, int path);
+/* Autotuner of the operator's FFT schedule on this handle's grid: times
+ * `reps` FP32 operator applications on n_rhs deterministic test vectors for
+ * each candidate configuration -- per axis the padded length of the default
+ * rule and the other of (next power of two >= 2n-1, smallest 2,3,5,7-smooth
+ * length), i.e. radix-16/8/4/2 four-step kernels or the mixed-radix Stockham
+ * engine, and for power-of-two lengths the register or the generic path --
+ * and keeps the fastest (rebuilding the kernel spectrum; body, solver state
+ * and stored currents are kept).  P_out (optional) receives the padded
+ * lengths, ms_per_apply (optional) the best time of one application.  The
+ * operator's values do not depend on the choice (any P >= 2n-1 embeds the
+ * same convolution); only rounding differs.  Errors: VIE_EINVAL, VIE_ENOMEM. */
+int vie_autotune(vie_handle* hd, int n_rhs, int reps, int P_out[3], double* ms_per_apply);
 
 /* Launch statistics: number of library kernels launched by this process. */
 long long vie_kernel_launches(void);

@@ -1,4 +1,5 @@
 // C ABI of libvie.so (declarations and contracts in include/vie.h).
+#include <array>
 #include <algorithm>
 #include <thread>
 #include <atomic>
@@ -577,6 +578,106 @@ int vie_cgemm(int M, int N, int K, const double* A, const double* B, double* C, 
         C[2 * i] = c[i].x;
         C[2 * i + 1] = c[i].y;
     }
+    return VIE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// deterministic test vectors for the autotuner's timed applications
+__global__ void k_fill_test(vie::c32* w, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        w[i] = vie::c32{(float)((z & 0xFFFF) / 65536.0 - 0.5), (float)(((z >> 16) & 0xFFFF) / 65536.0 - 0.5)};
+    }
+}
+
+// candidate padded lengths of an axis of n voxels: the default choice and the
+// other of (next power of two >= 2n-1, smallest 2,3,5,7-smooth length)
+std::vector<int> pad_candidates(int n) {
+    std::vector<int> c{vie::padded_size(n)};
+    const int sm = vie::smooth_size(2 * n - 1);
+    int p2 = 1;
+    while (p2 < 2 * n - 1) p2 *= 2;
+    for (int v : {sm, p2})
+        if (v != c[0] && v <= 1024 && v * 2 <= 5 * sm) c.push_back(v);
+    return c;
+}
+}  // namespace
+
+extern "C" {
+
+int vie_autotune(vie_handle* hd, int n_rhs, int reps, int P_out[3], double* ms_per_apply) {
+    if (!hd || n_rhs < 1 || reps < 1) return fail(VIE_EINVAL, "NULL handle, n_rhs < 1 or reps < 1");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    Operator& op = hd->op;
+    std::vector<int> cand[3];
+    for (int a = 0; a < 3; ++a) cand[a] = pad_candidates(op.n[a]);
+    std::vector<std::array<int, 4>> configs;  // P0, P1, P2, fft path
+    const bool cubic = op.n[0] == op.n[1] && op.n[1] == op.n[2];
+    for (int i0 = 0; i0 < (int)cand[0].size(); ++i0)
+        for (int i1 = 0; i1 < (int)cand[1].size(); ++i1)
+            for (int i2 = 0; i2 < (int)cand[2].size(); ++i2) {
+                if (cubic && (i0 != i1 || i1 != i2)) continue;
+                const int P[3] = {cand[0][i0], cand[1][i1], cand[2][i2]};
+                const bool any_fast = fast_length(P[0]) || fast_length(P[1]) || fast_length(P[2]);
+                for (int path = 0; path < (any_fast ? 2 : 1); ++path) configs.push_back({P[0], P[1], P[2], path});
+            }
+    const int P0[3] = {op.P[0], op.P[1], op.P[2]};
+    const int path0 = op.fft_path;
+    const long long nv = 3 * op.Nb;
+    c32 *w = nullptr, *y = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = VIE_OK;
+    cudaError_t ce = cudaMalloc(&w, sizeof(c32) * nv * n_rhs);
+    if (ce == cudaSuccess) ce = cudaMalloc(&y, sizeof(c32) * nv * n_rhs);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) st = cuda_fail(ce, "autotune buffers");
+    if (st == VIE_OK) {
+        k_fill_test<<<1024, 256, 0, op.stream>>>(w, nv * n_rhs);
+        count_launch();
+        std::vector<int> lst(n_rhs);
+        for (int i = 0; i < n_rhs; ++i) lst[i] = i;
+        st = op_set_list(op, lst.data(), n_rhs);
+    }
+    double best = 1e300;
+    int bi = -1;
+    for (int c = 0; st == VIE_OK && c < (int)configs.size(); ++c) {
+        const int P[3] = {configs[c][0], configs[c][1], configs[c][2]};
+        if (P[0] != op.P[0] || P[1] != op.P[1] || P[2] != op.P[2]) st = op_replan(op, P);
+        op.fft_path = configs[c][3];
+        if (st == VIE_OK) st = op_apply(op, VIE_PREC_MIXED, w, nv, y, nv, op.d_list, n_rhs);  // warm-up
+        if (st != VIE_OK) break;
+        cudaEventRecord(e0, op.stream);
+        for (int r = 0; st == VIE_OK && r < reps; ++r) st = op_apply(op, VIE_PREC_MIXED, w, nv, y, nv, op.d_list, n_rhs);
+        cudaEventRecord(e1, op.stream);
+        ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) st = cuda_fail(ce, "autotune timing");
+        float ms = 0.f;
+        if (st == VIE_OK) cudaEventElapsedTime(&ms, e0, e1);
+        if (st == VIE_OK && ms / reps < best) {
+            best = ms / reps;
+            bi = c;
+        }
+    }
+    // keep the fastest configuration (or restore the original one on error)
+    const int keep[3] = {bi >= 0 && st == VIE_OK ? configs[bi][0] : P0[0], bi >= 0 && st == VIE_OK ? configs[bi][1] : P0[1],
+                         bi >= 0 && st == VIE_OK ? configs[bi][2] : P0[2]};
+    const int st2 = (keep[0] != op.P[0] || keep[1] != op.P[1] || keep[2] != op.P[2]) ? op_replan(op, keep) : VIE_OK;
+    op.fft_path = bi >= 0 && st == VIE_OK ? configs[bi][3] : path0;
+    cudaFree(w);
+    cudaFree(y);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != VIE_OK) return st;
+    if (st2 != VIE_OK) return st2;
+    if (P_out)
+        for (int a = 0; a < 3; ++a) P_out[a] = op.P[a];
+    if (ms_per_apply) *ms_per_apply = best;
     return VIE_OK;
 }
 

@@ -119,7 +119,8 @@ int padded_size(int n) {
 
 int op_init_axes(Operator& op) {
     for (int a = 0; a < 3; ++a) {
-        op.P[a] = padded_size(op.n[a]);
+        op.P[a] = op.P_fixed[a] > 0 ? op.P_fixed[a] : padded_size(op.n[a]);
+        if (op.P[a] < 2 * op.n[a] - 1) return fail(VIE_EINVAL, "padded length below 2n - 1");
         op.H[a] = op.P[a] / 2 + 1;
         if (!make_plan(op.P[a], &op.ax[a].plan))
             return fail(VIE_EINVAL, "padded FFT size " + std::to_string(op.P[a]) + " exceeds the engine limit (1024)");
@@ -866,6 +867,35 @@ int op_apply(Operator& op, int prec, const void* w, long long wr, void* y, long 
     if (nr <= 0) return VIE_OK;
     if (prec == VIE_PREC_FP64) return apply_t<double>(op, (const c64*)w, wr, (c64*)y, yr, d_list, nr);
     return apply_t<float>(op, (const c32*)w, wr, (c32*)y, yr, d_list, nr);
+}
+
+int op_replan(Operator& op, const int P[3]) {
+    VIE_CUDA(cudaStreamSynchronize(op.stream));
+    for (int a = 0; a < 3; ++a) {
+        AxisFFT& x = op.ax[a];
+        const int n = std::max(1, x.plan.twlen);
+        dev_free(op, x.tw64, sizeof(c64) * n);
+        dev_free(op, x.tw32, sizeof(c32) * n);
+        dev_free(op, x.roots32, sizeof(c32) * 2 * x.plan.L);
+        x.tw64 = nullptr;
+        x.tw32 = nullptr;
+        x.roots32 = nullptr;
+    }
+    const long long HH = (long long)op.H[0] * op.H[1] * op.H[2];
+    dev_free(op, op.khat64, sizeof(c64) * 6 * HH);
+    dev_free(op, op.khat32, sizeof(c32) * 6 * HH);
+    op.khat64 = nullptr;
+    op.khat32 = nullptr;
+    for (int p = 0; p < 2; ++p) {
+        MatvecWork& W = op.work[p];
+        const size_t esz = p ? sizeof(c64) : sizeof(c32);
+        dev_free(op, W.A, esz * 3LL * op.n[0] * op.n[1] * op.P[2] * W.cap);
+        dev_free(op, W.B, esz * 3LL * op.n[0] * op.P[1] * op.P[2] * W.cap);
+        W = MatvecWork();
+    }
+    for (int a = 0; a < 3; ++a) op.P_fixed[a] = P[a];
+    VIE_TRY(op_init_axes(op));
+    return op_build_kernel(op);
 }
 
 void op_free(Operator& op) {

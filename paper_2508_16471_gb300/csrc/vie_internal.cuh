@@ -43,6 +43,7 @@ struct Operator {
     cudaStream_t stream = nullptr;
     double bytes = 0;        // device bytes held
     int fft_path = 0;        // 0: register four-step where the length allows, 1: generic only
+    int P_fixed[3] = {0, 0, 0};  // padded lengths chosen by the autotuner (0: padded_size)
     int ff_engine = 0;       // far-field contractions: 0 tcgen05 3xTF32, 1 CUDA-core FP32
 };
 
@@ -58,6 +59,9 @@ int padded_size(int n);
 // ---- operator (matvec.cu) ---------------------------------------------------
 int op_init_axes(Operator& op);
 int op_build_kernel(Operator& op);                 // K-hat octants (FP64 build)
+// new padded lengths: frees the twiddles, the kernel spectrum and the matvec
+// workspace, then rebuilds the axes and the spectrum (body data unchanged)
+int op_replan(Operator& op, const int P[3]);
 int op_set_body_device(Operator& op, const double* eps_dev);  // chi, idx_map, vox
 int op_reserve(Operator& op, int prec, int nrhs);  // matvec workspace
 int op_set_list(Operator& op, const int* host_list, int nr);  // uploads d_list

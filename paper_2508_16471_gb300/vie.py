@@ -27,7 +27,8 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_apply_noalloc", "vie_net_create", "vie_net_destroy", "vie_net_num_params",
            "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
            "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_guesses_rejected",
-           "vie_net_create_io", "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
+           "vie_net_create_io", "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune",
+           "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
 
 
 class VieError(RuntimeError):
@@ -110,6 +111,7 @@ def load():
     L.vie_attach_precond.argtypes = [P, P, C.c_int]
     L.vie_precond_pairs.argtypes = [P, C.c_int, P, C.c_int, P, P, P]
     L.vie_solve_many.argtypes = [P, P, P, C.c_int, C.POINTER(_Opts), P, C.c_int]
+    L.vie_autotune.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.vie_set_farfield_engine.argtypes = [P, C.c_int]
     L.vie_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int]
     L.vie_kernel_launches.restype = C.c_longlong
@@ -133,7 +135,7 @@ def load():
               "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_net_create",
               "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
               "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_net_create_io",
-              "vie_attach_precond", "vie_precond_pairs", "vie_solve_many"]:
+              "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -265,6 +267,14 @@ class Handle:
 
     def guesses_rejected(self):
         return int(load().vie_guesses_rejected(self._h))
+
+    def autotune(self, n_rhs=8, reps=3):
+        """vie_autotune: time the candidate FFT schedules and keep the fastest;
+        returns (padded lengths, ms per FP32 application)."""
+        P = (C.c_int * 3)()
+        ms = C.c_double()
+        _check(load().vie_autotune(self._h, int(n_rhs), int(reps), P, C.byref(ms)))
+        return tuple(P), ms.value
 
     def attach_precond(self, net, factor):
         """Network used as the FGMRES right preconditioner by solve(..., precond=1)."""

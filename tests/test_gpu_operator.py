@@ -142,3 +142,26 @@ def test_fast_and_generic_fft_paths_agree(vielib, n):
     s = np.abs(y64).max()
     assert np.abs(y_fast - y64).max() <= TOL32 * s
     assert np.abs(y_gen - y64).max() <= TOL32 * s
+
+
+def test_autotune_keeps_the_operator(vielib):
+    """The autotuner times the candidate padded lengths (80 on the mixed-radix
+    engine, 128 on the register or generic power-of-two kernels for a 40^3
+    grid) and keeps the fastest; the operator's values must not change beyond
+    rounding (FP64 1e-11, FP32 2e-5 of max |y|)."""
+    wl = inputs.random_body_workload(11, n_dirs=1)
+    g = wl.grid
+    assert g.n[0] == 40
+    rng = np.random.default_rng(3)
+    with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
+        nb = hd.info()["n_body"]
+        w = rng.standard_normal((2, 3, nb)) + 1j * rng.standard_normal((2, 3, nb))
+        y64 = hd.apply(w, precision=vielib.PREC_FP64)
+        P, ms = hd.autotune(n_rhs=4, reps=2)
+        assert P[0] == P[1] == P[2] and P[0] in (80, 128) and ms > 0
+        assert tuple(hd.info()["P"]) == P
+        z64 = hd.apply(w, precision=vielib.PREC_FP64)
+        z32 = hd.apply(w, precision=vielib.PREC_MIXED)
+    s = np.abs(y64).max()
+    assert np.abs(z64 - y64).max() <= 1e-11 * s
+    assert np.abs(z32 - y64).max() <= 2e-5 * s
