@@ -337,6 +337,8 @@ class Handle:
 
     def apply(self, w, precision=PREC_FP64):
         w = _c128(w)
+        if w.ndim != 5 or w.shape[1:] != (3,) + self.n:
+            raise ValueError(f"apply takes full-grid fields [n_rhs][3]{list(self.n)}, got {list(w.shape)}")
         R = w.shape[0]
         y = np.zeros_like(w)
         _check(load().vie_apply(self._h, _dptr(w.view(np.float64)), y.ctypes.data_as(C.POINTER(C.c_double)),
