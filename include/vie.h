@@ -145,6 +145,22 @@ void vie_default_opts(vie_solve_opts* opts);
  */
 int vie_setup(const vie_grid* g, const double* eps_r, double k0, vie_handle** out);
 
+/* ---- discretisations (vie_setup_disc) ------------------------------------ */
+#define VIE_DISC_D1 0 /* voxel-centred unknown w = chi E, ball-averaged dyadic kernel
+                         (the default of vie_setup)                                   */
+#define VIE_DISC_D2 1 /* the paper's rooftop expansion with pulse testing (Sec. II-C),
+                         read as: unknown w_a on the +a face of each cell (face contrast
+                         (chi(c) + chi(c + e_a))/2), scalar ball-averaged kernel G_h and
+                         the grad-div by differences on the staggered grid,
+                         y_a = w_a - chi_a (k^2 A_a + d+_a sum_b d-_b A_b), A = G_h * w;
+                         the unknown set is the body plus its -x/-y/-z neighbour cells;
+                         bodies should leave the first cell layer of the grid empty  */
+/* vie_setup with a discretisation; with VIE_DISC_D2 every entry point works on
+ * the face unknowns (layouts unchanged: component a of cell c is the +a face of
+ * c; far fields place it at the face centre).  The learned parts and
+ * vie_apply_noalloc are D1 only.  Errors: as vie_setup, VIE_EINVAL for disc. */
+int vie_setup_disc(const vie_grid* g, const double* eps_r, double k0, int disc, vie_handle** out);
+
 /* Replace the body on the same grid (keeps the kernel spectrum).  Host
  * [n0][n1][n2] eps_r.  Discards stored currents.  Errors as vie_setup. */
 int vie_set_eps(vie_handle* hd, const double* eps_r);

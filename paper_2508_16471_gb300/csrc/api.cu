@@ -161,7 +161,12 @@ const char* vie_last_error(void) { return g_err.c_str(); }
 long long vie_kernel_launches(void) { return g_launches.load(); }
 
 int vie_setup(const vie_grid* g, const double* eps_r, double k0, vie_handle** out) {
+    return vie_setup_disc(g, eps_r, k0, VIE_DISC_D1, out);
+}
+
+int vie_setup_disc(const vie_grid* g, const double* eps_r, double k0, int disc, vie_handle** out) {
     if (!out) return fail(VIE_EINVAL, "out is NULL");
+    if (disc != VIE_DISC_D1 && disc != VIE_DISC_D2) return fail(VIE_EINVAL, "disc must be VIE_DISC_D1 or VIE_DISC_D2");
     *out = nullptr;
     VIE_TRY(check_grid(g));
     if (!(k0 > 0) || !std::isfinite(k0)) return fail(VIE_EINVAL, "k0 must be positive and finite");
@@ -180,6 +185,7 @@ int vie_setup(const vie_grid* g, const double* eps_r, double k0, vie_handle** ou
     op.N = N;
     op.h = g->h;
     op.k0 = k0;
+    op.disc = disc;
     if (st == VIE_OK) st = op_init_axes(op);
     if (st == VIE_OK) st = op_build_kernel(op);
     double* deps = nullptr;
@@ -597,11 +603,12 @@ __global__ void k_fill_test(vie::c32* w, long long n) {
 
 // candidate padded lengths of an axis of n voxels: the default choice and the
 // other of (next power of two >= 2n-1, smallest 2,3,5,7-smooth length)
-std::vector<int> pad_candidates(int n) {
-    std::vector<int> c{vie::padded_size(n)};
-    const int sm = vie::smooth_size(2 * n - 1);
+std::vector<int> pad_candidates(int n, int disc) {
+    const int need = disc ? 2 * n : 2 * n - 1;
+    std::vector<int> c{vie::padded_len(need)};
+    const int sm = vie::smooth_size(need);
     int p2 = 1;
-    while (p2 < 2 * n - 1) p2 *= 2;
+    while (p2 < need) p2 *= 2;
     for (int v : {sm, p2})
         if (v != c[0] && v <= 1024 && v * 2 <= 5 * sm) c.push_back(v);
     return c;
@@ -615,7 +622,7 @@ int vie_autotune(vie_handle* hd, int n_rhs, int reps, int P_out[3], double* ms_p
     VIE_CUDA(cudaSetDevice(hd->device));
     Operator& op = hd->op;
     std::vector<int> cand[3];
-    for (int a = 0; a < 3; ++a) cand[a] = pad_candidates(op.n[a]);
+    for (int a = 0; a < 3; ++a) cand[a] = pad_candidates(op.n[a], op.disc);
     std::vector<std::array<int, 4>> configs;  // P0, P1, P2, fft path
     const bool cubic = op.n[0] == op.n[1] && op.n[1] == op.n[2];
     for (int i0 = 0; i0 < (int)cand[0].size(); ++i0)
@@ -804,6 +811,7 @@ int vie_net_train_step(vie_net* n, const float* x_dev, const float* t_dev, const
 
 int vie_net_features(vie_handle* hd, int factor, float* x_dev, float* t_dev, float* m_dev) {
     if (!hd || !x_dev) return fail(VIE_EINVAL, "NULL argument");
+    if (hd->op.disc) return fail(VIE_EINVAL, "the learned parts are built for the D1 discretisation");
     if (!hd->have_solution && t_dev) return fail(VIE_ESTATE, "training targets need a solve first");
     const Operator& op = hd->op;
     if (factor < 1 || op.n[0] != op.n[1] || op.n[0] != op.n[2] || op.n[0] % factor != 0)
@@ -818,6 +826,7 @@ int vie_net_features(vie_handle* hd, int factor, float* x_dev, float* t_dev, flo
 
 int vie_attach_net(vie_handle* hd, vie_net* n, int factor) {
     if (!hd) return fail(VIE_EINVAL, "NULL handle");
+    if (n && hd->op.disc) return fail(VIE_EINVAL, "the learned parts are built for the D1 discretisation");
     if (n && factor < 1) return fail(VIE_EINVAL, "factor must be >= 1");
     if (n && n->net.cin != NET_IN) return fail(VIE_EINVAL, "the initial-guess network takes 10 input channels");
     hd->net = n;
@@ -861,6 +870,7 @@ int vie_solve_many(vie_handle* const* hds, const vie_channel* const* ch, const i
 
 int vie_attach_precond(vie_handle* hd, vie_net* n, int factor) {
     if (!hd) return fail(VIE_EINVAL, "NULL handle");
+    if (n && hd->op.disc) return fail(VIE_EINVAL, "the learned parts are built for the D1 discretisation");
     if (n) {
         const Operator& op = hd->op;
         if (factor < 1 || op.n[0] != op.n[1] || op.n[0] != op.n[2] || op.n[0] % (8 * factor) != 0)
@@ -875,6 +885,7 @@ int vie_attach_precond(vie_handle* hd, vie_net* n, int factor) {
 int vie_precond_pairs(vie_handle* hd, int factor, const void* v_dev, int n, float* x_dev, float* t_dev,
                       float* m_dev) {
     if (!hd || !v_dev || !x_dev || !t_dev || !m_dev || n < 1) return fail(VIE_EINVAL, "NULL argument or n < 1");
+    if (hd->op.disc) return fail(VIE_EINVAL, "the learned parts are built for the D1 discretisation");
     Operator& op = hd->op;
     if (factor < 1 || op.n[0] != op.n[1] || op.n[0] != op.n[2] || op.n[0] % factor != 0)
         return fail(VIE_EINVAL, "pairs need a cubic grid with n divisible by the factor");

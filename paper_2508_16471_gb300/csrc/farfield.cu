@@ -22,9 +22,11 @@ namespace vie {
 // ---------------------------------------------------------------------------
 // right-hand sides (Eq. 24's right side in the w unknown: chi E_inc)
 // ---------------------------------------------------------------------------
+// D2 (chi_cs = Nb): component q sits at the +q face, h/2 beyond the cell centre,
+// with its own face contrast chi[q Nb + v]
 __global__ void k_rhs(c64* __restrict__ b, long long n3, const int* __restrict__ vox, const double* __restrict__ chi,
                       long long Nb, int n1, int n2, double h, double cx, double cy, double cz, double k0,
-                      const double* __restrict__ ch) {
+                      const double* __restrict__ ch, long long chi_cs) {
     const int r = blockIdx.y;
     const double* c = ch + 9 * r;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < Nb;
@@ -34,11 +36,12 @@ __global__ void k_rhs(c64* __restrict__ b, long long n3, const int* __restrict__
         const int j = (lin / n2) % n1;
         const int i = lin / (n1 * n2);
         const double px = cx + i * h, py = cy + j * h, pz = cz + k * h;
-        const double ph = k0 * (c[0] * px + c[1] * py + c[2] * pz);
-        double s, co;
-        sincos(ph, &s, &co);
-        const double x = chi[v];
+        const double ph0 = k0 * (c[0] * px + c[1] * py + c[2] * pz);
         for (int q = 0; q < 3; ++q) {
+            const double ph = chi_cs ? ph0 + 0.5 * k0 * h * c[q] : ph0;
+            double s, co;
+            sincos(ph, &s, &co);
+            const double x = chi[q * chi_cs + v];
             const double pr = c[3 + 2 * q], pi = c[4 + 2 * q];
             b[r * n3 + q * Nb + v] = c64{x * (pr * co - pi * s), x * (pr * s + pi * co)};
         }
@@ -58,7 +61,7 @@ int build_rhs(Operator& op, Solver& S, const vie_channel* chs, int n_rhs) {
         const double cy = op.origin[1] - 0.5 * (op.n[1] - 1) * op.h;
         const double cz = op.origin[2] - 0.5 * (op.n[2] - 1) * op.h;
         k_rhs<<<dim3(std::max(1, std::min(1024, ceil_div(op.Nb, 256))), n_rhs), 256, 0, op.stream>>>(
-            S.b, S.n3, op.vox, op.chi64, op.Nb, op.n[1], op.n[2], op.h, cx, cy, cz, op.k0, d);
+            S.b, S.n3, op.vox, op.chi64, op.Nb, op.n[1], op.n[2], op.h, cx, cy, cz, op.k0, d, op.chi_cs);
         count_launch();
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(op.stream);
@@ -148,13 +151,23 @@ __global__ void k_ff_dirs(const c64* __restrict__ x, long long n3, const int* __
 }
 
 // out[r][d][3] = basis components of C (I - dd) S
+// half_kh = k0 h / 2 for D2: component c of the sums sits at the +c faces and
+// takes the extra phase e^{-i k0 rhat_c h/2}; 0 for D1
 __global__ void k_ff_project(const c64* __restrict__ Sraw, const double* __restrict__ dirs, int D, int R,
-                             double C, int basis, c64* __restrict__ out) {
+                             double C, int basis, c64* __restrict__ out, double half_kh) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)D * R) return;
     const int d = (int)(i % D);
     const double dx = dirs[3 * d], dy = dirs[3 * d + 1], dz = dirs[3 * d + 2];
-    const c64* s = Sraw + i * 3;
+    c64 s[3] = {Sraw[i * 3], Sraw[i * 3 + 1], Sraw[i * 3 + 2]};
+    if (half_kh != 0.0) {
+        const double dd[3] = {dx, dy, dz};
+        for (int q = 0; q < 3; ++q) {
+            double sn, cs;
+            sincos(-half_kh * dd[q], &sn, &cs);
+            s[q] = c64{s[q].x * cs - s[q].y * sn, s[q].x * sn + s[q].y * cs};
+        }
+    }
     const c64 ds = {dx * s[0].x + dy * s[1].x + dz * s[2].x, dx * s[0].y + dy * s[1].y + dz * s[2].y};
     c64 F[3] = {{C * (s[0].x - dx * ds.x), C * (s[0].y - dx * ds.y)},
                 {C * (s[1].x - dy * ds.x), C * (s[1].y - dy * ds.y)},
@@ -211,7 +224,7 @@ int farfield_dirs(Operator& op, const c64* x, long long n3, int R, const double*
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
         k_ff_project<<<ceil_div((long long)D * R, 256), 256, 0, op.stream>>>(Sraw, ddirs, D, R, ff_constant(op), basis,
-                                                                             dout);
+                                                                             dout, op.disc ? 0.5 * op.k0 * op.h : 0.0);
         count_launch();
         e = cudaGetLastError();
     }
@@ -430,7 +443,7 @@ int farfield_grid(Operator& op, const c64* x, long long n3, int R, const double*
     k_ff_xreduce<<<ceil_div((long long)nt * np * RC, 256), 256, 0, s>>>(Bt, ex, nt, np, n0, RC, Sraw);
     k_grid_dirs<<<ceil_div(nt * np, 256), 256, 0, s>>>(dth, nt, dph, np, dirs);
     k_ff_project<<<ceil_div((long long)nt * np * R, 256), 256, 0, s>>>(Sraw, dirs, nt * np, R, ff_constant(op), basis,
-                                                                       dout);
+                                                                       dout, op.disc ? 0.5 * op.k0 * op.h : 0.0);
     count_launch(5);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

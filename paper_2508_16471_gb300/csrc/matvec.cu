@@ -110,17 +110,20 @@ static int upload_twiddles(Operator& op, AxisFFT& a) {
 // Padded length of one axis: the next power of two >= 2n-1 when it costs at
 // most 15 % more points than the smallest 2,3,5,7-smooth length (the power of
 // two runs on the register four-step kernels), else the smooth length.
-int padded_size(int n) {
-    const int sm = smooth_size(2 * n - 1);
+int padded_len(int m) {
+    const int sm = smooth_size(m);
     int p2 = 1;
-    while (p2 < 2 * n - 1) p2 *= 2;
+    while (p2 < m) p2 *= 2;
     return (p2 <= 512 && p2 * 100 <= sm * 115) ? p2 : sm;
 }
+int padded_size(int n) { return padded_len(2 * n - 1); }
 
 int op_init_axes(Operator& op) {
     for (int a = 0; a < 3; ++a) {
-        op.P[a] = op.P_fixed[a] > 0 ? op.P_fixed[a] : padded_size(op.n[a]);
-        if (op.P[a] < 2 * op.n[a] - 1) return fail(VIE_EINVAL, "padded length below 2n - 1");
+        // D2 takes differences of the convolution one cell beyond the grid: P >= 2n
+        const int need = op.disc ? 2 * op.n[a] : 2 * op.n[a] - 1;
+        op.P[a] = op.P_fixed[a] > 0 ? op.P_fixed[a] : padded_len(need);
+        if (op.P[a] < need) return fail(VIE_EINVAL, "padded length below the convolution's span");
         op.H[a] = op.P[a] / 2 + 1;
         if (!make_plan(op.P[a], &op.ax[a].plan))
             return fail(VIE_EINVAL, "padded FFT size " + std::to_string(op.P[a]) + " exceeds the engine limit (1024)");
@@ -230,7 +233,8 @@ template <typename T>
 __global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict__ w, long long w_rstride,
                        cplx<T>* __restrict__ y, long long y_rstride, const int* __restrict__ list,
                        const int* __restrict__ idx_map, const T* __restrict__ chi, int n0, int n1, int n2,
-                       long long Nb, long long nlines, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL) {
+                       long long Nb, long long nlines, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL,
+                       long long chi_cs) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
     const int L = plan.L;
@@ -261,7 +265,7 @@ __global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict_
         const long long rr = list[slot];
         const cplx<T> u = r[p * ld + l];
         const cplx<T> wv = w[rr * w_rstride + c * Nb + vi];
-        const T ch = chi[vi];
+        const T ch = chi[c * chi_cs + vi];
         y[rr * y_rstride + c * Nb + vi] = cplx<T>{wv.x - ch * u.x, wv.y - ch * u.y};
     }
 }
@@ -273,7 +277,8 @@ __global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict_
 template <typename T>
 __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int n0, long long inner, int P0, int P1, int P2,
                          const cplx<T>* __restrict__ khat, int H0, int H1, int H2, FFTPlan plan,
-                         const cplx<T>* __restrict__ twg, int TW) {
+                         const cplx<T>* __restrict__ twg, int TW, const cplx<T>* __restrict__ dtab, int dstride,
+                         T ksq) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
     const int L = plan.L;  // == P0
@@ -314,6 +319,19 @@ __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int 
         const bool flx = 2 * kx > P0, fly = 2 * ky > P1, flz = 2 * kz > P2;
         const int fx = flx ? P0 - kx : kx, fy = fly ? P1 - ky : ky, fz = flz ? P2 - kz : kz;
         const long long o = ((long long)fx * H1 + fy) * H2 + fz;
+        if (dtab) {
+            // D2: U_a = G (k^2 W_a + d+_a sum_b d-_b W_b), G scalar and even
+            const cplx<T> g = khat[o];
+            const cplx<T> dxp = dtab[kx], dxm = dtab[dstride + kx];
+            const cplx<T> dyp = dtab[2 * dstride + ky], dym = dtab[3 * dstride + ky];
+            const cplx<T> dzp = dtab[4 * dstride + kz], dzm = dtab[5 * dstride + kz];
+            const cplx<T> a = cur[0][e], b = cur[1][e], cc = cur[2][e];
+            const cplx<T> sd = dxm * a + dym * b + dzm * cc;
+            cur[0][e] = g * (ksq * a + dxp * sd);
+            cur[1][e] = g * (ksq * b + dyp * sd);
+            cur[2][e] = g * (ksq * cc + dzp * sd);
+            continue;
+        }
         cplx<T> kxx = khat[o], kxy = khat[HH + o], kxz = khat[2 * HH + o];
         cplx<T> kyy = khat[3 * HH + o], kyz = khat[4 * HH + o], kzz = khat[5 * HH + o];
         if (flx ^ fly) kxy = cplx<T>{-kxy.x, -kxy.y};
@@ -386,11 +404,33 @@ __global__ void k_kernel_circulant(c64* __restrict__ Kc, int n0, int n1, int n2,
     }
 }
 
+// D2 scalar kernel on the full periodic index range (m = p or p - P per axis)
+__global__ void k_scalar_circulant(c64* __restrict__ Kc, int P0, int P1, int P2, double h, double k0, double coef,
+                                   double g0r, double g0i) {
+    const long long tot = (long long)P0 * P1 * P2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int p2 = (int)(i % P2);
+        const long long r0 = i / P2;
+        const int p1 = (int)(r0 % P1), p0 = (int)(r0 / P1);
+        const int m0 = 2 * p0 <= P0 ? p0 : p0 - P0, m1 = 2 * p1 <= P1 ? p1 : p1 - P1, m2 = 2 * p2 <= P2 ? p2 : p2 - P2;
+        if (m0 == 0 && m1 == 0 && m2 == 0) {
+            Kc[i] = c64{g0r, g0i};
+        } else {
+            const double r = h * sqrt((double)m0 * m0 + (double)m1 * m1 + (double)m2 * m2);
+            double s, c;
+            sincos(k0 * r, &s, &c);
+            const double gi = coef / (4.0 * M_PI * r);
+            Kc[i] = c64{gi * c, gi * s};
+        }
+    }
+}
+
 __global__ void k_octant(const c64* __restrict__ Kc, c64* __restrict__ o64, c32* __restrict__ o32, int P0, int P1,
-                         int P2, int H0, int H1, int H2, double scale) {
+                         int P2, int H0, int H1, int H2, double scale, int ncomp) {
     const long long HH = (long long)H0 * H1 * H2;
     const long long PP = (long long)P0 * P1 * P2;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 6 * HH;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncomp * HH;
          i += (long long)gridDim.x * blockDim.x) {
         const int q = (int)(i / HH);
         const long long r = i - q * HH;
@@ -409,15 +449,28 @@ __global__ void k_octant(const c64* __restrict__ Kc, c64* __restrict__ o64, c32*
 // ---------------------------------------------------------------------------
 constexpr int SCAN_B = 1024;
 
+// unknown at voxel i: D1 where eps > 1; D2 (face unknowns on the +a faces)
+// where the cell or one of its +x/+y/+z neighbours has eps > 1
+__device__ __forceinline__ int body_flag(const double* __restrict__ eps, long long i, int n1, int n2, int disc,
+                                         long long N) {
+    if (eps[i] > 1.0) return 1;
+    if (!disc) return 0;
+    const int k = (int)(i % n2), j = (int)((i / n2) % n1);
+    const long long x = i / ((long long)n1 * n2);
+    const long long n0 = N / ((long long)n1 * n2);
+    return (x + 1 < n0 && eps[i + (long long)n1 * n2] > 1.0) || (j + 1 < n1 && eps[i + n2] > 1.0) ||
+           (k + 1 < n2 && eps[i + 1] > 1.0);
+}
+
 __global__ void k_body_count(const double* __restrict__ eps, long long N, int* __restrict__ bcount,
-                             int* __restrict__ err) {
+                             int* __restrict__ err, int n1, int n2, int disc) {
     __shared__ int ws[32];
     const long long i = (long long)blockIdx.x * SCAN_B + threadIdx.x;
     int f = 0;
     if (i < N) {
         const double e = eps[i];
         if (!(e >= 1.0) || !isfinite(e)) atomicOr(err, 1);
-        f = e > 1.0;
+        else f = body_flag(eps, i, n1, n2, disc, N);
     }
     int s = __syncthreads_count(f);
     (void)ws;
@@ -460,13 +513,14 @@ __global__ void k_scan_blocks(int* __restrict__ bcount, int nb, long long* __res
     if (threadIdx.x == 0) *total = carry;
 }
 
+// D1: chi[v] = eps - 1; D2: chi[a Nb + v] = (chi(cell) + chi(cell + e_a)) / 2
 __global__ void k_body_write(const double* __restrict__ eps, long long N, const int* __restrict__ boff,
                              int* __restrict__ idx_map, int* __restrict__ vox, float* __restrict__ chi32,
-                             double* __restrict__ chi64) {
+                             double* __restrict__ chi64, int n1, int n2, int disc, long long Nb) {
     __shared__ int wsum[32];
     const long long i = (long long)blockIdx.x * SCAN_B + threadIdx.x;
     const double e = i < N ? eps[i] : 1.0;
-    const int f = e > 1.0;
+    const int f = i < N ? body_flag(eps, i, n1, n2, disc, N) : 0;
     int x = f;
     for (int o = 1; o < 32; o <<= 1) {
         int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -488,8 +542,21 @@ __global__ void k_body_write(const double* __restrict__ eps, long long N, const 
         idx_map[i] = f ? excl : -1;
         if (f) {
             vox[excl] = (int)i;
-            chi32[excl] = (float)(e - 1.0);
-            chi64[excl] = e - 1.0;
+            if (!disc) {
+                chi32[excl] = (float)(e - 1.0);
+                chi64[excl] = e - 1.0;
+            } else {
+                const int k = (int)(i % n2), j = (int)((i / n2) % n1);
+                const long long x = i / ((long long)n1 * n2);
+                const long long n0 = N / ((long long)n1 * n2);
+                const double nb[3] = {x + 1 < n0 ? eps[i + (long long)n1 * n2] : 1.0, j + 1 < n1 ? eps[i + n2] : 1.0,
+                                      k + 1 < n2 ? eps[i + 1] : 1.0};
+                for (int a = 0; a < 3; ++a) {
+                    const double c = 0.5 * ((e - 1.0) + (nb[a] - 1.0));
+                    chi32[a * Nb + excl] = (float)c;
+                    chi64[a * Nb + excl] = c;
+                }
+            }
         }
     }
 }
@@ -548,6 +615,9 @@ template <typename T> static size_t xfused_smem(const FFTPlan& p, int TW) {
 template <typename T> static const cplx<T>* twp(const AxisFFT& a);
 template <> const c32* twp<float>(const AxisFFT& a) { return a.tw32; }
 template <> const c64* twp<double>(const AxisFFT& a) { return a.tw64; }
+template <typename T> static const cplx<T>* dtp(const Operator& op);
+template <> const c32* dtp<float>(const Operator& op) { return op.dtab32; }
+template <> const c64* dtp<double>(const Operator& op) { return op.dtab64; }
 
 template <typename T, bool INV>
 static int launch_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_in, int n_out, const FFTPlan& p,
@@ -616,6 +686,33 @@ int fft_lines_device(const void* in, void* out, int L, int count, int inverse, i
     return VIE_OK;
 }
 
+// D2 difference symbols per axis, forward-transform convention e^{-i kappa j}:
+// forward difference f(c+1) - f(c) -> (e^{i kappa} - 1)/h, backward
+// f(c) - f(c-1) -> (1 - e^{-i kappa})/h, kappa = 2 pi q / P.
+static int build_diff_tables(Operator& op) {
+    const int ds = std::max(op.P[0], std::max(op.P[1], op.P[2]));
+    std::vector<c64> t(6 * (size_t)ds, c64{0, 0});
+    for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < op.P[a]; ++q) {
+            const double kap = 2.0 * M_PI * q / op.P[a];
+            const double c = std::cos(kap), s = std::sin(kap);
+            t[(2 * a) * (size_t)ds + q] = c64{(c - 1.0) / op.h, s / op.h};       // (e^{ik} - 1)/h
+            t[(2 * a + 1) * (size_t)ds + q] = c64{(1.0 - c) / op.h, s / op.h};   // (1 - e^{-ik})/h
+        }
+    std::vector<c32> tf(t.size());
+    for (size_t i = 0; i < t.size(); ++i) tf[i] = c32{(float)t[i].x, (float)t[i].y};
+    if (op.dtab64) dev_free(op, op.dtab64, sizeof(c64) * 6 * (size_t)op.dstride);
+    if (op.dtab32) dev_free(op, op.dtab32, sizeof(c32) * 6 * (size_t)op.dstride);
+    op.dtab64 = nullptr;
+    op.dtab32 = nullptr;
+    op.dstride = ds;
+    VIE_TRY(dev_alloc(op, (void**)&op.dtab64, sizeof(c64) * t.size()));
+    VIE_TRY(dev_alloc(op, (void**)&op.dtab32, sizeof(c32) * t.size()));
+    VIE_CUDA(cudaMemcpy(op.dtab64, t.data(), sizeof(c64) * t.size(), cudaMemcpyHostToDevice));
+    VIE_CUDA(cudaMemcpy(op.dtab32, tf.data(), sizeof(c32) * t.size(), cudaMemcpyHostToDevice));
+    return VIE_OK;
+}
+
 int op_build_kernel(Operator& op) {
     const int P0 = op.P[0], P1 = op.P[1], P2 = op.P[2];
     const long long PP = (long long)P0 * P1 * P2;
@@ -632,24 +729,34 @@ int op_build_kernel(Operator& op) {
     const double self_re = (2.0 / 3.0) * ((cr + ka * sr) - 1.0) - 1.0 / 3.0;
     const double self_im = (2.0 / 3.0) * (sr - ka * cr);
     int st = VIE_OK;
-    k_kernel_circulant<<<1184, 256, 0, op.stream>>>(Kc, op.n[0], op.n[1], op.n[2], P0, P1, P2, op.h, op.k0, coef,
-                                                    self_re, self_im);
+    const int nc = op.disc ? 1 : 6;  // D2: one scalar kernel
+    if (op.disc) {
+        // D2: G_h(m) = kappa h^3 g(m h), G_h(0) = ((1 - i ka) e^{i ka} - 1) / k^2 on the whole periodic range
+        const double g0r = ((cr + ka * sr) - 1.0) / (op.k0 * op.k0), g0i = (sr - ka * cr) / (op.k0 * op.k0);
+        k_scalar_circulant<<<1184, 256, 0, op.stream>>>(Kc, P0, P1, P2, op.h, op.k0, coef / (op.k0 * op.k0), g0r, g0i);
+        VIE_TRY(build_diff_tables(op));
+    } else {
+        k_kernel_circulant<<<1184, 256, 0, op.stream>>>(Kc, op.n[0], op.n[1], op.n[2], P0, P1, P2, op.h, op.k0, coef,
+                                                        self_re, self_im);
+    }
     count_launch();
     if (cudaGetLastError() != cudaSuccess) st = fail(VIE_EDEVICE, "kernel build launch failed");
     // 3-D FFT, in place: z (contiguous lines), y, x
     if (st == VIE_OK)
-        st = launch_lines<double, false>(Kc, Kc, 6LL * P0 * P1, P2, P2, op.ax[2].plan, op.ax[2].tw64, op.stream);
+        st = launch_lines<double, false>(Kc, Kc, (long long)nc * P0 * P1, P2, P2, op.ax[2].plan, op.ax[2].tw64,
+                                         op.stream);
     if (st == VIE_OK)
-        st = launch_axis<double, false>(Kc, Kc, 6LL * P0, P1, P1, P2, op.ax[1].plan, op.ax[1].tw64, op.stream);
-    if (st == VIE_OK)
-        st = launch_axis<double, false>(Kc, Kc, 6LL, P0, P0, (long long)P1 * P2, op.ax[0].plan, op.ax[0].tw64,
+        st = launch_axis<double, false>(Kc, Kc, (long long)nc * P0, P1, P1, P2, op.ax[1].plan, op.ax[1].tw64,
                                         op.stream);
+    if (st == VIE_OK)
+        st = launch_axis<double, false>(Kc, Kc, (long long)nc, P0, P0, (long long)P1 * P2, op.ax[0].plan,
+                                        op.ax[0].tw64, op.stream);
     const long long HH = (long long)op.H[0] * op.H[1] * op.H[2];
     if (st == VIE_OK) st = dev_alloc(op, (void**)&op.khat64, sizeof(c64) * 6 * HH);
     if (st == VIE_OK) st = dev_alloc(op, (void**)&op.khat32, sizeof(c32) * 6 * HH);
     if (st == VIE_OK) {
         k_octant<<<1184, 256, 0, op.stream>>>(Kc, op.khat64, op.khat32, P0, P1, P2, op.H[0], op.H[1], op.H[2],
-                                              1.0 / (double)PP);
+                                              1.0 / (double)PP, nc);
         count_launch();
         if (cudaGetLastError() != cudaSuccess) st = fail(VIE_EDEVICE, "octant launch failed");
     }
@@ -670,7 +777,7 @@ int op_set_body_device(Operator& op, const double* eps) {
     VIE_CUDA(cudaMalloc(&err, sizeof(int)));
     VIE_CUDA(cudaMalloc(&total, sizeof(long long)));
     VIE_CUDA(cudaMemsetAsync(err, 0, sizeof(int), op.stream));
-    k_body_count<<<nb, SCAN_B, 0, op.stream>>>(eps, N, bcount, err);
+    k_body_count<<<nb, SCAN_B, 0, op.stream>>>(eps, N, bcount, err, op.n[1], op.n[2], op.disc);
     k_scan_blocks<<<1, 1024, 0, op.stream>>>(bcount, nb, total);
     count_launch(2);
     int herr = 0;
@@ -682,19 +789,23 @@ int op_set_body_device(Operator& op, const double* eps) {
     if (herr) st = fail(VIE_EINVAL, "eps_r must be finite and >= 1 everywhere");
     else if (Nb == 0) st = fail(VIE_EINVAL, "the body is empty (no voxel with eps_r > 1)");
     if (st == VIE_OK) {
+        const long long nchi_old = op.chi_cs ? 3 * op.Nb : op.Nb;
         if (op.vox) dev_free(op, op.vox, sizeof(int) * op.Nb);
-        if (op.chi32) dev_free(op, op.chi32, sizeof(float) * op.Nb);
-        if (op.chi64) dev_free(op, op.chi64, sizeof(double) * op.Nb);
+        if (op.chi32) dev_free(op, op.chi32, sizeof(float) * nchi_old);
+        if (op.chi64) dev_free(op, op.chi64, sizeof(double) * nchi_old);
         op.vox = nullptr;
         op.chi32 = nullptr;
         op.chi64 = nullptr;
         if (!op.idx_map) st = dev_alloc(op, (void**)&op.idx_map, sizeof(int) * N);
         if (st == VIE_OK) st = dev_alloc(op, (void**)&op.vox, sizeof(int) * Nb);
-        if (st == VIE_OK) st = dev_alloc(op, (void**)&op.chi32, sizeof(float) * Nb);
-        if (st == VIE_OK) st = dev_alloc(op, (void**)&op.chi64, sizeof(double) * Nb);
+        const long long nchi = op.disc ? 3 * Nb : Nb;
+        if (st == VIE_OK) st = dev_alloc(op, (void**)&op.chi32, sizeof(float) * nchi);
+        if (st == VIE_OK) st = dev_alloc(op, (void**)&op.chi64, sizeof(double) * nchi);
         if (st == VIE_OK) {
             op.Nb = Nb;
-            k_body_write<<<nb, SCAN_B, 0, op.stream>>>(eps, N, bcount, op.idx_map, op.vox, op.chi32, op.chi64);
+            op.chi_cs = op.disc ? Nb : 0;
+            k_body_write<<<nb, SCAN_B, 0, op.stream>>>(eps, N, bcount, op.idx_map, op.vox, op.chi32, op.chi64,
+                                                       op.n[1], op.n[2], op.disc, Nb);
             count_launch();
             cudaError_t e = cudaStreamSynchronize(op.stream);
             if (e != cudaSuccess) st = cuda_fail(e, "body compaction");
@@ -810,8 +921,12 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
         // pass 3
         if (fx) {
             tmr_begin(tid(TMR_XFUSED), op.stream);
+            D2Spec d2;
+            d2.dtab = op.dtab32;
+            d2.dstride = op.dstride;
+            d2.k2 = (float)(op.k0 * op.k0);
             VIE_TRY(fast_xfused((c32*)B, n0, (long long)P1 * P2, P0, P1, P2, (const c32*)kh, op.H, op.ax[0].roots32, ns,
-                                op.stream));
+                                op.stream, op.disc ? &d2 : nullptr));
             tmr_end(tid(TMR_XFUSED), op.stream, 2.0 * ns * lineB + 6.0 * op.H[0] * op.H[1] * op.H[2] * E);
             count_launch();
             VIE_CUDA(cudaGetLastError());
@@ -822,7 +937,8 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             const long long grid = (long long)ns * ((inner + TW - 1) / TW);
             tmr_begin(tid(TMR_XFUSED), op.stream);
             k_xfused<T><<<(unsigned)grid, 256, xfused_smem<T>(p, TW), op.stream>>>(
-                B, n0, inner, P0, P1, P2, kh, op.H[0], op.H[1], op.H[2], p, twp<T>(op.ax[0]), TW);
+                B, n0, inner, P0, P1, P2, kh, op.H[0], op.H[1], op.H[2], p, twp<T>(op.ax[0]), TW,
+                op.disc ? dtp<T>(op) : nullptr, op.dstride, (T)(op.k0 * op.k0));
             tmr_end(tid(TMR_XFUSED), op.stream, 2.0 * ns * lineB + 6.0 * op.H[0] * op.H[1] * op.H[2] * E);
             count_launch();
             VIE_CUDA(cudaGetLastError());
@@ -844,7 +960,7 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             const long long nlines = (long long)ns * 3 * n0 * n1;
             tmr_begin(tid(TMR_ZINV), op.stream);
             VIE_TRY(fast_zinv((const c32*)A, (const c32*)w, wr, (c32*)y, yr, list, op.idx_map, (const float*)chi, n0, n1,
-                              n2, op.Nb, nlines, P2, op.ax[2].roots32, op.stream));
+                              n2, op.Nb, nlines, P2, op.ax[2].roots32, op.stream, op.chi_cs));
             tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
@@ -854,7 +970,8 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             const long long nlines = (long long)ns * 3 * n0 * n1;
             tmr_begin(tid(TMR_ZINV), op.stream);
             k_zinv<T><<<(unsigned)((nlines + NL - 1) / NL), 256, lines_smem<T>(p, NL), op.stream>>>(
-                A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), NL);
+                A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), NL,
+                op.chi_cs);
             tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
@@ -909,6 +1026,10 @@ void op_free(Operator& op) {
     }
     cudaFree(op.khat32);
     cudaFree(op.khat64);
+    cudaFree(op.dtab32);
+    cudaFree(op.dtab64);
+    op.dtab32 = nullptr;
+    op.dtab64 = nullptr;
     cudaFree(op.idx_map);
     cudaFree(op.vox);
     cudaFree(op.chi32);

@@ -138,12 +138,17 @@ template <int L> struct XF {
     static constexpr int HR = R1 / 2;       // non-zero input rows per thread
     static constexpr bool PF = L <= 256;    // prefetch the next slot
     static constexpr size_t smem = sizeof(c32) * (2 * L + 6 * (size_t)HX * TW + 3 * (size_t)SC);
+    // D2: the x difference symbols (2 L) and the column ones (4 TW) follow
+    static constexpr size_t smem_d2 = smem + sizeof(c32) * (2 * L + 4 * TW);
 };
 
-template <int L>
+// D2 (rooftop discretisation): the kernel tile holds the scalar G only and the
+// multiply is U_a = G (k^2 W_a + d+_a (d-_x W_x + d-_y W_y + d-_z W_z)).
+template <int L, bool D2>
 __global__ void __launch_bounds__(XF<L>::NT) k_xfused_r(c32* __restrict__ B, int n0, long long inner, int P1,
                                                        int P2, const c32* __restrict__ khat, int H0, int H1, int H2,
-                                                       const c32* __restrict__ tw4, int nslots) {
+                                                       const c32* __restrict__ tw4, int nslots,
+                                                       const c32* __restrict__ dtab, int dstride, float ksq) {
     constexpr int R1 = XF<L>::R1, R2 = XF<L>::R2, TW = XF<L>::TW, NT = XF<L>::NT;
     constexpr int SR = XF<L>::SR, SC = XF<L>::SC, HX = XF<L>::HX, HR = XF<L>::HR;
     constexpr bool PF = XF<L>::PF;
@@ -152,7 +157,27 @@ __global__ void __launch_bounds__(XF<L>::NT) k_xfused_r(c32* __restrict__ B, int
     c32* TB = TA + L;
     c32* Kt = TB + L;          // [6][HX][TW]
     c32* S = Kt + 6 * HX * TW;  // [3][R1][SR]
+    c32* DX = S + 3 * SC;       // D2: [2][L] x symbols (+, -)
+    c32* DC = DX + 2 * L;       // D2: [4][TW] column symbols y+, y-, z+, z-
     stage_table(TA, tw4, 2 * L);
+    if (D2) {
+        for (int q = threadIdx.x; q < L; q += NT) {
+            DX[q] = dtab[q];
+            DX[L + q] = dtab[dstride + q];
+        }
+        if (threadIdx.x < TW) {
+            const long long ii = (long long)blockIdx.x * TW + threadIdx.x;
+            c32 v[4] = {z32(), z32(), z32(), z32()};
+            if (ii < inner) {
+                const int ky = (int)(ii / P2), kz = (int)(ii - (ii / P2) * P2);
+                v[0] = dtab[2 * dstride + ky];
+                v[1] = dtab[3 * dstride + ky];
+                v[2] = dtab[4 * dstride + kz];
+                v[3] = dtab[5 * dstride + kz];
+            }
+            for (int q = 0; q < 4; ++q) DC[q * TW + threadIdx.x] = v[q];
+        }
+    }
     const long long i0 = (long long)blockIdx.x * TW;
     const long long HH = (long long)H0 * H1 * H2;
     // kernel tile: rows fx = 0..L/2 of the 6 components for this CTA's columns.
@@ -168,14 +193,14 @@ __global__ void __launch_bounds__(XF<L>::NT) k_xfused_r(c32* __restrict__ B, int
             const int ky = (int)(ii / P2), kz = (int)(ii - (ii / P2) * P2);
             const bool fly = 2 * ky > P1, flz = 2 * kz > P2;
             off = (long long)(fly ? P1 - ky : ky) * H2 + (flz ? P2 - kz : kz);
-            ng = (unsigned char)((fly ? 2 : 0) | (flz ? 4 : 0) | ((fly ^ flz) ? 16 : 0));
+            ng = D2 ? 0 : (unsigned char)((fly ? 2 : 0) | (flz ? 4 : 0) | ((fly ^ flz) ? 16 : 0));
         }
         coff[threadIdx.x] = off;
         cneg[threadIdx.x] = ng;
     }
     __syncthreads();
     {
-        constexpr int NE = 6 * HX * TW, U = 8;
+        constexpr int NE = (D2 ? 1 : 6) * HX * TW, U = 8;
         const long long rowst = (long long)H1 * H2;
         for (int e0 = 0; e0 < NE; e0 += U * NT) {
             c32 v[U];
@@ -255,6 +280,21 @@ __global__ void __launch_bounds__(XF<L>::NT) k_xfused_r(c32* __restrict__ B, int
             // k2 > R2/2 always, for k2 = R2/2 unless k1 = 0
             const c32* kp = Kt + k1 * TW + tt;        // row kx
             const c32* km = Kt + (L - k1) * TW + tt;  // row L - kx (plus R1 k2 rows)
+            if (D2) {
+                const c32 dyp = DC[tt], dym = DC[TW + tt], dzp = DC[2 * TW + tt], dzm = DC[3 * TW + tt];
+#pragma unroll
+                for (int k2 = 0; k2 < R2; ++k2) {
+                    const bool flx = 2 * k2 > R2 || (2 * k2 == R2 && k1 > 0);
+                    const c32 g = *(flx ? km - R1 * k2 * TW : kp + R1 * k2 * TW);
+                    const int kx = k1 + R1 * k2;
+                    const c32 dxp = DX[kx], dxm = DX[L + kx];
+                    const c32 a0 = bx[k2], b0 = by[k2], c0 = bz[k2];
+                    const c32 sdiv = dxm * a0 + dym * b0 + dzm * c0;
+                    bx[k2] = g * (ksq * a0 + dxp * sdiv);
+                    by[k2] = g * (ksq * b0 + dyp * sdiv);
+                    bz[k2] = g * (ksq * c0 + dzp * sdiv);
+                }
+            } else
 #pragma unroll
             for (int k2 = 0; k2 < R2; ++k2) {
                 const bool flx = 2 * k2 > R2 || (2 * k2 == R2 && k1 > 0);
@@ -365,7 +405,8 @@ __global__ void __launch_bounds__(Z_THREADS) k_zinv_r(const c32* __restrict__ A,
                                                       long long w_rstride, c32* __restrict__ y, long long y_rstride,
                                                       const int* __restrict__ list, const int* __restrict__ idx_map,
                                                       const float* __restrict__ chi, int n0, int n1, int n2,
-                                                      long long Nb, long long nlines, const c32* __restrict__ tw4) {
+                                                      long long Nb, long long nlines, const c32* __restrict__ tw4,
+                                                      long long chi_cs) {
     constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2;
     constexpr int NL = Z_THREADS / R2;
     constexpr int RS = R2 + 1;
@@ -409,7 +450,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_zinv_r(const c32* __restrict__ A,
             if (vi >= 0) {
                 const c32 u = a[n1i];
                 const c32 wv = wr[vi];
-                const float ch = chi[vi];
+                const float ch = chi[c * chi_cs + vi];
                 yr[vi] = c32{wv.x - ch * u.x, wv.y - ch * u.y};
             }
         }
@@ -448,13 +489,20 @@ template <int L> int launch_axis_r(const c32* in, c32* out, long long outer, int
 }
 
 template <int L> int launch_xfused_r(c32* B, int n0, long long inner, int P1, int P2, const c32* kh, const int* H,
-                                     const c32* tw4, int ns, cudaStream_t s) {
-    const size_t sm = XF<L>::smem;
+                                     const c32* tw4, int ns, cudaStream_t s, const D2Spec* d2) {
+    const size_t sm = d2 ? XF<L>::smem_d2 : XF<L>::smem;
     if (sm > 227 * 1024) return fail(VIE_EINVAL, "fused x pass does not fit in shared memory");
     if (2 * n0 > L) return fail(VIE_EINVAL, "fused x pass: data rows exceed half the padded length");
-    VIE_TRY(set_smem(k_xfused_r<L>, sm));
     const long long grid = (inner + XF_TW - 1) / XF_TW;
-    k_xfused_r<L><<<(unsigned)grid, XF<L>::NT, sm, s>>>(B, n0, inner, P1, P2, kh, H[0], H[1], H[2], tw4, ns);
+    if (d2) {
+        VIE_TRY(set_smem(k_xfused_r<L, true>, sm));
+        k_xfused_r<L, true><<<(unsigned)grid, XF<L>::NT, sm, s>>>(B, n0, inner, P1, P2, kh, H[0], H[1], H[2], tw4, ns,
+                                                                  d2->dtab, d2->dstride, d2->k2);
+    } else {
+        VIE_TRY(set_smem(k_xfused_r<L, false>, sm));
+        k_xfused_r<L, false><<<(unsigned)grid, XF<L>::NT, sm, s>>>(B, n0, inner, P1, P2, kh, H[0], H[1], H[2], tw4,
+                                                                   ns, nullptr, 0, 0.f);
+    }
     return VIE_OK;
 }
 
@@ -471,13 +519,13 @@ template <int L> int launch_zfwd_r(const c32* w, long long wr, const int* list, 
 
 template <int L> int launch_zinv_r(const c32* A, const c32* w, long long wr, c32* y, long long yr, const int* list,
                                    const int* idx, const float* chi, int n0, int n1, int n2, long long Nb,
-                                   long long nlines, const c32* tw4, cudaStream_t s) {
+                                   long long nlines, const c32* tw4, cudaStream_t s, long long chi_cs) {
     constexpr int NL = Z_THREADS / Fac<L>::R2;
     const size_t sm = sizeof(c32) * (L + (size_t)NL * Fac<L>::R1 * (Fac<L>::R2 + 1));
     if (2 * n2 > L) return fail(VIE_EINVAL, "z pass: grid extent exceeds half the padded length");
     VIE_TRY(set_smem(k_zinv_r<L>, sm));
     k_zinv_r<L><<<(unsigned)((nlines + NL - 1) / NL), Z_THREADS, sm, s>>>(A, w, wr, y, yr, list, idx, chi, n0, n1,
-                                                                         n2, Nb, nlines, tw4);
+                                                                         n2, Nb, nlines, tw4, chi_cs);
     return VIE_OK;
 }
 
@@ -501,8 +549,8 @@ int fast_axis(const c32* in, c32* out, long long outer, int n_in, int n_out, lon
 }
 
 int fast_xfused(c32* B, int n0, long long inner, int L, int P1, int P2, const c32* kh, const int* H,
-                const c32* tw4, int ns, cudaStream_t s) {
-    VIE_DISPATCH_L(L, VIE_TRY(launch_xfused_r<LL>(B, n0, inner, P1, P2, kh, H, tw4, ns, s)));
+                const c32* tw4, int ns, cudaStream_t s, const D2Spec* d2) {
+    VIE_DISPATCH_L(L, VIE_TRY(launch_xfused_r<LL>(B, n0, inner, P1, P2, kh, H, tw4, ns, s, d2)));
     return VIE_OK;
 }
 
@@ -514,8 +562,9 @@ int fast_zfwd(const c32* w, long long wr, const int* list, const int* idx, c32* 
 
 int fast_zinv(const c32* A, const c32* w, long long wr, c32* y, long long yr, const int* list, const int* idx,
               const float* chi, int n0, int n1, int n2, long long Nb, long long nlines, int L, const c32* tw4,
-              cudaStream_t s) {
-    VIE_DISPATCH_L(L, VIE_TRY(launch_zinv_r<LL>(A, w, wr, y, yr, list, idx, chi, n0, n1, n2, Nb, nlines, tw4, s)));
+              cudaStream_t s, long long chi_cs) {
+    VIE_DISPATCH_L(L, VIE_TRY(launch_zinv_r<LL>(A, w, wr, y, yr, list, idx, chi, n0, n1, n2, Nb, nlines, tw4, s,
+                                                chi_cs)));
     return VIE_OK;
 }
 

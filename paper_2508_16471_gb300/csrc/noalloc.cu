@@ -81,6 +81,7 @@ extern "C" int vie_apply_noalloc(vie_handle* hd, const void* w_dev, void* y_dev,
     if (n_rhs < 1 || n_rhs > NOALLOC_MAX_RHS)
         return fail(VIE_EINVAL, "n_rhs must be in 1.." + std::to_string(NOALLOC_MAX_RHS));
     Operator& op = *handle_operator(hd);
+    if (op.disc) return fail(VIE_EINVAL, "vie_apply_noalloc covers the D1 discretisation only");
     const int n0 = op.n[0], n1 = op.n[1], n2 = op.n[2];
     const int P0 = op.P[0], P1 = op.P[1], P2 = op.P[2];
     if (!fast_length(P0) || !fast_length(P1) || !fast_length(P2))

@@ -31,7 +31,7 @@ struct Operator {
     long long N = 0, Nb = 0;
     double h = 0, k0 = 0, origin[3] = {0, 0, 0};
     AxisFFT ax[3];
-    c32* khat32 = nullptr;  // [6][H0][H1][H2], scaled by 1/(P0 P1 P2)
+    c32* khat32 = nullptr;  // [6][H0][H1][H2] (D1) or [1][H0][H1][H2] (D2 scalar), scaled by 1/(P0 P1 P2)
     c64* khat64 = nullptr;
     int* idx_map = nullptr;  // [N] compact index or -1
     int* vox = nullptr;      // [Nb] linear voxel index of body voxel
@@ -44,6 +44,13 @@ struct Operator {
     double bytes = 0;        // device bytes held
     int fft_path = 0;        // 0: register four-step where the length allows, 1: generic only
     int P_fixed[3] = {0, 0, 0};  // padded lengths chosen by the autotuner (0: padded_size)
+    // discretisation: 0 = D1 (voxel-centred unknowns, dyadic kernel), 1 = D2
+    // (rooftop unknowns on the +a faces, scalar kernel with discrete grad-div)
+    int disc = 0;
+    long long chi_cs = 0;    // component stride of chi32/chi64: 0 (D1) or Nb (D2, per-face contrast)
+    c32* dtab32 = nullptr;   // D2 difference symbols [3 axes][2 (+,-)][dstride]
+    c64* dtab64 = nullptr;
+    int dstride = 0;
     int ff_engine = 0;       // far-field contractions: 0 tcgen05 3xTF32, 1 CUDA-core FP32
 };
 
@@ -55,6 +62,8 @@ void dev_free(Operator& op, void* p, size_t bytes);
 int smooth_size(int m);
 // padded FFT length used for a grid axis of n voxels
 int padded_size(int n);
+// padded length >= m: power of two within 15 % of the smooth length, else smooth
+int padded_len(int m);
 
 // ---- operator (matvec.cu) ---------------------------------------------------
 int op_init_axes(Operator& op);
@@ -76,13 +85,19 @@ bool fast_length(int L);
 void fast_factors(int L, int* R1, int* R2);
 int fast_axis(const c32* in, c32* out, long long outer, int n_in, int n_out, long long inner, int L,
               const c32* roots, bool inv, cudaStream_t s);
+// D2 spectral multiply: U_a = G (k^2 W_a + d+_a sum_b d-_b W_b), d tables [3][2][dstride]
+struct D2Spec {
+    const c32* dtab = nullptr;
+    int dstride = 0;
+    float k2 = 0.f;
+};
 int fast_xfused(c32* B, int n0, long long inner, int L, int P1, int P2, const c32* kh, const int* H,
-                const c32* roots, int ns, cudaStream_t s);
+                const c32* roots, int ns, cudaStream_t s, const D2Spec* d2 = nullptr);
 int fast_zfwd(const c32* w, long long wr, const int* list, const int* idx, c32* A, int n0, int n1, int n2,
               long long Nb, long long nlines, int L, const c32* roots, cudaStream_t s);
 int fast_zinv(const c32* A, const c32* w, long long wr, c32* y, long long yr, const int* list, const int* idx,
               const float* chi, int n0, int n1, int n2, long long Nb, long long nlines, int L, const c32* roots,
-              cudaStream_t s);
+              cudaStream_t s, long long chi_cs = 0);
 
 // tensor-core batched complex GEMM (tc_gemm.cu): C = A B, complex64, strided
 int tc_cgemm(int M, int N, int K, int batch, const c32* A, long long sAb, long long sAm, long long sAk, const c32* B,

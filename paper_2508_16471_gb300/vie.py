@@ -19,6 +19,7 @@ VIE_ETIMEOUT, VIE_EUNDEF, VIE_EDEVICE, VIE_ESTATE = -4, -5, -6, -7
 PREC_MIXED, PREC_FP64 = 0, 1
 BASIS_CART, BASIS_SPH, BASIS_CIRC = 0, 1, 2
 SOLVER_GMRES, SOLVER_BICGSTAB = 0, 1
+DISC_D1, DISC_D2 = 0, 1
 
 EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device", "vie_solve",
            "vie_farfield", "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer",
@@ -28,7 +29,7 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
            "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_guesses_rejected",
            "vie_net_create_io", "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune",
-           "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
+           "vie_setup_disc", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
 
 
 class VieError(RuntimeError):
@@ -112,6 +113,7 @@ def load():
     L.vie_precond_pairs.argtypes = [P, C.c_int, P, C.c_int, P, P, P]
     L.vie_solve_many.argtypes = [P, P, P, C.c_int, C.POINTER(_Opts), P, C.c_int]
     L.vie_autotune.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.vie_setup_disc.argtypes = [C.POINTER(_Grid), dp, C.c_double, C.c_int, C.POINTER(P)]
     L.vie_set_farfield_engine.argtypes = [P, C.c_int]
     L.vie_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int]
     L.vie_kernel_launches.restype = C.c_longlong
@@ -135,7 +137,7 @@ def load():
               "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_net_create",
               "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
               "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_net_create_io",
-              "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune"]:
+              "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune", "vie_setup_disc"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -204,7 +206,7 @@ def _channels(chs):
 class Handle:
     """One grid + body on the current CUDA device (vie_setup ... vie_destroy)."""
 
-    def __init__(self, n, h, eps_r, k0=2.0 * np.pi, origin=(0.0, 0.0, 0.0)):
+    def __init__(self, n, h, eps_r, k0=2.0 * np.pi, origin=(0.0, 0.0, 0.0), disc=DISC_D1):
         L = load()
         g = _Grid()
         for a in range(3):
@@ -214,7 +216,7 @@ class Handle:
         self.n = tuple(int(v) for v in n)
         eps = np.ascontiguousarray(eps_r, dtype=np.float64).reshape(self.n)
         hp = C.c_void_p()
-        _check(L.vie_setup(C.byref(g), _dptr(eps), float(k0), C.byref(hp)))
+        _check(L.vie_setup_disc(C.byref(g), _dptr(eps), float(k0), int(disc), C.byref(hp)))
         self._h = hp
         self.n_rhs = 0
 
