@@ -397,6 +397,41 @@ def farfield(w, n, h, k0, dirs, origin=(0.0, 0.0, 0.0), chunk=256):
     return out
 
 
+def na_rule(center, theta_na, sigma, nt, nphi):
+    """Quadrature of a detector with a finite numerical aperture (Eq. NAfield):
+    directions rhat = cos(t) c + sin(t) (cos(p) u + sin(p) v) around the unit
+    axis c, t in [0, theta_na] on ``nt`` Gauss-Legendre nodes (a library rule),
+    p = 2 pi j / nphi, with weights W(t) sin(t) dt dp, W(t) = exp(-t^2 / (2
+    sigma^2)), normalised to sum 1.  Frame: u = (a x c)/|a x c| with a = z, or
+    a = x when |c_z| >= 0.9; v = c x u.  Returns (dirs (Q, 3), weights (Q,))."""
+    c = np.asarray(center, float)
+    c = c / np.linalg.norm(c)
+    a = np.array([0.0, 0.0, 1.0]) if abs(c[2]) < 0.9 else np.array([1.0, 0.0, 0.0])
+    u = np.cross(a, c)
+    u /= np.linalg.norm(u)
+    v = np.cross(c, u)
+    x, gw = np.polynomial.legendre.leggauss(nt)
+    t = 0.5 * theta_na * (x + 1.0)
+    wt = 0.5 * theta_na * gw * np.exp(-t * t / (2.0 * sigma * sigma)) * np.sin(t)
+    p = 2.0 * math.pi * np.arange(nphi) / nphi
+    T, Pp = np.meshgrid(t, p, indexing="ij")
+    W = np.broadcast_to(wt[:, None], T.shape) * (2.0 * math.pi / nphi)
+    dirs = (np.cos(T)[..., None] * c + np.sin(T)[..., None] * (np.cos(Pp)[..., None] * u + np.sin(Pp)[..., None] * v))
+    W = W.reshape(-1)
+    return dirs.reshape(-1, 3), W / W.sum()
+
+
+def farfield_na(w, n, h, k0, centers, pols, theta_na, sigma, nt, nphi):
+    """Aperture-collected detector amplitudes E_NA[d] = sum_q W_q pol_d . F(rhat_q)
+    (bilinear projection as Eq. Eproj) of one current ``w``; shape (D,)."""
+    out = np.zeros(len(centers), dtype=np.complex128)
+    for d, (c, p) in enumerate(zip(centers, pols)):
+        dirs, W = na_rule(c, theta_na, sigma, nt, nphi)
+        F = farfield(w, n, h, k0, dirs)
+        out[d] = np.sum(W * (F @ np.asarray(p, dtype=np.complex128)))
+    return out
+
+
 def spherical_unit_vectors(dirs):
     """(e_theta, e_phi) for unit vectors ``dirs`` (D, 3); theta = acos(z),
     phi = atan2(y, x)."""

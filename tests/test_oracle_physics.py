@@ -247,3 +247,23 @@ def test_mie_general_incidence_pins():
     assert np.abs(Fr - F0 @ Q.T).max() <= 1e-12 * np.abs(F0).max()
     # transversality
     assert np.abs(np.sum(Fr * (d[sel] @ Q.T), axis=1)).max() <= 1e-13 * np.abs(F0).max()
+
+
+def test_na_rule_pins():
+    """The finite-NA quadrature: weights sum to one, the weighted mean
+    direction is the axis times the W-weighted mean of cos(t) (a 1-D integral
+    done here by scipy.integrate.quad), and a vanishing aperture returns the
+    axis value of a smooth field."""
+    from scipy.integrate import quad
+    c = np.array([0.3, -0.5, 0.8])
+    c /= np.linalg.norm(c)
+    tna, sg = 0.4, 0.25
+    dirs, W = vie.na_rule(c, tna, sg, 12, 16)
+    assert abs(W.sum() - 1.0) < 1e-14
+    num = quad(lambda t: np.exp(-t * t / (2 * sg * sg)) * np.sin(t) * np.cos(t), 0, tna)[0]
+    den = quad(lambda t: np.exp(-t * t / (2 * sg * sg)) * np.sin(t), 0, tna)[0]
+    assert np.abs(W @ dirs - c * num / den).max() < 1e-12
+    assert np.abs(np.linalg.norm(dirs, axis=1) - 1).max() < 1e-14
+    f = lambda d: np.exp(1j * 3.0 * (d @ np.array([1.0, 2.0, -0.5])))
+    d0, W0 = vie.na_rule(c, 1e-4, 1.0, 4, 8)
+    assert abs(np.sum(W0 * f(d0)) - f(c[None])[0]) < 1e-6
