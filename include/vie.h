@@ -213,6 +213,22 @@ int vie_farfield(vie_handle* hd, const double* theta, int nt, const double* phi,
  * with D directions: [n_rhs][D][3] complex.  Evaluated in FP64. */
 int vie_farfield_dirs(vie_handle* hd, const double* dirs, int D, int basis, double* out);
 
+/* Finite numerical aperture (Eq. NAfield): each detector d collects its field
+ * over a cone around the unit axis centers[d] with the angular weight
+ * W(t) = exp(-t^2 / (2 sigma^2)), t the angle to the axis, t <= theta_na:
+ *   out[r][d] = sum_q w_q pol_d . F_r(rhat_q)   (bilinear, as Eq. Eproj),
+ * on a product rule -- nt Gauss-Legendre nodes in t on [0, theta_na], nphi
+ * uniform azimuths about the axis (frame u = (a x c)/|a x c|, a = z, or x when
+ * |c_z| >= 0.9, v = c x u) -- with weights W sin(t) dt dphi normalised to sum 1,
+ * so a vanishing aperture gives the point detector of Eq. Eproj.  The
+ * amplitudes enter hom_transfer / vie_hom_map like point-detector ones (the
+ * collected field operator is linear in the input modes).
+ *   centers [D][3], pols [D][3] complex (interleaved), out [n_rhs][D] complex.
+ * Errors: VIE_EINVAL (nt 1..64, nphi 1..256, 0 < theta_na <= pi/2, sigma > 0),
+ * VIE_ESTATE (no solution), VIE_ENOMEM. */
+int vie_farfield_na(vie_handle* hd, const double* centers, const double* pols, int D, double theta_na, double sigma,
+                    int nt, int nphi, double* out);
+
 /* Device variant of vie_farfield_dirs: dirs_dev [D][3] doubles and out_dev
  * [n_rhs][D][3] complex doubles on the device; enqueued on the handle's stream
  * and synchronised before return. */

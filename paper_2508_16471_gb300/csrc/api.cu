@@ -307,6 +307,97 @@ int vie_farfield_dirs_device(vie_handle* hd, const double* dirs_dev, int D, int 
     return farfield_dirs(hd->op, hd->S.x, hd->S.n3, hd->n_rhs, dirs_dev, D, basis, (c64*)out_dev);
 }
 
+}  // extern "C"
+
+namespace {
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n from the
+// Chebyshev-like initial guesses cos(pi (i + 3/4) / (n + 1/2)))
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pn = n == 0 ? 1.0 : (n == 1 ? z : p1), pm = n == 1 ? 1.0 : p0;
+            dp = n * (z * pn - pm) / (z * z - 1.0);
+            const double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+}  // namespace
+
+extern "C" {
+
+int vie_farfield_na(vie_handle* hd, const double* centers, const double* pols, int D, double theta_na, double sigma,
+                    int nt, int nphi, double* out) {
+    if (!hd || !centers || !pols || !out || D < 1 || nt < 1 || nt > 64 || nphi < 1 || nphi > 256)
+        return fail(VIE_EINVAL, "bad arguments (nt in 1..64, nphi in 1..256)");
+    if (!(theta_na > 0) || !(theta_na <= M_PI / 2) || !(sigma > 0))
+        return fail(VIE_EINVAL, "aperture half-angle in (0, pi/2] and sigma > 0 required");
+    if (!hd->have_solution) return fail(VIE_ESTATE, "no solution stored: call vie_solve first");
+    const int Q = nt * nphi;
+    std::vector<double> gx, gw, dirs(3 * (size_t)D * Q), wts((size_t)D * Q);
+    gauss_legendre(nt, gx, gw);
+    for (int d = 0; d < D; ++d) {
+        double c[3] = {centers[3 * d], centers[3 * d + 1], centers[3 * d + 2]};
+        const double cn = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        if (!(cn > 0)) return fail(VIE_EINVAL, "detector axis is zero");
+        for (double& v : c) v /= cn;
+        // frame: u = (a x c)/|a x c|, a = z (x when |c_z| >= 0.9); v = c x u
+        const double a[3] = {std::fabs(c[2]) < 0.9 ? 0.0 : 1.0, 0.0, std::fabs(c[2]) < 0.9 ? 1.0 : 0.0};
+        double u[3] = {a[1] * c[2] - a[2] * c[1], a[2] * c[0] - a[0] * c[2], a[0] * c[1] - a[1] * c[0]};
+        const double un = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        for (double& v : u) v /= un;
+        const double v[3] = {c[1] * u[2] - c[2] * u[1], c[2] * u[0] - c[0] * u[2], c[0] * u[1] - c[1] * u[0]};
+        double tot = 0.0;
+        for (int i = 0; i < nt; ++i) {
+            const double t = 0.5 * theta_na * (gx[i] + 1.0);
+            const double wt = 0.5 * theta_na * gw[i] * std::exp(-t * t / (2.0 * sigma * sigma)) * std::sin(t) *
+                              (2.0 * M_PI / nphi);
+            for (int j = 0; j < nphi; ++j) {
+                const double p = 2.0 * M_PI * j / nphi;
+                const size_t q = (size_t)d * Q + (size_t)i * nphi + j;
+                for (int k = 0; k < 3; ++k)
+                    dirs[3 * q + k] = std::cos(t) * c[k] + std::sin(t) * (std::cos(p) * u[k] + std::sin(p) * v[k]);
+                wts[q] = wt;
+                tot += wt;
+            }
+        }
+        for (int q = 0; q < Q; ++q) wts[(size_t)d * Q + q] /= tot;
+    }
+    VIE_CUDA(cudaSetDevice(hd->device));
+    const int R = hd->n_rhs;
+    double *dd = nullptr, *dw = nullptr, *dp = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc(&dd, sizeof(double) * dirs.size());
+    if (e == cudaSuccess) e = cudaMalloc(&dw, sizeof(double) * wts.size());
+    if (e == cudaSuccess) e = cudaMalloc(&dp, sizeof(double) * 6 * D);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(double) * 2 * (size_t)D * R);
+    if (e == cudaSuccess) e = cudaMemcpy(dd, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dw, wts.data(), sizeof(double) * wts.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dp, pols, sizeof(double) * 6 * D, cudaMemcpyHostToDevice);
+    int st = e == cudaSuccess ? VIE_OK : cuda_fail(e, "aperture buffers");
+    if (st == VIE_OK) st = farfield_na(hd->op, hd->S.x, hd->S.n3, R, dd, dw, (const c64*)dp, D, Q, (c64*)dout);
+    if (st == VIE_OK) {
+        e = cudaMemcpy(out, dout, sizeof(double) * 2 * (size_t)D * R, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "aperture copy");
+    }
+    cudaFree(dd);
+    cudaFree(dw);
+    cudaFree(dp);
+    cudaFree(dout);
+    return st;
+}
+
 int vie_farfield_dirs(vie_handle* hd, const double* dirs, int D, int basis, double* out) {
     if (!hd || !dirs || !out || D < 1) return fail(VIE_EINVAL, "bad arguments");
     for (int d = 0; d < D; ++d) {

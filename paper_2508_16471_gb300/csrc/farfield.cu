@@ -71,6 +71,45 @@ int build_rhs(Operator& op, Solver& S, const vie_channel* chs, int n_rhs) {
 }
 
 // ---------------------------------------------------------------------------
+// finite numerical aperture (Eq. NAfield): weighted sums of projected far fields
+// ---------------------------------------------------------------------------
+__global__ void k_na_reduce(const c64* __restrict__ F, const double* __restrict__ w, const c64* __restrict__ pol,
+                            int D, int Q, c64* __restrict__ out) {
+    // one warp per (detector, RHS)
+    const int d = blockIdx.x, r = blockIdx.y;
+    const c64 p0 = pol[3 * d], p1 = pol[3 * d + 1], p2 = pol[3 * d + 2];
+    double ar = 0.0, ai = 0.0;
+    for (int q = threadIdx.x; q < Q; q += 32) {
+        const c64* f = F + ((long long)r * D * Q + (long long)d * Q + q) * 3;
+        const c64 e = p0 * f[0] + p1 * f[1] + p2 * f[2];
+        const double ww = w[(long long)d * Q + q];
+        ar += ww * e.x;
+        ai += ww * e.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (threadIdx.x == 0) out[(long long)r * D + d] = c64{ar, ai};
+}
+
+int farfield_na(Operator& op, const c64* x, long long n3, int R, const double* ddirs, const double* dw,
+                const c64* dpol, int D, int Q, c64* dout) {
+    c64* F = nullptr;
+    VIE_CUDA(cudaMalloc(&F, sizeof(c64) * 3 * (size_t)D * Q * R));
+    int st = farfield_dirs(op, x, n3, R, ddirs, D * Q, VIE_BASIS_CART, F);
+    if (st == VIE_OK) {
+        k_na_reduce<<<dim3(D, R), 32, 0, op.stream>>>(F, dw, dpol, D, Q, dout);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(op.stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "finite-aperture reduction");
+    }
+    cudaFree(F);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
 // far field on a direction list (FP64)
 // ---------------------------------------------------------------------------
 constexpr int FF_DB = 2;  // directions per block

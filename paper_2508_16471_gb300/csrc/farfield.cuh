@@ -49,6 +49,9 @@ __host__ __device__ inline double hom_nc(const HomScalars& s, double dtau, doubl
 }
 
 int farfield_dirs(Operator& op, const c64* x, long long n3, int R, const double* ddirs, int D, int basis, c64* dout);
+// finite aperture: out[r][d] = sum_q wq[d Q + q] pol_d . F_r(dirs[d Q + q]) (device arrays; F of D Q directions)
+int farfield_na(Operator& op, const c64* x, long long n3, int R, const double* ddirs, const double* dw,
+                const c64* dpol, int D, int Q, c64* dout);
 int farfield_grid(Operator& op, const c64* x, long long n3, int R, const double* dth, int nt, const double* dph,
                   int np, int basis, c64* dout);
 int hom_map_device(const c64* Ea, int nA, const c64* Eb, int nB, double* g2, double* vis, double* p2,

@@ -29,7 +29,7 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
            "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_guesses_rejected",
            "vie_net_create_io", "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune",
-           "vie_setup_disc", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
+           "vie_setup_disc", "vie_farfield_na", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
 
 
 class VieError(RuntimeError):
@@ -114,6 +114,7 @@ def load():
     L.vie_solve_many.argtypes = [P, P, P, C.c_int, C.POINTER(_Opts), P, C.c_int]
     L.vie_autotune.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.vie_setup_disc.argtypes = [C.POINTER(_Grid), dp, C.c_double, C.c_int, C.POINTER(P)]
+    L.vie_farfield_na.argtypes = [P, dp, dp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, dp]
     L.vie_set_farfield_engine.argtypes = [P, C.c_int]
     L.vie_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int]
     L.vie_kernel_launches.restype = C.c_longlong
@@ -137,7 +138,8 @@ def load():
               "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_net_create",
               "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
               "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_net_create_io",
-              "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune", "vie_setup_disc"]:
+              "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune", "vie_setup_disc",
+              "vie_farfield_na"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -269,6 +271,16 @@ class Handle:
 
     def guesses_rejected(self):
         return int(load().vie_guesses_rejected(self._h))
+
+    def farfield_na(self, centers, pols, theta_na, sigma, nt=12, nphi=16):
+        """vie_farfield_na: aperture-collected detector amplitudes [n_rhs][D] complex."""
+        c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 3)
+        p = _c128(np.asarray(pols).reshape(-1, 3))
+        D = c.shape[0]
+        out = np.zeros((self.n_rhs, D), dtype=np.complex128)
+        _check(load().vie_farfield_na(self._h, _dptr(c), _dptr(p.view(np.float64)), D, float(theta_na),
+                                      float(sigma), int(nt), int(nphi), _dptr(out.view(np.float64))))
+        return out
 
     def autotune(self, n_rhs=8, reps=3):
         """vie_autotune: time the candidate FFT schedules and keep the fastest;

@@ -274,3 +274,27 @@ def test_solve_many_rejects_repeated_handle(vielib):
         with pytest.raises(vielib.VieError) as e:
             vielib.solve_many([hd, hd], [chs, chs])
         assert e.value.code == vielib.VIE_EINVAL
+
+
+def test_finite_aperture_detectors(vielib, config1):
+    """Eq. NAfield: aperture-collected amplitudes of the 16^3 sphere's two
+    channels (z-polarised detectors at (60, 0) and (60, 180) deg, Gaussian
+    aperture of half-angle 15 deg) against the oracle's on the oracle currents,
+    the resulting g2 against the oracle's, and the point-detector limit."""
+    wl, chs, w_or = config1
+    g = wl.grid
+    cen = np.stack([inputs.spherical_basis(math.radians(t), math.radians(p))[0]
+                    for t, p in wl.extra["detectors_deg"]])
+    pols = np.array([[0, 0, 1.0], [0, 0, 1.0]], dtype=complex)
+    tna, sg = math.radians(15.0), math.radians(8.0)
+    with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
+        hd.solve(chs, tol=1e-10, restart=40)
+        Ena = hd.farfield_na(cen, pols, tna, sg, nt=10, nphi=12)
+        E0 = hd.farfield_na(cen, pols, 1e-5, 1.0, nt=2, nphi=4)
+        Fp = hd.farfield_dirs(cen)
+    E_or = np.stack([ovie.farfield_na(w_or[j], g.n, g.h, wl.k0, cen, pols, tna, sg, 10, 12) for j in range(2)])
+    assert np.abs(Ena - E_or).max() <= 1e-8 * np.abs(E_or).max()
+    assert np.abs(E0 - Fp[:, :, 2]).max() <= 1e-6 * np.abs(Fp).max()
+    g2, _, _, code = vielib.hom_transfer(Ena.T, sigma=1.2, dtau=np.array([0.0]))
+    assert code == 0
+    assert abs(g2 - ohom.g2_degenerate(E_or.T)) < 1e-6
