@@ -298,3 +298,18 @@ def test_finite_aperture_detectors(vielib, config1):
     g2, _, _, code = vielib.hom_transfer(Ena.T, sigma=1.2, dtau=np.array([0.0]))
     assert code == 0
     assert abs(g2 - ohom.g2_degenerate(E_or.T)) < 1e-6
+
+
+def test_grid_beyond_the_fft_engine_is_rejected(vielib):
+    """Axes whose padded length would exceed the FFT engine's 1024 points
+    (n > 512 with the default rule) are refused at set-up with VIE_EINVAL, and
+    the largest accepted axis (512 voxels on a thin slab) sets up."""
+    eps = np.ones((2, 2, 520))
+    eps[1, 1, 5] = 2.0
+    with pytest.raises(vielib.VieError) as e:
+        vielib.Handle(eps.shape, 0.01, eps, K0)
+    assert e.value.code == vielib.VIE_EINVAL
+    eps = np.ones((2, 2, 512))
+    eps[1, 1, 5] = 2.0
+    with vielib.Handle(eps.shape, 0.01, eps, K0) as hd:
+        assert max(hd.info()["P"]) == 1024
