@@ -712,7 +712,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
     std::vector<int> outer_active(R), it(R, 0), outer(R, 0);
     for (int r = 0; r < R; ++r) outer_active[r] = r;
     std::vector<double> hb(R), hr(R), htarget(R);
-    std::vector<int> hflag(R), hk(R);
+    std::vector<int> hflag(R), hk(R), hreo(R, 0);
 
     // b norms
     VIE_TRY(op_set_list(op, outer_active.data(), R));
@@ -894,19 +894,21 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
             dim3 gi(nblk, ni);
             for (int pass = 0; pass < 2; ++pass) {
                 const int* gate = pass ? S.reorth : nullptr;
+                // the second (re-orthogonalisation) pass runs only for the RHS its gate
+                // selects: its bytes are added after the step, once the gate is known
                 tmr_begin(TMR_DOTS, st);
                 k_dots<T><<<dim3(nblk_d, ni), KB, sizeof(double) * 2 * (KB / 32) * (j + 2), st>>>(
                     V, vrs, n, j, op.d_list, S.partial, mp1 + 1, n, nblk_d, gate);
-                tmr_end(TMR_DOTS, st, (double)ni * (j + 2) * n * ET);
+                tmr_end(TMR_DOTS, st, pass ? 0.0 : (double)ni * (j + 2) * n * ET);
                 LAUNCH_CHECK();
                 tmr_begin(TMR_REDUCE, st);
                 k_reduce_dots<<<dim3(j + 2, ni), KB, 0, st>>>(S.partial, S.coef, S.H, j, op.d_list, mp1, nblk_d, pass,
                                                                gate);
-                tmr_end(TMR_REDUCE, st, (double)ni * (j + 1) * nblk_d * 16.0);
+                tmr_end(TMR_REDUCE, st, pass ? 0.0 : (double)ni * (j + 1) * nblk_d * 16.0);
                 LAUNCH_CHECK();
                 tmr_begin(TMR_UPDATE, st);
                 k_update<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.coef, S.normpart, mp1, n, nblk, gate);
-                tmr_end(TMR_UPDATE, st, (double)ni * (j + 3) * n * ET);
+                tmr_end(TMR_UPDATE, st, pass ? 0.0 : (double)ni * (j + 3) * n * ET);
                 if (pass == 0) {
                     k_reorth_check<<<ceil_div(ni, 64), 64, 0, st>>>(S.normpart, nblk, S.coef, j, op.d_list, ni, mp1,
                                                                    S.reorth);
@@ -924,7 +926,17 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
             tmr_end(TMR_SCALE, st, 2.0 * ni * n * ET);
             LAUNCH_CHECK();
             VIE_CUDA(cudaMemcpyAsync(hflag.data(), S.flag, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+            if (tmr_enabled())
+                VIE_CUDA(cudaMemcpyAsync(hreo.data(), S.reorth, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
             VIE_CUDA(cudaStreamSynchronize(st));
+            if (tmr_enabled()) {
+                long long nre = 0;
+                for (int r : inner) nre += hreo[r] != 0;
+                tmr_add(TMR_DOTS, (double)nre * (j + 2) * n * ET, 0);
+                tmr_add(TMR_REDUCE, (double)nre * (j + 1) * nblk_d * 16.0, 0);
+                tmr_add(TMR_UPDATE, (double)nre * (j + 3) * n * ET, 0);
+                tmr_add(TMR_REORTH, 0.0, nre);
+            }
             std::vector<int> nxt;
             steps_sum += ni;
             for (int r : inner) {

@@ -57,10 +57,17 @@ void flush() {
 }
 const char* kNames[TMR_COUNT] = {"zfwd", "yfwd", "xfused", "yinv", "zinv", "dots", "reduce_dots", "update",
                                  "finish", "scale", "xupdate", "residual", "start_cycle", "rhs", "other",
-                                 "matvec_fp64"};
+                                 "matvec_fp64", "reorth_steps"};
 }  // namespace
 
 bool tmr_enabled() { return T().on; }
+
+void tmr_add(int id, double bytes, long long count) {
+    TimerState& t = T();
+    if (!t.on) return;
+    t.bytes[id] += bytes;
+    t.cnt[id] += count;
+}
 
 void tmr_begin(int id, cudaStream_t s) {
     TimerState& t = T();
