@@ -102,6 +102,10 @@ typedef struct vie_solve_opts {
                           refinement; needs restart >= 8 (its 7 vectors use the
                           basis storage), use_x0 0 or 1, precond 0             */
     int reserved[1];
+    double reorth_eta; /* GMRES: a second classical Gram-Schmidt pass runs for an
+                          RHS when the first left ||w'||^2 < reorth_eta ||w||^2
+                          (Daniel-Gragg-Kaufman-Stewart test; default 0.1, i.e.
+                          ||w'|| < 0.32 ||w||; 0 never, values >= 1 always)       */
 } vie_solve_opts;
 
 typedef struct vie_solve_stats {

@@ -154,6 +154,8 @@ void vie_default_opts(vie_solve_opts* o) {
     o->use_x0 = 0;
     o->precond = 0;
     o->solver = VIE_SOLVER_GMRES;
+    o->reserved[0] = 0;
+    o->reorth_eta = 0.1;
 }
 
 const char* vie_last_error(void) { return g_err.c_str(); }
@@ -257,6 +259,7 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
     if (o.use_x0 == 2 && !hd->net) return fail(VIE_ESTATE, "use_x0 = 2 needs a network attached with vie_attach_net");
     if (o.use_x0 < 0 || o.use_x0 > 2) return fail(VIE_EINVAL, "use_x0 must be 0, 1 or 2");
     if (o.precond != 0 && o.precond != 1) return fail(VIE_EINVAL, "precond must be 0 or 1");
+    if (!(o.reorth_eta >= 0) || !std::isfinite(o.reorth_eta)) return fail(VIE_EINVAL, "reorth_eta must be >= 0");
     if (o.solver != VIE_SOLVER_GMRES && o.solver != VIE_SOLVER_BICGSTAB)
         return fail(VIE_EINVAL, "solver must be VIE_SOLVER_GMRES or VIE_SOLVER_BICGSTAB");
     if (o.solver == VIE_SOLVER_BICGSTAB && (o.restart < 8 || o.precond || o.use_x0 == 2))

@@ -229,14 +229,14 @@ __global__ void k_update(cplx<T>* __restrict__ V, long long rstride, long long v
 // Gram-Schmidt pass is needed when the projection cancelled most of w,
 // ||w'|| < ||w|| / sqrt(2).  One thread per listed RHS.
 __global__ void k_reorth_check(const double* __restrict__ normpart, int nblk, const c64* __restrict__ coef, int j,
-                               const int* __restrict__ list, int nr, int mp1, int* __restrict__ gate) {
+                               const int* __restrict__ list, int nr, int mp1, int* __restrict__ gate, double eta) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nr) return;
     const int r = list[s];
     double t = 0;
     for (int b = 0; b < nblk; ++b) t += normpart[(long long)r * nblk + b];
     const double before = coef[(long long)r * (mp1 + 1) + j + 1].x;
-    gate[r] = (t < 0.5 * before) ? 1 : 0;
+    gate[r] = (t < eta * before) ? 1 : 0;
 }
 
 // One thread per listed RHS: finish step j (Givens rotations, residual estimate).
@@ -911,7 +911,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
                 tmr_end(TMR_UPDATE, st, pass ? 0.0 : (double)ni * (j + 3) * n * ET);
                 if (pass == 0) {
                     k_reorth_check<<<ceil_div(ni, 64), 64, 0, st>>>(S.normpart, nblk, S.coef, j, op.d_list, ni, mp1,
-                                                                   S.reorth);
+                                                                   S.reorth, o.reorth_eta);
                     LAUNCH_CHECK();
                 }
                 LAUNCH_CHECK();
