@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--bodies", type=int, default=8)
     p.add_argument("--restart", type=int, default=64)
+    p.add_argument("--inner-floor", type=float, default=0.7,
+                   help="mixed mode: inner solves stop at inner_floor x tol x ||b|| at the latest")
     p.add_argument("--reorth-eta", type=float, default=0.1,
                    help="GMRES re-orthogonalisation threshold (second Gram-Schmidt pass when ||w'||^2 < eta ||w||^2)")
     p.add_argument("--inner-tol", type=float, default=1e-6,
@@ -298,7 +300,7 @@ def run_ours(args):
     hd = V.Handle(g.n, g.h, wls[0].eps, wls[0].k0)
     stream = torch.cuda.ExternalStream(hd.stream())
     opts = dict(tol=1e-6, restart=args.restart, precision=V.PREC_MIXED, max_iter=args.max_iter,
-                inner_tol=args.inner_tol, reorth_eta=args.reorth_eta)
+                inner_tol=args.inner_tol, reorth_eta=args.reorth_eta, inner_floor=args.inner_floor)
 
     def step(i):
         hd.set_eps_device(eps_dev[i % len(eps_dev)].data_ptr())

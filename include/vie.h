@@ -106,6 +106,9 @@ typedef struct vie_solve_opts {
                           RHS when the first left ||w'||^2 < reorth_eta ||w||^2
                           (Daniel-Gragg-Kaufman-Stewart test; default 0.1, i.e.
                           ||w'|| < 0.32 ||w||; 0 never, values >= 1 always)       */
+    double inner_floor; /* mixed mode: an inner solve stops once its recurrence
+                          residual is below max(inner_tol ||r||, inner_floor tol
+                          ||b||) (default 0.7, in (0, 1])                         */
 } vie_solve_opts;
 
 typedef struct vie_solve_stats {

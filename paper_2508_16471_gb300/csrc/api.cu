@@ -156,6 +156,7 @@ void vie_default_opts(vie_solve_opts* o) {
     o->solver = VIE_SOLVER_GMRES;
     o->reserved[0] = 0;
     o->reorth_eta = 0.1;
+    o->inner_floor = 0.7;
 }
 
 const char* vie_last_error(void) { return g_err.c_str(); }
@@ -260,6 +261,7 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
     if (o.use_x0 < 0 || o.use_x0 > 2) return fail(VIE_EINVAL, "use_x0 must be 0, 1 or 2");
     if (o.precond != 0 && o.precond != 1) return fail(VIE_EINVAL, "precond must be 0 or 1");
     if (!(o.reorth_eta >= 0) || !std::isfinite(o.reorth_eta)) return fail(VIE_EINVAL, "reorth_eta must be >= 0");
+    if (!(o.inner_floor > 0) || !(o.inner_floor <= 1)) return fail(VIE_EINVAL, "inner_floor must be in (0, 1]");
     if (o.solver != VIE_SOLVER_GMRES && o.solver != VIE_SOLVER_BICGSTAB)
         return fail(VIE_EINVAL, "solver must be VIE_SOLVER_GMRES or VIE_SOLVER_BICGSTAB");
     if (o.solver == VIE_SOLVER_BICGSTAB && (o.restart < 8 || o.precond || o.use_x0 == 2))

@@ -860,7 +860,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         for (int r : cyc) {
             outer[r]++;
             double t = 0.99 * o.tol * hb[r];
-            if (prec_in == VIE_PREC_MIXED) t = std::max(o.inner_tol * hr[r], 0.3 * o.tol * hb[r]);
+            if (prec_in == VIE_PREC_MIXED) t = std::max(o.inner_tol * hr[r], o.inner_floor * o.tol * hb[r]);
             htarget[r] = t;
         }
         VIE_CUDA(cudaMemcpyAsync(S.target, htarget.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
@@ -1254,7 +1254,7 @@ static int bicgstab_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveRes
         for (int r : cyc) {
             outer[r]++;
             double t = 0.99 * o.tol * hb[r];
-            if (prec_in == VIE_PREC_MIXED) t = std::max(o.inner_tol * hr[r], 0.3 * o.tol * hb[r]);
+            if (prec_in == VIE_PREC_MIXED) t = std::max(o.inner_tol * hr[r], o.inner_floor * o.tol * hb[r]);
             htarget[r] = t;
         }
         VIE_CUDA(cudaMemcpyAsync(S.target, htarget.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));

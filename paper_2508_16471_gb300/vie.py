@@ -50,7 +50,7 @@ class _Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iter", C.c_int),
                 ("precision", C.c_int), ("inner_tol", C.c_double), ("use_x0", C.c_int),
                 ("precond", C.c_int), ("solver", C.c_int), ("reserved", C.c_int * 1),
-                ("reorth_eta", C.c_double)]
+                ("reorth_eta", C.c_double), ("inner_floor", C.c_double)]
 
 
 class _Stats(C.Structure):
