@@ -719,7 +719,7 @@ int vie_autotune(vie_handle* hd, int n_rhs, int reps, int P_out[3], double* ms_p
     Operator& op = hd->op;
     std::vector<int> cand[3];
     for (int a = 0; a < 3; ++a) cand[a] = pad_candidates(op.n[a], op.disc);
-    std::vector<std::array<int, 4>> configs;  // P0, P1, P2, fft path
+    std::vector<std::array<int, 4>> cands;  // P0, P1, P2, fft path
     const bool cubic = op.n[0] == op.n[1] && op.n[1] == op.n[2];
     for (int i0 = 0; i0 < (int)cand[0].size(); ++i0)
         for (int i1 = 0; i1 < (int)cand[1].size(); ++i1)
@@ -727,7 +727,7 @@ int vie_autotune(vie_handle* hd, int n_rhs, int reps, int P_out[3], double* ms_p
                 if (cubic && (i0 != i1 || i1 != i2)) continue;
                 const int P[3] = {cand[0][i0], cand[1][i1], cand[2][i2]};
                 const bool any_fast = fast_length(P[0]) || fast_length(P[1]) || fast_length(P[2]);
-                for (int path = 0; path < (any_fast ? 2 : 1); ++path) configs.push_back({P[0], P[1], P[2], path});
+                for (int path = 0; path < (any_fast ? 2 : 1); ++path) cands.push_back({P[0], P[1], P[2], path});
             }
     const int P0[3] = {op.P[0], op.P[1], op.P[2]};
     const int path0 = op.fft_path;
@@ -749,10 +749,10 @@ int vie_autotune(vie_handle* hd, int n_rhs, int reps, int P_out[3], double* ms_p
     }
     double best = 1e300;
     int bi = -1;
-    for (int c = 0; st == VIE_OK && c < (int)configs.size(); ++c) {
-        const int P[3] = {configs[c][0], configs[c][1], configs[c][2]};
+    for (int c = 0; st == VIE_OK && c < (int)cands.size(); ++c) {
+        const int P[3] = {cands[c][0], cands[c][1], cands[c][2]};
         if (P[0] != op.P[0] || P[1] != op.P[1] || P[2] != op.P[2]) st = op_replan(op, P);
-        op.fft_path = configs[c][3];
+        op.fft_path = cands[c][3];
         if (st == VIE_OK) st = op_apply(op, VIE_PREC_MIXED, w, nv, y, nv, op.d_list, n_rhs);  // warm-up
         if (st != VIE_OK) break;
         cudaEventRecord(e0, op.stream);
@@ -768,10 +768,10 @@ int vie_autotune(vie_handle* hd, int n_rhs, int reps, int P_out[3], double* ms_p
         }
     }
     // keep the fastest configuration (or restore the original one on error)
-    const int keep[3] = {bi >= 0 && st == VIE_OK ? configs[bi][0] : P0[0], bi >= 0 && st == VIE_OK ? configs[bi][1] : P0[1],
-                         bi >= 0 && st == VIE_OK ? configs[bi][2] : P0[2]};
+    const int keep[3] = {bi >= 0 && st == VIE_OK ? cands[bi][0] : P0[0], bi >= 0 && st == VIE_OK ? cands[bi][1] : P0[1],
+                         bi >= 0 && st == VIE_OK ? cands[bi][2] : P0[2]};
     const int st2 = (keep[0] != op.P[0] || keep[1] != op.P[1] || keep[2] != op.P[2]) ? op_replan(op, keep) : VIE_OK;
-    op.fft_path = bi >= 0 && st == VIE_OK ? configs[bi][3] : path0;
+    op.fft_path = bi >= 0 && st == VIE_OK ? cands[bi][3] : path0;
     cudaFree(w);
     cudaFree(y);
     if (e0) cudaEventDestroy(e0);

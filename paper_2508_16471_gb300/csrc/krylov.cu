@@ -821,7 +821,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         VIE_CUDA(cudaMemcpyAsync(hr.data(), S.rnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
         VIE_CUDA(cudaStreamSynchronize(st));
         if (guess_pending) {
-            // the true FP64 residual judges a supplied initial guess: where it is
+            // the true FP64 residual decides on a supplied initial guess: where it is
             // no better than x0 = 0, fall back to zero
             guess_pending = false;
             std::vector<int> bad;

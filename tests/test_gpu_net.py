@@ -99,7 +99,7 @@ def test_learned_initial_guess_gains_over_zero(vielib):
     then solve held-out bodies from x0 = 0 and from the network's guess,
     entered as the residual-minimising combination of the Born term and the
     predicted correction.  No guess may be rejected by the FP64-residual
-    judge, every RHS must reach the target and the learned start must not
+    check, every RHS must reach the target and the learned start must not
     cost iterations; the measured saving is printed."""
     from paper_2508_16471_gb300 import learned
     n, h, f, dirs = 64, 1.0 / 64.0, 4, 8
