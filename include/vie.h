@@ -134,7 +134,8 @@ typedef struct vie_info {
     double device_bytes; /* device memory held by the handle                     */
 } vie_info;
 
-/* Default options (tol 1e-6, restart 30, max_iter 5000, mixed, inner 1e-3). */
+/* Default options: tol 1e-6, restart 30, max_iter 5000, mixed precision, inner_tol 1e-6,
+ * reorth_eta 0.1, inner_floor 0.7, GMRES, no start guess, no preconditioner. */
 void vie_default_opts(vie_solve_opts* opts);
 
 /*
@@ -148,7 +149,14 @@ void vie_default_opts(vie_solve_opts* opts);
  *   eps_r  : host [n0][n1][n2] real relative permittivity, >= 1, finite.
  *   k0     : free-space wavenumber > 0.
  *   out    : receives the new handle (device = the current CUDA device).
- * Errors: VIE_EINVAL (bad g, eps_r, k0; body empty), VIE_ENOMEM, VIE_EDEVICE.
+ * Size limits: at most 2^28 voxels; padded lengths up to 8192 per axis, the
+ * first one up to 3200 (the fused x pass holds three components of a column
+ * in shared memory) and the last up to 6400 (two FP64 line buffers): long
+ * boxes go shortest axis first, longest last.  Device memory grows with the
+ * padded grid: about 18 B (FP32 work) + 36 B (FP64 work) + 24 B x 6 / 8
+ * (kernel octants) per padded point, plus the Krylov basis.
+ * Errors: VIE_EINVAL (bad g, eps_r, k0; body empty; a padded length beyond
+ * the limits), VIE_ENOMEM, VIE_EDEVICE.
  */
 int vie_setup(const vie_grid* g, const double* eps_r, double k0, vie_handle** out);
 
@@ -315,7 +323,7 @@ int vie_apply_device(vie_handle* hd, const void* w_dev, void* y_dev, int n_rhs, 
 int vie_apply_noalloc(vie_handle* hd, const void* w_dev, void* y_dev, int n_rhs);
 
 /* Kernel-level check: batched 1-D complex DFT of `count` contiguous lines of
- * length L (2,3,5,7-smooth, <= 1024) by the library's FFT engine, host
+ * length L (2,3,5,7-smooth, <= 8192; FP64 <= 6400) by the library's FFT engine, host
  * in/out [count][L] complex doubles, forward (sign -1) when inverse == 0,
  * unnormalised inverse otherwise, in FP32 (precision MIXED) or FP64. */
 int vie_fft_lines(const double* in, double* out, int L, int count, int inverse, int precision);

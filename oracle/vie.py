@@ -213,6 +213,23 @@ def convolve_direct_points_multi(n, h, k0, W, targets):
     return out
 
 
+def convolve_points_sparse(src, Wsrc, h, k0, targets, chunk=1 << 20):
+    """(K * w)(t) = sum_s K(t - s) w(s) over an explicit source list, for grids
+    too large to hold as dense fields: ``src`` (S, 3) integer voxel indices,
+    ``Wsrc`` (R, 3, S) their currents, ``targets`` (T, 3).  Returns (R, 3, T).
+    Sources are taken in chunks of ``chunk`` (memory only; same sum)."""
+    src = np.asarray(src, dtype=np.int64)
+    Wsrc = np.asarray(Wsrc)
+    out = np.zeros((Wsrc.shape[0], 3, len(targets)), dtype=np.complex128)
+    for t, tv in enumerate(np.asarray(targets, dtype=np.int64)):
+        for c0 in range(0, len(src), chunk):
+            K = kernel_at(tv[None, :] - src[c0:c0 + chunk], h, k0)  # (S', 6)
+            Wc = Wsrc[:, :, c0:c0 + chunk]
+            for i in range(3):
+                out[:, i, t] += sum(Wc[:, j] @ K[:, CIDX[i][j]] for j in range(3))
+    return out
+
+
 def apply_direct(Ktab, n, chi, w):
     """y = w - chi (K * w) with the direct-sum convolution."""
     return w - chi[None] * convolve_direct(Ktab, n, w)

@@ -8,7 +8,8 @@
 // performs an R-point DFT in registers and writes the results in autosorted
 // position; two buffers alternate between stages.  Twiddles are precomputed
 // on the host in FP64 (rounded once to the working precision) and staged in
-// shared memory.
+// shared memory, or read from global memory (through L1) for lengths whose
+// tables would crowd the line buffers out of shared memory.
 //
 // Forward transforms use exp(-2 pi i j k / L), inverse exp(+2 pi i j k / L),
 // both unnormalised.
@@ -19,7 +20,7 @@
 namespace vie {
 
 constexpr int FFT_MAX_STAGES = 10;
-constexpr int FFT_MAX_L = 1024;
+constexpr int FFT_MAX_L = 8192;
 
 struct FFTPlan {
     int L;

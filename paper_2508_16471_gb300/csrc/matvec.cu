@@ -118,6 +118,8 @@ int padded_len(int m) {
 }
 int padded_size(int n) { return padded_len(2 * n - 1); }
 
+static int check_tiles(const Operator& op);
+
 int op_init_axes(Operator& op) {
     for (int a = 0; a < 3; ++a) {
         // D2 takes differences of the convolution one cell beyond the grid: P >= 2n
@@ -126,10 +128,10 @@ int op_init_axes(Operator& op) {
         if (op.P[a] < need) return fail(VIE_EINVAL, "padded length below the convolution's span");
         op.H[a] = op.P[a] / 2 + 1;
         if (!make_plan(op.P[a], &op.ax[a].plan))
-            return fail(VIE_EINVAL, "padded FFT size " + std::to_string(op.P[a]) + " exceeds the engine limit (1024)");
+            return fail(VIE_EINVAL, "padded FFT size " + std::to_string(op.P[a]) + " exceeds the engine limit (8192)");
         VIE_TRY(upload_twiddles(op, op.ax[a]));
     }
-    return VIE_OK;
+    return check_tiles(op);
 }
 
 // ---------------------------------------------------------------------------
@@ -138,16 +140,32 @@ int op_init_axes(Operator& op) {
 template <typename T> __device__ __forceinline__ cplx<T> czero() { return cplx<T>{(T)0, (T)0}; }
 
 // Generic contiguous lines: in [count][n_in] -> out [count][n_out], length L.
+// Twiddles: staged in shared memory when `stw`, else read from `twg` directly.
+// Lines are padded to NL + 1 columns against bank conflicts when NL > 1.
+__host__ __device__ __forceinline__ int lines_ld(int NL) { return NL > 1 ? NL + 1 : 1; }
+
+template <typename T>
+__device__ __forceinline__ cplx<T>* tw_setup(unsigned char* smraw, const cplx<T>* __restrict__ twg,
+                                             const FFTPlan& plan, int stw, const cplx<T>** tw) {
+    cplx<T>* s = reinterpret_cast<cplx<T>*>(smraw);
+    if (!stw) {
+        *tw = twg;
+        return s;
+    }
+    load_twiddles(s, twg, plan.twlen);
+    *tw = s;
+    return s + ((plan.twlen + 1) & ~1);
+}
+
 template <typename T, bool INV>
 __global__ void k_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_in,
-                        int n_out, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL) {
+                        int n_out, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL, int stw) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+    const cplx<T>* tw;
     const int L = plan.L;
-    const int ld = NL + 1;
-    cplx<T>* bA = tw + ((plan.twlen + 1) & ~1);
+    const int ld = lines_ld(NL);
+    cplx<T>* bA = tw_setup<T>(smraw, twg, plan, stw, &tw);
     cplx<T>* bB = bA + L * ld;
-    load_twiddles(tw, twg, plan.twlen);
     const long long line0 = (long long)blockIdx.x * NL;
     for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
         const int l = e / L, p = e - (e / L) * L;
@@ -168,13 +186,12 @@ __global__ void k_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_
 // Middle-axis transform: in [outer][n_in][inner] -> out [outer][n_out][inner].
 template <typename T, bool INV>
 __global__ void k_axis(const cplx<T>* in, cplx<T>* out, long long inner, int n_in,
-                       int n_out, FFTPlan plan, const cplx<T>* __restrict__ twg, int TW) {
+                       int n_out, FFTPlan plan, const cplx<T>* __restrict__ twg, int TW, int stw) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+    const cplx<T>* tw;
     const int L = plan.L;
-    cplx<T>* bA = tw + ((plan.twlen + 1) & ~1);
+    cplx<T>* bA = tw_setup<T>(smraw, twg, plan, stw, &tw);
     cplx<T>* bB = bA + L * TW;
-    load_twiddles(tw, twg, plan.twlen);
     const long long ntile = (inner + TW - 1) / TW;
     const long long o = blockIdx.x / ntile;
     const long long i0 = (blockIdx.x - o * ntile) * TW;
@@ -196,14 +213,14 @@ __global__ void k_axis(const cplx<T>* in, cplx<T>* out, long long inner, int n_i
 template <typename T>
 __global__ void k_zfwd(const cplx<T>* __restrict__ w, long long w_rstride, const int* __restrict__ list,
                        const int* __restrict__ idx_map, cplx<T>* __restrict__ A, int n0, int n1, int n2,
-                       long long Nb, long long nlines, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL) {
+                       long long Nb, long long nlines, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL,
+                       int stw) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+    const cplx<T>* tw;
     const int L = plan.L;
-    const int ld = NL + 1;
-    cplx<T>* bA = tw + ((plan.twlen + 1) & ~1);
+    const int ld = lines_ld(NL);
+    cplx<T>* bA = tw_setup<T>(smraw, twg, plan, stw, &tw);
     cplx<T>* bB = bA + L * ld;
-    load_twiddles(tw, twg, plan.twlen);
     const long long line0 = (long long)blockIdx.x * NL;
     const long long plane = (long long)n0 * n1;
     for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
@@ -234,14 +251,13 @@ __global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict_
                        cplx<T>* __restrict__ y, long long y_rstride, const int* __restrict__ list,
                        const int* __restrict__ idx_map, const T* __restrict__ chi, int n0, int n1, int n2,
                        long long Nb, long long nlines, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL,
-                       long long chi_cs) {
+                       long long chi_cs, int stw) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+    const cplx<T>* tw;
     const int L = plan.L;
-    const int ld = NL + 1;
-    cplx<T>* bA = tw + ((plan.twlen + 1) & ~1);
+    const int ld = lines_ld(NL);
+    cplx<T>* bA = tw_setup<T>(smraw, twg, plan, stw, &tw);
     cplx<T>* bB = bA + L * ld;
-    load_twiddles(tw, twg, plan.twlen);
     const long long line0 = (long long)blockIdx.x * NL;
     const long long plane = (long long)n0 * n1;
     for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
@@ -278,14 +294,13 @@ template <typename T>
 __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int n0, long long inner, int P0, int P1, int P2,
                          const cplx<T>* __restrict__ khat, int H0, int H1, int H2, FFTPlan plan,
                          const cplx<T>* __restrict__ twg, int TW, const cplx<T>* __restrict__ dtab, int dstride,
-                         T ksq) {
+                         T ksq, int stw) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    cplx<T>* tw = reinterpret_cast<cplx<T>*>(smraw);
+    const cplx<T>* tw;
     const int L = plan.L;  // == P0
     cplx<T>* D[4];
-    D[0] = tw + ((plan.twlen + 1) & ~1);
+    D[0] = tw_setup<T>(smraw, twg, plan, stw, &tw);
     for (int i = 1; i < 4; ++i) D[i] = D[i - 1] + L * TW;
-    load_twiddles(tw, twg, plan.twlen);
     const long long ntile = (inner + TW - 1) / TW;
     const long long slot = blockIdx.x / ntile;
     const long long i0 = (blockIdx.x - slot * ntile) * TW;
@@ -358,9 +373,10 @@ __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int 
     }
 }
 
-// Periodic embedding of the discrete kernel K(m) (six components, FP64).
-__global__ void k_kernel_circulant(c64* __restrict__ Kc, int n0, int n1, int n2, int P0, int P1, int P2, double h,
-                                   double k0, double coef, double self_re, double self_im) {
+// Periodic embedding of component q of the discrete kernel K(m) (FP64);
+// q = 0..5 for xx, xy, xz, yy, yz, zz.
+__global__ void k_kernel_circulant(c64* __restrict__ Kc, int q, int n0, int n1, int n2, int P0, int P1, int P2,
+                                   double h, double k0, double coef, double self_re, double self_im) {
     const long long tot = (long long)P0 * P1 * P2;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
          i += (long long)gridDim.x * blockDim.x) {
@@ -376,10 +392,11 @@ __global__ void k_kernel_circulant(c64* __restrict__ Kc, int n0, int n1, int n2,
             else if (pp[a] >= PP[a] - nn[a] + 1) m[a] = pp[a] - PP[a];
             else ok = false;
         }
-        c64 out[6] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        c64 out = {0, 0};
+        const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
         if (ok) {
             if (m[0] == 0 && m[1] == 0 && m[2] == 0) {
-                out[0] = out[3] = out[5] = c64{self_re, self_im};
+                if (I[q] == J[q]) out = c64{self_re, self_im};
             } else {
                 const double R[3] = {m[0] * h, m[1] * h, m[2] * h};
                 const double r = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
@@ -392,15 +409,12 @@ __global__ void k_kernel_circulant(c64* __restrict__ Kc, int n0, int n1, int n2,
                 const c64 A = {1.0 - ikr2, ikr};
                 const c64 Bc = {-1.0 + 3.0 * ikr2, -3.0 * ikr};
                 const double u[3] = {R[0] / r, R[1] / r, R[2] / r};
-                const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
-                for (int q = 0; q < 6; ++q) {
-                    c64 t = {Bc.x * u[I[q]] * u[J[q]], Bc.y * u[I[q]] * u[J[q]]};
-                    if (I[q] == J[q]) t = t + A;
-                    out[q] = g * t;
-                }
+                c64 t = {Bc.x * u[I[q]] * u[J[q]], Bc.y * u[I[q]] * u[J[q]]};
+                if (I[q] == J[q]) t = t + A;
+                out = g * t;
             }
         }
-        for (int q = 0; q < 6; ++q) Kc[q * tot + i] = out[q];
+        Kc[i] = out;
     }
 }
 
@@ -426,18 +440,16 @@ __global__ void k_scalar_circulant(c64* __restrict__ Kc, int P0, int P1, int P2,
     }
 }
 
+// keep the octant (P/2 + 1 per axis) of one transformed component, scaled
 __global__ void k_octant(const c64* __restrict__ Kc, c64* __restrict__ o64, c32* __restrict__ o32, int P0, int P1,
-                         int P2, int H0, int H1, int H2, double scale, int ncomp) {
+                         int P2, int H0, int H1, int H2, double scale) {
     const long long HH = (long long)H0 * H1 * H2;
-    const long long PP = (long long)P0 * P1 * P2;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncomp * HH;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HH;
          i += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(i / HH);
-        const long long r = i - q * HH;
-        const int fz = (int)(r % H2);
-        const int fy = (int)((r / H2) % H1);
-        const int fx = (int)(r / ((long long)H1 * H2));
-        const c64 v = Kc[q * PP + ((long long)fx * P1 + fy) * P2 + fz];
+        const int fz = (int)(i % H2);
+        const int fy = (int)((i / H2) % H1);
+        const int fx = (int)(i / ((long long)H1 * H2));
+        const c64 v = Kc[((long long)fx * P1 + fy) * P2 + fz];
         const c64 s = {v.x * scale, v.y * scale};
         o64[i] = s;
         o32[i] = c32{(float)s.x, (float)s.y};
@@ -581,35 +593,66 @@ template <typename T> static size_t tw_bytes(const FFTPlan& p) {
     return sizeof(cplx<T>) * (size_t)((p.twlen + 1) & ~1);
 }
 
-// lines per CTA for the contiguous-line kernels (two buffers of L*(NL+1))
-template <typename T> static int lines_per_cta(int L) {
+// Launch shape of a generic FFT pass: lines (or columns) per CTA, whether the
+// twiddle table is staged in shared memory, and the dynamic shared memory.
+// The table is staged while the whole CTA stays within half of an SM's shared
+// memory (two resident CTAs); longer transforms read it through L1 instead.
+struct TileCfg {
+    int w = 1;
+    int stw = 1;
+    size_t smem = 0;
+    bool ok = false;
+};
+static const size_t SMEM_STAGE = 100 * 1024;
+template <typename T> static TileCfg finish_cfg(const FFTPlan& p, int w, size_t data) {
+    TileCfg c;
+    c.w = w;
+    c.stw = tw_bytes<T>(p) + data <= SMEM_STAGE ? 1 : 0;
+    c.smem = data + (c.stw ? tw_bytes<T>(p) : 0);
+    c.ok = c.smem <= SMEM_CAP;
+    return c;
+}
+
+// contiguous-line kernels: two buffers of L x lines_ld(NL)
+template <typename T> static TileCfg lines_cfg(const FFTPlan& p) {
     const int budget = 48 * 1024;
-    int nl = budget / (2 * (int)sizeof(cplx<T>) * std::max(L, 1)) - 1;
-    return std::max(1, std::min(32, pow2_floor(std::max(1, nl))));
+    int nl = budget / (2 * (int)sizeof(cplx<T>) * std::max(p.L, 1)) - 1;
+    nl = std::max(1, std::min(32, pow2_floor(std::max(1, nl))));
+    return finish_cfg<T>(p, nl, 2 * sizeof(cplx<T>) * (size_t)p.L * lines_ld(nl));
 }
-template <typename T> static size_t lines_smem(const FFTPlan& p, int NL) {
-    return tw_bytes<T>(p) + 2 * sizeof(cplx<T>) * (size_t)p.L * (NL + 1);
-}
-// tile width for the strided-axis kernels (two buffers of L*TW)
-template <typename T> static int axis_tile(int L, long long inner) {
+// strided-axis kernels: two buffers of L x TW; TW is raised to one 32-byte
+// sector of adjacent columns where that fits, so the strided rows coalesce
+template <typename T> static TileCfg axis_cfg(const FFTPlan& p, long long inner) {
     const int budget = 64 * 1024;
-    int tw = budget / (2 * (int)sizeof(cplx<T>) * std::max(L, 1));
+    const size_t row = 2 * sizeof(cplx<T>) * (size_t)std::max(p.L, 1);
+    int tw = (int)(budget / row);
     tw = std::max(1, std::min(32, pow2_floor(std::max(1, tw))));
+    const int sector = 32 / (int)sizeof(cplx<T>);
+    while (tw < sector && row * (size_t)(2 * tw) <= SMEM_CAP) tw *= 2;
     while (tw > 1 && tw / 2 >= inner) tw /= 2;
-    return tw;
+    return finish_cfg<T>(p, tw, row * tw);
 }
-template <typename T> static size_t axis_smem(const FFTPlan& p, int TW) {
-    return tw_bytes<T>(p) + 2 * sizeof(cplx<T>) * (size_t)p.L * TW;
-}
-template <typename T> static int xfused_tile(int L, long long inner) {
+// fused x pass: four buffers of L x TW (three components and a scratch)
+template <typename T> static TileCfg xfused_cfg(const FFTPlan& p, long long inner) {
     const int budget = 96 * 1024;
-    int tw = budget / (4 * (int)sizeof(cplx<T>) * std::max(L, 1));
+    int tw = budget / (4 * (int)sizeof(cplx<T>) * std::max(p.L, 1));
     tw = std::max(1, std::min(32, pow2_floor(std::max(1, tw))));
     while (tw > 1 && tw / 2 >= inner) tw /= 2;
-    return tw;
+    return finish_cfg<T>(p, tw, 4 * sizeof(cplx<T>) * (size_t)p.L * tw);
 }
-template <typename T> static size_t xfused_smem(const FFTPlan& p, int TW) {
-    return tw_bytes<T>(p) + 4 * sizeof(cplx<T>) * (size_t)p.L * TW;
+
+// Every generic pass must fit in shared memory at FP64 (the larger element).
+// The fused x pass holds three components of a column at once, so the first
+// axis has the tightest limit (3200 points at FP64): long grids put their
+// longest axis last.
+static int check_tiles(const Operator& op) {
+    if (!xfused_cfg<double>(op.ax[0].plan, (long long)op.P[1] * op.P[2]).ok)
+        return fail(VIE_EINVAL, "padded length " + std::to_string(op.P[0]) +
+                                    " of the first axis is too long for the fused x pass (order the axes "
+                                    "shortest first)");
+    if (!axis_cfg<double>(op.ax[1].plan, op.P[2]).ok || !lines_cfg<double>(op.ax[2].plan).ok)
+        return fail(VIE_EINVAL, "padded FFT length does not fit in shared memory");
+    return VIE_OK;
 }
 
 template <typename T> static const cplx<T>* twp(const AxisFFT& a);
@@ -627,11 +670,11 @@ static int launch_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_
         VIE_TRY(allow_smem(k_lines<T, INV>));
         init = true;
     }
-    const int NL = lines_per_cta<T>(p.L);
-    const size_t sm = lines_smem<T>(p, NL);
-    const long long grid = (count + NL - 1) / NL;
+    const TileCfg c = lines_cfg<T>(p);
+    if (!c.ok) return fail(VIE_EINVAL, "FFT length " + std::to_string(p.L) + " does not fit in shared memory");
+    const long long grid = (count + c.w - 1) / c.w;
     if (grid <= 0) return VIE_OK;
-    k_lines<T, INV><<<(unsigned)grid, 256, sm, s>>>(in, out, count, n_in, n_out, p, tw, NL);
+    k_lines<T, INV><<<(unsigned)grid, 256, c.smem, s>>>(in, out, count, n_in, n_out, p, tw, c.w, c.stw);
     count_launch();
     VIE_CUDA(cudaGetLastError());
     return VIE_OK;
@@ -646,12 +689,12 @@ static int launch_axis(const cplx<T>* in, cplx<T>* out, long long outer, int n_i
         VIE_TRY(allow_smem(k_axis<T, INV>));
         init = true;
     }
-    const int TW = axis_tile<T>(p.L, inner);
-    const size_t sm = axis_smem<T>(p, TW);
-    const long long grid = outer * ((inner + TW - 1) / TW);
+    const TileCfg c = axis_cfg<T>(p, inner);
+    if (!c.ok) return fail(VIE_EINVAL, "FFT length " + std::to_string(p.L) + " does not fit in shared memory");
+    const long long grid = outer * ((inner + c.w - 1) / c.w);
     if (grid <= 0) return VIE_OK;
     tmr_begin(tid, s);
-    k_axis<T, INV><<<(unsigned)grid, 256, sm, s>>>(in, out, inner, n_in, n_out, p, tw, TW);
+    k_axis<T, INV><<<(unsigned)grid, 256, c.smem, s>>>(in, out, inner, n_in, n_out, p, tw, c.w, c.stw);
     tmr_end(tid, s, bytes);
     count_launch();
     VIE_CUDA(cudaGetLastError());
@@ -660,7 +703,7 @@ static int launch_axis(const cplx<T>* in, cplx<T>* out, long long outer, int n_i
 
 int fft_lines_device(const void* in, void* out, int L, int count, int inverse, int prec, cudaStream_t s) {
     FFTPlan p;
-    if (!make_plan(L, &p)) return fail(VIE_EINVAL, "FFT length must be 2,3,5,7-smooth and <= 1024");
+    if (!make_plan(L, &p)) return fail(VIE_EINVAL, "FFT length must be 2,3,5,7-smooth and <= 8192");
     const int n = std::max(1, p.twlen);
     std::vector<double> t(2 * n, 0.0);
     plan_twiddles(p, t.data());
@@ -716,8 +759,6 @@ static int build_diff_tables(Operator& op) {
 int op_build_kernel(Operator& op) {
     const int P0 = op.P[0], P1 = op.P[1], P2 = op.P[2];
     const long long PP = (long long)P0 * P1 * P2;
-    c64* Kc = nullptr;
-    VIE_TRY(dev_alloc(op, (void**)&Kc, sizeof(c64) * 6 * PP));
     const double a = op.h * std::cbrt(3.0 / (4.0 * M_PI));
     const double ka = op.k0 * a;
     double kap;
@@ -728,40 +769,46 @@ int op_build_kernel(Operator& op) {
     const double cr = std::cos(ka), sr = std::sin(ka);
     const double self_re = (2.0 / 3.0) * ((cr + ka * sr) - 1.0) - 1.0 / 3.0;
     const double self_im = (2.0 / 3.0) * (sr - ka * cr);
-    int st = VIE_OK;
     const int nc = op.disc ? 1 : 6;  // D2: one scalar kernel
-    if (op.disc) {
-        // D2: G_h(m) = kappa h^3 g(m h), G_h(0) = ((1 - i ka) e^{i ka} - 1) / k^2 on the whole periodic range
-        const double g0r = ((cr + ka * sr) - 1.0) / (op.k0 * op.k0), g0i = (sr - ka * cr) / (op.k0 * op.k0);
-        k_scalar_circulant<<<1184, 256, 0, op.stream>>>(Kc, P0, P1, P2, op.h, op.k0, coef / (op.k0 * op.k0), g0r, g0i);
-        VIE_TRY(build_diff_tables(op));
-    } else {
-        k_kernel_circulant<<<1184, 256, 0, op.stream>>>(Kc, op.n[0], op.n[1], op.n[2], P0, P1, P2, op.h, op.k0, coef,
-                                                        self_re, self_im);
-    }
-    count_launch();
-    if (cudaGetLastError() != cudaSuccess) st = fail(VIE_EDEVICE, "kernel build launch failed");
-    // 3-D FFT, in place: z (contiguous lines), y, x
-    if (st == VIE_OK)
-        st = launch_lines<double, false>(Kc, Kc, (long long)nc * P0 * P1, P2, P2, op.ax[2].plan, op.ax[2].tw64,
-                                         op.stream);
-    if (st == VIE_OK)
-        st = launch_axis<double, false>(Kc, Kc, (long long)nc * P0, P1, P1, P2, op.ax[1].plan, op.ax[1].tw64,
-                                        op.stream);
-    if (st == VIE_OK)
-        st = launch_axis<double, false>(Kc, Kc, (long long)nc, P0, P0, (long long)P1 * P2, op.ax[0].plan,
-                                        op.ax[0].tw64, op.stream);
+    if (op.disc) VIE_TRY(build_diff_tables(op));
     const long long HH = (long long)op.H[0] * op.H[1] * op.H[2];
-    if (st == VIE_OK) st = dev_alloc(op, (void**)&op.khat64, sizeof(c64) * 6 * HH);
-    if (st == VIE_OK) st = dev_alloc(op, (void**)&op.khat32, sizeof(c32) * 6 * HH);
-    if (st == VIE_OK) {
-        k_octant<<<1184, 256, 0, op.stream>>>(Kc, op.khat64, op.khat32, P0, P1, P2, op.H[0], op.H[1], op.H[2],
-                                              1.0 / (double)PP, nc);
+    VIE_TRY(dev_alloc(op, (void**)&op.khat64, sizeof(c64) * 6 * HH));
+    VIE_TRY(dev_alloc(op, (void**)&op.khat32, sizeof(c32) * 6 * HH));
+    // one component at a time through a single FP64 periodic array
+    c64* Kc = nullptr;
+    VIE_TRY(dev_alloc(op, (void**)&Kc, sizeof(c64) * PP));
+    int st = VIE_OK;
+    for (int q = 0; q < nc && st == VIE_OK; ++q) {
+        if (op.disc) {
+            // D2: G_h(m) = kappa h^3 g(m h), G_h(0) = ((1 - i ka) e^{i ka} - 1) / k^2 on the whole periodic range
+            const double g0r = ((cr + ka * sr) - 1.0) / (op.k0 * op.k0), g0i = (sr - ka * cr) / (op.k0 * op.k0);
+            k_scalar_circulant<<<1184, 256, 0, op.stream>>>(Kc, P0, P1, P2, op.h, op.k0, coef / (op.k0 * op.k0), g0r,
+                                                            g0i);
+        } else {
+            k_kernel_circulant<<<1184, 256, 0, op.stream>>>(Kc, q, op.n[0], op.n[1], op.n[2], P0, P1, P2, op.h, op.k0,
+                                                            coef, self_re, self_im);
+        }
         count_launch();
-        if (cudaGetLastError() != cudaSuccess) st = fail(VIE_EDEVICE, "octant launch failed");
+        if (cudaGetLastError() != cudaSuccess) st = fail(VIE_EDEVICE, "kernel build launch failed");
+        // 3-D FFT, in place: z (contiguous lines), y, x
+        if (st == VIE_OK)
+            st = launch_lines<double, false>(Kc, Kc, (long long)P0 * P1, P2, P2, op.ax[2].plan, op.ax[2].tw64,
+                                             op.stream);
+        if (st == VIE_OK)
+            st = launch_axis<double, false>(Kc, Kc, (long long)P0, P1, P1, P2, op.ax[1].plan, op.ax[1].tw64,
+                                            op.stream);
+        if (st == VIE_OK)
+            st = launch_axis<double, false>(Kc, Kc, 1, P0, P0, (long long)P1 * P2, op.ax[0].plan, op.ax[0].tw64,
+                                            op.stream);
+        if (st == VIE_OK) {
+            k_octant<<<1184, 256, 0, op.stream>>>(Kc, op.khat64 + q * HH, op.khat32 + q * HH, P0, P1, P2, op.H[0],
+                                                  op.H[1], op.H[2], 1.0 / (double)PP);
+            count_launch();
+            if (cudaGetLastError() != cudaSuccess) st = fail(VIE_EDEVICE, "octant launch failed");
+        }
     }
     cudaError_t e = cudaStreamSynchronize(op.stream);
-    dev_free(op, Kc, sizeof(c64) * 6 * PP);
+    dev_free(op, Kc, sizeof(c64) * PP);
     if (st != VIE_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "kernel spectrum build");
     return VIE_OK;
@@ -897,11 +944,11 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             VIE_CUDA(cudaGetLastError());
         } else {
             const FFTPlan& p = op.ax[2].plan;
-            const int NL = lines_per_cta<T>(p.L);
+            const TileCfg c = lines_cfg<T>(p);
             const long long nlines = (long long)ns * 3 * n0 * n1;
             tmr_begin(tid(TMR_ZFWD), op.stream);
-            k_zfwd<T><<<(unsigned)((nlines + NL - 1) / NL), 256, lines_smem<T>(p, NL), op.stream>>>(
-                w, wr, list, op.idx_map, A, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), NL);
+            k_zfwd<T><<<(unsigned)((nlines + c.w - 1) / c.w), 256, c.smem, op.stream>>>(
+                w, wr, list, op.idx_map, A, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), c.w, c.stw);
             tmr_end(tid(TMR_ZFWD), op.stream, ns * (vec + lineA) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
@@ -933,12 +980,12 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
         } else {
             const FFTPlan& p = op.ax[0].plan;
             const long long inner = (long long)P1 * P2;
-            const int TW = xfused_tile<T>(p.L, inner);
-            const long long grid = (long long)ns * ((inner + TW - 1) / TW);
+            const TileCfg c = xfused_cfg<T>(p, inner);
+            const long long grid = (long long)ns * ((inner + c.w - 1) / c.w);
             tmr_begin(tid(TMR_XFUSED), op.stream);
-            k_xfused<T><<<(unsigned)grid, 256, xfused_smem<T>(p, TW), op.stream>>>(
-                B, n0, inner, P0, P1, P2, kh, op.H[0], op.H[1], op.H[2], p, twp<T>(op.ax[0]), TW,
-                op.disc ? dtp<T>(op) : nullptr, op.dstride, (T)(op.k0 * op.k0));
+            k_xfused<T><<<(unsigned)grid, 256, c.smem, op.stream>>>(
+                B, n0, inner, P0, P1, P2, kh, op.H[0], op.H[1], op.H[2], p, twp<T>(op.ax[0]), c.w,
+                op.disc ? dtp<T>(op) : nullptr, op.dstride, (T)(op.k0 * op.k0), c.stw);
             tmr_end(tid(TMR_XFUSED), op.stream, 2.0 * ns * lineB + 6.0 * op.H[0] * op.H[1] * op.H[2] * E);
             count_launch();
             VIE_CUDA(cudaGetLastError());
@@ -966,12 +1013,12 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             VIE_CUDA(cudaGetLastError());
         } else {
             const FFTPlan& p = op.ax[2].plan;
-            const int NL = lines_per_cta<T>(p.L);
+            const TileCfg c = lines_cfg<T>(p);
             const long long nlines = (long long)ns * 3 * n0 * n1;
             tmr_begin(tid(TMR_ZINV), op.stream);
-            k_zinv<T><<<(unsigned)((nlines + NL - 1) / NL), 256, lines_smem<T>(p, NL), op.stream>>>(
-                A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), NL,
-                op.chi_cs);
+            k_zinv<T><<<(unsigned)((nlines + c.w - 1) / c.w), 256, c.smem, op.stream>>>(
+                A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), c.w,
+                op.chi_cs, c.stw);
             tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());

@@ -11,6 +11,8 @@ Workloads (sizes follow the paper's examples, Sec. III):
   * ``sphere_config1``  -- 16^3, h = 1/20, R = 0.4, eps_r = 2.25, two channels.
   * ``sphere_config2``  -- 64^3, h = 1/32, R = 1.0, eps_r = 4.0, 8 channels.
   * ``metasurface``     -- 256x256x32 PB-phase nanofin array (Sec. III-B, Eq. 32).
+  * ``metasurface_paper`` -- the same design at the paper's scale, 40 x 12 x 2
+    wavelengths at 62 cells per wavelength (2480 x 744 x 124 cells).
   * ``random_body``     -- random unions of ellipsoids / cuboids, eps_r in [1.5, 6].
 """
 from __future__ import annotations
@@ -146,6 +148,70 @@ def metasurface(seed: int = 0, n=(256, 256, 32), fins=(8, 8), eps_r: float = 5.8
             inside = (np.abs(u) <= lx) & (np.abs(v) <= ly) & (np.abs(Z) <= lz)
             eps[inside] = eps_r
     return grid, eps, angles
+
+
+# The paper-scale PB metasurface (Sec. III-B): unit cells of pitch 667 nm with
+# silicon nanofins (n = 3.44) of 486 x 219 x 830 nm at 1550 nm, simulated in a
+# 40 x 12 x 2 wavelength box at 62 cells per wavelength.
+META_FIN_PAPER = (486.0 / 1550.0, 219.0 / 1550.0, 830.0 / 1550.0)
+META_EPS_SI = 3.44 ** 2
+
+# Axis order of the paper-scale grid: grid axis a holds paper axis
+# PAPER_AXES[a] (height first, the 40-wavelength axis last).  Swapping x and z
+# is its own inverse; vectors map with ``to_grid_frame`` both ways.
+PAPER_AXES = (2, 1, 0)
+
+
+def to_grid_frame(v):
+    """Map vectors (..., 3) between the paper frame and the paper-scale grid frame."""
+    v = np.asarray(v)
+    return v[..., list(PAPER_AXES)]
+
+
+def metasurface_paper(cells_per_lambda: int = 62, box=(40.0, 12.0, 2.0), eps_r: float = META_EPS_SI,
+                      theta0: float = 0.0):
+    """Free-standing PB-phase silicon nanofin array filling a ``box`` (paper
+    x, y, z in wavelengths) at ``cells_per_lambda``.
+
+    Column m of fins (along the paper x axis) is rotated in-plane by
+    theta0 + 0.5 k0 sin(10 deg) m p (Eq. 32); fins are centred in their p x p
+    cells and in the box height; a voxel belongs to a fin when its centre does.
+    The array is returned in the grid frame (axes ordered by ``PAPER_AXES``:
+    shape (n_z, n_y, n_x)).  Returns ``(Grid, eps_r, info)`` with the fin
+    counts and angles in ``info``."""
+    h = 1.0 / cells_per_lambda
+    n_p = tuple(int(round(b * cells_per_lambda)) for b in box)  # paper x, y, z
+    n_g = tuple(n_p[a] for a in PAPER_AXES)
+    eps = np.ones(n_g, dtype=np.float64)
+    p = META_PITCH
+    mx, my = int(box[0] // p), int(box[1] // p)
+    l, d, hf = META_FIN_PAPER
+    step = math.radians(pb_rotation_increment_deg())
+    ax = [(np.arange(n_p[a]) - 0.5 * (n_p[a] - 1)) * h for a in range(3)]
+    zsel = np.flatnonzero(np.abs(ax[2]) <= 0.5 * hf)
+    z0, z1 = int(zsel[0]), int(zsel[-1]) + 1
+    reach = 0.5 * math.hypot(l, d) + h
+    angles = np.zeros((mx, my))
+    for m in range(mx):
+        th = theta0 + step * m
+        c, s = math.cos(th), math.sin(th)
+        cx = (m + 0.5 - 0.5 * mx) * p
+        for q in range(my):
+            angles[m, q] = th
+            cy = (q + 0.5 - 0.5 * my) * p
+            i0 = max(0, int(math.floor((cx - reach) / h + 0.5 * (n_p[0] - 1))))
+            i1 = min(n_p[0], int(math.ceil((cx + reach) / h + 0.5 * (n_p[0] - 1))) + 1)
+            j0 = max(0, int(math.floor((cy - reach) / h + 0.5 * (n_p[1] - 1))))
+            j1 = min(n_p[1], int(math.ceil((cy + reach) / h + 0.5 * (n_p[1] - 1))) + 1)
+            dx = ax[0][i0:i1, None] - cx
+            dy = ax[1][None, j0:j1] - cy
+            u = c * dx + s * dy
+            v = -s * dx + c * dy
+            inside = (np.abs(u) <= 0.5 * l) & (np.abs(v) <= 0.5 * d)  # [x][y]
+            sub = eps[z0:z1, j0:j1, i0:i1]  # grid frame: [z][y][x]
+            sub[:, inside.T] = eps_r
+    info = {"fins": (mx, my), "angles": angles, "n_paper": n_p, "z_cells": z1 - z0}
+    return Grid(n_g, h), eps, info
 
 
 # --------------------------------------------------------------------------- #

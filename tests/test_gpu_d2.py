@@ -42,6 +42,28 @@ def test_d2_operator_matches_oracle(vielib, n):
     assert np.abs(y32 - ref).max() <= 2e-5 * s
 
 
+def test_d2_operator_long_axis(vielib):
+    """D2 with a padded z length of 4410 (generic line kernels, twiddles from
+    global memory), against the oracle's FFT form of the D2 operator."""
+    n = (3, 4, 2200)
+    rng = np.random.default_rng(5)
+    h = 0.02
+    eps = np.where(rng.uniform(size=n) < 0.5, rng.uniform(1.5, 5.0, n), 1.0)
+    eps[0] = 1.0
+    chi = ovie.contrast(eps)
+    S = _support(chi)
+    w = (rng.standard_normal((2, 3) + n) + 1j * rng.standard_normal((2, 3) + n)) * S
+    op = od2.FFTOperator(n, h, K0, chi, workers=-1)
+    ref = np.stack([op(w[r]) for r in range(2)])
+    with vielib.Handle(n, h, eps, K0, disc=vielib.DISC_D2) as hd:
+        assert hd.info()["P"][2] > 4096
+        y64 = hd.apply(w, precision=vielib.PREC_FP64)
+        y32 = hd.apply(w, precision=vielib.PREC_MIXED)
+    s = np.abs(ref).max()
+    assert np.abs(y64 - ref).max() <= 1e-11 * s
+    assert np.abs(y32 - ref).max() <= 2e-5 * s
+
+
 def test_d2_sphere_solve_matches_oracle(vielib):
     N, R = 16, 0.3
     h = 2 * R / N

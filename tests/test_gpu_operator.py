@@ -20,16 +20,22 @@ TOL64 = 1e-11
 TOL32 = 2e-5
 
 
-@pytest.mark.parametrize("L", [1, 2, 3, 7, 16, 32, 75, 96, 125, 128, 192, 256, 343, 512, 1024])
+@pytest.mark.parametrize("L", [1, 2, 3, 7, 16, 32, 75, 96, 125, 128, 192, 256, 343, 512, 1024, 1500, 4096, 5000,
+                               6561, 8192])
 def test_fft_lines_vs_numpy(vielib, L):
     rng = np.random.default_rng(L)
     x = rng.standard_normal((5, L)) + 1j * rng.standard_normal((5, L))
     ref = np.fft.fft(x, axis=1)
     refi = np.fft.ifft(x, axis=1) * L
     s = np.abs(ref).max()
+    assert np.abs(vielib.fft_lines(x, precision=vielib.PREC_MIXED) - ref).max() <= 2e-6 * s * max(1, math.log2(L))
+    if L > 6400:
+        # two FP64 line buffers of L points exceed the shared memory of one CTA
+        with pytest.raises(vielib.VieError):
+            vielib.fft_lines(x, precision=vielib.PREC_FP64)
+        return
     assert np.abs(vielib.fft_lines(x, precision=vielib.PREC_FP64) - ref).max() <= 1e-13 * s * max(1, math.log2(L))
     assert np.abs(vielib.fft_lines(x, inverse=True, precision=vielib.PREC_FP64) - refi).max() <= 1e-13 * s * max(1, math.log2(L))
-    assert np.abs(vielib.fft_lines(x, precision=vielib.PREC_MIXED) - ref).max() <= 2e-6 * s * max(1, math.log2(L))
 
 
 def _case_random(n, seed, fill=0.6):
@@ -163,3 +169,35 @@ def test_autotune_keeps_the_operator(vielib):
     s = np.abs(y64).max()
     assert np.abs(z64 - y64).max() <= 1e-11 * s
     assert np.abs(z32 - y64).max() <= 2e-5 * s
+
+
+@pytest.mark.parametrize("n", [(3, 4, 2500), (3, 700, 4), (2, 620, 30)])
+def test_apply_long_padded_axes(vielib, n):
+    """Padded lengths beyond 1024 (5000 on z, 1400 and 1250 on y): one line or
+    four columns per CTA with the twiddles read from global memory, against the
+    oracle's FFT operator (itself pinned to the direct sum)."""
+    rng = np.random.default_rng(sum(n))
+    eps = 1.0 + rng.uniform(0.3, 3.0, n) * (rng.uniform(size=n) < 0.5)
+    h = 0.02
+    g = inputs.Grid(n, h)
+    w = inputs.random_field(g, 2, 4, eps > 1.0)
+    op = ovie.FFTOperator(n, h, K0, ovie.contrast(eps), workers=-1)
+    ref = np.stack([op(w[r]) for r in range(2)])
+    with vielib.Handle(n, h, eps, K0) as hd:
+        assert max(hd.info()["P"]) > 1024
+        y64 = hd.apply(w, precision=vielib.PREC_FP64)
+        y32 = hd.apply(w, precision=vielib.PREC_MIXED)
+    s = np.abs(ref).max()
+    assert np.abs(y64 - ref).max() <= TOL64 * s
+    assert np.abs(y32 - ref).max() <= TOL32 * s
+
+
+def test_first_axis_too_long_is_rejected(vielib):
+    """The fused x pass keeps three components of a column in shared memory,
+    which bounds the first padded length (about 3200 at FP64): set-up refuses
+    a longer first axis before any kernel runs."""
+    n = (2000, 2, 2)
+    eps = np.full(n, 2.0)
+    with pytest.raises(vielib.VieError) as e:
+        vielib.Handle(n, 0.02, eps, K0)
+    assert "first axis" in str(e.value)
