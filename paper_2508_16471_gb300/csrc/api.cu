@@ -73,7 +73,7 @@ static int check_grid(const vie_grid* g) {
     if (!g) return fail(VIE_EINVAL, "grid is NULL");
     long long N = 1;
     for (int a = 0; a < 3; ++a) {
-        if (g->n[a] < 1 || g->n[a] > 512) return fail(VIE_EINVAL, "grid size per axis must be in 1..512");
+        if (g->n[a] < 1 || g->n[a] > 4096) return fail(VIE_EINVAL, "grid size per axis must be in 1..4096");
         N *= g->n[a];
     }
     if (N > (1LL << 28)) return fail(VIE_EINVAL, "grid has more than 2^28 voxels");

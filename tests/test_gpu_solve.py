@@ -301,15 +301,17 @@ def test_finite_aperture_detectors(vielib, config1):
 
 
 def test_grid_beyond_the_fft_engine_is_rejected(vielib):
-    """Axes whose padded length would exceed the FFT engine's 1024 points
-    (n > 512 with the default rule) are refused at set-up with VIE_EINVAL, and
-    the largest accepted axis (512 voxels on a thin slab) sets up."""
-    eps = np.ones((2, 2, 520))
-    eps[1, 1, 5] = 2.0
-    with pytest.raises(vielib.VieError) as e:
-        vielib.Handle(eps.shape, 0.01, eps, K0)
-    assert e.value.code == vielib.VIE_EINVAL
-    eps = np.ones((2, 2, 512))
+    """Axes beyond 4096 voxels (padded length over the FFT engine's 8192) and a
+    last axis whose FP64 line buffers exceed shared memory (padded length over
+    6400) are refused at set-up with VIE_EINVAL; a thin slab with a 3200-voxel
+    last axis (padded 6400) sets up."""
+    for nz in (4100, 3300):
+        eps = np.ones((2, 2, nz))
+        eps[1, 1, 5] = 2.0
+        with pytest.raises(vielib.VieError) as e:
+            vielib.Handle(eps.shape, 0.01, eps, K0)
+        assert e.value.code == vielib.VIE_EINVAL
+    eps = np.ones((2, 2, 3200))
     eps[1, 1, 5] = 2.0
     with vielib.Handle(eps.shape, 0.01, eps, K0) as hd:
-        assert max(hd.info()["P"]) == 1024
+        assert max(hd.info()["P"]) == 6400
