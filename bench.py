@@ -74,6 +74,10 @@ def parse():
                    help="with --apply-only: apply the FP64 operator instead of the FP32 one")
     p.add_argument("--workload", default="bodies128", choices=["bodies128", "metasurface-paper"],
                    help="metasurface-paper: one solve of the paper-scale PB metasurface (its own JSON line)")
+    p.add_argument("--box", type=float, nargs=3, default=(40.0, 12.0, 2.0),
+                   help="metasurface-paper: box in wavelengths (paper x, y, z)")
+    p.add_argument("--solver", default="gmres", choices=["gmres", "bicgstab", "cocr"],
+                   help="metasurface-paper: inner Krylov solver")
     p.add_argument("--profile-solve", type=int, default=0,
                    help="profiling aid: a 12-iteration solve with this many RHS on the first bench body, then exit")
     return p.parse_args()
@@ -498,8 +502,9 @@ def run_metasurface_paper(args):
     V.load()
     log = lambda *a: print(*a, file=sys.stderr, flush=True)  # noqa: E731
     t0 = time.perf_counter()
-    g, eps, info = inputs.metasurface_paper()
+    g, eps, info = inputs.metasurface_paper(box=tuple(args.box))
     t_gen = time.perf_counter() - t0
+    solver = {"gmres": V.SOLVER_GMRES, "bicgstab": V.SOLVER_BICGSTAB, "cocr": V.SOLVER_COCR}[args.solver]
     chs_p = [(c.khat, c.pol) for c in inputs.channels_metasurface([0.0])]  # L, R along +z
     chs = [(inputs.to_grid_frame(k), inputs.to_grid_frame(p)) for k, p in chs_p]
     torch.cuda.synchronize()
@@ -554,7 +559,7 @@ def run_metasurface_paper(args):
     t0 = time.perf_counter()
     st = hd.solve(chs, tol=1e-6, restart=args.restart, precision=V.PREC_MIXED, max_iter=args.max_iter,
                   inner_tol=args.inner_tol, reorth_eta=args.reorth_eta, inner_floor=args.inner_floor,
-                  allow_noconv=True)
+                  solver=solver, allow_noconv=True)
     e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -598,15 +603,17 @@ def run_metasurface_paper(args):
     peaks_deg = {f"{cin}_in_{cout}_out": float(deg[int(np.argmax(np.abs(circ[r, :, c]) ** 2))])
                  for r, cin in enumerate("LR") for c, cout in enumerate("LR")}
     line = {
-        "metric": "paper-scale PB metasurface: mixed-precision GMRES solve to FP64 residual 1e-6 "
-                  "(2480x744x124 cells, 2 RHS)",
+        "metric": f"PB metasurface ({args.solver}): mixed-precision solve to FP64 residual 1e-6 "
+                  f"({info['n_paper'][0]}x{info['n_paper'][1]}x{info['n_paper'][2]} cells, 2 RHS)",
         "value": solve_s, "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f32+f64",
         "data": "synthetic (Sec. III-B design rule, Eq. 32)",
-        "config": {"workload": f"PB metasurface 40x12x2 lambda at 62 cells/lambda, {info['fins'][0]}x"
+        "config": {"workload": f"PB metasurface {args.box[0]:g}x{args.box[1]:g}x{args.box[2]:g} lambda at 62 "
+                               f"cells/lambda, {info['fins'][0]}x"
                                f"{info['fins'][1]} Si fins (eps_r {inputs.META_EPS_SI:.3f}), no substrate",
                    "grid": list(g.n), "padded": list(inf["P"]), "body_voxels": Nb, "unknowns": 3 * Nb,
-                   "rhs": "normal incidence, L and R", "solver": f"GMRES({args.restart}) FP32 matvec + FP64 "
-                                                               "refinement", "max_iter": args.max_iter},
+                   "rhs": "normal incidence, L and R",
+                   "solver": (f"GMRES({args.restart})" if args.solver == "gmres" else args.solver.upper()) +
+                             " FP32 matvec + FP64 refinement", "max_iter": args.max_iter},
         "converged": int(st["converged"]), "iters": st["iters"].tolist(), "relres": st["relres"].tolist(),
         "outer_max": int(st["outer_max"]), "matvecs32": int(st["matvecs32"]), "matvecs64": int(st["matvecs64"]),
         "seconds_per_rhs": solve_s / 2.0, "wall_s": wall, "setup_s": t_setup, "generate_s": t_gen,

@@ -58,6 +58,11 @@ extern "C" {
 /* ---- Krylov solvers (vie_solve_opts.solver) ----------------------------- */
 #define VIE_SOLVER_GMRES    0 /* batched restarted GMRES(m), CGS + selective reorth.  */
 #define VIE_SOLVER_BICGSTAB 1 /* batched BiCGStab (van der Vorst), the paper's solver */
+#define VIE_SOLVER_COCR     2 /* batched COCR (conjugate orthogonal conjugate residual,
+                                 Sogabe-Zhang): A = I - diag(chi) K is symmetric in
+                                 the bilinear form sum x y / chi because K is
+                                 (reciprocity), so a short recurrence with one
+                                 operator application per step and no restart applies */
 
 /* ---- far-field component bases (vie_farfield*) -------------------------- */
 #define VIE_BASIS_CART 0 /* (F_x, F_y, F_z)                                      */
@@ -85,7 +90,7 @@ typedef struct vie_solve_opts {
     int max_iter;      /* cap on inner iterations per RHS (default 5000)         */
     int precision;     /* VIE_PREC_MIXED (default) or VIE_PREC_FP64              */
     double inner_tol;  /* mixed mode: relative reduction asked of each FP32 inner
-                          solve, floored at 0.3 tol ||b|| (default 1e-6)          */
+                          solve, floored at inner_floor tol ||b|| (default 1e-6)  */
     int use_x0;        /* 0: x0 = 0; 1: start from the currents stored in the
                           handle (same n_rhs, restart and precision as the previous
                           solve); 2: initial currents from the network attached
@@ -97,10 +102,12 @@ typedef struct vie_solve_opts {
                           replaced by zero.                                       */
     int precond;       /* 0: GMRES; 1: FGMRES with the learned right preconditioner
                           attached by vie_attach_precond (mixed or FP64 basis)   */
-    int solver;        /* VIE_SOLVER_GMRES (default) or VIE_SOLVER_BICGSTAB: the
-                          paper's solver (Sec. II-C) inside the same FP64
-                          refinement; needs restart >= 8 (its 7 vectors use the
-                          basis storage), use_x0 0 or 1, precond 0             */
+    int solver;        /* VIE_SOLVER_GMRES (default), VIE_SOLVER_BICGSTAB (the
+                          paper's solver, Sec. II-C) or VIE_SOLVER_COCR, inside
+                          the same FP64 refinement.  BiCGStab needs restart >= 8
+                          (its 7 vectors use the basis storage), COCR restart >= 4
+                          (5 vectors; restart has no other meaning for either);
+                          both need use_x0 0 or 1 and precond 0                */
     int reserved[1];
     double reorth_eta; /* GMRES: a second classical Gram-Schmidt pass runs for an
                           RHS when the first left ||w'||^2 < reorth_eta ||w||^2

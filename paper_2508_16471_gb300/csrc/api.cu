@@ -262,10 +262,12 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
     if (o.precond != 0 && o.precond != 1) return fail(VIE_EINVAL, "precond must be 0 or 1");
     if (!(o.reorth_eta >= 0) || !std::isfinite(o.reorth_eta)) return fail(VIE_EINVAL, "reorth_eta must be >= 0");
     if (!(o.inner_floor > 0) || !(o.inner_floor <= 1)) return fail(VIE_EINVAL, "inner_floor must be in (0, 1]");
-    if (o.solver != VIE_SOLVER_GMRES && o.solver != VIE_SOLVER_BICGSTAB)
-        return fail(VIE_EINVAL, "solver must be VIE_SOLVER_GMRES or VIE_SOLVER_BICGSTAB");
+    if (o.solver != VIE_SOLVER_GMRES && o.solver != VIE_SOLVER_BICGSTAB && o.solver != VIE_SOLVER_COCR)
+        return fail(VIE_EINVAL, "solver must be VIE_SOLVER_GMRES, VIE_SOLVER_BICGSTAB or VIE_SOLVER_COCR");
     if (o.solver == VIE_SOLVER_BICGSTAB && (o.restart < 8 || o.precond || o.use_x0 == 2))
         return fail(VIE_EINVAL, "BiCGStab needs restart >= 8, precond 0 and use_x0 0 or 1");
+    if (o.solver == VIE_SOLVER_COCR && (o.restart < 4 || o.precond || o.use_x0 == 2))
+        return fail(VIE_EINVAL, "COCR needs restart >= 4, precond 0 and use_x0 0 or 1");
     if (o.precond == 1 && !hd->pctx.net)
         return fail(VIE_ESTATE, "precond = 1 needs a network attached with vie_attach_precond");
     VIE_CUDA(cudaSetDevice(hd->device));

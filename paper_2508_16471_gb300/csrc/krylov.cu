@@ -1331,6 +1331,317 @@ static int bicgstab_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveRes
     return VIE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// COCR (conjugate orthogonal conjugate residual) for the complex-symmetric
+// structure of the VIE.  The Green's tensor convolution K is symmetric
+// (K_ab(m) = K_ba(m) = K_ab(-m), reciprocity), so A = I - diag(chi) K
+// satisfies [Ax, y] = [x, Ay] in the bilinear form [x, y] = sum x_i y_i / chi_i
+// (no conjugation; terms with chi_i = 0 are dropped: such unknowns stay zero).
+// COCR is the conjugate-residual recurrence in that form: one operator
+// application per step, five vectors, no restart.  It runs as the inner solver
+// of the same FP64 refinement as GMRES and BiCGStab.  Vector slots of V:
+// 0 r, 1 p, 2 Ar, 3 Ap, 4 d (the correction); per-RHS scalars in coef.
+// ---------------------------------------------------------------------------
+enum { CO_R = 0, CO_P, CO_AR, CO_AP, CO_D, CO_NV };
+enum { CS_RHO = 0, CS_SIGMA, CS_ALPHA, CS_RHON, CS_BETA, CS_RR, CS_N };
+
+// partial[(r*ps + q)*nblk + b]: block sums of mode-q products of V_a[q], V_b[q]:
+// mode 0 Hermitian conj(x).y, mode 1 the chi-weighted bilinear x.y / chi
+template <typename T>
+__global__ void k_co_dots(const cplx<T>* __restrict__ V, long long vrs, long long n, long long Nb,
+                          const T* __restrict__ chi, long long chi_cs, const int* __restrict__ list, int np,
+                          int a0, int b0, int m0, int a1, int b1, int m1, c64* __restrict__ partial, int ps,
+                          int nblk) {
+    __shared__ double sre[2][KB / 32], sim[2][KB / 32];
+    const int r = list[blockIdx.y];
+    const cplx<T>* Vr = V + r * vrs;
+    const int av[2] = {a0, a1}, bv[2] = {b0, b1}, mv[2] = {m0, m1};
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = 0; q < np; ++q) {
+        const cplx<T>* x = Vr + (long long)av[q] * n;
+        const cplx<T>* y = Vr + (long long)bv[q] * n;
+        T ar = 0, ai = 0;
+#pragma unroll
+        for (int k = 0; k < KE; ++k) {
+            const long long e = e0 + k * KB;
+            if (e < n) {
+                const cplx<T> u = x[e], w = y[e];
+                if (mv[q] == 0) {
+                    ar += u.x * w.x + u.y * w.y;
+                    ai += u.x * w.y - u.y * w.x;
+                } else {
+                    const long long c = e / Nb, v = e - c * Nb;
+                    const T ch = chi[c * chi_cs + v];
+                    const T mu = ch > (T)0 ? (T)1 / ch : (T)0;
+                    ar += mu * (u.x * w.x - u.y * w.y);
+                    ai += mu * (u.x * w.y + u.y * w.x);
+                }
+            }
+        }
+        const double dr = warp_sum_comp(ar), di = warp_sum_comp(ai);
+        if (lane == 0) {
+            sre[q][wid] = dr;
+            sim[q][wid] = di;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < np) {
+        double tr = 0, ti = 0;
+        for (int w = 0; w < KB / 32; ++w) {
+            tr += sre[threadIdx.x][w];
+            ti += sim[threadIdx.x][w];
+        }
+        partial[((long long)r * ps + threadIdx.x) * nblk + blockIdx.x] = c64{tr, ti};
+    }
+}
+
+// stage 0: alpha = rho / sigma; stage 1: beta = rho_new / rho, rho = rho_new;
+// stage 2 (start of an inner solve): rho = rho_new, beta = 0.  A vanishing
+// denominator stops the RHS (flag 2) with the step's scalar zeroed.
+__global__ void k_co_scalars(c64* __restrict__ coef, int cs, const int* __restrict__ list, int nr, int stage,
+                             int* __restrict__ flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    const int r = list[i];
+    c64* c = coef + (long long)r * cs;
+    if (stage == 0) {
+        if (tiny(c[CS_SIGMA])) {
+            c[CS_ALPHA] = c64{0, 0};
+            flag[r] = 2;
+        } else {
+            c[CS_ALPHA] = cdiv(c[CS_RHO], c[CS_SIGMA]);
+        }
+    } else if (stage == 1) {
+        if (tiny(c[CS_RHO])) {
+            c[CS_BETA] = c64{0, 0};
+            flag[r] = 2;
+        } else {
+            c[CS_BETA] = cdiv(c[CS_RHON], c[CS_RHO]);
+        }
+        c[CS_RHO] = c[CS_RHON];
+    } else {
+        c[CS_RHO] = c[CS_RHON];
+        c[CS_BETA] = c64{0, 0};
+    }
+}
+
+// stage 0: d += alpha p, r -= alpha Ap;  stage 1: p = r + beta p, Ap = Ar + beta Ap
+template <typename T>
+__global__ void k_co_update(cplx<T>* __restrict__ V, long long vrs, long long n, const int* __restrict__ list,
+                            const c64* __restrict__ coef, int cs, int stage) {
+    const int r = list[blockIdx.y];
+    cplx<T>* Vr = V + r * vrs;
+    const c64* c = coef + (long long)r * cs;
+    const cplx<T> alpha = {(T)c[CS_ALPHA].x, (T)c[CS_ALPHA].y};
+    const cplx<T> beta = {(T)c[CS_BETA].x, (T)c[CS_BETA].y};
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e >= n) continue;
+        if (stage == 0) {
+            const cplx<T> pp = Vr[CO_P * n + e], ap = Vr[CO_AP * n + e];
+            Vr[CO_D * n + e] = Vr[CO_D * n + e] + alpha * pp;
+            Vr[CO_R * n + e] = Vr[CO_R * n + e] - alpha * ap;
+        } else {
+            Vr[CO_P * n + e] = Vr[CO_R * n + e] + beta * Vr[CO_P * n + e];
+            Vr[CO_AP * n + e] = Vr[CO_AR * n + e] + beta * Vr[CO_AP * n + e];
+        }
+    }
+}
+
+// start of an inner solve: r = (T) res, p = Ap = d = 0
+template <typename T>
+__global__ void k_co_start(const c64* __restrict__ res, long long rs, cplx<T>* __restrict__ V, long long vrs,
+                           const int* __restrict__ list, long long n) {
+    const int r = list[blockIdx.y];
+    cplx<T>* Vr = V + r * vrs;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+    const cplx<T> z = {(T)0, (T)0};
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e >= n) continue;
+        const c64 v = res[r * rs + e];
+        Vr[CO_R * n + e] = cplx<T>{(T)v.x, (T)v.y};
+        Vr[CO_P * n + e] = z;
+        Vr[CO_AP * n + e] = z;
+        Vr[CO_D * n + e] = z;
+    }
+}
+
+// x += (double) d
+template <typename T>
+__global__ void k_co_xupdate(c64* __restrict__ x, long long xs, const cplx<T>* __restrict__ V, long long vrs,
+                             const int* __restrict__ list, long long n) {
+    const int r = list[blockIdx.y];
+    const cplx<T>* d = V + r * vrs + CO_D * n;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e >= n) continue;
+        const c64 xv = x[r * xs + e];
+        x[r * xs + e] = c64{xv.x + (double)d[e].x, xv.y + (double)d[e].y};
+    }
+}
+
+template <typename T>
+static int cocr_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult& out) {
+    const long long n = S.n3;
+    const int R = S.R, m = S.m, nblk = S.nblk;
+    const int cs = m + 2;
+    const int ps = m + 2;
+    if (m + 1 < CO_NV || cs < CS_N) return fail(VIE_EINVAL, "COCR needs restart >= 4 (vector slots)");
+    const long long vrs = n * (m + 1);
+    cplx<T>* V = (cplx<T>*)S.V;
+    const T* chi;
+    if constexpr (sizeof(T) == 8) chi = (const T*)op.chi64;
+    else chi = (const T*)op.chi32;
+    cudaStream_t st = op.stream;
+    const int prec_in = sizeof(T) == 8 ? VIE_PREC_FP64 : VIE_PREC_MIXED;
+    const double ET = sizeof(cplx<T>);
+
+    std::vector<int> all(R), it(R, 0), outer(R, 0), done(R, 0), hflag(R);
+    for (int r = 0; r < R; ++r) all[r] = r;
+    std::vector<double> hb(R), hr(R), htarget(R);
+    VIE_TRY(op_set_list(op, all.data(), R));
+    k_residual<<<dim3(nblk, R), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 1);
+    LAUNCH_CHECK();
+    k_norm_finish<<<ceil_div(R, 128), 128, 0, st>>>(S.normpart, nblk, S.bnorm, op.d_list, R);
+    LAUNCH_CHECK();
+    VIE_CUDA(cudaMemcpyAsync(hb.data(), S.bnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; ++r)
+        if (!(hb[r] > 0) || !std::isfinite(hb[r])) return fail(VIE_EINVAL, "right-hand side is zero or not finite");
+    out.matvecs32 = out.matvecs64 = 0;
+    out.guesses_rejected = 0;
+    bool first = !o.use_x0;
+    auto dots = [&](int ni, int np, int a0, int b0, int m0, int a1, int b1, int m1, int s0, int s1) -> int {
+        tmr_begin(TMR_DOTS, st);
+        k_co_dots<T><<<dim3(nblk, ni), KB, 0, st>>>(V, vrs, n, op.Nb, chi, op.chi_cs, op.d_list, np, a0, b0, m0,
+                                                     a1, b1, m1, S.partial, ps, nblk);
+        tmr_end(TMR_DOTS, st, (double)ni * np * 2.0 * n * ET);
+        LAUNCH_CHECK();
+        tmr_begin(TMR_REDUCE, st);
+        k_bi_reduce<<<dim3(np, ni), KB, 0, st>>>(S.partial, ps, nblk, S.coef, cs, op.d_list, s0, s1, 0);
+        tmr_end(TMR_REDUCE, st, (double)ni * np * nblk * 16.0);
+        LAUNCH_CHECK();
+        return VIE_OK;
+    };
+    auto matvec = [&](int ni) -> int {
+        VIE_TRY(op_apply(op, prec_in, V + CO_R * n, vrs, V + CO_AR * n, vrs, op.d_list, ni));
+        if (prec_in == VIE_PREC_FP64) out.matvecs64 += ni;
+        else out.matvecs32 += ni;
+        return VIE_OK;
+    };
+    auto update = [&](int ni, int stage) -> int {
+        tmr_begin(TMR_UPDATE, st);
+        k_co_update<T><<<dim3(nblk, ni), KB, 0, st>>>(V, vrs, n, op.d_list, S.coef, cs, stage);
+        tmr_end(TMR_UPDATE, st, 6.0 * ni * n * ET);
+        LAUNCH_CHECK();
+        return VIE_OK;
+    };
+    auto scalars = [&](int ni, int stage) -> int {
+        k_co_scalars<<<ceil_div(ni, 64), 64, 0, st>>>(S.coef, cs, op.d_list, ni, stage, S.flag);
+        LAUNCH_CHECK();
+        return VIE_OK;
+    };
+    while (true) {
+        std::vector<int> act;
+        for (int r = 0; r < R; ++r)
+            if (!done[r]) act.push_back(r);
+        if (act.empty()) break;
+        const int na = (int)act.size();
+        VIE_TRY(op_set_list(op, act.data(), na));
+        if (first) {
+            k_residual<<<dim3(nblk, na), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 1);
+        } else {
+            VIE_TRY(op_apply(op, VIE_PREC_FP64, S.x, n, S.res, n, op.d_list, na));
+            out.matvecs64 += na;
+            k_residual<<<dim3(nblk, na), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 0);
+        }
+        LAUNCH_CHECK();
+        first = false;
+        k_norm_finish<<<ceil_div(na, 128), 128, 0, st>>>(S.normpart, nblk, S.rnorm, op.d_list, na);
+        LAUNCH_CHECK();
+        VIE_CUDA(cudaMemcpyAsync(hr.data(), S.rnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        VIE_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> cyc;
+        for (int r : act) {
+            const double rel = hr[r] / hb[r];
+            out.relres[r] = rel;
+            if (rel <= o.tol || !std::isfinite(rel)) done[r] = 1;
+            else if (it[r] >= o.max_iter) done[r] = 2;
+            else cyc.push_back(r);
+        }
+        if (cyc.empty()) break;
+        for (int r : cyc) {
+            outer[r]++;
+            double t = 0.99 * o.tol * hb[r];
+            if (prec_in == VIE_PREC_MIXED) t = std::max(o.inner_tol * hr[r], o.inner_floor * o.tol * hb[r]);
+            htarget[r] = t;
+        }
+        VIE_CUDA(cudaMemcpyAsync(S.target, htarget.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+        VIE_CUDA(cudaMemsetAsync(S.flag, 0, sizeof(int) * R, st));
+        const int nc = (int)cyc.size();
+        VIE_TRY(op_set_list(op, cyc.data(), nc));
+        // r = res, d = p = Ap = 0; Ar = A r; rho = [r, Ar]; p = r, Ap = Ar
+        k_co_start<T><<<dim3(nblk, nc), KB, 0, st>>>(S.res, n, V, vrs, op.d_list, n);
+        LAUNCH_CHECK();
+        VIE_TRY(matvec(nc));
+        VIE_TRY(dots(nc, 1, CO_R, CO_AR, 1, 0, 0, 0, CS_RHON, 0));
+        VIE_TRY(scalars(nc, 2));
+        VIE_TRY(update(nc, 1));
+        std::vector<int> inner = cyc;
+        while (!inner.empty()) {
+            const int ni = (int)inner.size();
+            VIE_TRY(op_set_list(op, inner.data(), ni));
+            // alpha = rho / [Ap, Ap]; d += alpha p; r -= alpha Ap; ||r|| against the target
+            VIE_TRY(dots(ni, 1, CO_AP, CO_AP, 1, 0, 0, 0, CS_SIGMA, 0));
+            VIE_TRY(scalars(ni, 0));
+            VIE_TRY(update(ni, 0));
+            VIE_TRY(dots(ni, 1, CO_R, CO_R, 0, 0, 0, 0, CS_RR, 0));
+            k_bi_check<<<ceil_div(ni, 64), 64, 0, st>>>(S.coef, cs, S.target, op.d_list, ni, CS_RR, S.flag);
+            LAUNCH_CHECK();
+            VIE_CUDA(cudaMemcpyAsync(hflag.data(), S.flag, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+            VIE_CUDA(cudaStreamSynchronize(st));
+            std::vector<int> nxt;
+            for (int r : inner) {
+                it[r]++;
+                if (!hflag[r] && it[r] < o.max_iter) nxt.push_back(r);
+            }
+            inner.swap(nxt);
+            if (inner.empty()) break;
+            // Ar = A r; beta = [r, Ar] / rho; p = r + beta p; Ap = Ar + beta Ap
+            const int nn = (int)inner.size();
+            VIE_TRY(op_set_list(op, inner.data(), nn));
+            VIE_TRY(matvec(nn));
+            VIE_TRY(dots(nn, 1, CO_R, CO_AR, 1, 0, 0, 0, CS_RHON, 0));
+            VIE_TRY(scalars(nn, 1));
+            VIE_TRY(update(nn, 1));
+        }
+        VIE_TRY(op_set_list(op, cyc.data(), nc));
+        tmr_begin(TMR_XUPDATE, st);
+        k_co_xupdate<T><<<dim3(nblk, nc), KB, 0, st>>>(S.x, n, V, vrs, op.d_list, n);
+        tmr_end(TMR_XUPDATE, st, (double)nc * n * (ET + 32.0));
+        LAUNCH_CHECK();
+    }
+    out.converged = 0;
+    out.iters_max = 0;
+    out.outer_max = 0;
+    out.relres_max = 0;
+    for (int r = 0; r < R; ++r) {
+        out.iters[r] = it[r];
+        out.converged += done[r] == 1;
+        out.iters_max = std::max(out.iters_max, it[r]);
+        out.outer_max = std::max(out.outer_max, outer[r]);
+        out.relres_max = std::max(out.relres_max, out.relres[r]);
+    }
+    return VIE_OK;
+}
+
 int solver_run(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult& out) {
     out.iters.assign(S.R, 0);
     out.relres.assign(S.R, 0.0);
@@ -1338,6 +1649,10 @@ int solver_run(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult& ou
     if (o.solver == VIE_SOLVER_BICGSTAB) {
         if (S.prec == VIE_PREC_FP64) return bicgstab_t<double>(op, S, o, out);
         return bicgstab_t<float>(op, S, o, out);
+    }
+    if (o.solver == VIE_SOLVER_COCR) {
+        if (S.prec == VIE_PREC_FP64) return cocr_t<double>(op, S, o, out);
+        return cocr_t<float>(op, S, o, out);
     }
     if (S.prec == VIE_PREC_FP64) return gmres_t<double>(op, S, o, out);
     return gmres_t<float>(op, S, o, out);

@@ -18,7 +18,7 @@ VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_ENOCONV = 0, -1, -2, -3
 VIE_ETIMEOUT, VIE_EUNDEF, VIE_EDEVICE, VIE_ESTATE = -4, -5, -6, -7
 PREC_MIXED, PREC_FP64 = 0, 1
 BASIS_CART, BASIS_SPH, BASIS_CIRC = 0, 1, 2
-SOLVER_GMRES, SOLVER_BICGSTAB = 0, 1
+SOLVER_GMRES, SOLVER_BICGSTAB, SOLVER_COCR = 0, 1, 2
 DISC_D1, DISC_D2 = 0, 1
 
 EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device", "vie_solve",

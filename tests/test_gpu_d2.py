@@ -81,7 +81,12 @@ def test_d2_sphere_solve_matches_oracle(vielib):
         W = np.stack([hd.get_current(r) for r in range(2)])
         Fd = hd.farfield_dirs(dirs)
         Fg = hd.farfield(th, ph).reshape(2, -1, 3)
+        # COCR on the face unknowns (weights 1/chi_f; faces with chi_f = 0 stay zero)
+        st = hd.solve(chs, tol=1e-10, restart=4, solver=vielib.SOLVER_COCR)
+        assert st["converged"] == 2
+        Wc = np.stack([hd.get_current(r) for r in range(2)])
     assert np.abs(W - W_or).max() <= 1e-8 * np.abs(W_or).max()
+    assert np.abs(Wc - W_or).max() <= 1e-8 * np.abs(W_or).max()
     F_or = np.stack([od2.farfield(W_or[j], g.n, h, K0, dirs) for j in range(2)])
     assert np.linalg.norm(Fd - F_or) <= 1e-8 * np.linalg.norm(F_or)
     assert np.linalg.norm(Fg - F_or) <= 1e-5 * np.linalg.norm(F_or)

@@ -69,6 +69,30 @@ def test_bicgstab_config1_currents(vielib, config1, prec):
     assert _maxrel(w, w_or) < 1e-8
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_cocr_config1_currents(vielib, config1, prec):
+    """COCR (the short recurrence for A symmetric in the chi-weighted bilinear
+    form) inside the same FP64 refinement reaches the oracle's currents of the
+    16^3 sphere, with five vector slots (restart = 4)."""
+    wl, chs, w_or = config1
+    g = wl.grid
+    with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
+        st = hd.solve(chs, tol=1e-10, restart=4, precision=prec, solver=vielib.SOLVER_COCR)
+        assert st["converged"] == 2 and st["relres_max"] <= 1e-10
+        w = np.stack([hd.get_current(r) for r in range(2)])
+    assert _maxrel(w, w_or) < 1e-8
+
+
+def test_cocr_rejects_bad_options(vielib, config1):
+    wl, chs, _ = config1
+    g = wl.grid
+    with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
+        with pytest.raises(vielib.VieError):
+            hd.solve(chs, restart=3, solver=vielib.SOLVER_COCR)
+        with pytest.raises(vielib.VieError):
+            hd.solve(chs, restart=8, solver=3)
+
+
 def test_config1_g2_and_coincidences(vielib, config1):
     wl, chs, w_or = config1
     g = wl.grid
@@ -189,6 +213,13 @@ def test_bicgstab_bench_body_solution_satisfies_oracle_equation(vielib):
     """BiCGStab on the 128^3 bench body (8 of its RHS), sampled oracle residual."""
     wl = inputs.random_body_workload(20001, n_axis=128, h=1.0 / 128.0, n_dirs=16)
     _sampled_residual_check(vielib, wl, (0, 5), restart=64, nsamp=3, seed=6, solver=1, n_rhs=8)
+
+
+def test_cocr_bench_body_solution_satisfies_oracle_equation(vielib):
+    """COCR on a 128^3 bench body (contrast varying over [0.5, 5], so the
+    1/chi weights of the bilinear form matter), 8 RHS, sampled oracle residual."""
+    wl = inputs.random_body_workload(20001, n_axis=128, h=1.0 / 128.0, n_dirs=16)
+    _sampled_residual_check(vielib, wl, (0, 5), restart=4, nsamp=3, seed=7, solver=2, n_rhs=8)
 
 
 def test_optical_theorem_on_gpu_solution(vielib):

@@ -119,3 +119,45 @@ def test_sparse_source_direct_sum_matches_table_sum():
         for r in range(2):
             ref = vie.convolve_direct(T, n, W[r], targets=pts)
             assert np.abs(got[r] - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_operator_is_symmetric_in_the_contrast_weighted_bilinear_form():
+    """Reciprocity of the discrete kernel (K_ab(m) = K_ba(-m)) makes
+    A = I - diag(chi) K symmetric in [x, y] = sum x_i y_i / chi_i: diag(1/chi) A
+    equals its transpose (not its conjugate transpose).  This is the structure
+    the COCR solver relies on; a dropped transpose or a conjugated kernel
+    breaks it."""
+    n = (4, 3, 5)
+    h = 0.07
+    rng = np.random.default_rng(12)
+    chi = rng.uniform(0.3, 9.0, n)
+    A = vie.dense_operator(n, h, K0, chi)
+    mu = np.tile(1.0 / chi.reshape(-1), 3)
+    MA = mu[:, None] * A
+    s = np.abs(MA).max()
+    assert np.abs(MA - MA.T).max() <= 1e-14 * s
+    assert np.abs(MA - MA.conj().T).max() > 1e-3 * s  # complex symmetric, not Hermitian
+
+
+def test_d2_operator_is_symmetric_in_the_face_contrast_weighted_form():
+    """The same for the rooftop / pulse operator: y = w - chi_f (K2 w) with the
+    face contrast chi_f; K2 (scalar kernel plus staggered grad-div) is
+    symmetric, so diag(1/chi_f) A is, on the faces with chi_f > 0."""
+    from oracle import d2
+    n = (3, 3, 3)
+    h = 0.08
+    rng = np.random.default_rng(13)
+    eps = 1.0 + rng.uniform(0.5, 5.0, n)
+    eps[0] = 1.0
+    chi = vie.contrast(eps)
+    chi_f = d2.face_contrast(chi)
+    keep = np.flatnonzero(chi_f.reshape(-1) > 0)
+    cols = []
+    for j in keep:
+        e = np.zeros(chi_f.size, dtype=np.complex128)
+        e[j] = 1.0
+        cols.append(d2.apply_direct(n, h, K0, chi_f, e.reshape((3,) + n)).reshape(-1)[keep])
+    A = np.stack(cols, 1)
+    MA = A / chi_f.reshape(-1)[keep][:, None]
+    s = np.abs(MA).max()
+    assert np.abs(MA - MA.T).max() <= 1e-13 * s
