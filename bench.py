@@ -78,6 +78,10 @@ def parse():
                    help="metasurface-paper: box in wavelengths (paper x, y, z)")
     p.add_argument("--solver", default="gmres", choices=["gmres", "bicgstab", "cocr"],
                    help="metasurface-paper: inner Krylov solver")
+    p.add_argument("--precond", default="none", choices=["none", "cells", "blocks7"],
+                   help="metasurface-paper: block-Jacobi preconditioner over the fin unit cells or over 7 x 7 "
+                        "lateral blocks (FGMRES)")
+    p.add_argument("--inner", type=int, default=8, help="metasurface-paper: inner COCR steps per block solve")
     p.add_argument("--profile-solve", type=int, default=0,
                    help="profiling aid: a 12-iteration solve with this many RHS on the first bench body, then exit")
     return p.parse_args()
@@ -533,8 +537,33 @@ def run_metasurface_paper(args):
         V.timer_enable(False)
         return e0.elapsed_time(e1) / reps, V.timer_read()
 
+    t_pc = None
+    if args.precond != "none":
+        cuts = info["cell_cuts"] if args.precond == "cells" else \
+            [[], inputs.even_cuts(g.n[1], 7), inputs.even_cuts(g.n[2], 7)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hd.set_block_precond(cuts, inner=args.inner)
+        torch.cuda.synchronize()
+        t_pc = time.perf_counter() - t0
+        log(f"block preconditioner ({args.precond}) set up in {t_pc:.1f}s")
     ms32, tm32 = time_apply(V.PREC_MIXED, torch.complex64, 3)
     ms64, _ = time_apply(V.PREC_FP64, torch.complex128, 1)
+    ms_blk = None
+    if t_pc is not None:
+        w = torch.randn(3, Nb, dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(w)
+        hd.block_apply_device(w.data_ptr(), y.data_ptr())
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            hd.block_apply_device(w.data_ptr(), y.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_blk = e0.elapsed_time(e1) / 3.0
+        del w, y
+        log(f"block operator: {ms_blk:.1f} ms per vector")
     torch.cuda.empty_cache()
     log(f"operator: FP32 {ms32:.1f} ms, FP64 {ms64:.1f} ms per RHS")
 
@@ -559,7 +588,7 @@ def run_metasurface_paper(args):
     t0 = time.perf_counter()
     st = hd.solve(chs, tol=1e-6, restart=args.restart, precision=V.PREC_MIXED, max_iter=args.max_iter,
                   inner_tol=args.inner_tol, reorth_eta=args.reorth_eta, inner_floor=args.inner_floor,
-                  solver=solver, allow_noconv=True)
+                  solver=solver, precond=2 if args.precond != "none" else 0, allow_noconv=True)
     e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -613,12 +642,15 @@ def run_metasurface_paper(args):
                    "grid": list(g.n), "padded": list(inf["P"]), "body_voxels": Nb, "unknowns": 3 * Nb,
                    "rhs": "normal incidence, L and R",
                    "solver": (f"GMRES({args.restart})" if args.solver == "gmres" else args.solver.upper()) +
-                             " FP32 matvec + FP64 refinement", "max_iter": args.max_iter},
+                             " FP32 matvec + FP64 refinement", "max_iter": args.max_iter,
+                   "precond": None if args.precond == "none" else
+                   {"blocks": args.precond, "inner_cocr_steps": args.inner, "setup_s": t_pc}},
         "converged": int(st["converged"]), "iters": st["iters"].tolist(), "relres": st["relres"].tolist(),
         "outer_max": int(st["outer_max"]), "matvecs32": int(st["matvecs32"]), "matvecs64": int(st["matvecs64"]),
         "seconds_per_rhs": solve_s / 2.0, "wall_s": wall, "setup_s": t_setup, "generate_s": t_gen,
         "device_bytes": inf["device_bytes"],
         "operator_fp32": op32, "operator_fp64_ms": round(ms64, 1),
+        "block_operator_ms": round(ms_blk, 2) if ms_blk is not None else None,
         "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
         "g_LR_at_m10_p10": float(g2[i1, i2]),
         "g_LR_row_theta1_m10": {"min": float(row.min()), "theta2_at_min": float(deg[int(np.argmin(row))]),

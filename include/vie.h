@@ -101,7 +101,9 @@ typedef struct vie_solve_opts {
                           guess whose FP64 residual is not below ||b|| is
                           replaced by zero.                                       */
     int precond;       /* 0: GMRES; 1: FGMRES with the learned right preconditioner
-                          attached by vie_attach_precond (mixed or FP64 basis)   */
+                          attached by vie_attach_precond (mixed or FP64 basis);
+                          2: FGMRES with the block-Jacobi preconditioner set up by
+                          vie_set_block_precond (mixed precision, GMRES)          */
     int solver;        /* VIE_SOLVER_GMRES (default), VIE_SOLVER_BICGSTAB (the
                           paper's solver, Sec. II-C) or VIE_SOLVER_COCR, inside
                           the same FP64 refinement.  BiCGStab needs restart >= 8
@@ -379,6 +381,24 @@ int vie_net_features(vie_handle* hd, int factor, float* x_dev, float* t_dev, flo
 int vie_attach_net(vie_handle* hd, vie_net* net, int factor);
 /* number of RHS of the last solve whose supplied initial guess was rejected */
 int vie_guesses_rejected(const vie_handle* hd);
+
+/* ---- block-Jacobi preconditioner (FGMRES, opts.precond = 2) ---------------
+ * The paper's solver applies a block preconditioner over blocks of the volume
+ * (7 x 7 lateral blocks of the metasurface, Sec. III-B) without further detail.
+ * Here: M(v) approximately solves A_bd z = v, A_bd = I - diag(chi) K_bd with
+ * K_bd keeping only interactions between voxels of the same block, by
+ * `inner_iters` COCR steps from z = 0 (FP32 vectors, FP64 scalars).  The blocks
+ * are the cells of the tiling given by interior cut positions per axis:
+ * cuts = [axis 0 cuts..., axis 1 cuts..., axis 2 cuts...], ncuts[a] of them
+ * on axis a, strictly increasing inside (0, n_a); no cut on an axis keeps it
+ * whole.  Each block is cropped to the bounding box of its body voxels; A_bd
+ * runs as one batched FFT operator on the largest box, one slot per non-empty
+ * block.  Set up again after every change of the body (vie_set_eps drops it).
+ * D1 only.  Errors: VIE_EINVAL (cuts, iterations, D2), VIE_ENOMEM. */
+int vie_set_block_precond(vie_handle* hd, const int* cuts, const int ncuts[3], int inner_iters);
+/* y = A_bd w for one FP32 compact vector [3][n_body] (device, float2); for
+ * checks of the block operator.  Enqueued on the handle's stream. */
+int vie_block_apply_device(vie_handle* hd, const void* w_dev, void* y_dev);
 
 /* ---- learned right preconditioner (FGMRES, opts.precond = 1) --------------
  * Each Krylov vector v (unit norm) is mapped to z = v + up(Net(x)) / sqrt(3 Nb)

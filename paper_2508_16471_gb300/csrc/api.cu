@@ -27,6 +27,7 @@ struct vie_handle {
     int net_factor = 4;         // coarsening of the network grid
     int guesses_rejected = 0;
     vie::PrecondCtx pctx;       // attached preconditioner network (pctx.net not owned)
+    vie::BlockPrecond bpc;      // block-Jacobi preconditioner (vie_set_block_precond)
 };
 
 namespace vie {
@@ -103,6 +104,7 @@ static int refresh_vox_host(vie_handle* hd) {
 
 static int set_eps_dev(vie_handle* hd, const double* eps_dev) {
     hd->S.release(hd->op);
+    hd->bpc.release(hd->op);  // its blocks follow the body
     hd->have_solution = false;
     hd->n_rhs = 0;
     VIE_TRY(op_set_body_device(hd->op, eps_dev));
@@ -259,7 +261,10 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
         return fail(VIE_ESTATE, "use_x0 needs a stored solution with the same n_rhs, restart and precision");
     if (o.use_x0 == 2 && !hd->net) return fail(VIE_ESTATE, "use_x0 = 2 needs a network attached with vie_attach_net");
     if (o.use_x0 < 0 || o.use_x0 > 2) return fail(VIE_EINVAL, "use_x0 must be 0, 1 or 2");
-    if (o.precond != 0 && o.precond != 1) return fail(VIE_EINVAL, "precond must be 0 or 1");
+    if (o.precond < 0 || o.precond > 2) return fail(VIE_EINVAL, "precond must be 0, 1 or 2");
+    if (o.precond == 2 && (!hd->bpc.T || o.precision != VIE_PREC_MIXED || o.solver != VIE_SOLVER_GMRES ||
+                           o.use_x0 == 2))
+        return fail(VIE_ESTATE, "precond = 2 needs vie_set_block_precond, mixed precision, GMRES and use_x0 0 or 1");
     if (!(o.reorth_eta >= 0) || !std::isfinite(o.reorth_eta)) return fail(VIE_EINVAL, "reorth_eta must be >= 0");
     if (!(o.inner_floor > 0) || !(o.inner_floor <= 1)) return fail(VIE_EINVAL, "inner_floor must be in (0, 1]");
     if (o.solver != VIE_SOLVER_GMRES && o.solver != VIE_SOLVER_BICGSTAB && o.solver != VIE_SOLVER_COCR)
@@ -278,8 +283,10 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
     if (o.use_x0 == 2) VIE_TRY(net_guess(hd, n_rhs));
     SolveResult res;
     hd->S.pc = o.precond == 1 ? &hd->pctx : nullptr;
+    hd->S.bpc = o.precond == 2 ? &hd->bpc : nullptr;
     int st = solver_run(hd->op, hd->S, o, res);
     hd->S.pc = nullptr;
+    hd->S.bpc = nullptr;
     VIE_CUDA(cudaStreamSynchronize(hd->op.stream));
     auto t1 = std::chrono::steady_clock::now();
     if (st != VIE_OK) return st;
@@ -799,9 +806,25 @@ void vie_destroy(vie_handle* hd) {
     cudaSetDevice(hd->device);
     if (hd->op.stream) cudaStreamSynchronize(hd->op.stream);
     hd->S.release(hd->op);
+    hd->bpc.release(hd->op);
     op_free(hd->op);
     if (hd->op.stream) cudaStreamDestroy(hd->op.stream);
     delete hd;
+}
+
+// ---- block-Jacobi preconditioner -------------------------------------------
+int vie_set_block_precond(vie_handle* hd, const int* cuts, const int ncuts[3], int inner_iters) {
+    if (!hd || !ncuts || (!cuts && ncuts[0] + ncuts[1] + ncuts[2] > 0)) return fail(VIE_EINVAL, "NULL argument");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    VIE_CUDA(cudaStreamSynchronize(hd->op.stream));
+    static const int none = 0;
+    return block_precond_setup(hd->op, hd->bpc, cuts ? cuts : &none, ncuts, inner_iters);
+}
+
+int vie_block_apply_device(vie_handle* hd, const void* w_dev, void* y_dev) {
+    if (!hd || !w_dev || !y_dev) return fail(VIE_EINVAL, "NULL argument");
+    VIE_CUDA(cudaSetDevice(hd->device));
+    return block_apply(hd->op, hd->bpc, (const c32*)w_dev, (c32*)y_dev);
 }
 
 // ---- learned initial guess ------------------------------------------------

@@ -697,7 +697,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
     const int nblk_d = (int)ceil_div(S.n3, (long long)KCH_D);  // inner-product blocks (<= nblk)
     const long long vrs = n * mp1;  // per-RHS stride in V
     const long long zrs = n * m;    // per-RHS stride in Z (FGMRES)
-    if (S.pc && !S.Z) VIE_TRY(dev_alloc(op, &S.Z, sizeof(cplx<T>) * n * R * m));
+    if ((S.pc || S.bpc) && !S.Z) VIE_TRY(dev_alloc(op, &S.Z, sizeof(cplx<T>) * n * R * m));
     cplx<T>* V = (cplx<T>*)S.V;
     cudaStream_t st = op.stream;
     const int prec_in = sizeof(T) == 8 ? VIE_PREC_FP64 : VIE_PREC_MIXED;
@@ -878,12 +878,20 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
             const int ni = (int)inner.size();
             VIE_TRY(op_set_list(op, inner.data(), ni));
             // V_{j+1} = A_T V_j
-            if (S.pc) {
+            if (S.pc || S.bpc) {
                 // FGMRES: z_j = M(v_j), v_{j+1} = A z_j
                 cplx<T>* Zj = (cplx<T>*)S.Z + (long long)j * n;
-                tmr_begin(TMR_OTHER, st);
-                VIE_TRY(precond_apply<T>(op, *S.pc, V + (long long)j * n, vrs, Zj, zrs, op.d_list, ni, st));
-                tmr_end(TMR_OTHER, st);
+                if (S.bpc) {
+                    if constexpr (sizeof(T) == 4)
+                        VIE_TRY(block_precond_apply(op, *S.bpc, V + (long long)j * n, vrs, Zj, zrs, op.d_list,
+                                                    inner.data(), ni, R));
+                    else
+                        return fail(VIE_EINVAL, "the block preconditioner needs the mixed-precision solver");
+                } else {
+                    tmr_begin(TMR_OTHER, st);
+                    VIE_TRY(precond_apply<T>(op, *S.pc, V + (long long)j * n, vrs, Zj, zrs, op.d_list, ni, st));
+                    tmr_end(TMR_OTHER, st);
+                }
                 VIE_TRY(op_apply(op, prec_in, Zj, zrs, V + (long long)(j + 1) * n, vrs, op.d_list, ni));
             } else {
                 VIE_TRY(op_apply(op, prec_in, V + (long long)j * n, vrs, V + (long long)(j + 1) * n, vrs, op.d_list,
@@ -953,7 +961,8 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         tmr_end(TMR_OTHER, st);
         LAUNCH_CHECK();
         tmr_begin(TMR_XUPDATE, st);
-        if (S.pc) k_xupdate<T><<<dim3(nblk, nc), KB, 0, st>>>(S.x, n, (cplx<T>*)S.Z, zrs, n, S.y, S.kcount, op.d_list, m, n);
+        if (S.pc || S.bpc)
+            k_xupdate<T><<<dim3(nblk, nc), KB, 0, st>>>(S.x, n, (cplx<T>*)S.Z, zrs, n, S.y, S.kcount, op.d_list, m, n);
         else k_xupdate<T><<<dim3(nblk, nc), KB, 0, st>>>(S.x, n, V, vrs, n, S.y, S.kcount, op.d_list, m, n);
         tmr_end(TMR_XUPDATE, st, (double)steps_sum * n * ET + 2.0 * nc * n * 16.0);
         LAUNCH_CHECK();
@@ -1639,6 +1648,227 @@ static int cocr_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult&
         out.outer_max = std::max(out.outer_max, outer[r]);
         out.relres_max = std::max(out.relres_max, out.relres[r]);
     }
+    return VIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// block-Jacobi preconditioner
+// ---------------------------------------------------------------------------
+void BlockPrecond::release(Operator& op) {
+    (void)op;
+    bop.chi32 = nullptr;  // borrowed from the main operator
+    bop.chi64 = nullptr;
+    op_free(bop);
+    bop = Operator();
+    cudaFree(tiles);
+    cudaFree(V);
+    cudaFree(coef);
+    cudaFree(partial);
+    cudaFree(flag);
+    tiles = nullptr;
+    V = nullptr;
+    coef = nullptr;
+    partial = nullptr;
+    flag = nullptr;
+    T = rcap = 0;
+    n3 = 0;
+}
+
+int block_precond_setup(Operator& op, BlockPrecond& bp, const int* cuts, const int ncuts[3], int iters) {
+    if (op.disc) return fail(VIE_EINVAL, "the block preconditioner supports the D1 discretisation only");
+    if (iters < 1 || iters > 1000) return fail(VIE_EINVAL, "inner iterations must be in 1..1000");
+    // tile index of every coordinate along each axis (number of cuts at or below it)
+    std::vector<int> tix[3];
+    int nt[3];
+    const int* c = cuts;
+    for (int a = 0; a < 3; ++a) {
+        if (ncuts[a] < 0) return fail(VIE_EINVAL, "negative cut count");
+        for (int i = 0; i < ncuts[a]; ++i)
+            if (c[i] <= 0 || c[i] >= op.n[a] || (i > 0 && c[i] <= c[i - 1]))
+                return fail(VIE_EINVAL, "cuts must increase strictly inside (0, n) on each axis");
+        tix[a].assign(op.n[a], 0);
+        for (int x = 0, t = 0; x < op.n[a]; ++x) {
+            while (t < ncuts[a] && c[t] <= x) ++t;
+            tix[a][x] = t;
+        }
+        nt[a] = ncuts[a] + 1;
+        c += ncuts[a];
+    }
+    const long long Nb = op.Nb;
+    std::vector<int> vox(Nb);
+    VIE_CUDA(cudaMemcpy(vox.data(), op.vox, sizeof(int) * Nb, cudaMemcpyDeviceToHost));
+    const long long ntt = (long long)nt[0] * nt[1] * nt[2];
+    if (ntt > (1LL << 24)) return fail(VIE_EINVAL, "too many blocks");
+    std::vector<int> lo(3 * ntt, 1 << 30), hi(3 * ntt, -1), tid(Nb);
+    const long long n12 = (long long)op.n[1] * op.n[2];
+    for (long long v = 0; v < Nb; ++v) {
+        const long long lin = vox[v];
+        const int i = (int)(lin / n12), j = (int)((lin / op.n[2]) % op.n[1]), k = (int)(lin % op.n[2]);
+        const long long t = ((long long)tix[0][i] * nt[1] + tix[1][j]) * nt[2] + tix[2][k];
+        tid[v] = (int)t;
+        const int xyz[3] = {i, j, k};
+        for (int a = 0; a < 3; ++a) {
+            lo[3 * t + a] = std::min(lo[3 * t + a], xyz[a]);
+            hi[3 * t + a] = std::max(hi[3 * t + a], xyz[a]);
+        }
+    }
+    std::vector<int> slot(ntt, -1);
+    int T = 0;
+    int box[3] = {1, 1, 1};
+    for (long long t = 0; t < ntt; ++t)
+        if (hi[3 * t] >= 0) {
+            slot[t] = T++;
+            for (int a = 0; a < 3; ++a) box[a] = std::max(box[a], hi[3 * t + a] - lo[3 * t + a] + 1);
+        }
+    const long long G = (long long)box[0] * box[1] * box[2];
+    if ((double)G * T > 2e9) return fail(VIE_EINVAL, "block voxel maps too large");
+    std::vector<int> map((size_t)(G * T), -1);
+    for (long long v = 0; v < Nb; ++v) {
+        const long long lin = vox[v];
+        const int i = (int)(lin / n12), j = (int)((lin / op.n[2]) % op.n[1]), k = (int)(lin % op.n[2]);
+        const long long t = tid[v];
+        const long long loc = ((long long)(i - lo[3 * t]) * box[1] + (j - lo[3 * t + 1])) * box[2] + (k - lo[3 * t + 2]);
+        map[(size_t)(slot[t] * G + loc)] = (int)v;
+    }
+    bp.release(op);
+    Operator& b = bp.bop;
+    for (int a = 0; a < 3; ++a) {
+        b.n[a] = box[a];
+        bp.box[a] = box[a];
+    }
+    b.N = G;
+    b.Nb = Nb;
+    b.h = op.h;
+    b.k0 = op.k0;
+    b.stream = op.stream;
+    b.disc = 0;
+    b.chi_cs = op.chi_cs;
+    b.idx_stride = G;
+    VIE_TRY(op_init_axes(b));
+    VIE_TRY(op_build_kernel(b));
+    VIE_TRY(dev_alloc(b, (void**)&b.idx_map, sizeof(int) * (size_t)(G * T)));
+    VIE_CUDA(cudaMemcpy(b.idx_map, map.data(), sizeof(int) * (size_t)(G * T), cudaMemcpyHostToDevice));
+    b.chi32 = op.chi32;
+    b.chi64 = op.chi64;
+    std::vector<int> ids(T);
+    for (int t = 0; t < T; ++t) ids[t] = t;
+    VIE_CUDA(cudaMalloc(&bp.tiles, sizeof(int) * T));
+    VIE_CUDA(cudaMemcpy(bp.tiles, ids.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
+    bp.T = T;
+    bp.iters = iters;
+    bp.n3 = 3 * Nb;
+    return VIE_OK;
+}
+
+int block_apply(Operator& op, BlockPrecond& bp, const c32* w, c32* y) {
+    (void)op;
+    if (!bp.T) return fail(VIE_ESTATE, "no block preconditioner set up");
+    return op_apply(bp.bop, VIE_PREC_MIXED, w, 0, y, 0, bp.tiles, bp.T);
+}
+
+// inner start: r = v, d = p = Ap = 0
+__global__ void k_bp_start(const c32* __restrict__ v, long long vrs, c32* __restrict__ V, long long ivrs,
+                           const int* __restrict__ list, long long n) {
+    const int r = list[blockIdx.y];
+    c32* Vr = V + r * ivrs;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+    const c32 z = {0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e >= n) continue;
+        Vr[CO_R * n + e] = v[r * vrs + e];
+        Vr[CO_P * n + e] = z;
+        Vr[CO_AP * n + e] = z;
+        Vr[CO_D * n + e] = z;
+    }
+}
+
+// z = d
+__global__ void k_bp_finish(const c32* __restrict__ V, long long ivrs, c32* __restrict__ z, long long zrs,
+                            const int* __restrict__ list, long long n) {
+    const int r = list[blockIdx.y];
+    const c32* d = V + r * ivrs + CO_D * n;
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) z[r * zrs + e] = d[e];
+    }
+}
+
+int block_precond_apply(Operator& op, BlockPrecond& bp, const c32* v, long long vrs, c32* z, long long zrs,
+                        const int* d_list, const int* hlist, int ni, int R) {
+    const long long n = bp.n3;
+    const int nblk = (int)ceil_div(n, (long long)KCH);
+    cudaStream_t st = op.stream;
+    constexpr int cs = 8, ps = 2;
+    if (bp.rcap < R) {
+        cudaFree(bp.V);
+        cudaFree(bp.coef);
+        cudaFree(bp.partial);
+        cudaFree(bp.flag);
+        bp.V = nullptr;
+        bp.coef = nullptr;
+        bp.partial = nullptr;
+        bp.flag = nullptr;
+        bp.rcap = 0;
+        VIE_CUDA(cudaMalloc(&bp.V, sizeof(c32) * (size_t)R * CO_NV * n));
+        VIE_CUDA(cudaMalloc(&bp.coef, sizeof(c64) * (size_t)R * cs));
+        VIE_CUDA(cudaMalloc(&bp.partial, sizeof(c64) * (size_t)R * ps * nblk));
+        VIE_CUDA(cudaMalloc(&bp.flag, sizeof(int) * R));
+        bp.rcap = R;
+    }
+    c32* V = (c32*)bp.V;
+    const long long ivrs = CO_NV * n;
+    dim3 g(nblk, ni);
+    auto dots = [&](int a, int b, int slot) -> int {
+        tmr_begin(TMR_DOTS, st);
+        k_co_dots<float><<<g, KB, 0, st>>>(V, ivrs, n, op.Nb, op.chi32, op.chi_cs, d_list, 1, a, b, 1, 0, 0, 0,
+                                           bp.partial, ps, nblk);
+        tmr_end(TMR_DOTS, st, 2.0 * ni * n * sizeof(c32));
+        LAUNCH_CHECK();
+        k_bi_reduce<<<dim3(1, ni), KB, 0, st>>>(bp.partial, ps, nblk, bp.coef, cs, d_list, slot, 0, 0);
+        LAUNCH_CHECK();
+        return VIE_OK;
+    };
+    auto update = [&](int stage) -> int {
+        tmr_begin(TMR_UPDATE, st);
+        k_co_update<float><<<g, KB, 0, st>>>(V, ivrs, n, d_list, bp.coef, cs, stage);
+        tmr_end(TMR_UPDATE, st, 6.0 * ni * n * sizeof(c32));
+        LAUNCH_CHECK();
+        return VIE_OK;
+    };
+    auto scalars = [&](int stage) -> int {
+        k_co_scalars<<<ceil_div(ni, 64), 64, 0, st>>>(bp.coef, cs, d_list, ni, stage, bp.flag);
+        LAUNCH_CHECK();
+        return VIE_OK;
+    };
+    auto apply = [&]() -> int {  // Ar = A_bd r, one RHS at a time (the block slots fill each launch)
+        for (int q = 0; q < ni; ++q) {
+            c32* Vr = V + (long long)hlist[q] * ivrs;
+            VIE_TRY(block_apply(op, bp, Vr + CO_R * n, Vr + CO_AR * n));
+        }
+        return VIE_OK;
+    };
+    k_bp_start<<<g, KB, 0, st>>>(v, vrs, V, ivrs, d_list, n);
+    LAUNCH_CHECK();
+    VIE_TRY(apply());
+    VIE_TRY(dots(CO_R, CO_AR, CS_RHON));
+    VIE_TRY(scalars(2));
+    VIE_TRY(update(1));
+    for (int it = 0; it < bp.iters; ++it) {
+        VIE_TRY(dots(CO_AP, CO_AP, CS_SIGMA));
+        VIE_TRY(scalars(0));
+        VIE_TRY(update(0));
+        if (it + 1 == bp.iters) break;
+        VIE_TRY(apply());
+        VIE_TRY(dots(CO_R, CO_AR, CS_RHON));
+        VIE_TRY(scalars(1));
+        VIE_TRY(update(1));
+    }
+    k_bp_finish<<<g, KB, 0, st>>>(V, ivrs, z, zrs, d_list, n);
+    LAUNCH_CHECK();
     return VIE_OK;
 }
 

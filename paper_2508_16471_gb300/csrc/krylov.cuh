@@ -25,6 +25,35 @@ template <typename T>
 int precond_apply(Operator& op, PrecondCtx& pc, const cplx<T>* v, long long vrs, cplx<T>* z, long long zrs,
                   const int* list, int n, cudaStream_t s);
 
+// Block-Jacobi right preconditioner of FGMRES (the block preconditioner of
+// Sec. III-B): z approximately solves A_bd z = v, where A_bd keeps only the
+// interactions inside each block.  Blocks are the cells of a tiling of the
+// grid (cut positions per axis), each cropped to the bounding box of its body
+// voxels; A_bd is one batched FFT operator on the largest such box (`bop`),
+// one batch slot per block with its own voxel map into the global compact
+// vector.  The inner solve is a fixed number of COCR steps from z = 0 (A_bd is
+// symmetric in the same chi-weighted bilinear form as A).
+struct BlockPrecond {
+    Operator bop;             // block-grid operator; chi borrowed from the main operator
+    int T = 0;                // non-empty blocks
+    int* tiles = nullptr;     // [T] slot list 0..T-1 (device)
+    int iters = 8;            // inner COCR steps
+    int box[3] = {0, 0, 0};   // block grid
+    void* V = nullptr;        // [rcap][5][n3] FP32 inner vectors
+    c64* coef = nullptr;      // [rcap][8] inner scalars
+    c64* partial = nullptr;   // [rcap][2][nblk]
+    int* flag = nullptr;      // [rcap] breakdown flags (inner steps continue with zeroed scalars)
+    int rcap = 0;
+    long long n3 = 0;
+    void release(Operator& op);
+};
+int block_precond_setup(Operator& op, BlockPrecond& bp, const int* cuts, const int ncuts[3], int iters);
+// y = A_bd w for one FP32 compact vector
+int block_apply(Operator& op, BlockPrecond& bp, const c32* w, c32* y);
+// z[r] = M(v[r]) for the RHS in d_list / hlist (n of them), FP32 basis
+int block_precond_apply(Operator& op, BlockPrecond& bp, const c32* v, long long vrs, c32* z, long long zrs,
+                        const int* d_list, const int* hlist, int n, int R);
+
 struct Solver {
     int R = 0, m = 0, prec = 0, nblk = 0;
     long long n3 = 0;          // vector length 3 * Nb
@@ -50,6 +79,7 @@ struct Solver {
     double* chans = nullptr;   // [R][9] channels of the current right-hand sides
     void* Z = nullptr;         // [R][m][n3] preconditioned basis (FGMRES; allocated on first use)
     PrecondCtx* pc = nullptr;  // learned right preconditioner for the next solve (not owned), or null
+    BlockPrecond* bpc = nullptr;  // block-Jacobi right preconditioner for the next solve (not owned), or null
 
     int alloc(Operator& op, int R, int m, int prec);
     void release(Operator& op);

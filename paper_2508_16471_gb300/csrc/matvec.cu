@@ -214,7 +214,7 @@ template <typename T>
 __global__ void k_zfwd(const cplx<T>* __restrict__ w, long long w_rstride, const int* __restrict__ list,
                        const int* __restrict__ idx_map, cplx<T>* __restrict__ A, int n0, int n1, int n2,
                        long long Nb, long long nlines, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL,
-                       int stw) {
+                       int stw, long long idx_stride) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const cplx<T>* tw;
     const int L = plan.L;
@@ -231,7 +231,7 @@ __global__ void k_zfwd(const cplx<T>* __restrict__ w, long long w_rstride, const
             const long long sc = line / plane;
             const long long xy = line - sc * plane;
             const int slot = (int)(sc / 3), c = (int)(sc - (sc / 3) * 3);
-            const int vi = idx_map[xy * n2 + p];
+            const int vi = idx_map[(long long)list[slot] * idx_stride + xy * n2 + p];
             if (vi >= 0) v = w[(long long)list[slot] * w_rstride + c * Nb + vi];
         }
         bA[p * ld + l] = v;
@@ -251,7 +251,7 @@ __global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict_
                        cplx<T>* __restrict__ y, long long y_rstride, const int* __restrict__ list,
                        const int* __restrict__ idx_map, const T* __restrict__ chi, int n0, int n1, int n2,
                        long long Nb, long long nlines, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL,
-                       long long chi_cs, int stw) {
+                       long long chi_cs, int stw, long long idx_stride) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const cplx<T>* tw;
     const int L = plan.L;
@@ -275,10 +275,10 @@ __global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict_
         if (line >= nlines) continue;
         const long long sc = line / plane;
         const long long xy = line - sc * plane;
-        const int vi = idx_map[xy * n2 + p];
-        if (vi < 0) continue;
         const int slot = (int)(sc / 3), c = (int)(sc - (sc / 3) * 3);
         const long long rr = list[slot];
+        const int vi = idx_map[rr * idx_stride + xy * n2 + p];
+        if (vi < 0) continue;
         const cplx<T> u = r[p * ld + l];
         const cplx<T> wv = w[rr * w_rstride + c * Nb + vi];
         const T ch = chi[c * chi_cs + vi];
@@ -869,8 +869,15 @@ int op_reserve(Operator& op, int prec, int nrhs) {
     const size_t esz = prec ? sizeof(c64) : sizeof(c32);
     const long long perA = 3LL * op.n[0] * op.n[1] * op.P[2];
     const long long perB = 3LL * op.n[0] * op.P[1] * op.P[2];
-    // cap the workspace at ~24 GB per precision; larger batches run in chunks
-    const double limit = 24e9;
+    // The workspace of a precision takes up to 24 GB, or up to 45 % of the device memory that is free (counting
+    // what it already holds) when that is more: on large grids two or more RHS per launch amortise the kernel
+    // octant tile of the fused x pass.  Larger batches run in chunks of `cap` RHS.
+    double limit = 24e9;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+        limit = std::max(limit, 0.45 * ((double)fr + (double)esz * (perA + perB) * W.cap));
+    else
+        cudaGetLastError();
     int cap = std::max(1, std::min(nrhs, (int)(limit / ((perA + perB) * (double)esz))));
     if (W.cap >= cap) return VIE_OK;
     if (W.A) dev_free(op, W.A, esz * perA * W.cap);
@@ -938,7 +945,7 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             const long long nlines = (long long)ns * 3 * n0 * n1;
             tmr_begin(tid(TMR_ZFWD), op.stream);
             VIE_TRY(fast_zfwd((const c32*)w, wr, list, op.idx_map, (c32*)A, n0, n1, n2, op.Nb, nlines, P2,
-                              op.ax[2].roots32, op.stream));
+                              op.ax[2].roots32, op.stream, op.idx_stride));
             tmr_end(tid(TMR_ZFWD), op.stream, ns * (vec + lineA) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
@@ -948,7 +955,8 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             const long long nlines = (long long)ns * 3 * n0 * n1;
             tmr_begin(tid(TMR_ZFWD), op.stream);
             k_zfwd<T><<<(unsigned)((nlines + c.w - 1) / c.w), 256, c.smem, op.stream>>>(
-                w, wr, list, op.idx_map, A, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), c.w, c.stw);
+                w, wr, list, op.idx_map, A, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), c.w, c.stw,
+                op.idx_stride);
             tmr_end(tid(TMR_ZFWD), op.stream, ns * (vec + lineA) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
@@ -1007,7 +1015,7 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             const long long nlines = (long long)ns * 3 * n0 * n1;
             tmr_begin(tid(TMR_ZINV), op.stream);
             VIE_TRY(fast_zinv((const c32*)A, (const c32*)w, wr, (c32*)y, yr, list, op.idx_map, (const float*)chi, n0, n1,
-                              n2, op.Nb, nlines, P2, op.ax[2].roots32, op.stream, op.chi_cs));
+                              n2, op.Nb, nlines, P2, op.ax[2].roots32, op.stream, op.chi_cs, op.idx_stride));
             tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
@@ -1018,7 +1026,7 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             tmr_begin(tid(TMR_ZINV), op.stream);
             k_zinv<T><<<(unsigned)((nlines + c.w - 1) / c.w), 256, c.smem, op.stream>>>(
                 A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), c.w,
-                op.chi_cs, c.stw);
+                op.chi_cs, c.stw, op.idx_stride);
             tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());

@@ -346,7 +346,8 @@ template <int L>
 __global__ void __launch_bounds__(Z_THREADS) k_zfwd_r(const c32* __restrict__ w, long long w_rstride,
                                                       const int* __restrict__ list, const int* __restrict__ idx_map,
                                                       c32* __restrict__ A, int n0, int n1, int n2, long long Nb,
-                                                      long long nlines, const c32* __restrict__ tw4) {
+                                                      long long nlines, const c32* __restrict__ tw4,
+                                                      long long idx_stride) {
     constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2;
     constexpr int NL = Z_THREADS / R2;
     constexpr int RS = R2 + 1;  // padded row
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_zfwd_r(const c32* __restrict__ w,
         const long long xy = line - sc * plane;
         const int slot = (int)(sc / 3), c = (int)(sc - (sc / 3) * 3);
         const c32* wr = w + (long long)list[slot] * w_rstride + c * Nb;
-        const int* im = idx_map + xy * n2;
+        const int* im = idx_map + (long long)list[slot] * idx_stride + xy * n2;
 #pragma unroll
         for (int n1i = 0; n1i < R1 / 2; ++n1i) {  // n2 <= L/2: the upper half is padding
             const int z = n1i * R2 + q2;
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_zinv_r(const c32* __restrict__ A,
                                                       const int* __restrict__ list, const int* __restrict__ idx_map,
                                                       const float* __restrict__ chi, int n0, int n1, int n2,
                                                       long long Nb, long long nlines, const c32* __restrict__ tw4,
-                                                      long long chi_cs) {
+                                                      long long chi_cs, long long idx_stride) {
     constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2;
     constexpr int NL = Z_THREADS / R2;
     constexpr int RS = R2 + 1;
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_zinv_r(const c32* __restrict__ A,
     const long long rr = list[slot];
     const c32* wr = w + rr * w_rstride + c * Nb;
     c32* yr = y + rr * y_rstride + c * Nb;
-    const int* im = idx_map + xy * n2;
+    const int* im = idx_map + rr * idx_stride + xy * n2;
 #pragma unroll
     for (int n1i = 0; n1i < R1 / 2; ++n1i) {
         const int z = n1i * R2 + q2;
@@ -507,25 +508,27 @@ template <int L> int launch_xfused_r(c32* B, int n0, long long inner, int P1, in
 }
 
 template <int L> int launch_zfwd_r(const c32* w, long long wr, const int* list, const int* idx, c32* A, int n0,
-                                   int n1, int n2, long long Nb, long long nlines, const c32* tw4, cudaStream_t s) {
+                                   int n1, int n2, long long Nb, long long nlines, const c32* tw4, cudaStream_t s,
+                                   long long idx_stride) {
     constexpr int NL = Z_THREADS / Fac<L>::R2;
     const size_t sm = sizeof(c32) * (L + (size_t)NL * Fac<L>::R1 * (Fac<L>::R2 + 1));
     if (2 * n2 > L) return fail(VIE_EINVAL, "z pass: grid extent exceeds half the padded length");
     VIE_TRY(set_smem(k_zfwd_r<L>, sm));
     k_zfwd_r<L><<<(unsigned)((nlines + NL - 1) / NL), Z_THREADS, sm, s>>>(w, wr, list, idx, A, n0, n1, n2, Nb, nlines,
-                                                                         tw4);
+                                                                         tw4, idx_stride);
     return VIE_OK;
 }
 
 template <int L> int launch_zinv_r(const c32* A, const c32* w, long long wr, c32* y, long long yr, const int* list,
                                    const int* idx, const float* chi, int n0, int n1, int n2, long long Nb,
-                                   long long nlines, const c32* tw4, cudaStream_t s, long long chi_cs) {
+                                   long long nlines, const c32* tw4, cudaStream_t s, long long chi_cs,
+                                   long long idx_stride) {
     constexpr int NL = Z_THREADS / Fac<L>::R2;
     const size_t sm = sizeof(c32) * (L + (size_t)NL * Fac<L>::R1 * (Fac<L>::R2 + 1));
     if (2 * n2 > L) return fail(VIE_EINVAL, "z pass: grid extent exceeds half the padded length");
     VIE_TRY(set_smem(k_zinv_r<L>, sm));
     k_zinv_r<L><<<(unsigned)((nlines + NL - 1) / NL), Z_THREADS, sm, s>>>(A, w, wr, y, yr, list, idx, chi, n0, n1,
-                                                                         n2, Nb, nlines, tw4, chi_cs);
+                                                                         n2, Nb, nlines, tw4, chi_cs, idx_stride);
     return VIE_OK;
 }
 
@@ -555,16 +558,16 @@ int fast_xfused(c32* B, int n0, long long inner, int L, int P1, int P2, const c3
 }
 
 int fast_zfwd(const c32* w, long long wr, const int* list, const int* idx, c32* A, int n0, int n1, int n2,
-              long long Nb, long long nlines, int L, const c32* tw4, cudaStream_t s) {
-    VIE_DISPATCH_L(L, VIE_TRY(launch_zfwd_r<LL>(w, wr, list, idx, A, n0, n1, n2, Nb, nlines, tw4, s)));
+              long long Nb, long long nlines, int L, const c32* tw4, cudaStream_t s, long long idx_stride) {
+    VIE_DISPATCH_L(L, VIE_TRY(launch_zfwd_r<LL>(w, wr, list, idx, A, n0, n1, n2, Nb, nlines, tw4, s, idx_stride)));
     return VIE_OK;
 }
 
 int fast_zinv(const c32* A, const c32* w, long long wr, c32* y, long long yr, const int* list, const int* idx,
               const float* chi, int n0, int n1, int n2, long long Nb, long long nlines, int L, const c32* tw4,
-              cudaStream_t s, long long chi_cs) {
+              cudaStream_t s, long long chi_cs, long long idx_stride) {
     VIE_DISPATCH_L(L, VIE_TRY(launch_zinv_r<LL>(A, w, wr, y, yr, list, idx, chi, n0, n1, n2, Nb, nlines, tw4, s,
-                                                chi_cs)));
+                                                chi_cs, idx_stride)));
     return VIE_OK;
 }
 

@@ -52,6 +52,9 @@ struct Operator {
     c64* dtab64 = nullptr;
     int dstride = 0;
     int ff_engine = 0;       // far-field contractions: 0 tcgen05 3xTF32, 1 CUDA-core FP32
+    // voxel maps per batch slot: slot list[s] reads idx_map + list[s] * idx_stride (0: one map for all slots;
+    // the block operator of the block-Jacobi preconditioner keeps one map per block)
+    long long idx_stride = 0;
 };
 
 // device allocation helpers (track bytes)
@@ -93,11 +96,12 @@ struct D2Spec {
 };
 int fast_xfused(c32* B, int n0, long long inner, int L, int P1, int P2, const c32* kh, const int* H,
                 const c32* roots, int ns, cudaStream_t s, const D2Spec* d2 = nullptr);
+// idx_stride: voxel maps per slot (slot list[s] uses idx + list[s] * idx_stride); 0 = one shared map
 int fast_zfwd(const c32* w, long long wr, const int* list, const int* idx, c32* A, int n0, int n1, int n2,
-              long long Nb, long long nlines, int L, const c32* roots, cudaStream_t s);
+              long long Nb, long long nlines, int L, const c32* roots, cudaStream_t s, long long idx_stride = 0);
 int fast_zinv(const c32* A, const c32* w, long long wr, c32* y, long long yr, const int* list, const int* idx,
               const float* chi, int n0, int n1, int n2, long long Nb, long long nlines, int L, const c32* roots,
-              cudaStream_t s, long long chi_cs = 0);
+              cudaStream_t s, long long chi_cs = 0, long long idx_stride = 0);
 
 // tensor-core batched complex GEMM (tc_gemm.cu): C = A B, complex64, strided
 int tc_cgemm(int M, int N, int K, int batch, const c32* A, long long sAb, long long sAm, long long sAk, const c32* B,

@@ -210,8 +210,19 @@ def metasurface_paper(cells_per_lambda: int = 62, box=(40.0, 12.0, 2.0), eps_r: 
             inside = (np.abs(u) <= 0.5 * l) & (np.abs(v) <= 0.5 * d)  # [x][y]
             sub = eps[z0:z1, j0:j1, i0:i1]  # grid frame: [z][y][x]
             sub[:, inside.T] = eps_r
-    info = {"fins": (mx, my), "angles": angles, "n_paper": n_p, "z_cells": z1 - z0}
+    # unit-cell boundaries as interior cut positions (first cell past each boundary), grid frame
+    cuts_p = []
+    for a, m in ((0, mx), (1, my)):
+        cuts_p.append([int(math.floor((k - 0.5 * m) * p / h + 0.5 * (n_p[a] - 1))) + 1 for k in range(1, m)])
+    cuts_p.append([])
+    info = {"fins": (mx, my), "angles": angles, "n_paper": n_p, "z_cells": z1 - z0,
+            "cell_cuts": [cuts_p[a] for a in PAPER_AXES]}
     return Grid(n_g, h), eps, info
+
+
+def even_cuts(n: int, parts: int):
+    """Interior cut positions splitting ``n`` cells into ``parts`` near-equal blocks."""
+    return [int(round(k * n / parts)) for k in range(1, parts)]
 
 
 # --------------------------------------------------------------------------- #

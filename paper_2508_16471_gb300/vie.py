@@ -29,7 +29,8 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
            "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_guesses_rejected",
            "vie_net_create_io", "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune",
-           "vie_setup_disc", "vie_farfield_na", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count"]
+           "vie_setup_disc", "vie_farfield_na", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count",
+           "vie_set_block_precond", "vie_block_apply_device"]
 
 
 class VieError(RuntimeError):
@@ -117,6 +118,8 @@ def load():
     L.vie_setup_disc.argtypes = [C.POINTER(_Grid), dp, C.c_double, C.c_int, C.POINTER(P)]
     L.vie_farfield_na.argtypes = [P, dp, dp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, dp]
     L.vie_set_farfield_engine.argtypes = [P, C.c_int]
+    L.vie_set_block_precond.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]
+    L.vie_block_apply_device.argtypes = [P, P, P]
     L.vie_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int]
     L.vie_kernel_launches.restype = C.c_longlong
     L.vie_stream.argtypes = [P]
@@ -140,7 +143,7 @@ def load():
               "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
               "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_net_create_io",
               "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune", "vie_setup_disc",
-              "vie_farfield_na"]:
+              "vie_farfield_na", "vie_set_block_precond", "vie_block_apply_device"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -290,6 +293,19 @@ class Handle:
         ms = C.c_double()
         _check(load().vie_autotune(self._h, int(n_rhs), int(reps), P, C.byref(ms)))
         return tuple(P), ms.value
+
+    def set_block_precond(self, cuts=((), (), ()), inner=8):
+        """Block-Jacobi preconditioner used by solve(..., precond=2): blocks are
+        the cells of the tiling with interior cut positions cuts[a] on axis a,
+        each solved approximately by `inner` COCR steps."""
+        nc = (C.c_int * 3)(*[len(c) for c in cuts])
+        flat = [int(v) for c in cuts for v in c]
+        arr = (C.c_int * max(1, len(flat)))(*flat) if flat else None
+        _check(load().vie_set_block_precond(self._h, arr, nc, int(inner)))
+
+    def block_apply_device(self, w_ptr: int, y_ptr: int):
+        """y = A_bd w (block operator) for one complex64 compact vector [3][n_body]."""
+        _check(load().vie_block_apply_device(self._h, C.c_void_p(w_ptr), C.c_void_p(y_ptr)))
 
     def attach_precond(self, net, factor):
         """Network used as the FGMRES right preconditioner by solve(..., precond=1)."""
