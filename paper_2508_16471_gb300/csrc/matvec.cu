@@ -872,6 +872,7 @@ int op_reserve(Operator& op, int prec, int nrhs) {
     // The workspace of a precision takes up to 24 GB, or up to 45 % of the device memory that is free (counting
     // what it already holds) when that is more: on large grids two or more RHS per launch amortise the kernel
     // octant tile of the fused x pass.  Larger batches run in chunks of `cap` RHS.
+    if (W.cap >= nrhs) return VIE_OK;
     double limit = 24e9;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
