@@ -29,7 +29,18 @@ struct FFTPlan {
     int Ns[FFT_MAX_STAGES];
     int twoff[FFT_MAX_STAGES];
     int twlen;  // total twiddle entries
+    // division by the stage span Ns and by L as a multiply-high:
+    // x / d = umulhi(x, ceil(2^32 / d)) for x d < 2^32 (0 when d = 1)
+    unsigned int nsmag[FFT_MAX_STAGES];
+    unsigned int lmag;
 };
+
+// x / d for the divisors of a plan (d >= 1, x d < 2^32)
+__device__ __forceinline__ int div_mag(int x, int d, unsigned int mag) {
+    return d == 1 ? x : (int)__umulhi((unsigned int)x, mag);
+}
+// log2 of a power of two
+__device__ __forceinline__ int log2_p2(int v) { return __ffs(v) - 1; }
 
 // ---- small DFTs in registers ----------------------------------------------
 // multiply by -i (forward) or +i (inverse)
@@ -201,19 +212,23 @@ template <typename T, int R, bool INV> __device__ __forceinline__ void dft(cplx<
 }
 
 // ---- one Stockham stage over nl lines in column layout ---------------------
+// nl is a power of two (the lines or columns of the tile); Ns is divided by
+// its multiply-high constant.
 template <typename T, int R, bool INV>
 __device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out,
-                                               int L, int Ns, int nl, int ld,
+                                               int L, int Ns, unsigned int nsmag, int nl, int ld,
                                                const cplx<T>* __restrict__ tw) {
     const int nbf = L / R;
     const int total = nbf * nl;
+    const int nlsh = log2_p2(nl);
     for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        const int l = b % nl;
-        const int j = b / nl;
+        const int l = b & (nl - 1);
+        const int j = b >> nlsh;
         cplx<T> a[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) a[t] = in[(j + t * nbf) * ld + l];
-        const int k = j % Ns;
+        const int jq = div_mag(j, Ns, nsmag);
+        const int k = j - jq * Ns;
         if (Ns > 1) {
             const cplx<T>* w = tw + k * (R - 1);
 #pragma unroll
@@ -224,7 +239,7 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ in, c
             }
         }
         dft<T, R, INV>(a);
-        const int base = (j / Ns) * Ns * R + k;
+        const int base = jq * Ns * R + k;
 #pragma unroll
         for (int t = 0; t < R; ++t) out[(base + t * Ns) * ld + l] = a[t];
     }
@@ -239,14 +254,16 @@ __device__ cplx<T>* fft_tile(cplx<T>* a, cplx<T>* b, const FFTPlan& p, const cpl
     cplx<T>* out = b;
     for (int s = 0; s < p.nst; ++s) {
         const cplx<T>* t = tw + p.twoff[s];
+        const int Ns = p.Ns[s];
+        const unsigned int mg = p.nsmag[s];
         switch (p.R[s]) {
-            case 16: stockham_stage<T, 16, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
-            case 8: stockham_stage<T, 8, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
-            case 4: stockham_stage<T, 4, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
-            case 2: stockham_stage<T, 2, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
-            case 3: stockham_stage<T, 3, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
-            case 5: stockham_stage<T, 5, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
-            default: stockham_stage<T, 7, INV>(in, out, p.L, p.Ns[s], nl, ld, t); break;
+            case 16: stockham_stage<T, 16, INV>(in, out, p.L, Ns, mg, nl, ld, t); break;
+            case 8: stockham_stage<T, 8, INV>(in, out, p.L, Ns, mg, nl, ld, t); break;
+            case 4: stockham_stage<T, 4, INV>(in, out, p.L, Ns, mg, nl, ld, t); break;
+            case 2: stockham_stage<T, 2, INV>(in, out, p.L, Ns, mg, nl, ld, t); break;
+            case 3: stockham_stage<T, 3, INV>(in, out, p.L, Ns, mg, nl, ld, t); break;
+            case 5: stockham_stage<T, 5, INV>(in, out, p.L, Ns, mg, nl, ld, t); break;
+            default: stockham_stage<T, 7, INV>(in, out, p.L, Ns, mg, nl, ld, t); break;
         }
         __syncthreads();
         cplx<T>* tmp = in;

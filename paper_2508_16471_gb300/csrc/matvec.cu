@@ -50,6 +50,12 @@ bool make_plan(int L, FFTPlan* p) {
     }
     if (r != 1) return false;
     p->twlen = off;
+    // multiply-high divisors (exact for x d < 2^32; here x < 2^18 and d <= 8192)
+    auto mag = [](int d) -> unsigned int {
+        return d <= 1 ? 0u : (unsigned int)((((unsigned long long)1 << 32) + (unsigned long long)d - 1) / d);
+    };
+    for (int s = 0; s < p->nst; ++s) p->nsmag[s] = mag(p->Ns[s]);
+    p->lmag = mag(L);
     return true;
 }
 
@@ -138,6 +144,10 @@ int op_init_axes(Operator& op) {
 // kernels
 // ---------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ cplx<T> czero() { return cplx<T>{(T)0, (T)0}; }
+// multiply-high constant of a runtime divisor d >= 1 (div_mag(x, d, .) exact for x d < 2^32)
+__device__ __forceinline__ unsigned int mag_of(int d) {
+    return d <= 1 ? 0u : (unsigned int)((0x100000000ull + (unsigned long long)d - 1) / (unsigned long long)d);
+}
 
 // Generic contiguous lines: in [count][n_in] -> out [count][n_out], length L.
 // Twiddles: staged in shared memory when `stw`, else read from `twg` directly.
@@ -168,7 +178,7 @@ __global__ void k_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_
     cplx<T>* bB = bA + L * ld;
     const long long line0 = (long long)blockIdx.x * NL;
     for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
-        const int l = e / L, p = e - (e / L) * L;
+        const int l = div_mag(e, L, plan.lmag), p = e - l * L;
         const long long line = line0 + l;
         cplx<T> v = czero<T>();
         if (line < count && p < n_in) v = in[line * n_in + p];
@@ -176,8 +186,9 @@ __global__ void k_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_
     }
     __syncthreads();
     cplx<T>* r = fft_tile<T, INV>(bA, bB, plan, tw, NL, ld);
+    const unsigned int omag = mag_of(n_out);
     for (int e = threadIdx.x; e < NL * n_out; e += blockDim.x) {
-        const int l = e / n_out, p = e - l * n_out;
+        const int l = div_mag(e, n_out, omag), p = e - l * n_out;
         const long long line = line0 + l;
         if (line < count) out[line * n_out + p] = r[p * ld + l];
     }
@@ -195,8 +206,9 @@ __global__ void k_axis(const cplx<T>* in, cplx<T>* out, long long inner, int n_i
     const long long ntile = (inner + TW - 1) / TW;
     const long long o = blockIdx.x / ntile;
     const long long i0 = (blockIdx.x - o * ntile) * TW;
+    const int twsh = log2_p2(TW);
     for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
-        const int p = e / TW, t = e - (e / TW) * TW;
+        const int p = e >> twsh, t = e & (TW - 1);
         cplx<T> v = czero<T>();
         if (p < n_in && i0 + t < inner) v = in[(o * n_in + p) * inner + i0 + t];
         bA[p * TW + t] = v;
@@ -204,7 +216,7 @@ __global__ void k_axis(const cplx<T>* in, cplx<T>* out, long long inner, int n_i
     __syncthreads();
     cplx<T>* r = fft_tile<T, INV>(bA, bB, plan, tw, TW, TW);
     for (int e = threadIdx.x; e < n_out * TW; e += blockDim.x) {
-        const int p = e / TW, t = e - (e / TW) * TW;
+        const int p = e >> twsh, t = e & (TW - 1);
         if (i0 + t < inner) out[(o * n_out + p) * inner + i0 + t] = r[p * TW + t];
     }
 }
@@ -224,7 +236,7 @@ __global__ void k_zfwd(const cplx<T>* __restrict__ w, long long w_rstride, const
     const long long line0 = (long long)blockIdx.x * NL;
     const long long plane = (long long)n0 * n1;
     for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
-        const int l = e / L, p = e - (e / L) * L;
+        const int l = div_mag(e, L, plan.lmag), p = e - l * L;
         const long long line = line0 + l;
         cplx<T> v = czero<T>();
         if (line < nlines && p < n2) {
@@ -239,7 +251,7 @@ __global__ void k_zfwd(const cplx<T>* __restrict__ w, long long w_rstride, const
     __syncthreads();
     cplx<T>* r = fft_tile<T, false>(bA, bB, plan, tw, NL, ld);
     for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
-        const int l = e / L, p = e - l * L;
+        const int l = div_mag(e, L, plan.lmag), p = e - l * L;
         const long long line = line0 + l;
         if (line < nlines) A[line * L + p] = r[p * ld + l];
     }
@@ -261,7 +273,7 @@ __global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict_
     const long long line0 = (long long)blockIdx.x * NL;
     const long long plane = (long long)n0 * n1;
     for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
-        const int l = e / L, p = e - (e / L) * L;
+        const int l = div_mag(e, L, plan.lmag), p = e - l * L;
         const long long line = line0 + l;
         cplx<T> v = czero<T>();
         if (line < nlines) v = A[line * L + p];
@@ -269,8 +281,9 @@ __global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict_
     }
     __syncthreads();
     cplx<T>* r = fft_tile<T, true>(bA, bB, plan, tw, NL, ld);
+    const unsigned int n2mag = mag_of(n2);
     for (int e = threadIdx.x; e < NL * n2; e += blockDim.x) {
-        const int l = e / n2, p = e - l * n2;
+        const int l = div_mag(e, n2, n2mag), p = e - l * n2;
         const long long line = line0 + l;
         if (line >= nlines) continue;
         const long long sc = line / plane;
@@ -305,10 +318,10 @@ __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int 
     const long long slot = blockIdx.x / ntile;
     const long long i0 = (blockIdx.x - slot * ntile) * TW;
     cplx<T>* base = B + slot * 3 * (long long)n0 * inner;
+    const int twsh = log2_p2(TW);
     for (int e = threadIdx.x; e < 3 * L * TW; e += blockDim.x) {
-        const int c = e / (L * TW);
-        const int q = e - c * (L * TW);
-        const int p = q / TW, t = q - (q / TW) * TW;
+        const int cp = e >> twsh, t = e & (TW - 1);  // cp = c L + p
+        const int c = div_mag(cp, L, plan.lmag), p = cp - c * L;
         cplx<T> v = czero<T>();
         if (p < n0 && i0 + t < inner) v = base[((long long)c * n0 + p) * inner + i0 + t];
         D[c][p * TW + t] = v;
@@ -323,13 +336,15 @@ __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int 
             cur[c] = r;
         }
     }
-    // spectral multiply
+    // spectral multiply (a thread keeps its column: blockDim is a multiple of TW)
     const long long HH = (long long)H0 * H1 * H2;
+    const long long iic = i0 + (threadIdx.x & (TW - 1));
+    const int kyc = (int)(iic / P2), kzc = (int)(iic - (iic / P2) * P2);
     for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
-        const int p = e / TW, t = e - (e / TW) * TW;
-        const long long ii = i0 + t;
+        const int p = e >> twsh;
+        const long long ii = iic;
         if (ii >= inner) continue;
-        const int ky = (int)(ii / P2), kz = (int)(ii - (ii / P2) * P2);
+        const int ky = kyc, kz = kzc;
         const int kx = p;
         const bool flx = 2 * kx > P0, fly = 2 * ky > P1, flz = 2 * kz > P2;
         const int fx = flx ? P0 - kx : kx, fy = fly ? P1 - ky : ky, fz = flz ? P2 - kz : kz;
@@ -365,10 +380,10 @@ __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int 
             cur[c] = r;
         }
     }
+    const unsigned int n0mag = mag_of(n0);
     for (int e = threadIdx.x; e < 3 * n0 * TW; e += blockDim.x) {
-        const int c = e / (n0 * TW);
-        const int q = e - c * (n0 * TW);
-        const int p = q / TW, t = q - (q / TW) * TW;
+        const int cp = e >> twsh, t = e & (TW - 1);  // cp = c n0 + p
+        const int c = div_mag(cp, n0, n0mag), p = cp - c * n0;
         if (i0 + t < inner) base[((long long)c * n0 + p) * inner + i0 + t] = cur[c][p * TW + t];
     }
 }
