@@ -598,6 +598,24 @@ template <typename KernelT> static int allow_smem(KernelT k) {
     return VIE_OK;
 }
 
+// Threads per CTA of a generic FFT pass.  Short transforms keep 256.  Transforms
+// longer than 1024 points hold one or two lines per CTA, so the CTA is widened
+// to as many threads as the register file allows for the CTAs that fit by
+// shared memory (at most 512): more warps hide the stage barriers and each
+// stage takes fewer sequential butterflies per thread.
+template <typename KernelT> static int fft_threads(KernelT k, int L, size_t smem) {
+    if (L <= 1024) return 256;
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, k) != cudaSuccess || a.numRegs <= 0) {
+        cudaGetLastError();
+        return 256;
+    }
+    const int ctas = std::max(1, (int)((227 * 1024) / std::max<size_t>(smem + 1024, 1)));
+    int t = 65536 / (ctas * a.numRegs);
+    t = std::min(512, std::min(a.maxThreadsPerBlock, t)) / 32 * 32;
+    return std::max(256, t);
+}
+
 static int pow2_floor(int v) {
     int p = 1;
     while (p * 2 <= v) p *= 2;
@@ -689,7 +707,8 @@ static int launch_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_
     if (!c.ok) return fail(VIE_EINVAL, "FFT length " + std::to_string(p.L) + " does not fit in shared memory");
     const long long grid = (count + c.w - 1) / c.w;
     if (grid <= 0) return VIE_OK;
-    k_lines<T, INV><<<(unsigned)grid, 256, c.smem, s>>>(in, out, count, n_in, n_out, p, tw, c.w, c.stw);
+    const int nt = fft_threads(k_lines<T, INV>, p.L, c.smem);
+    k_lines<T, INV><<<(unsigned)grid, nt, c.smem, s>>>(in, out, count, n_in, n_out, p, tw, c.w, c.stw);
     count_launch();
     VIE_CUDA(cudaGetLastError());
     return VIE_OK;
@@ -708,8 +727,9 @@ static int launch_axis(const cplx<T>* in, cplx<T>* out, long long outer, int n_i
     if (!c.ok) return fail(VIE_EINVAL, "FFT length " + std::to_string(p.L) + " does not fit in shared memory");
     const long long grid = outer * ((inner + c.w - 1) / c.w);
     if (grid <= 0) return VIE_OK;
+    const int nt = fft_threads(k_axis<T, INV>, p.L, c.smem);
     tmr_begin(tid, s);
-    k_axis<T, INV><<<(unsigned)grid, 256, c.smem, s>>>(in, out, inner, n_in, n_out, p, tw, c.w, c.stw);
+    k_axis<T, INV><<<(unsigned)grid, nt, c.smem, s>>>(in, out, inner, n_in, n_out, p, tw, c.w, c.stw);
     tmr_end(tid, s, bytes);
     count_launch();
     VIE_CUDA(cudaGetLastError());
@@ -969,8 +989,9 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             const FFTPlan& p = op.ax[2].plan;
             const TileCfg c = lines_cfg<T>(p);
             const long long nlines = (long long)ns * 3 * n0 * n1;
+            const int nt = fft_threads(k_zfwd<T>, p.L, c.smem);
             tmr_begin(tid(TMR_ZFWD), op.stream);
-            k_zfwd<T><<<(unsigned)((nlines + c.w - 1) / c.w), 256, c.smem, op.stream>>>(
+            k_zfwd<T><<<(unsigned)((nlines + c.w - 1) / c.w), nt, c.smem, op.stream>>>(
                 w, wr, list, op.idx_map, A, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), c.w, c.stw,
                 op.idx_stride);
             tmr_end(tid(TMR_ZFWD), op.stream, ns * (vec + lineA) + 4.0 * op.N);
@@ -1039,8 +1060,9 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             const FFTPlan& p = op.ax[2].plan;
             const TileCfg c = lines_cfg<T>(p);
             const long long nlines = (long long)ns * 3 * n0 * n1;
+            const int nt = fft_threads(k_zinv<T>, p.L, c.smem);
             tmr_begin(tid(TMR_ZINV), op.stream);
-            k_zinv<T><<<(unsigned)((nlines + c.w - 1) / c.w), 256, c.smem, op.stream>>>(
+            k_zinv<T><<<(unsigned)((nlines + c.w - 1) / c.w), nt, c.smem, op.stream>>>(
                 A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), c.w,
                 op.chi_cs, c.stw, op.idx_stride);
             tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
