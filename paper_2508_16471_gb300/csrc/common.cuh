@@ -24,6 +24,25 @@ template <typename T> __host__ __device__ __forceinline__ cplx<T> operator+(cplx
 template <typename T> __host__ __device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) {
     return {a.x - b.x, a.y - b.y};
 }
+// FP32 complex sums and differences as one packed FP32x2 instruction on the
+// device (round to nearest, the same result per part as two scalar adds).
+__host__ __device__ __forceinline__ cplx<float> operator+(cplx<float> a, cplx<float> b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    return {r.x, r.y};
+#else
+    return {a.x + b.x, a.y + b.y};
+#endif
+}
+__host__ __device__ __forceinline__ cplx<float> operator-(cplx<float> a, cplx<float> b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    // a - b = fma(b, -1, a): exact negation, one rounding
+    const float2 r = __ffma2_rn(make_float2(b.x, b.y), make_float2(-1.0f, -1.0f), make_float2(a.x, a.y));
+    return {r.x, r.y};
+#else
+    return {a.x - b.x, a.y - b.y};
+#endif
+}
 template <typename T> __host__ __device__ __forceinline__ cplx<T> operator*(cplx<T> a, cplx<T> b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
