@@ -43,17 +43,6 @@ __host__ __device__ __forceinline__ cplx<float> operator-(cplx<float> a, cplx<fl
     return {a.x - b.x, a.y - b.y};
 #endif
 }
-// FP32 complex product as two packed instructions: (a.x b.x, a.x b.y), then
-// + (-a.y b.y, a.y b.x) fused (the same roundings as a contracted scalar form).
-__host__ __device__ __forceinline__ cplx<float> operator*(cplx<float> a, cplx<float> b) {
-#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
-    const float2 t = __fmul2_rn(make_float2(a.x, a.x), make_float2(b.x, b.y));
-    const float2 r = __ffma2_rn(make_float2(-a.y, a.y), make_float2(b.y, b.x), t);
-    return {r.x, r.y};
-#else
-    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-#endif
-}
 template <typename T> __host__ __device__ __forceinline__ cplx<T> operator*(cplx<T> a, cplx<T> b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
