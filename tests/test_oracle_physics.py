@@ -267,3 +267,36 @@ def test_na_rule_pins():
     f = lambda d: np.exp(1j * 3.0 * (d @ np.array([1.0, 2.0, -0.5])))
     d0, W0 = vie.na_rule(c, 1e-4, 1.0, 4, 8)
     assert abs(np.sum(W0 * f(d0)) - f(c[None])[0]) < 1e-6
+
+
+def test_axis_swap_covariance_of_circular_amplitudes():
+    """The paper-scale grid is stored with the x and z axes swapped (a
+    reflection).  Solving a chiral body in the swapped frame, with incidence,
+    polarisation and directions mapped by the same swap, and mapping the far
+    field back must give the paper-frame circular amplitudes (Eq. 30) exactly:
+    the dyadic kernel is covariant under any orthogonal map.  A handedness
+    slip (recomputing the circular basis in the swapped frame) fails this."""
+    n = (6, 5, 7)
+    h = 0.08
+    rng = np.random.default_rng(31)
+    eps = np.where(rng.uniform(size=n) < 0.5, rng.uniform(1.5, 4.0, n), 1.0)  # no mirror symmetry
+    chs = [(c.khat, c.pol) for c in inputs.channels_metasurface([10.0])]      # L, R
+    deg = np.array([-25.0, -10.0, 0.0, 10.0, 25.0])
+    t = np.radians(deg)
+    d_p = np.stack([np.sin(t), np.zeros_like(t), np.cos(t)], -1)
+    W, _ = vie.solve_channels(n, h, K0, eps, chs, method="lu")
+    F_p = np.stack([vie.farfield(W[r], n, h, K0, d_p) for r in range(2)])
+    # the same problem on the swapped grid
+    eps_g = np.ascontiguousarray(np.transpose(eps, inputs.PAPER_AXES))
+    n_g = eps_g.shape
+    chs_g = [(inputs.to_grid_frame(k), inputs.to_grid_frame(p)) for k, p in chs]
+    W_g, _ = vie.solve_channels(n_g, h, K0, eps_g, chs_g, method="lu")
+    F_g = np.stack([vie.farfield(W_g[r], n_g, h, K0, inputs.to_grid_frame(d_p)) for r in range(2)])
+    F_back = inputs.to_grid_frame(F_g)
+    assert np.abs(F_back - F_p).max() <= 1e-10 * np.abs(F_p).max()
+    # circular amplitudes in the paper frame agree; in the swapped frame's own basis they do not
+    C_p = np.stack([vie.project(F_p[r], d_p, 2) for r in range(2)])
+    C_b = np.stack([vie.project(F_back[r], d_p, 2) for r in range(2)])
+    assert np.abs(C_b - C_p).max() <= 1e-10 * np.abs(C_p).max()
+    C_wrong = np.stack([vie.project(F_g[r], inputs.to_grid_frame(d_p), 2) for r in range(2)])
+    assert np.abs(C_wrong - C_p).max() > 1e-3 * np.abs(C_p).max()
