@@ -488,6 +488,21 @@ def run_ours(args):
     return 0
 
 
+def circular_components(F, deg):
+    """(E_L, E_R) = (E_theta +/- i E_phi)/sqrt2 (Eq. 30) of far fields F [R][D][3]
+    (paper frame) at signed angles ``deg`` in the xz-plane (phi = 0 for
+    theta >= 0, 180 deg below); returns [R][D][2]."""
+    import numpy as np
+    from paper_2508_16471_gb300 import inputs
+    circ = np.zeros(F.shape[:2] + (2,), dtype=np.complex128)
+    for i, th in enumerate(np.radians(np.asarray(deg, float))):
+        _, et, ep = inputs.spherical_basis(abs(th), 0.0 if th >= 0 else math.pi)
+        Et, Ep = F[:, i] @ et, F[:, i] @ ep
+        circ[:, i, 0] = (Et + 1j * Ep) / math.sqrt(2.0)
+        circ[:, i, 1] = (Et - 1j * Ep) / math.sqrt(2.0)
+    return circ
+
+
 def run_metasurface_paper(args):
     """The PB metasurface of Sec. III-B at the paper's scale: 40 x 12 x 2
     wavelengths at 62 cells per wavelength (2480 x 744 x 124 cells, 92 x 27
@@ -622,12 +637,7 @@ def run_metasurface_paper(args):
     t = np.radians(deg)
     d_p = np.stack([np.sin(t), np.zeros_like(t), np.cos(t)], -1)
     F = inputs.to_grid_frame(hd.farfield_dirs(inputs.to_grid_frame(d_p), basis=V.BASIS_CART))  # [2][D][3]
-    circ = np.zeros((2, len(deg), 2), dtype=np.complex128)  # (E_L, E_R), Eq. 30
-    for i, th in enumerate(t):
-        _, et, ep = inputs.spherical_basis(abs(th), 0.0 if th >= 0 else math.pi)
-        Et, Ep = F[:, i] @ et, F[:, i] @ ep
-        circ[:, i, 0] = (Et + 1j * Ep) / math.sqrt(2.0)
-        circ[:, i, 1] = (Et - 1j * Ep) / math.sqrt(2.0)
+    circ = circular_components(F, deg)
     s2 = math.sqrt(2.0)
     H = (circ[0] + circ[1]) / s2          # Eq. 28 inverted: H = (L + R)/sqrt2
     Vv = (circ[0] - circ[1]) / (1j * s2)  # V = (L - R)/(i sqrt2)

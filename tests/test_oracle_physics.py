@@ -300,3 +300,20 @@ def test_axis_swap_covariance_of_circular_amplitudes():
     assert np.abs(C_b - C_p).max() <= 1e-10 * np.abs(C_p).max()
     C_wrong = np.stack([vie.project(F_g[r], inputs.to_grid_frame(d_p), 2) for r in range(2)])
     assert np.abs(C_wrong - C_p).max() > 1e-3 * np.abs(C_p).max()
+
+
+def test_bench_circular_projection_matches_eq30():
+    """The paper-scale bench mode takes the circular components (Eq. 30) of
+    paper-frame far fields itself; they must equal the oracle's projection
+    onto (E_L, E_R) at the same signed xz-plane directions."""
+    import bench
+    rng = np.random.default_rng(4)
+    deg = np.arange(-30.0, 30.0 + 1e-9, 7.5)
+    t = np.radians(deg)
+    d = np.stack([np.sin(t), np.zeros_like(t), np.cos(t)], -1)
+    F = rng.standard_normal((2, len(deg), 3)) + 1j * rng.standard_normal((2, len(deg), 3))
+    F = F - d[None] * np.sum(F * d[None], axis=-1, keepdims=True)  # transverse
+    got = bench.circular_components(F, deg)
+    for r in range(2):
+        ref = vie.project(F[r], d, 2)[:, :2]
+        assert np.abs(got[r] - ref).max() <= 1e-13 * np.abs(ref).max()
