@@ -396,6 +396,15 @@ int vie_guesses_rejected(const vie_handle* hd);
  * block.  Set up again after every change of the body (vie_set_eps drops it).
  * D1 only.  Errors: VIE_EINVAL (cuts, iterations, D2), VIE_ENOMEM. */
 int vie_set_block_precond(vie_handle* hd, const int* cuts, const int ncuts[3], int inner_iters);
+/* The block layout alone, on the host (no device work): for a grid n, body
+ * voxels vox[n_body] (increasing C-order linear indices) and the cuts of
+ * vie_set_block_precond, box_out = the block box (largest cropped extent per
+ * axis), *blocks_out = non-empty blocks; map_out, when not NULL, receives
+ * [blocks][box0][box1][box2] compact body indices (-1 where a block has no
+ * voxel) and must hold blocks x box0 x box1 x box2 ints (call once with NULL
+ * to size it).  Errors: VIE_EINVAL. */
+int vie_block_layout(const int n[3], const int* vox, long long n_body, const int* cuts, const int ncuts[3],
+                     int box_out[3], int* blocks_out, int* map_out);
 /* y = A_bd w for one FP32 compact vector [3][n_body] (device, float2); for
  * checks of the block operator.  Enqueued on the handle's stream. */
 int vie_block_apply_device(vie_handle* hd, const void* w_dev, void* y_dev);

@@ -821,6 +821,18 @@ int vie_set_block_precond(vie_handle* hd, const int* cuts, const int ncuts[3], i
     return block_precond_setup(hd->op, hd->bpc, cuts ? cuts : &none, ncuts, inner_iters);
 }
 
+int vie_block_layout(const int n[3], const int* vox, long long n_body, const int* cuts, const int ncuts[3],
+                     int box_out[3], int* blocks_out, int* map_out) {
+    if (!n || !ncuts || !box_out || !blocks_out || (n_body > 0 && !vox) || n_body < 0 ||
+        (!cuts && ncuts[0] + ncuts[1] + ncuts[2] > 0))
+        return fail(VIE_EINVAL, "NULL or negative argument");
+    static const int none = 0;
+    std::vector<int> map;
+    VIE_TRY(block_layout(n, vox, n_body, cuts ? cuts : &none, ncuts, box_out, blocks_out, map_out ? &map : nullptr));
+    if (map_out) std::copy(map.begin(), map.end(), map_out);
+    return VIE_OK;
+}
+
 int vie_block_apply_device(vie_handle* hd, const void* w_dev, void* y_dev) {
     if (!hd || !w_dev || !y_dev) return fail(VIE_EINVAL, "NULL argument");
     VIE_CUDA(cudaSetDevice(hd->device));

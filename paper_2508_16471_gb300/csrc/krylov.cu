@@ -1674,36 +1674,36 @@ void BlockPrecond::release(Operator& op) {
     n3 = 0;
 }
 
-int block_precond_setup(Operator& op, BlockPrecond& bp, const int* cuts, const int ncuts[3], int iters) {
-    if (op.disc) return fail(VIE_EINVAL, "the block preconditioner supports the D1 discretisation only");
-    if (iters < 1 || iters > 1000) return fail(VIE_EINVAL, "inner iterations must be in 1..1000");
+int block_layout(const int n[3], const int* vox, long long Nb, const int* cuts, const int ncuts[3], int box[3],
+                 int* T_out, std::vector<int>* map) {
     // tile index of every coordinate along each axis (number of cuts at or below it)
     std::vector<int> tix[3];
     int nt[3];
     const int* c = cuts;
     for (int a = 0; a < 3; ++a) {
+        if (n[a] < 1) return fail(VIE_EINVAL, "grid size must be positive");
         if (ncuts[a] < 0) return fail(VIE_EINVAL, "negative cut count");
         for (int i = 0; i < ncuts[a]; ++i)
-            if (c[i] <= 0 || c[i] >= op.n[a] || (i > 0 && c[i] <= c[i - 1]))
+            if (c[i] <= 0 || c[i] >= n[a] || (i > 0 && c[i] <= c[i - 1]))
                 return fail(VIE_EINVAL, "cuts must increase strictly inside (0, n) on each axis");
-        tix[a].assign(op.n[a], 0);
-        for (int x = 0, t = 0; x < op.n[a]; ++x) {
+        tix[a].assign(n[a], 0);
+        for (int x = 0, t = 0; x < n[a]; ++x) {
             while (t < ncuts[a] && c[t] <= x) ++t;
             tix[a][x] = t;
         }
         nt[a] = ncuts[a] + 1;
         c += ncuts[a];
     }
-    const long long Nb = op.Nb;
-    std::vector<int> vox(Nb);
-    VIE_CUDA(cudaMemcpy(vox.data(), op.vox, sizeof(int) * Nb, cudaMemcpyDeviceToHost));
     const long long ntt = (long long)nt[0] * nt[1] * nt[2];
     if (ntt > (1LL << 24)) return fail(VIE_EINVAL, "too many blocks");
+    const long long N = (long long)n[0] * n[1] * n[2];
     std::vector<int> lo(3 * ntt, 1 << 30), hi(3 * ntt, -1), tid(Nb);
-    const long long n12 = (long long)op.n[1] * op.n[2];
+    const long long n12 = (long long)n[1] * n[2];
     for (long long v = 0; v < Nb; ++v) {
         const long long lin = vox[v];
-        const int i = (int)(lin / n12), j = (int)((lin / op.n[2]) % op.n[1]), k = (int)(lin % op.n[2]);
+        if (lin < 0 || lin >= N || (v > 0 && lin <= vox[v - 1]))
+            return fail(VIE_EINVAL, "body voxels must be increasing linear indices inside the grid");
+        const int i = (int)(lin / n12), j = (int)((lin / n[2]) % n[1]), k = (int)(lin % n[2]);
         const long long t = ((long long)tix[0][i] * nt[1] + tix[1][j]) * nt[2] + tix[2][k];
         tid[v] = (int)t;
         const int xyz[3] = {i, j, k};
@@ -1714,22 +1714,37 @@ int block_precond_setup(Operator& op, BlockPrecond& bp, const int* cuts, const i
     }
     std::vector<int> slot(ntt, -1);
     int T = 0;
-    int box[3] = {1, 1, 1};
+    for (int a = 0; a < 3; ++a) box[a] = 1;
     for (long long t = 0; t < ntt; ++t)
         if (hi[3 * t] >= 0) {
             slot[t] = T++;
             for (int a = 0; a < 3; ++a) box[a] = std::max(box[a], hi[3 * t + a] - lo[3 * t + a] + 1);
         }
+    *T_out = T;
     const long long G = (long long)box[0] * box[1] * box[2];
     if ((double)G * T > 2e9) return fail(VIE_EINVAL, "block voxel maps too large");
-    std::vector<int> map((size_t)(G * T), -1);
+    if (!map) return VIE_OK;
+    map->assign((size_t)(G * T), -1);
     for (long long v = 0; v < Nb; ++v) {
         const long long lin = vox[v];
-        const int i = (int)(lin / n12), j = (int)((lin / op.n[2]) % op.n[1]), k = (int)(lin % op.n[2]);
+        const int i = (int)(lin / n12), j = (int)((lin / n[2]) % n[1]), k = (int)(lin % n[2]);
         const long long t = tid[v];
         const long long loc = ((long long)(i - lo[3 * t]) * box[1] + (j - lo[3 * t + 1])) * box[2] + (k - lo[3 * t + 2]);
-        map[(size_t)(slot[t] * G + loc)] = (int)v;
+        (*map)[(size_t)(slot[t] * G + loc)] = (int)v;
     }
+    return VIE_OK;
+}
+
+int block_precond_setup(Operator& op, BlockPrecond& bp, const int* cuts, const int ncuts[3], int iters) {
+    if (op.disc) return fail(VIE_EINVAL, "the block preconditioner supports the D1 discretisation only");
+    if (iters < 1 || iters > 1000) return fail(VIE_EINVAL, "inner iterations must be in 1..1000");
+    const long long Nb = op.Nb;
+    std::vector<int> vox(Nb);
+    VIE_CUDA(cudaMemcpy(vox.data(), op.vox, sizeof(int) * Nb, cudaMemcpyDeviceToHost));
+    int box[3], T = 0;
+    std::vector<int> map;
+    VIE_TRY(block_layout(op.n, vox.data(), Nb, cuts, ncuts, box, &T, &map));
+    const long long G = (long long)box[0] * box[1] * box[2];
     bp.release(op);
     Operator& b = bp.bop;
     for (int a = 0; a < 3; ++a) {

@@ -47,6 +47,11 @@ struct BlockPrecond {
     long long n3 = 0;
     void release(Operator& op);
 };
+// Host part: blocks of the tiling given by `cuts` (ncuts[a] interior cuts on axis a), each cropped to the box
+// of its body voxels (vox: increasing linear indices); box = the largest extent per axis; T = non-empty
+// blocks; map (optional) [T][box voxels] = compact index or -1.
+int block_layout(const int n[3], const int* vox, long long Nb, const int* cuts, const int ncuts[3], int box[3],
+                 int* T, std::vector<int>* map);
 int block_precond_setup(Operator& op, BlockPrecond& bp, const int* cuts, const int ncuts[3], int iters);
 // y = A_bd w for one FP32 compact vector
 int block_apply(Operator& op, BlockPrecond& bp, const c32* w, c32* y);

@@ -30,7 +30,7 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_guesses_rejected",
            "vie_net_create_io", "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune",
            "vie_setup_disc", "vie_farfield_na", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count",
-           "vie_set_block_precond", "vie_block_apply_device"]
+           "vie_set_block_precond", "vie_block_apply_device", "vie_block_layout"]
 
 
 class VieError(RuntimeError):
@@ -120,6 +120,8 @@ def load():
     L.vie_set_farfield_engine.argtypes = [P, C.c_int]
     L.vie_set_block_precond.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]
     L.vie_block_apply_device.argtypes = [P, P, P]
+    L.vie_block_layout.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_longlong, C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.vie_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int]
     L.vie_kernel_launches.restype = C.c_longlong
     L.vie_stream.argtypes = [P]
@@ -143,7 +145,7 @@ def load():
               "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
               "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_net_create_io",
               "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune", "vie_setup_disc",
-              "vie_farfield_na", "vie_set_block_precond", "vie_block_apply_device"]:
+              "vie_farfield_na", "vie_set_block_precond", "vie_block_apply_device", "vie_block_layout"]:
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -508,6 +510,23 @@ def cgemm(A, B, engine=0):
     _check(load().vie_cgemm(M, N, K, _dptr(a.view(np.float64)), _dptr(b.view(np.float64)),
                             c.ctypes.data_as(C.POINTER(C.c_double)), int(engine)))
     return c
+
+
+def block_layout(n, vox, cuts=((), (), ())):
+    """Host-side block layout of vie_set_block_precond: (box, blocks, map[blocks][box0][box1][box2])."""
+    L = load()
+    nn = (C.c_int * 3)(*[int(v) for v in n])
+    vx = np.ascontiguousarray(vox, dtype=np.int32)
+    nc = (C.c_int * 3)(*[len(c) for c in cuts])
+    flat = [int(v) for c in cuts for v in c]
+    arr = (C.c_int * max(1, len(flat)))(*flat) if flat else None
+    box = (C.c_int * 3)()
+    T = C.c_int()
+    vp = vx.ctypes.data_as(C.POINTER(C.c_int))
+    _check(L.vie_block_layout(nn, vp, len(vx), arr, nc, box, C.byref(T), None))
+    m = np.zeros((T.value, box[0], box[1], box[2]), dtype=np.int32)
+    _check(L.vie_block_layout(nn, vp, len(vx), arr, nc, box, C.byref(T), m.ctypes.data_as(C.POINTER(C.c_int))))
+    return tuple(box), T.value, m
 
 
 def fft_lines(x, inverse=False, precision=PREC_FP64):
