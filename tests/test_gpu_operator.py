@@ -201,3 +201,34 @@ def test_first_axis_too_long_is_rejected(vielib):
     with pytest.raises(vielib.VieError) as e:
         vielib.Handle(n, 0.02, eps, K0)
     assert "first axis" in str(e.value)
+
+
+def test_apply_bench_launch_configuration_sampled(vielib):
+    """The bench's launch configuration: the 128^3 body, 32 RHS in one FP32
+    operator application (32 slots per fused-x launch, next-slot prefetch)
+    through the device layout; sampled voxels of the first, a middle and the
+    last RHS against the oracle's direct sum over all sources."""
+    import torch
+    wl = inputs.random_body_workload(20000, n_axis=128, h=1.0 / 128.0)
+    g = wl.grid
+    mask = wl.eps > 1.0
+    vox = np.flatnonzero(mask)
+    Nb = len(vox)
+    R = 32
+    rng = np.random.default_rng(77)
+    w = (rng.standard_normal((R, 3, Nb)) + 1j * rng.standard_normal((R, 3, Nb))).astype(np.complex64)
+    with vielib.Handle(g.n, g.h, wl.eps, K0) as hd:
+        wd = torch.from_numpy(w).cuda().contiguous()
+        yd = torch.full_like(wd, complex(float("nan"), 0.0))
+        hd.apply_device(wd.data_ptr(), yd.data_ptr(), R, vielib.PREC_MIXED)
+        torch.cuda.synchronize()
+        y = yd.cpu().numpy().astype(np.complex128)
+    assert np.isfinite(y).all()
+    picks = rng.choice(Nb, size=4, replace=False)
+    rr = [0, 17, 31]
+    src = np.stack(np.unravel_index(vox, g.n), -1)
+    conv = ovie.convolve_points_sparse(src, w[rr].astype(np.complex128), g.h, K0, src[picks])  # (3 rhs, 3, T)
+    chi = wl.eps.reshape(-1)[vox[picks]] - 1.0
+    for q, r in enumerate(rr):
+        ref = w[r][:, picks] - chi[None, :] * conv[q]
+        assert np.abs(y[r][:, picks] - ref).max() <= TOL32 * np.abs(ref).max(), r
