@@ -23,6 +23,12 @@ Reported on one JSON line (rank 0):
 
 Multi-GPU: replicas (each rank solves its own bodies, no collective on the
 data path), weak scaling.  ``--impl reference`` times the oracle instead.
+
+``--workload metasurface-paper`` prints a separate line for the PB metasurface
+of Sec. III-B at the paper's scale (or a ``--box`` piece of it): one batched
+solve of the L and R channels with ``--solver`` GMRES / BiCGStab / COCR and an
+optional block-Jacobi preconditioner (``--precond cells|blocks7``), the
+operator timings, and the far-field g_LR check of Eq. 31.
 """
 from __future__ import annotations
 
