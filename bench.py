@@ -15,14 +15,15 @@ Reported on one JSON line (rank 0):
   value        solved RHS per second, whole job (all ranks), device-resident inputs
   e2e          same through the host-buffer C ABI (eps upload, solve, far field
                at the two detector directions read back to the host)
-  plain_fp64   plain FP64 GMRES on the same body (subset of channels), for the
-               batched-mixed vs plain comparison
+  plain_fp64   plain FP64 GMRES on the first timed body, all 32 channels, next to
+               the mixed solver's time on exactly that body (speedup_vs_plain)
   roofline     live CUDA-event timing of the dominant kernel (library timer) vs
                the measured HBM copy bandwidth
   cpu_baseline the FP64 oracle timed on this host on a bounded sample
 
 Multi-GPU: replicas (each rank solves its own bodies, no collective on the
-data path), weak scaling.  ``--impl reference`` times the oracle instead.
+data path), weak scaling.  ``--impl reference`` runs one complete FP64 oracle
+solve on this host instead (RHS 0 of the first timed body, minutes).
 
 ``--workload metasurface-paper`` prints a separate line for the PB metasurface
 of Sec. III-B at the paper's scale (or a ``--box`` piece of it): one batched
@@ -66,7 +67,6 @@ def parse():
                    help="GMRES re-orthogonalisation threshold (second Gram-Schmidt pass when ||w'||^2 < eta ||w||^2)")
     p.add_argument("--inner-tol", type=float, default=1e-6,
                    help="mixed mode: relative residual reduction asked of each FP32 inner solve")
-    p.add_argument("--plain-rhs", type=int, default=4)
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-bicgstab", action="store_true",
                    help="skip the comparison solve with BiCGStab (the paper's solver) on the first timed body")
@@ -83,7 +83,7 @@ def parse():
     p.add_argument("--box", type=float, nargs=3, default=(40.0, 12.0, 2.0),
                    help="metasurface-paper: box in wavelengths (paper x, y, z)")
     p.add_argument("--solver", default="gmres", choices=["gmres", "bicgstab", "cocr"],
-                   help="metasurface-paper: inner Krylov solver")
+                   help="inner Krylov solver (the FP64 refinement around it is the same)")
     p.add_argument("--precond", default="none", choices=["none", "cells", "blocks7"],
                    help="metasurface-paper: block-Jacobi preconditioner over the fin unit cells or over 7 x 7 "
                         "lateral blocks (FGMRES)")
@@ -176,12 +176,7 @@ class ClockSampler:
 # --------------------------------------------------------------------------- #
 # oracle timing (CPU baseline and the reference arm)
 # --------------------------------------------------------------------------- #
-def oracle_sample(iters_per_solve, n_iter=3, seed=SEED0):
-    """Time the FP64 oracle on this host at the bench workload: operator setup
-    once, then ``n_iter`` GMRES iterations on one right-hand side.  Returns
-    (solves/s extrapolated to ``iters_per_solve`` iterations, details)."""
-    import numpy as np
-
+def _oracle_setup(seed):
     from oracle import vie as ovie
     from paper_2508_16471_gb300 import inputs
     wl = inputs.random_body_workload(seed, n_axis=N_AXIS, h=H, n_dirs=N_DIRS)
@@ -192,47 +187,76 @@ def oracle_sample(iters_per_solve, n_iter=3, seed=SEED0):
     t_setup = time.perf_counter() - t0
     c = wl.channels[0]
     b = ovie.rhs(chi, ovie.incident_field(g.n, g.h, wl.k0, c.khat, c.pol))
+    return ovie, op, b, t_setup
+
+
+def oracle_full_solve(seed, restart):
+    """One complete FP64 oracle solve (GMRES(restart) to 1e-6) of RHS 0 of the
+    bench body ``seed`` on this host: the measured wall time and iteration
+    count, nothing extrapolated."""
+    ovie, op, b, t_setup = _oracle_setup(seed)
     t0 = time.perf_counter()
-    ovie.gmres(op, b, tol=1e-6, restart=64, maxiter=n_iter)
+    _, info = ovie.gmres(op, b, tol=1e-6, restart=restart, maxiter=100000)
+    t = time.perf_counter() - t0
+    return dict(seconds=t, iters=int(info["iters"]), relres=float(info["relres"]),
+                converged=bool(info["converged"]), setup_s=t_setup, cores=os.cpu_count())
+
+
+def oracle_sample(iters, restart, n_iter=6, seed=SEED0):
+    """Bounded sample of the FP64 oracle at the bench workload: operator setup
+    once, ``n_iter`` GMRES iterations on RHS 0 of body ``seed`` (time t per
+    iteration at Krylov dimensions 1..n_iter), plus the time g of one
+    Gram-Schmidt projection (an inner product and an update over one basis
+    vector, the work GMRES adds per basis vector).  A solve of ``iters``
+    iterations with restart ``restart`` then costs
+        iters * t + g * (sum over its iterations of the Krylov dimension - the sample's mean),
+    which is returned as solves/s with the details."""
+    import numpy as np
+    ovie, op, b, t_setup = _oracle_setup(seed)
+    t0 = time.perf_counter()
+    ovie.gmres(op, b, tol=1e-6, restart=restart, maxiter=n_iter)
     t_it = (time.perf_counter() - t0) / n_iter
-    per_solve = t_it * iters_per_solve
-    return 1.0 / per_solve, dict(setup_s=t_setup, s_per_iter=t_it, iters_per_solve=iters_per_solve,
-                                 cores=os.cpu_count())
-
-
-# GMRES(64) iterations per solve on the timed bench bodies (seeds 20003-20006 at
-# the default --warmup 3): the mean measured on GB300 for the FP64 solver and the
-# mixed solver agree to within a few iterations; the reference arm, which cannot
-# run a full oracle solve in its time budget, extrapolates with this count.
-REF_ITERS = 70
+    v = b.reshape(-1) / np.linalg.norm(b)
+    w = v.copy()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        hcoef = np.vdot(v, w)
+        w = w - hcoef * v
+    g = (time.perf_counter() - t0) / reps
+    dims = [(i % restart) + 1 for i in range(iters)]
+    sample_mean = (n_iter + 1) / 2.0
+    per_solve = iters * t_it + g * (sum(dims) - iters * sample_mean)
+    return 1.0 / per_solve, dict(setup_s=t_setup, s_per_iter=t_it, s_per_projection=g, iters_per_solve=iters,
+                                 n_iter=n_iter, seconds_per_solve=per_solve, cores=os.cpu_count())
 
 
 def run_reference(args):
+    """The oracle arm: one complete FP64 oracle GMRES solve of RHS 0 of the
+    first timed bench body (the body our arm times first), measured end to end
+    on this host.  The oracle keeps no state between solves, so there is
+    nothing to warm up; one solve takes minutes, so the arm runs exactly one
+    and reports it (steps = 1)."""
     rank, world, local = dist_env()
     if rank != 0:
         return 0
-    iters = REF_ITERS
-    vals = []
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state beyond its setup, timed inside each step
-    t0 = time.perf_counter()
-    det = None
-    for _ in range(args.steps):
-        v, det = oracle_sample(iters, n_iter=2)
-        vals.append(v)
-    wall = time.perf_counter() - t0
-    value = sum(vals) / len(vals)
+    seed = body_seeds(0, args.bodies)[args.warmup % args.bodies]
+    r = oracle_full_solve(seed, args.restart)
+    value = (1.0 / r["seconds"]) if r["converged"] else 0.0
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(1, args.steps),
+            "steps": 1, "warmup": 0, "ms_per_step": 1000.0 * r["seconds"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"random bodies {N_AXIS}^3, h=lambda/128 (1 lambda box), {2 * N_DIRS} RHS/body",
+                       "solver": f"FP64 GMRES({args.restart}), modified Gram-Schmidt (oracle)",
                        "l2": "inputs larger than L2"},
-            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": det["cores"],
-                             "sample": (f"FP64 oracle (NumPy/SciPy FFT operator, GMRES) on body seed {SEED0}: "
-                                        f"setup {det['setup_s']:.1f}s + 2 GMRES iterations per step, "
-                                        f"{det['s_per_iter']:.2f} s/iteration, extrapolated to {iters} "
-                                        f"iterations per solve")},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": r["cores"],
+                             "sample": (f"one complete FP64 oracle solve (NumPy/SciPy FFT operator, GMRES("
+                                        f"{args.restart}) to 1e-6) of RHS 0 of body seed {seed}: {r['iters']} "
+                                        f"iterations, {r['seconds']:.1f} s, relres {r['relres']:.2e}; operator "
+                                        f"setup {r['setup_s']:.1f} s not timed; requested --steps "
+                                        f"{args.steps} --warmup {args.warmup} do not apply (one solve)")},
+            "oracle_iters": r["iters"],
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -294,6 +318,7 @@ def run_ours(args):
             dt, prec = (torch.complex128, V.PREC_FP64) if args.apply_fp64 else (torch.complex64, V.PREC_MIXED)
             w = torch.randn(args.apply_only, 3, nb, dtype=dt, device="cuda")
             y = torch.empty_like(w)
+            torch.cuda.synchronize()
             for _ in range(2):
                 hd0.apply_device(w.data_ptr(), y.data_ptr(), args.apply_only, prec)
             torch.cuda.synchronize()
@@ -313,10 +338,12 @@ def run_ours(args):
     R = len(chs)
     eps_dev = [torch.from_numpy(np.ascontiguousarray(w.eps)).cuda() for w in wls]
     eps_host = [torch.from_numpy(np.ascontiguousarray(w.eps)).pin_memory() for w in wls]
+    torch.cuda.synchronize()  # the library runs on the handle's own stream
     hd = V.Handle(g.n, g.h, wls[0].eps, wls[0].k0)
     stream = torch.cuda.ExternalStream(hd.stream())
+    solver = {"gmres": V.SOLVER_GMRES, "bicgstab": V.SOLVER_BICGSTAB, "cocr": V.SOLVER_COCR}[args.solver]
     opts = dict(tol=1e-6, restart=args.restart, precision=V.PREC_MIXED, max_iter=args.max_iter,
-                inner_tol=args.inner_tol, reorth_eta=args.reorth_eta, inner_floor=args.inner_floor)
+                inner_tol=args.inner_tol, reorth_eta=args.reorth_eta, inner_floor=args.inner_floor, solver=solver)
 
     def step(i):
         hd.set_eps_device(eps_dev[i % len(eps_dev)].data_ptr())
@@ -347,7 +374,7 @@ def run_ours(args):
         if t_first is None:
             t_first = time.perf_counter() - ts
         if first_iters is None:
-            first_iters = st["iters"][:args.plain_rhs].tolist()
+            first_iters = st["iters"].tolist()
             first_all_iters = st["iters"].tolist()
         solved += int(st["converged"])
         mv32 += int(st["matvecs32"])
@@ -391,23 +418,27 @@ def run_ours(args):
         e2e = {"value": solved_e2e / te, "unit": UNIT, "h2d_bytes_per_step": int(8 * g.size + 72 * R),
                "d2h_bytes_per_step": int(F.nbytes + 12 * R)}
 
-    # ---- plain FP64 GMRES on a subset (same body as step 0) ----------------
+    # ---- plain FP64 GMRES on the first timed body, all its RHS ---------------
+    # the same body and the same 32 channels that the first timed step solved in
+    # mixed precision (t_first), so the two times divide the same work
     plain = None
     b0 = args.warmup % len(eps_dev)  # the body of the first timed step
     if not args.no_plain and rank == 0:
         hd.set_eps_device(eps_dev[b0].data_ptr())
-        sub = chs[:args.plain_rhs]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = hd.solve(sub, allow_noconv=True, tol=1e-6, restart=args.restart, precision=V.PREC_FP64,
+        st = hd.solve(chs, allow_noconv=True, tol=1e-6, restart=args.restart, precision=V.PREC_FP64,
                       max_iter=args.max_iter)
         torch.cuda.synchronize()
         tp = time.perf_counter() - t0
-        plain = {"value": int(st["converged"]) / tp, "unit": UNIT, "rhs": len(sub),
+        plain = {"value": int(st["converged"]) / tp, "unit": UNIT, "rhs": R, "body_seed": seeds[b0],
+                 "subset": f"body seed {seeds[b0]} (the first timed step), all {R} RHS",
                  "converged": int(st["converged"]), "seconds": tp,
-                 "iters_mean": float(np.mean(st["iters"])), "precision": "f64",
-                 "mixed_iters_mean_same_rhs": float(np.mean(first_iters)) if first_iters else None,
-                 "body_seed": seeds[b0]}
+                 "iters_mean": float(np.mean(st["iters"])), "iters_rhs0": int(st["iters"][0]),
+                 "precision": "f64",
+                 "mixed_seconds_same_set": t_first,
+                 "mixed_iters_mean_same_set": float(np.mean(first_all_iters)) if first_all_iters else None,
+                 "speedup_same_set": (tp / t_first) if t_first else None}
 
     # ---- the paper's solver (BiCGStab) on the same body, same refinement ------
     bicg = None
@@ -458,13 +489,18 @@ def run_ours(args):
         return 0
     cpu = None
     if not args.no_cpu:
-        its = float(np.mean(iters)) if iters else 100.0
+        # iterations of the oracle's FP64 GMRES on RHS 0 of the first timed body: plain FP64 GMRES on the
+        # GPU runs the same algorithm on the same equations (same restart), so its count stands in for the
+        # oracle's (the reference arm runs that solve in full and reports its own count)
+        its = plain["iters_rhs0"] if plain else (int(round(float(np.mean(iters)))) if iters else 100)
         try:
-            v, det = oracle_sample(its, n_iter=2, seed=seeds[b0])
+            v, det = oracle_sample(its, args.restart, n_iter=6, seed=seeds[b0])
             cpu = {"value": v, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
-                   "sample": (f"FP64 oracle on body seed {seeds[b0]} ({N_AXIS}^3, 1 RHS): operator setup "
-                              f"{det['setup_s']:.1f}s, 2 GMRES iterations at {det['s_per_iter']:.2f} s each, "
-                              f"extrapolated to the GPU run's mean {its:.0f} inner iterations per solve")}
+                   "sample": (f"FP64 oracle on body seed {seeds[b0]} ({N_AXIS}^3, RHS 0): operator setup "
+                              f"{det['setup_s']:.1f}s, 6 GMRES iterations at {det['s_per_iter']:.2f} s each, "
+                              f"one Gram-Schmidt projection {det['s_per_projection'] * 1e3:.1f} ms; modelled "
+                              f"for a {its}-iteration GMRES({args.restart}) solve (the plain FP64 GPU solve's "
+                              f"count for that RHS): {det['seconds_per_solve']:.0f} s per solve")}
         except Exception as ex:  # pragma: no cover
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {ex}"}
@@ -475,12 +511,13 @@ def run_ours(args):
         "data": "synthetic (seeded random bodies)",
         "config": {"workload": f"random bodies {N_AXIS}^3, h=lambda/128 (1 lambda box), eps_r in [1.5,6], "
                                f"{R} RHS/body ({N_DIRS} Fibonacci directions x 2 pol), tol 1e-6",
-                   "solver": f"mixed FP32 matvec / FP64 Arnoldi GMRES({args.restart}) + FP64 refinement",
+                   "solver": (f"mixed FP32 matvec / FP64 Arnoldi GMRES({args.restart})" if args.solver == "gmres"
+                              else f"mixed FP32 matvec {args.solver.upper()}") + " + FP64 refinement",
                    "bodies_per_rank": args.bodies, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (no flush)"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         "roofline": roof, "matvec_fp32": matvec, "cpu_baseline": cpu, "plain_fp64": plain, "bicgstab": bicg,
-        "speedup_vs_plain": (value / plain["value"]) if plain and plain["value"] else None,
+        "speedup_vs_plain": plain["speedup_same_set"] if plain else None,
         "solver_stats": {"solved": tot_solved, "rhs_total": args.steps * R * world,
                          "iters_mean": float(np.mean(iters)) if iters else None,
                          "iters_max": int(max(iters)) if iters else None, "outer_max": max(outers) if outers else None,
@@ -544,6 +581,7 @@ def run_metasurface_paper(args):
     if args.apply_only:  # operator applications only (profiling)
         w = torch.randn(args.apply_only, 3, Nb, dtype=torch.complex64, device="cuda")
         y = torch.empty_like(w)
+        torch.cuda.synchronize()
         for _ in range(2):
             hd.apply_device(w.data_ptr(), y.data_ptr(), args.apply_only, V.PREC_MIXED)
         torch.cuda.synchronize()
@@ -553,6 +591,7 @@ def run_metasurface_paper(args):
     def time_apply(prec, dt, reps):
         w = torch.randn(1, 3, Nb, dtype=dt, device="cuda")
         y = torch.empty_like(w)
+        torch.cuda.synchronize()
         hd.apply_device(w.data_ptr(), y.data_ptr(), 1, prec)  # allocates the work arrays
         torch.cuda.synchronize()
         V.timer_reset()
@@ -582,6 +621,7 @@ def run_metasurface_paper(args):
     if t_pc is not None:
         w = torch.randn(3, Nb, dtype=torch.complex64, device="cuda")
         y = torch.empty_like(w)
+        torch.cuda.synchronize()
         hd.block_apply_device(w.data_ptr(), y.data_ptr())
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

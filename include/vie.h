@@ -54,6 +54,12 @@ extern "C" {
 #define VIE_PREC_MIXED 0 /* FP32 FFT matvec inside GMRES (FP64 Arnoldi and
                             Givens), iterative refinement on the FP64 residual  */
 #define VIE_PREC_FP64  1 /* plain FP64 GMRES(m): FP64 matvec and basis          */
+#define VIE_PREC_F32X2 2 /* operator only (vie_apply, vie_apply_device): FP64
+                            inputs and outputs, the FFTs, spectral multiply and
+                            contrast in double-float arithmetic (pairs of FP32
+                            numbers, ~2^-47 rounding; Knuth TwoSum and the FMA
+                            TwoProduct).  The mixed solver forms its residuals
+                            with this operator unless opts.resid_fp64 is set.   */
 
 /* ---- Krylov solvers (vie_solve_opts.solver) ----------------------------- */
 #define VIE_SOLVER_GMRES    0 /* batched restarted GMRES(m), CGS + selective reorth.  */
@@ -110,7 +116,11 @@ typedef struct vie_solve_opts {
                           (its 7 vectors use the basis storage), COCR restart >= 4
                           (5 vectors; restart has no other meaning for either);
                           both need use_x0 0 or 1 and precond 0                */
-    int reserved[1];
+    int resid_fp64;    /* mixed mode: 0 (default) forms the refinement residual
+                          b - A x with the double-float operator (VIE_PREC_F32X2,
+                          FP64 accuracy within a few 2^-47, several times faster
+                          on GB300, whose FP64 rate is 1/64 of FP32); 1 with the
+                          FP64 operator                                           */
     double reorth_eta; /* GMRES: a second classical Gram-Schmidt pass runs for an
                           RHS when the first left ||w'||^2 < reorth_eta ||w||^2
                           (Daniel-Gragg-Kaufman-Stewart test; default 0.1, i.e.
@@ -306,7 +316,7 @@ int vie_apply(vie_handle* hd, const double* w, double* y, int n_rhs, int precisi
 
 /* Device variant on the compact body-voxel layout: w_dev, y_dev are
  * [n_rhs][3][n_body] complex (float2 for VIE_PREC_MIXED, double2 for
- * VIE_PREC_FP64), body voxels in C order.  Enqueued on the handle's stream;
+ * VIE_PREC_FP64 and VIE_PREC_F32X2), body voxels in C order.  Enqueued on the handle's stream;
  * not synchronised. */
 int vie_apply_device(vie_handle* hd, const void* w_dev, void* y_dev, int n_rhs, int precision);
 
@@ -323,7 +333,10 @@ int vie_apply_device(vie_handle* hd, const void* w_dev, void* y_dev, int n_rhs, 
  * Limits: every padded size must be a power of two (16..512), and the
  * workspace of one RHS (3 n0 n1 P2 + 3 n0 P1 P2 complex64 words) must fit in
  * the array (grids up to 64^3 do); otherwise VIE_EINVAL, with the sizes in
- * vie_last_error().  The first call on each device looks up the array's device
+ * vie_last_error().  It always runs the register FFT passes: a handle set to
+ * the generic path (vie_set_fft_path(hd, 1)) is refused with VIE_EINVAL, as
+ * are D2 handles.  Like every entry point it makes the handle's device current
+ * (cudaSetDevice).  The first call on each device looks up the array's device
  * address with that device current; make that first call before any stream
  * capture.  All calls share the array and leave their data in it: calls that
  * can overlap on the GPU (other streams, unordered handles) race; calls on one

@@ -65,6 +65,7 @@ void dev_free(Operator& op, void* p, size_t bytes) {
 }
 
 Operator* handle_operator(vie_handle* hd) { return &hd->op; }
+int handle_device(const vie_handle* hd) { return hd->device; }
 
 }  // namespace vie
 
@@ -156,7 +157,7 @@ void vie_default_opts(vie_solve_opts* o) {
     o->use_x0 = 0;
     o->precond = 0;
     o->solver = VIE_SOLVER_GMRES;
-    o->reserved[0] = 0;
+    o->resid_fp64 = 0;
     o->reorth_eta = 0.1;
     o->inner_floor = 0.7;
 }
@@ -538,7 +539,8 @@ int vie_get_current(vie_handle* hd, int rhs, double* out) {
 
 int vie_apply_device(vie_handle* hd, const void* w_dev, void* y_dev, int n_rhs, int precision) {
     if (!hd || !w_dev || !y_dev || n_rhs < 1) return fail(VIE_EINVAL, "bad arguments");
-    if (precision != VIE_PREC_MIXED && precision != VIE_PREC_FP64) return fail(VIE_EINVAL, "bad precision");
+    if (precision != VIE_PREC_MIXED && precision != VIE_PREC_FP64 && precision != VIE_PREC_F32X2)
+        return fail(VIE_EINVAL, "bad precision");
     VIE_CUDA(cudaSetDevice(hd->device));
     std::vector<int> list(n_rhs);
     for (int r = 0; r < n_rhs; ++r) list[r] = r;
@@ -549,17 +551,19 @@ int vie_apply_device(vie_handle* hd, const void* w_dev, void* y_dev, int n_rhs, 
 
 int vie_apply(vie_handle* hd, const double* w, double* y, int n_rhs, int precision) {
     if (!hd || !w || !y || n_rhs < 1) return fail(VIE_EINVAL, "bad arguments");
-    if (precision != VIE_PREC_MIXED && precision != VIE_PREC_FP64) return fail(VIE_EINVAL, "bad precision");
+    if (precision != VIE_PREC_MIXED && precision != VIE_PREC_FP64 && precision != VIE_PREC_F32X2)
+        return fail(VIE_EINVAL, "bad precision");
     VIE_CUDA(cudaSetDevice(hd->device));
     const long long Nb = hd->op.Nb, N = hd->op.N, n3 = 3 * Nb;
-    const size_t esz = precision == VIE_PREC_FP64 ? sizeof(c64) : sizeof(c32);
+    const bool io64 = precision != VIE_PREC_MIXED;  // FP64 and F32X2 take double vectors
+    const size_t esz = io64 ? sizeof(c64) : sizeof(c32);
     std::vector<unsigned char> hbuf(esz * n3 * n_rhs);
     for (int r = 0; r < n_rhs; ++r)
         for (int c = 0; c < 3; ++c)
             for (long long v = 0; v < Nb; ++v) {
                 const long long i = ((long long)r * 3 * N + c * N + hd->vox_host[v]) * 2;
                 const long long o = (long long)r * n3 + c * Nb + v;
-                if (precision == VIE_PREC_FP64) reinterpret_cast<c64*>(hbuf.data())[o] = c64{w[i], w[i + 1]};
+                if (io64) reinterpret_cast<c64*>(hbuf.data())[o] = c64{w[i], w[i + 1]};
                 else reinterpret_cast<c32*>(hbuf.data())[o] = c32{(float)w[i], (float)w[i + 1]};
             }
     void *dw = nullptr, *dy = nullptr;
@@ -583,7 +587,7 @@ int vie_apply(vie_handle* hd, const double* w, double* y, int n_rhs, int precisi
             for (long long v = 0; v < Nb; ++v) {
                 const long long i = ((long long)r * 3 * N + c * N + hd->vox_host[v]) * 2;
                 const long long o = (long long)r * n3 + c * Nb + v;
-                if (precision == VIE_PREC_FP64) {
+                if (io64) {
                     const c64 a = reinterpret_cast<c64*>(hbuf.data())[o];
                     y[i] = a.x;
                     y[i + 1] = a.y;

@@ -612,6 +612,15 @@ __global__ void k_start_cycle(const c64* __restrict__ res, long long rs, cplx<T>
         for (int i = threadIdx.x; i <= m; i += KB) g[(long long)r * (m + 1) + i] = i == 0 ? c64{nr, 0} : c64{0, 0};
 }
 
+// Operator of the refinement residual b - A x (x, b, r in FP64): the FP64
+// operator in the plain FP64 solver; in mixed mode the double-float operator
+// (FP64 accuracy within a few 2^-47 at several times the FP64 speed on GB300)
+// unless the caller asks for FP64.
+template <typename T> static int resid_prec(const Operator& op, const vie_solve_opts& o) {
+    (void)op;
+    return (sizeof(T) == 4 && !o.resid_fp64) ? VIE_PREC_F32X2 : VIE_PREC_FP64;
+}
+
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
@@ -788,7 +797,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
                 // FP64 residual r = b - A64 x
                 const int n64 = (int)act64.size();
                 VIE_TRY(op_set_list(op, act64.data(), n64));
-                VIE_TRY(op_apply(op, VIE_PREC_FP64, S.x, n, S.res, n, op.d_list, n64));
+                VIE_TRY(op_apply(op, resid_prec<T>(op, o), S.x, n, S.res, n, op.d_list, n64));
                 out.matvecs64 += n64;
                 tmr_begin(TMR_RESIDUAL, st);
                 k_residual<<<dim3(nblk, n64), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 0);
@@ -1241,7 +1250,7 @@ static int bicgstab_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveRes
         if (first) {
             k_residual<<<dim3(nblk, na), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 1);
         } else {
-            VIE_TRY(op_apply(op, VIE_PREC_FP64, S.x, n, S.res, n, op.d_list, na));
+            VIE_TRY(op_apply(op, resid_prec<T>(op, o), S.x, n, S.res, n, op.d_list, na));
             out.matvecs64 += na;
             k_residual<<<dim3(nblk, na), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 0);
         }
@@ -1567,7 +1576,7 @@ static int cocr_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult&
         if (first) {
             k_residual<<<dim3(nblk, na), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 1);
         } else {
-            VIE_TRY(op_apply(op, VIE_PREC_FP64, S.x, n, S.res, n, op.d_list, na));
+            VIE_TRY(op_apply(op, resid_prec<T>(op, o), S.x, n, S.res, n, op.d_list, na));
             out.matvecs64 += na;
             k_residual<<<dim3(nblk, na), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 0);
         }

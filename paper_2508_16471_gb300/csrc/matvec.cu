@@ -23,6 +23,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <type_traits>
+
 #include "vie_internal.cuh"
 
 namespace vie {
@@ -92,6 +94,10 @@ static int upload_twiddles(Operator& op, AxisFFT& a) {
     VIE_TRY(dev_alloc(op, (void**)&a.tw32, sizeof(c32) * n));
     VIE_CUDA(cudaMemcpy(a.tw64, t.data(), sizeof(c64) * n, cudaMemcpyHostToDevice));
     VIE_CUDA(cudaMemcpy(a.tw32, tf.data(), sizeof(c32) * n, cudaMemcpyHostToDevice));
+    std::vector<cdf> td(n);
+    for (int i = 0; i < n; ++i) td[i] = cdf{dfl(t[2 * i]), dfl(t[2 * i + 1])};
+    VIE_TRY(dev_alloc(op, (void**)&a.twdf, sizeof(cdf) * n));
+    VIE_CUDA(cudaMemcpy(a.twdf, td.data(), sizeof(cdf) * n, cudaMemcpyHostToDevice));
     if (fast_length(a.plan.L)) {
         // four-step twiddles w_L^{k1 n2} in two orders: TA[k1][n2] then TB[n2][k1]
         const int L = a.plan.L;
@@ -144,6 +150,16 @@ int op_init_axes(Operator& op) {
 // kernels
 // ---------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ cplx<T> czero() { return cplx<T>{(T)0, (T)0}; }
+// vectors in memory (TI) to the arithmetic type (T) and back: the identity,
+// or double <-> double-float for the F32X2 operator
+template <typename T, typename TI> __device__ __forceinline__ cplx<T> ld_as(const cplx<TI>* p, long long i) {
+    if constexpr (std::is_same<T, TI>::value) return p[i];
+    else return to_cdf(p[i]);
+}
+template <typename T, typename TI> __device__ __forceinline__ void st_as(cplx<TI>* p, long long i, cplx<T> v) {
+    if constexpr (std::is_same<T, TI>::value) p[i] = v;
+    else p[i] = to_c64(v);
+}
 // multiply-high constant of a runtime divisor d >= 1 (div_mag(x, d, .) exact for x d < 2^32)
 __device__ __forceinline__ unsigned int mag_of(int d) {
     return d <= 1 ? 0u : (unsigned int)((0x100000000ull + (unsigned long long)d - 1) / (unsigned long long)d);
@@ -222,8 +238,8 @@ __global__ void k_axis(const cplx<T>* in, cplx<T>* out, long long inner, int n_i
 }
 
 // Pass 1: gather compact w, zero-pad z, forward FFT along z.
-template <typename T>
-__global__ void k_zfwd(const cplx<T>* __restrict__ w, long long w_rstride, const int* __restrict__ list,
+template <typename T, typename TI>
+__global__ void k_zfwd(const cplx<TI>* __restrict__ w, long long w_rstride, const int* __restrict__ list,
                        const int* __restrict__ idx_map, cplx<T>* __restrict__ A, int n0, int n1, int n2,
                        long long Nb, long long nlines, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL,
                        int stw, long long idx_stride) {
@@ -244,7 +260,7 @@ __global__ void k_zfwd(const cplx<T>* __restrict__ w, long long w_rstride, const
             const long long xy = line - sc * plane;
             const int slot = (int)(sc / 3), c = (int)(sc - (sc / 3) * 3);
             const int vi = idx_map[(long long)list[slot] * idx_stride + xy * n2 + p];
-            if (vi >= 0) v = w[(long long)list[slot] * w_rstride + c * Nb + vi];
+            if (vi >= 0) v = ld_as<T, TI>(w, (long long)list[slot] * w_rstride + c * Nb + vi);
         }
         bA[p * ld + l] = v;
     }
@@ -258,9 +274,9 @@ __global__ void k_zfwd(const cplx<T>* __restrict__ w, long long w_rstride, const
 }
 
 // Pass 5: inverse FFT along z, crop, epilogue y = w - chi u on body voxels.
-template <typename T>
-__global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict__ w, long long w_rstride,
-                       cplx<T>* __restrict__ y, long long y_rstride, const int* __restrict__ list,
+template <typename T, typename TI>
+__global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<TI>* __restrict__ w, long long w_rstride,
+                       cplx<TI>* __restrict__ y, long long y_rstride, const int* __restrict__ list,
                        const int* __restrict__ idx_map, const T* __restrict__ chi, int n0, int n1, int n2,
                        long long Nb, long long nlines, FFTPlan plan, const cplx<T>* __restrict__ twg, int NL,
                        long long chi_cs, int stw, long long idx_stride) {
@@ -293,9 +309,9 @@ __global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<T>* __restrict_
         const int vi = idx_map[rr * idx_stride + xy * n2 + p];
         if (vi < 0) continue;
         const cplx<T> u = r[p * ld + l];
-        const cplx<T> wv = w[rr * w_rstride + c * Nb + vi];
+        const cplx<T> wv = ld_as<T, TI>(w, rr * w_rstride + c * Nb + vi);
         const T ch = chi[c * chi_cs + vi];
-        y[rr * y_rstride + c * Nb + vi] = cplx<T>{wv.x - ch * u.x, wv.y - ch * u.y};
+        st_as<T, TI>(y, rr * y_rstride + c * Nb + vi, cplx<T>{wv.x - ch * u.x, wv.y - ch * u.y});
     }
 }
 
@@ -386,6 +402,19 @@ __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int 
         const int c = div_mag(cp, n0, n0mag), p = cp - c * n0;
         if (i0 + t < inner) base[((long long)c * n0 + p) * inner + i0 + t] = cur[c][p * TW + t];
     }
+}
+
+// out[i] = nearest double-float of in[i] (complex arrays convert part by part)
+__global__ void k_to_dfl(const double* __restrict__ in, dfl* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = dfl(in[i]);
+}
+static int to_dfl(const double* in, dfl* out, long long n, cudaStream_t s) {
+    if (n <= 0) return VIE_OK;
+    k_to_dfl<<<(unsigned)std::min<long long>(4096, (n + 255) / 256), 256, 0, s>>>(in, out, n);
+    count_launch();
+    VIE_CUDA(cudaGetLastError());
+    return VIE_OK;
 }
 
 // Periodic embedding of component q of the discrete kernel K(m) (FP64);
@@ -691,9 +720,11 @@ static int check_tiles(const Operator& op) {
 template <typename T> static const cplx<T>* twp(const AxisFFT& a);
 template <> const c32* twp<float>(const AxisFFT& a) { return a.tw32; }
 template <> const c64* twp<double>(const AxisFFT& a) { return a.tw64; }
+template <> const cdf* twp<dfl>(const AxisFFT& a) { return a.twdf; }
 template <typename T> static const cplx<T>* dtp(const Operator& op);
 template <> const c32* dtp<float>(const Operator& op) { return op.dtab32; }
 template <> const c64* dtp<double>(const Operator& op) { return op.dtab64; }
+template <> const cdf* dtp<dfl>(const Operator& op) { return op.dtabdf; }
 
 template <typename T, bool INV>
 static int launch_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_in, int n_out, const FFTPlan& p,
@@ -779,15 +810,21 @@ static int build_diff_tables(Operator& op) {
         }
     std::vector<c32> tf(t.size());
     for (size_t i = 0; i < t.size(); ++i) tf[i] = c32{(float)t[i].x, (float)t[i].y};
+    std::vector<cdf> td(t.size());
+    for (size_t i = 0; i < t.size(); ++i) td[i] = cdf{dfl(t[i].x), dfl(t[i].y)};
     if (op.dtab64) dev_free(op, op.dtab64, sizeof(c64) * 6 * (size_t)op.dstride);
     if (op.dtab32) dev_free(op, op.dtab32, sizeof(c32) * 6 * (size_t)op.dstride);
+    if (op.dtabdf) dev_free(op, op.dtabdf, sizeof(cdf) * 6 * (size_t)op.dstride);
     op.dtab64 = nullptr;
     op.dtab32 = nullptr;
+    op.dtabdf = nullptr;
     op.dstride = ds;
     VIE_TRY(dev_alloc(op, (void**)&op.dtab64, sizeof(c64) * t.size()));
     VIE_TRY(dev_alloc(op, (void**)&op.dtab32, sizeof(c32) * t.size()));
+    VIE_TRY(dev_alloc(op, (void**)&op.dtabdf, sizeof(cdf) * t.size()));
     VIE_CUDA(cudaMemcpy(op.dtab64, t.data(), sizeof(c64) * t.size(), cudaMemcpyHostToDevice));
     VIE_CUDA(cudaMemcpy(op.dtab32, tf.data(), sizeof(c32) * t.size(), cudaMemcpyHostToDevice));
+    VIE_CUDA(cudaMemcpy(op.dtabdf, td.data(), sizeof(cdf) * t.size(), cudaMemcpyHostToDevice));
     return VIE_OK;
 }
 
@@ -809,6 +846,7 @@ int op_build_kernel(Operator& op) {
     const long long HH = (long long)op.H[0] * op.H[1] * op.H[2];
     VIE_TRY(dev_alloc(op, (void**)&op.khat64, sizeof(c64) * 6 * HH));
     VIE_TRY(dev_alloc(op, (void**)&op.khat32, sizeof(c32) * 6 * HH));
+    VIE_TRY(dev_alloc(op, (void**)&op.khatdf, sizeof(cdf) * 6 * HH));
     // one component at a time through a single FP64 periodic array
     c64* Kc = nullptr;
     VIE_TRY(dev_alloc(op, (void**)&Kc, sizeof(c64) * PP));
@@ -842,6 +880,7 @@ int op_build_kernel(Operator& op) {
             if (cudaGetLastError() != cudaSuccess) st = fail(VIE_EDEVICE, "octant launch failed");
         }
     }
+    if (st == VIE_OK) st = to_dfl((const double*)op.khat64, (dfl*)op.khatdf, 2LL * nc * HH, op.stream);
     cudaError_t e = cudaStreamSynchronize(op.stream);
     dev_free(op, Kc, sizeof(c64) * PP);
     if (st != VIE_OK) return st;
@@ -875,22 +914,26 @@ int op_set_body_device(Operator& op, const double* eps) {
         if (op.vox) dev_free(op, op.vox, sizeof(int) * op.Nb);
         if (op.chi32) dev_free(op, op.chi32, sizeof(float) * nchi_old);
         if (op.chi64) dev_free(op, op.chi64, sizeof(double) * nchi_old);
+        if (op.chidf) dev_free(op, op.chidf, sizeof(dfl) * nchi_old);
         op.vox = nullptr;
         op.chi32 = nullptr;
         op.chi64 = nullptr;
+        op.chidf = nullptr;
         if (!op.idx_map) st = dev_alloc(op, (void**)&op.idx_map, sizeof(int) * N);
         if (st == VIE_OK) st = dev_alloc(op, (void**)&op.vox, sizeof(int) * Nb);
         const long long nchi = op.disc ? 3 * Nb : Nb;
         if (st == VIE_OK) st = dev_alloc(op, (void**)&op.chi32, sizeof(float) * nchi);
         if (st == VIE_OK) st = dev_alloc(op, (void**)&op.chi64, sizeof(double) * nchi);
+        if (st == VIE_OK) st = dev_alloc(op, (void**)&op.chidf, sizeof(dfl) * nchi);
         if (st == VIE_OK) {
             op.Nb = Nb;
             op.chi_cs = op.disc ? Nb : 0;
             k_body_write<<<nb, SCAN_B, 0, op.stream>>>(eps, N, bcount, op.idx_map, op.vox, op.chi32, op.chi64,
                                                        op.n[1], op.n[2], op.disc, Nb);
             count_launch();
+            st = to_dfl(op.chi64, op.chidf, nchi, op.stream);
             cudaError_t e = cudaStreamSynchronize(op.stream);
-            if (e != cudaSuccess) st = cuda_fail(e, "body compaction");
+            if (st == VIE_OK && e != cudaSuccess) st = cuda_fail(e, "body compaction");
         }
     }
     cudaFree(bcount);
@@ -938,16 +981,19 @@ int op_set_list(Operator& op, const int* host_list, int nr) {
     return VIE_OK;
 }
 
-template <typename T>
-static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, long long yr, const int* d_list,
+// T: arithmetic (float, double or double-float); TI: the vectors' scalar in
+// memory (T, or double for double-float)
+template <typename T, typename TI>
+static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, long long yr, const int* d_list,
                    int nr) {
-    const int pi = sizeof(T) == 8 ? 1 : 0;
+    constexpr bool F32 = std::is_same<T, float>::value, DF = std::is_same<T, dfl>::value;
+    const int pi = F32 ? 0 : 1;  // work arrays: double and double-float elements are both 16 bytes
     VIE_TRY(op_reserve(op, pi, nr));
     MatvecWork& W = op.work[pi];
     static std::atomic<bool> init{false};  // repeated attribute calls from racing threads are harmless
     if (!init) {
-        VIE_TRY(allow_smem(k_zfwd<T>));
-        VIE_TRY(allow_smem(k_zinv<T>));
+        VIE_TRY(allow_smem(k_zfwd<T, TI>));
+        VIE_TRY(allow_smem(k_zinv<T, TI>));
         VIE_TRY(allow_smem(k_xfused<T>));
         init = true;
     }
@@ -957,7 +1003,10 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
     cplx<T>* B = (cplx<T>*)W.B;
     const cplx<T>* kh;
     const T* chi;
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (DF) {
+        kh = (const cplx<T>*)op.khatdf;
+        chi = (const T*)op.chidf;
+    } else if constexpr (!F32) {
         kh = (const cplx<T>*)op.khat64;
         chi = (const T*)op.chi64;
     } else {
@@ -965,17 +1014,18 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
         chi = (const T*)op.chi32;
     }
     const double E = sizeof(cplx<T>);
+    const double EI = sizeof(cplx<TI>);
     const double lineA = 3.0 * n0 * n1 * P2 * E;  // one slot of A
     const double lineB = 3.0 * n0 * P1 * P2 * E;  // one slot of B
-    const double vec = 3.0 * op.Nb * E;           // one compact vector
-    // FP64 passes are timed under one id (FP64-bound on GB300, kept apart from the FP32 roofline)
-    auto tid = [](int id) { return sizeof(T) == 8 ? (int)TMR_MV64 : id; };
+    const double vec = 3.0 * op.Nb * EI;          // one compact vector
+    // FP64 and double-float passes are timed under one id each (ALU-bound, kept apart from the FP32 roofline)
+    auto tid = [](int id) { return F32 ? id : (DF ? (int)TMR_MVDF : (int)TMR_MV64); };
     for (int s0 = 0; s0 < nr; s0 += W.cap) {
         const int ns = std::min(W.cap, nr - s0);
         const int* list = d_list + s0;
-        const bool fz = sizeof(T) == 4 && op.fft_path == 0 && fast_length(P2);
-        const bool fy = sizeof(T) == 4 && op.fft_path == 0 && fast_length(P1);
-        const bool fx = sizeof(T) == 4 && op.fft_path == 0 && fast_length(P0);
+        const bool fz = F32 && op.fft_path == 0 && fast_length(P2);
+        const bool fy = F32 && op.fft_path == 0 && fast_length(P1);
+        const bool fx = F32 && op.fft_path == 0 && fast_length(P0);
         // pass 1
         if (fz) {
             const long long nlines = (long long)ns * 3 * n0 * n1;
@@ -989,9 +1039,9 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             const FFTPlan& p = op.ax[2].plan;
             const TileCfg c = lines_cfg<T>(p);
             const long long nlines = (long long)ns * 3 * n0 * n1;
-            const int nt = fft_threads(k_zfwd<T>, p.L, c.smem);
+            const int nt = fft_threads(k_zfwd<T, TI>, p.L, c.smem);
             tmr_begin(tid(TMR_ZFWD), op.stream);
-            k_zfwd<T><<<(unsigned)((nlines + c.w - 1) / c.w), nt, c.smem, op.stream>>>(
+            k_zfwd<T, TI><<<(unsigned)((nlines + c.w - 1) / c.w), nt, c.smem, op.stream>>>(
                 w, wr, list, op.idx_map, A, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), c.w, c.stw,
                 op.idx_stride);
             tmr_end(tid(TMR_ZFWD), op.stream, ns * (vec + lineA) + 4.0 * op.N);
@@ -1060,9 +1110,9 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
             const FFTPlan& p = op.ax[2].plan;
             const TileCfg c = lines_cfg<T>(p);
             const long long nlines = (long long)ns * 3 * n0 * n1;
-            const int nt = fft_threads(k_zinv<T>, p.L, c.smem);
+            const int nt = fft_threads(k_zinv<T, TI>, p.L, c.smem);
             tmr_begin(tid(TMR_ZINV), op.stream);
-            k_zinv<T><<<(unsigned)((nlines + c.w - 1) / c.w), nt, c.smem, op.stream>>>(
+            k_zinv<T, TI><<<(unsigned)((nlines + c.w - 1) / c.w), nt, c.smem, op.stream>>>(
                 A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), c.w,
                 op.chi_cs, c.stw, op.idx_stride);
             tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
@@ -1075,8 +1125,9 @@ static int apply_t(Operator& op, const cplx<T>* w, long long wr, cplx<T>* y, lon
 
 int op_apply(Operator& op, int prec, const void* w, long long wr, void* y, long long yr, const int* d_list, int nr) {
     if (nr <= 0) return VIE_OK;
-    if (prec == VIE_PREC_FP64) return apply_t<double>(op, (const c64*)w, wr, (c64*)y, yr, d_list, nr);
-    return apply_t<float>(op, (const c32*)w, wr, (c32*)y, yr, d_list, nr);
+    if (prec == VIE_PREC_FP64) return apply_t<double, double>(op, (const c64*)w, wr, (c64*)y, yr, d_list, nr);
+    if (prec == VIE_PREC_F32X2) return apply_t<dfl, double>(op, (const c64*)w, wr, (c64*)y, yr, d_list, nr);
+    return apply_t<float, float>(op, (const c32*)w, wr, (c32*)y, yr, d_list, nr);
 }
 
 int op_replan(Operator& op, const int P[3]) {
@@ -1087,15 +1138,19 @@ int op_replan(Operator& op, const int P[3]) {
         dev_free(op, x.tw64, sizeof(c64) * n);
         dev_free(op, x.tw32, sizeof(c32) * n);
         dev_free(op, x.roots32, sizeof(c32) * 2 * x.plan.L);
+        dev_free(op, x.twdf, sizeof(cdf) * n);
         x.tw64 = nullptr;
         x.tw32 = nullptr;
         x.roots32 = nullptr;
+        x.twdf = nullptr;
     }
     const long long HH = (long long)op.H[0] * op.H[1] * op.H[2];
     dev_free(op, op.khat64, sizeof(c64) * 6 * HH);
     dev_free(op, op.khat32, sizeof(c32) * 6 * HH);
+    dev_free(op, op.khatdf, sizeof(cdf) * 6 * HH);
     op.khat64 = nullptr;
     op.khat32 = nullptr;
+    op.khatdf = nullptr;
     for (int p = 0; p < 2; ++p) {
         MatvecWork& W = op.work[p];
         const size_t esz = p ? sizeof(c64) : sizeof(c32);
@@ -1113,20 +1168,28 @@ void op_free(Operator& op) {
         cudaFree(op.ax[a].tw32);
         cudaFree(op.ax[a].tw64);
         cudaFree(op.ax[a].roots32);
+        cudaFree(op.ax[a].twdf);
         op.ax[a].tw32 = nullptr;
         op.ax[a].tw64 = nullptr;
         op.ax[a].roots32 = nullptr;
+        op.ax[a].twdf = nullptr;
     }
     cudaFree(op.khat32);
     cudaFree(op.khat64);
+    cudaFree(op.khatdf);
     cudaFree(op.dtab32);
     cudaFree(op.dtab64);
+    cudaFree(op.dtabdf);
     op.dtab32 = nullptr;
     op.dtab64 = nullptr;
+    op.dtabdf = nullptr;
+    op.khatdf = nullptr;
     cudaFree(op.idx_map);
     cudaFree(op.vox);
     cudaFree(op.chi32);
     cudaFree(op.chi64);
+    cudaFree(op.chidf);
+    op.chidf = nullptr;
     for (int p = 0; p < 2; ++p) {
         cudaFree(op.work[p].A);
         cudaFree(op.work[p].B);

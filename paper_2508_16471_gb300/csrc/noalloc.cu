@@ -23,6 +23,7 @@
 
 namespace vie {
 Operator* handle_operator(vie_handle* hd);
+int handle_device(const vie_handle* hd);
 }
 
 using namespace vie;
@@ -82,6 +83,12 @@ extern "C" int vie_apply_noalloc(vie_handle* hd, const void* w_dev, void* y_dev,
         return fail(VIE_EINVAL, "n_rhs must be in 1.." + std::to_string(NOALLOC_MAX_RHS));
     Operator& op = *handle_operator(hd);
     if (op.disc) return fail(VIE_EINVAL, "vie_apply_noalloc covers the D1 discretisation only");
+    // one voxel map and one contrast for every slot (a plain vie_setup handle)
+    if (op.idx_stride != 0 || op.chi_cs != 0)
+        return fail(VIE_EINVAL, "vie_apply_noalloc needs one shared voxel map and contrast per handle");
+    if (op.fft_path != 0)
+        return fail(VIE_EINVAL, "vie_apply_noalloc runs the register FFT passes only; the handle is set to the "
+                                "generic path (vie_set_fft_path)");
     const int n0 = op.n[0], n1 = op.n[1], n2 = op.n[2];
     const int P0 = op.P[0], P1 = op.P[1], P2 = op.P[2];
     if (!fast_length(P0) || !fast_length(P1) || !fast_length(P2))
@@ -93,8 +100,10 @@ extern "C" int vie_apply_noalloc(vie_handle* hd, const void* w_dev, void* y_dev,
     if (per > NOALLOC_SCRATCH_BYTES)
         return fail(VIE_EINVAL, "grid too large for the fixed scratch: one RHS needs " + std::to_string(per) +
                                     " bytes, the array holds " + std::to_string(NOALLOC_SCRATCH_BYTES));
-    int dev = 0;
-    VIE_CUDA(cudaGetDevice(&dev));
+    // the handle's device, as every other entry point: its stream, maps and
+    // spectra live there, so the scratch address must be that device's too
+    const int dev = handle_device(hd);
+    VIE_CUDA(cudaSetDevice(dev));
     DeviceScratch* ds = nullptr;
     VIE_TRY(noalloc_setup(dev, &ds));
     const int cap = (int)(NOALLOC_SCRATCH_BYTES / (slotA_al + slotB));
@@ -108,12 +117,13 @@ extern "C" int vie_apply_noalloc(vie_handle* hd, const void* w_dev, void* y_dev,
         c32* B = reinterpret_cast<c32*>(ds->scratch + ((ns * slotA + 255) & ~(size_t)255));
         const int* list = ds->iota + s0;
         const long long nlines = (long long)ns * 3 * n0 * n1;
-        VIE_TRY(fast_zfwd(w, n3, list, op.idx_map, A, n0, n1, n2, op.Nb, nlines, P2, op.ax[2].roots32, s));
+        VIE_TRY(fast_zfwd(w, n3, list, op.idx_map, A, n0, n1, n2, op.Nb, nlines, P2, op.ax[2].roots32, s,
+                          op.idx_stride));
         VIE_TRY(fast_axis(A, B, (long long)ns * 3 * n0, n1, P1, P2, P1, op.ax[1].roots32, false, s));
         VIE_TRY(fast_xfused(B, n0, (long long)P1 * P2, P0, P1, P2, op.khat32, op.H, op.ax[0].roots32, ns, s));
         VIE_TRY(fast_axis(B, A, (long long)ns * 3 * n0, P1, n1, P2, P1, op.ax[1].roots32, true, s));
         VIE_TRY(fast_zinv(A, w, n3, y, n3, list, op.idx_map, op.chi32, n0, n1, n2, op.Nb, nlines, P2,
-                          op.ax[2].roots32, s));
+                          op.ax[2].roots32, s, op.chi_cs, op.idx_stride));
         count_launch(5);
         VIE_CUDA(cudaGetLastError());
     }

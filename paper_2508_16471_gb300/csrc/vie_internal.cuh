@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "fft.cuh"
 
 namespace vie {
@@ -14,6 +15,7 @@ struct AxisFFT {
     c32* tw32 = nullptr;
     c64* tw64 = nullptr;
     c32* roots32 = nullptr;  // fast path: w_P^{k1 n2} as [k1][n2] then [n2][k1] (2P entries)
+    cdf* twdf = nullptr;     // generic-plan twiddles in double-float (the F32X2 operator)
 };
 
 // matvec workspace of one precision
@@ -33,10 +35,12 @@ struct Operator {
     AxisFFT ax[3];
     c32* khat32 = nullptr;  // [6][H0][H1][H2] (D1) or [1][H0][H1][H2] (D2 scalar), scaled by 1/(P0 P1 P2)
     c64* khat64 = nullptr;
+    cdf* khatdf = nullptr;   // khat64 in double-float (the F32X2 operator)
     int* idx_map = nullptr;  // [N] compact index or -1
     int* vox = nullptr;      // [Nb] linear voxel index of body voxel
     float* chi32 = nullptr;  // [Nb]
     double* chi64 = nullptr; // [Nb]
+    dfl* chidf = nullptr;    // chi64 in double-float
     MatvecWork work[2];      // 0: FP32, 1: FP64
     int* d_list = nullptr;   // RHS index list for batched launches
     int list_cap = 0;
@@ -50,6 +54,7 @@ struct Operator {
     long long chi_cs = 0;    // component stride of chi32/chi64: 0 (D1) or Nb (D2, per-face contrast)
     c32* dtab32 = nullptr;   // D2 difference symbols [3 axes][2 (+,-)][dstride]
     c64* dtab64 = nullptr;
+    cdf* dtabdf = nullptr;
     int dstride = 0;
     int ff_engine = 0;       // far-field contractions: 0 tcgen05 3xTF32, 1 CUDA-core FP32
     // voxel maps per batch slot: slot list[s] reads idx_map + list[s] * idx_stride (0: one map for all slots;
@@ -78,7 +83,8 @@ int op_set_body_device(Operator& op, const double* eps_dev);  // chi, idx_map, v
 int op_reserve(Operator& op, int prec, int nrhs);  // matvec workspace
 int op_set_list(Operator& op, const int* host_list, int nr);  // uploads d_list
 // y[list[s]] = A w[list[s]] for s < nr.  w, y on the compact layout with RHS
-// stride `rstride` elements; prec 0 = float, 1 = double.
+// stride `rstride` elements; prec 0 = float, 1 = double, 2 = double-float
+// arithmetic on double inputs and outputs.
 int op_apply(Operator& op, int prec, const void* w, long long w_rstride, void* y, long long y_rstride,
              const int* d_list, int nr);
 void op_free(Operator& op);

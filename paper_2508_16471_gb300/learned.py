@@ -36,7 +36,9 @@ def generate(n_axis, h, seeds, n_dirs, factor, restart=64, tol=1e-6, max_iter=20
             x = torch.empty(R, 10, Vc, device="cuda")
             t = torch.empty(R, 6, Vc, device="cuda")
             m = torch.empty(R, Vc, device="cuda")
+            torch.cuda.synchronize()  # the library runs on the handle's own stream
             hd.net_features(factor, x.data_ptr(), t.data_ptr(), m.data_ptr())
+            torch.cuda.synchronize()
             Xs.append(x)
             Ts.append(t)
             Ms.append(m)
@@ -61,6 +63,7 @@ def train(net, X, T, M, D, epochs=20, batch=8, lr=2e-3, seed=0, lr_decay=0.9):
             xb = X.index_select(0, idx).contiguous()
             tb = T.index_select(0, idx).contiguous()
             mb = M.index_select(0, idx).contiguous()
+            torch.cuda.synchronize()  # the network runs on its own stream
             tot += net.train_step(xb.data_ptr(), tb.data_ptr(), mb.data_ptr(), batch, D, lr)
             nb += 1
         hist.append(tot / max(nb, 1))
@@ -96,6 +99,7 @@ def generate_precond(n_axis, h, seeds, n_dirs, factor, powers=3, restart=64, tol
                 x = torch.empty(R, 7, Vc, device="cuda")
                 t = torch.empty(R, 6, Vc, device="cuda")
                 m = torch.empty(R, Vc, device="cuda")
+                torch.cuda.synchronize()  # the library runs on the handle's own stream
                 hd.precond_pairs(factor, v.data_ptr(), R, x.data_ptr(), t.data_ptr(), m.data_ptr())
                 Xs.append(x)
                 Ts.append(t)
@@ -104,6 +108,7 @@ def generate_precond(n_axis, h, seeds, n_dirs, factor, powers=3, restart=64, tol
                     u = torch.empty_like(v)
                     hd.apply_device(v.data_ptr(), u.data_ptr(), R, V.PREC_MIXED)
                     v = u
+                torch.cuda.synchronize()
     finally:
         if hd is not None:
             hd.close()

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "libvie.so")
 
 VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_ENOCONV = 0, -1, -2, -3
 VIE_ETIMEOUT, VIE_EUNDEF, VIE_EDEVICE, VIE_ESTATE = -4, -5, -6, -7
-PREC_MIXED, PREC_FP64 = 0, 1
+PREC_MIXED, PREC_FP64, PREC_F32X2 = 0, 1, 2
 BASIS_CART, BASIS_SPH, BASIS_CIRC = 0, 1, 2
 SOLVER_GMRES, SOLVER_BICGSTAB, SOLVER_COCR = 0, 1, 2
 DISC_D1, DISC_D2 = 0, 1
@@ -50,7 +50,7 @@ class _Channel(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iter", C.c_int),
                 ("precision", C.c_int), ("inner_tol", C.c_double), ("use_x0", C.c_int),
-                ("precond", C.c_int), ("solver", C.c_int), ("reserved", C.c_int * 1),
+                ("precond", C.c_int), ("solver", C.c_int), ("resid_fp64", C.c_int),
                 ("reorth_eta", C.c_double), ("inner_floor", C.c_double)]
 
 

@@ -44,8 +44,10 @@ def _gpu_block_apply(vielib, g, eps, w, cuts):
     import torch
     with vielib.Handle(g.n, g.h, eps, K0) as hd:
         hd.set_block_precond(cuts, inner=4)
-        wd = torch.from_numpy(w.astype(np.complex64)).cuda().contiguous()
+        w_h = np.ascontiguousarray(w, dtype=np.complex64)  # kept alive until the copy is done
+        wd = torch.from_numpy(w_h).cuda().contiguous()
         yd = torch.full_like(wd, complex(float("nan"), 0.0))
+        torch.cuda.synchronize()  # the library runs on its own stream
         hd.block_apply_device(wd.data_ptr(), yd.data_ptr())
         torch.cuda.synchronize()
         return yd.cpu().numpy().astype(np.complex128)

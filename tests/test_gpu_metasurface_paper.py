@@ -34,8 +34,10 @@ def test_paper_scale_operator_sampled(vielib):
         assert inf["n_body"] == Nb and inf["P"] == (256, 1500, 5000)
         out = {}
         for prec, dt in ((vielib.PREC_FP64, torch.complex128), (vielib.PREC_MIXED, torch.complex64)):
-            wd = torch.from_numpy(w.astype(np.complex128)).to(dt).cuda().reshape(1, 3, Nb).contiguous()
+            w_h = np.ascontiguousarray(w, dtype=np.complex128)  # kept alive until the copy is done
+            wd = torch.from_numpy(w_h).to(dt).cuda().reshape(1, 3, Nb).contiguous()
             yd = torch.full_like(wd, complex(float("nan"), 0.0))
+            torch.cuda.synchronize()  # the library runs on its own stream
             hd.apply_device(wd.data_ptr(), yd.data_ptr(), 1, prec)
             torch.cuda.synchronize()
             y = yd[0].cpu().numpy().astype(np.complex128)

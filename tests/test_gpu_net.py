@@ -62,7 +62,9 @@ def test_forward_and_gradients_match_oracle(vielib, bf16, tol_y, tol_g, tol_all,
     x, t, m = _data(B, D, 7, cin)
     xd, td, md = (torch.from_numpy(a).cuda().contiguous() for a in (x, t, m))
     yd = torch.empty(B, 6, D, D, D, device="cuda")
+    torch.cuda.synchronize()  # the network runs on its own stream
     net.forward(xd.data_ptr(), yd.data_ptr(), B, D)
+    torch.cuda.synchronize()
     y_or, cache = onet.forward(P, x.astype(np.float64), specs, keep=True)
     y = yd.cpu().numpy()
     assert np.abs(y - y_or).max() <= tol_y * np.abs(y_or).max()
@@ -89,6 +91,7 @@ def test_training_reduces_loss(vielib):
     # learnable target: a fixed smooth function of the input channels
     t = np.concatenate([x[:, 1:7] * 0.5 + x[:, :1] * 0.25], axis=1).astype(np.float32)
     xd, td, md = (torch.from_numpy(a).cuda().contiguous() for a in (x, t, m))
+    torch.cuda.synchronize()  # the network runs on its own stream
     losses = [net.train_step(xd.data_ptr(), td.data_ptr(), md.data_ptr(), B, D, 3e-3) for _ in range(300)]
     assert np.all(np.isfinite(losses))
     assert np.mean(losses[-10:]) < 0.6 * losses[0], (losses[0], losses[-1])

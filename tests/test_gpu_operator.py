@@ -13,6 +13,7 @@ import pytest
 
 from oracle import vie as ovie
 from paper_2508_16471_gb300 import inputs
+from sample_points import pick_voxels
 
 pytestmark = pytest.mark.gpu
 K0 = 2.0 * math.pi
@@ -56,11 +57,14 @@ def _check_apply(vielib, n, h, eps, R=2, seed=0):
     with vielib.Handle(n, h, eps, K0) as hd:
         y64 = hd.apply(w, precision=vielib.PREC_FP64)
         y32 = hd.apply(w, precision=vielib.PREC_MIXED)
+        ydf = hd.apply(w, precision=vielib.PREC_F32X2)
     s = np.abs(ref).max()
     e64 = np.abs(y64 - ref).max() / s
     e32 = np.abs(y32 - ref).max() / s
+    edf = np.abs(ydf - ref).max() / s
     assert e64 <= TOL64, e64
     assert e32 <= TOL32, e32
+    assert edf <= TOL64, edf  # double-float arithmetic meets the FP64 tolerance
 
 
 @pytest.mark.parametrize("n", [(1, 1, 1), (2, 3, 1), (5, 6, 4), (7, 5, 9), (12, 10, 7)])
@@ -113,7 +117,7 @@ def _sampled_parity(vielib, n, h, eps, R, seed, nsamp, prec_list):
         conv = convs[r]
         ref = np.stack([w[r][:, a, b, c] - chi[a, b, c] * conv[:, i] for i, (a, b, c) in enumerate(pts)], 1)
         s = np.abs(ref).max()
-        for p, tol in ((vielib.PREC_FP64, TOL64), (vielib.PREC_MIXED, TOL32)):
+        for p, tol in ((vielib.PREC_FP64, TOL64), (vielib.PREC_MIXED, TOL32), (vielib.PREC_F32X2, TOL64)):
             if p not in out:
                 continue
             got = np.stack([out[p][r][:, a, b, c] for (a, b, c) in pts], 1)
@@ -123,13 +127,15 @@ def _sampled_parity(vielib, n, h, eps, R, seed, nsamp, prec_list):
 def test_apply_sphere64_sampled(vielib):
     wl = inputs.sphere_config2()
     _sampled_parity(vielib, wl.grid.n, wl.grid.h, wl.eps, 2, 11, 24,
-                    (vielib.PREC_FP64, vielib.PREC_MIXED))
+                    (vielib.PREC_FP64, vielib.PREC_MIXED, vielib.PREC_F32X2))
 
 
 def test_apply_bench_size_sampled(vielib):
-    """The 128^3 random-body workload the bench times, 4 RHS, sampled voxels."""
+    """The 128^3 random-body workload the bench times, 4 RHS, sampled voxels;
+    the double-float operator is the one the bench's residuals use."""
     wl = inputs.random_body_workload(20000, n_axis=128, h=1.0 / 128.0)
-    _sampled_parity(vielib, wl.grid.n, wl.grid.h, wl.eps, 4, 12, 6, (vielib.PREC_MIXED, vielib.PREC_FP64))
+    _sampled_parity(vielib, wl.grid.n, wl.grid.h, wl.eps, 4, 12, 6,
+                    (vielib.PREC_MIXED, vielib.PREC_FP64, vielib.PREC_F32X2))
 
 
 @pytest.mark.parametrize("n", [(16, 16, 16), (32, 24, 20), (64, 64, 64)])
@@ -203,32 +209,55 @@ def test_first_axis_too_long_is_rejected(vielib):
     assert "first axis" in str(e.value)
 
 
-def test_apply_bench_launch_configuration_sampled(vielib):
-    """The bench's launch configuration: the 128^3 body, 32 RHS in one FP32
-    operator application (32 slots per fused-x launch, next-slot prefetch)
-    through the device layout; sampled voxels of the first, a middle and the
-    last RHS against the oracle's direct sum over all sources."""
+def _apply_sampled(vielib, g, eps, R, seed, rr, count):
+    """One FP32 application of R random vectors through the device layout;
+    ``count`` picked voxels of the RHS ``rr`` against the oracle's direct sum
+    over all source voxels."""
     import torch
-    wl = inputs.random_body_workload(20000, n_axis=128, h=1.0 / 128.0)
-    g = wl.grid
-    mask = wl.eps > 1.0
+    mask = eps > 1.0
     vox = np.flatnonzero(mask)
     Nb = len(vox)
-    R = 32
-    rng = np.random.default_rng(77)
+    rng = np.random.default_rng(seed)
     w = (rng.standard_normal((R, 3, Nb)) + 1j * rng.standard_normal((R, 3, Nb))).astype(np.complex64)
-    with vielib.Handle(g.n, g.h, wl.eps, K0) as hd:
+    with vielib.Handle(g.n, g.h, eps, K0) as hd:
         wd = torch.from_numpy(w).cuda().contiguous()
         yd = torch.full_like(wd, complex(float("nan"), 0.0))
+        torch.cuda.synchronize()  # the library runs on its own stream
         hd.apply_device(wd.data_ptr(), yd.data_ptr(), R, vielib.PREC_MIXED)
         torch.cuda.synchronize()
         y = yd.cpu().numpy().astype(np.complex128)
     assert np.isfinite(y).all()
-    picks = rng.choice(Nb, size=4, replace=False)
-    rr = [0, 17, 31]
+    pts = pick_voxels(mask, count, seed)
+    lin = np.ravel_multi_index(tuple(pts.T), g.n)
+    picks = np.searchsorted(vox, lin)
+    assert np.array_equal(vox[picks], lin)
     src = np.stack(np.unravel_index(vox, g.n), -1)
-    conv = ovie.convolve_points_sparse(src, w[rr].astype(np.complex128), g.h, K0, src[picks])  # (3 rhs, 3, T)
-    chi = wl.eps.reshape(-1)[vox[picks]] - 1.0
+    conv = ovie.convolve_points_sparse(src, w[rr].astype(np.complex128), g.h, K0, pts)  # (len(rr), 3, T)
+    chi = eps.reshape(-1)[lin] - 1.0
     for q, r in enumerate(rr):
         ref = w[r][:, picks] - chi[None, :] * conv[q]
         assert np.abs(y[r][:, picks] - ref).max() <= TOL32 * np.abs(ref).max(), r
+
+
+def test_apply_bench_launch_configuration_sampled(vielib):
+    """The bench's launch configuration: the 128^3 body, 32 RHS in one FP32
+    operator application (32 slots per fused-x launch, next-slot prefetch)
+    through the device layout; 32 voxels (the body's extreme ones along each
+    axis, the ones nearest the grid corners, surface and random ones) of the
+    first, a middle and the last RHS against the oracle's direct sum over all
+    sources."""
+    wl = inputs.random_body_workload(20000, n_axis=128, h=1.0 / 128.0)
+    _apply_sampled(vielib, wl.grid, wl.eps, 32, 77, [0, 17, 31], 32)
+
+
+def test_apply_128_body_filling_the_grid_sampled(vielib):
+    """A 128^3 random medium that fills the grid (40 % of the voxels, all eight
+    corners included), 4 RHS: the voxels where zero padding and cropping act
+    (grid corners and faces) against the oracle's direct sum."""
+    n = (128, 128, 128)
+    rng = np.random.default_rng(128)
+    eps = 1.0 + rng.uniform(0.5, 3.0, n) * (rng.uniform(size=n) < 0.4)
+    for c in np.stack(np.meshgrid([0, 127], [0, 127], [0, 127], indexing="ij"), -1).reshape(-1, 3):
+        eps[tuple(c)] = 2.5
+    g = inputs.Grid(n, 1.0 / 128.0)
+    _apply_sampled(vielib, g, eps, 4, 78, [0, 3], 32)
