@@ -78,8 +78,13 @@ def parse():
                         "first bench body, then exit (no JSON line)")
     p.add_argument("--apply-fp64", action="store_true",
                    help="with --apply-only: apply the FP64 operator instead of the FP32 one")
-    p.add_argument("--workload", default="bodies128", choices=["bodies128", "metasurface-paper"],
-                   help="metasurface-paper: one solve of the paper-scale PB metasurface (its own JSON line)")
+    p.add_argument("--apply-f32x2", action="store_true",
+                   help="with --apply-only: apply the double-float operator (the residual operator of the solves)")
+    p.add_argument("--workload", default="bodies128", choices=["bodies128", "metasurface-paper", "bodies-uneven"],
+                   help="metasurface-paper: one solve of the paper-scale PB metasurface (its own JSON line); "
+                        "bodies-uneven: the random-body set of uneven grids (32^3..96^3) in multi-body batches")
+    p.add_argument("--n-bodies", type=int, default=64, help="bodies-uneven: bodies (seeds 0..n-1)")
+    p.add_argument("--batch", type=int, default=8, help="bodies-uneven: bodies per multi-body batch")
     p.add_argument("--box", type=float, nargs=3, default=(40.0, 12.0, 2.0),
                    help="metasurface-paper: box in wavelengths (paper x, y, z)")
     p.add_argument("--solver", default="gmres", choices=["gmres", "bicgstab", "cocr"],
@@ -315,7 +320,8 @@ def run_ours(args):
         wl = inputs.random_body_workload(SEED0, n_axis=N_AXIS, h=H, n_dirs=N_DIRS)
         with V.Handle(wl.grid.n, wl.grid.h, wl.eps, wl.k0) as hd0:
             nb = hd0.info()["n_body"]
-            dt, prec = (torch.complex128, V.PREC_FP64) if args.apply_fp64 else (torch.complex64, V.PREC_MIXED)
+            dt, prec = ((torch.complex128, V.PREC_FP64) if args.apply_fp64 else
+                        (torch.complex128, V.PREC_F32X2) if args.apply_f32x2 else (torch.complex64, V.PREC_MIXED))
             w = torch.randn(args.apply_only, 3, nb, dtype=dt, device="cuda")
             y = torch.empty_like(w)
             torch.cuda.synchronize()
@@ -732,12 +738,89 @@ def run_metasurface_paper(args):
     return 0
 
 
+def run_bodies_uneven(args):
+    """Random bodies of uneven grids (the generator's 32^3..96^3 draw, 1-lambda
+    box: h = 1/n), 16 RHS each (8 Fibonacci directions x 2 polarisations),
+    mixed-precision GMRES to an FP64 residual of 1e-6.  Bodies are sorted by
+    size and solved in multi-body batches (vie_batch_*: the FP32 operator of
+    all rows of a batch in one launch per pass and padded size); the same
+    bodies are then solved one handle at a time for comparison.  Set-up (kernel
+    spectra) is outside both timings."""
+    import numpy as np
+    import torch
+    from paper_2508_16471_gb300 import build as libbuild
+    from paper_2508_16471_gb300 import inputs
+    from paper_2508_16471_gb300 import vie as V
+    torch.cuda.set_device(0)
+    libbuild.build()
+    V.load()
+    log = lambda *a: print(*a, file=sys.stderr, flush=True)  # noqa: E731
+    bodies = []
+    for s in range(args.n_bodies):
+        g, eps = inputs.random_body(s)
+        n = g.n[0]
+        bodies.append(((n, n, n), 1.0 / n, eps))
+    order = sorted(range(len(bodies)), key=lambda i: bodies[i][0][0])
+    chs = [(c.khat, c.pol) for c in inputs.channels_fibonacci(8)]
+    R = len(chs)
+    opts = dict(tol=1e-6, restart=args.restart, max_iter=args.max_iter)
+    groups = [order[i:i + args.batch] for i in range(0, len(order), args.batch)]
+    t_batch, solved, iters, launches = 0.0, 0, [], 0
+    clocks = ClockSampler(0)
+    clocks.start()
+    for grp in groups:
+        bt = V.Batch([bodies[i] for i in grp], 2.0 * math.pi)
+        torch.cuda.synchronize()
+        l0 = V.kernel_launches()
+        t0 = time.perf_counter()
+        st = bt.solve(chs, allow_noconv=True, **opts)
+        torch.cuda.synchronize()
+        t_batch += time.perf_counter() - t0
+        launches += V.kernel_launches() - l0
+        solved += int(st["converged"])
+        iters.extend(st["iters"].reshape(-1).tolist())
+        log(f"batch n={[bodies[i][0][0] for i in grp]} P={sorted({bt.info(k)['P'][0] for k in range(len(grp))})} "
+            f"{time.perf_counter() - t0:.2f}s converged {st['converged']}/{R * len(grp)}")
+        bt.close()
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    t_single, solved1 = 0.0, 0
+    if not args.no_plain:
+        for i in order:
+            n, h, eps = bodies[i]
+            with V.Handle(n, h, eps, 2.0 * math.pi) as hd:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = hd.solve(chs, allow_noconv=True, **opts)
+                torch.cuda.synchronize()
+                t_single += time.perf_counter() - t0
+                solved1 += int(st["converged"])
+    sizes = [bodies[i][0][0] for i in order]
+    line = {"metric": "random bodies of uneven grids: solves/sec to FP64 residual 1e-6 in multi-body batches",
+            "value": solved / t_batch, "unit": "solves/s", "higher_is_better": True, "n_gpus": 1,
+            "dtype": "f32+f64", "data": "synthetic (seeded random bodies)",
+            "config": {"workload": f"{len(bodies)} random bodies (seeds 0..{len(bodies) - 1}), n in "
+                                   f"{min(sizes)}..{max(sizes)} (drawn 32..96), h = lambda/n, eps_r in [1.5, 6], "
+                                   f"{R} RHS each", "batch": args.batch,
+                       "solver": f"mixed FP32 matvec / FP64 Arnoldi GMRES({args.restart}) + double-float residual"},
+            "bodies_per_s": len(bodies) * (solved / (R * len(bodies))) / t_batch, "seconds": t_batch,
+            "solved": solved, "rhs_total": R * len(bodies), "iters_mean": float(np.mean(iters)),
+            "gpu_launches": int(launches), "clocks": clk,
+            "one_handle_per_body": {"seconds": t_single, "solved": solved1,
+                                    "value": (solved1 / t_single) if t_single else None} if t_single else None,
+            "speedup_vs_one_handle_per_body": (t_single / t_batch) if t_single else None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "metasurface-paper":
         return run_metasurface_paper(args)
+    if args.workload == "bodies-uneven":
+        return run_bodies_uneven(args)
     return run_ours(args)
 
 

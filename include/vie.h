@@ -352,6 +352,44 @@ int vie_fft_lines(const double* in, double* out, int L, int count, int inverse, 
 
 int vie_get_info(const vie_handle* hd, vie_info* info);
 
+/* ---- multi-body batches (many bodies of uneven grids in one launch) ----
+ * North_star's batching pattern applied to bodies: a batch holds bodies of
+ * different grids (each its own n, h, origin and eps_r; one k0), each padded
+ * to a power of two per body (the smallest >= 2n - 1 over its axes, 32..256,
+ * so n <= 128 per axis).  Body b's RHS j is row b * n_rhs + j of batch-wide
+ * compact vectors [rows][3][stride], stride = vie_batch_stride() = the
+ * largest body's n_body; a body uses the first n_body entries of each
+ * component (the rest is zero and ignored).  The FP32 operator runs its five
+ * passes (Sec. II-C, Eq. 24) over all rows of all bodies that share a padded
+ * size in one launch per pass, each row with its own grid, voxel map,
+ * contrast and kernel spectrum; the FP64-accuracy residual runs each body's
+ * own operator.  The handle owns all device memory; not thread-safe.
+ * Errors: VIE_EINVAL (bad sizes, eps_r < 1, an empty body), VIE_ENOMEM,
+ * VIE_EDEVICE. */
+typedef struct vie_batch vie_batch;
+int vie_batch_create(int n_bodies, const vie_grid* grids, const double* const* eps_r, double k0,
+                     vie_batch** out);
+void vie_batch_destroy(vie_batch* bt);
+long long vie_batch_stride(const vie_batch* bt);
+/* per-body n, P, n_body; device_bytes = the whole batch */
+int vie_batch_info(const vie_batch* bt, int body, vie_info* info);
+/* y = A w for n_rhs rows per body (all bodies): w_dev, y_dev device
+ * [n_bodies * n_rhs][3][stride], float2 (VIE_PREC_MIXED) or double2 (VIE_PREC_FP64,
+ * VIE_PREC_F32X2).  Enqueued on the batch's stream (synchronised by the call
+ * that uploads the slot table). */
+int vie_batch_apply_device(vie_batch* bt, const void* w_dev, void* y_dev, int n_rhs, int precision);
+/* The same n_rhs channels for every body, solved together: mixed-precision
+ * GMRES (opts: precision MIXED, solver GMRES, precond 0, use_x0 0) with the
+ * refinement of vie_solve.  stats->iters / relres: [n_bodies * n_rhs].
+ * Errors: as vie_solve. */
+int vie_batch_solve(vie_batch* bt, const vie_channel* ch, int n_rhs, const vie_solve_opts* opts,
+                    vie_solve_stats* stats);
+/* current of (body, rhs) on the body's full grid, host out[3][n0][n1][n2] complex */
+int vie_batch_get_current(vie_batch* bt, int body, int rhs, double* out);
+/* far field of every RHS of one body at D directions (Eq. 25, FP64), host
+ * out[n_rhs][D][3] complex in the basis of vie_farfield_dirs */
+int vie_batch_farfield_dirs(vie_batch* bt, int body, const double* dirs, int D, int basis, double* out);
+
 /* ---- learned initial guess ----------------------------------------------
  * A 4-level 3-D U-Net (channels c0..c3, 3x3x3 convolutions with ReLU, 2x2x2
  * average pooling, nearest upsampling, skip concatenations, 1x1x1 head) maps

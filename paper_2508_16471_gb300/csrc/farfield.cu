@@ -26,7 +26,7 @@ namespace vie {
 // with its own face contrast chi[q Nb + v]
 __global__ void k_rhs(c64* __restrict__ b, long long n3, const int* __restrict__ vox, const double* __restrict__ chi,
                       long long Nb, int n1, int n2, double h, double cx, double cy, double cz, double k0,
-                      const double* __restrict__ ch, long long chi_cs) {
+                      const double* __restrict__ ch, long long chi_cs, long long cst) {
     const int r = blockIdx.y;
     const double* c = ch + 9 * r;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < Nb;
@@ -43,9 +43,32 @@ __global__ void k_rhs(c64* __restrict__ b, long long n3, const int* __restrict__
             sincos(ph, &s, &co);
             const double x = chi[q * chi_cs + v];
             const double pr = c[3 + 2 * q], pi = c[4 + 2 * q];
-            b[r * n3 + q * Nb + v] = c64{x * (pr * co - pi * s), x * (pr * s + pi * co)};
+            b[r * n3 + q * cst + v] = c64{x * (pr * co - pi * s), x * (pr * s + pi * co)};
         }
     }
+}
+
+int build_rhs_rows(Operator& op, c64* b, long long n3, double* chans_dev, const vie_channel* chs, int n_rhs) {
+    std::vector<double> hc(9 * n_rhs);
+    for (int r = 0; r < n_rhs; ++r) {
+        for (int q = 0; q < 3; ++q) hc[9 * r + q] = chs[r].khat[q];
+        for (int q = 0; q < 6; ++q) hc[9 * r + 3 + q] = chs[r].pol[q];
+    }
+    cudaError_t e = cudaMemcpyAsync(chans_dev, hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice,
+                                    op.stream);
+    if (e == cudaSuccess) {
+        const double cx = op.origin[0] - 0.5 * (op.n[0] - 1) * op.h;
+        const double cy = op.origin[1] - 0.5 * (op.n[1] - 1) * op.h;
+        const double cz = op.origin[2] - 0.5 * (op.n[2] - 1) * op.h;
+        k_rhs<<<dim3(std::max(1, std::min(1024, ceil_div(op.Nb, 256))), n_rhs), 256, 0, op.stream>>>(
+            b, n3, op.vox, op.chi64, op.Nb, op.n[1], op.n[2], op.h, cx, cy, cz, op.k0, chans_dev, op.chi_cs,
+            comp_stride(op));
+        count_launch();
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(op.stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "rhs build");
+    return VIE_OK;
 }
 
 int build_rhs(Operator& op, Solver& S, const vie_channel* chs, int n_rhs) {
@@ -61,7 +84,8 @@ int build_rhs(Operator& op, Solver& S, const vie_channel* chs, int n_rhs) {
         const double cy = op.origin[1] - 0.5 * (op.n[1] - 1) * op.h;
         const double cz = op.origin[2] - 0.5 * (op.n[2] - 1) * op.h;
         k_rhs<<<dim3(std::max(1, std::min(1024, ceil_div(op.Nb, 256))), n_rhs), 256, 0, op.stream>>>(
-            S.b, S.n3, op.vox, op.chi64, op.Nb, op.n[1], op.n[2], op.h, cx, cy, cz, op.k0, d, op.chi_cs);
+            S.b, S.n3, op.vox, op.chi64, op.Nb, op.n[1], op.n[2], op.h, cx, cy, cz, op.k0, d, op.chi_cs,
+            comp_stride(op));
         count_launch();
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(op.stream);
@@ -117,7 +141,7 @@ constexpr int FF_DB = 2;  // directions per block
 // Sraw[r][d][3] = sum_v w[r][c][v] e^{-i k0 d.r_v}
 __global__ void k_ff_dirs(const c64* __restrict__ x, long long n3, const int* __restrict__ vox, long long Nb, int n0,
                           int n1, int n2, double h, double cx, double cy, double cz, double k0,
-                          const double* __restrict__ dirs, int D, c64* __restrict__ Sraw) {
+                          const double* __restrict__ dirs, int D, c64* __restrict__ Sraw, long long cst) {
     extern __shared__ __align__(16) unsigned char smraw[];
     c64* tab = reinterpret_cast<c64*>(smraw);  // [FF_DB][n0 + n1 + n2]
     const int nt = n0 + n1 + n2;
@@ -153,7 +177,7 @@ __global__ void k_ff_dirs(const c64* __restrict__ x, long long n3, const int* __
         const int k = lin % n2;
         const int j = (lin / n2) % n1;
         const int i = lin / (n1 * n2);
-        const c64 w0 = xr[v], w1 = xr[Nb + v], w2 = xr[2 * Nb + v];
+        const c64 w0 = xr[v], w1 = xr[cst + v], w2 = xr[2 * cst + v];
 #pragma unroll
         for (int q = 0; q < FF_DB; ++q) {
             const c64* t = tab + q * nt;
@@ -258,7 +282,8 @@ int farfield_dirs(Operator& op, const c64* x, long long n3, int R, const double*
     const size_t sm = sizeof(c64) * FF_DB * (op.n[0] + op.n[1] + op.n[2]);
     cudaFuncSetAttribute(k_ff_dirs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     k_ff_dirs<<<dim3(ceil_div(D, FF_DB), R), 256, sm, op.stream>>>(x, n3, op.vox, op.Nb, op.n[0], op.n[1], op.n[2],
-                                                                   op.h, cx, cy, cz, op.k0, ddirs, D, Sraw);
+                                                                   op.h, cx, cy, cz, op.k0, ddirs, D, Sraw,
+                                                                   comp_stride(op));
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
@@ -278,12 +303,12 @@ int farfield_dirs(Operator& op, const c64* x, long long n3, int R, const double*
 // ---------------------------------------------------------------------------
 // full-grid FP32 copy of the currents: W[r][c][x][y][z]
 __global__ void k_scatter_full(const c64* __restrict__ x, long long n3, const int* __restrict__ vox, long long Nb,
-                               long long N, c32* __restrict__ W) {
+                               long long N, c32* __restrict__ W, long long cst) {
     const int rc = blockIdx.y;  // r*3 + c
     const int r = rc / 3, c = rc % 3;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < Nb;
          v += (long long)gridDim.x * blockDim.x) {
-        const c64 a = x[r * n3 + c * Nb + v];
+        const c64 a = x[r * n3 + c * cst + v];
         W[(long long)rc * N + vox[v]] = c32{(float)a.x, (float)a.y};
     }
 }
@@ -451,7 +476,7 @@ int farfield_grid(Operator& op, const c64* x, long long n3, int R, const double*
     const double cz = op.origin[2] - 0.5 * (n2 - 1) * op.h;
     cudaMemsetAsync(W, 0, sizeof(c32) * N * RC, s);
     k_scatter_full<<<dim3(std::max(1, std::min(2048, ceil_div(op.Nb, 256))), RC), 256, 0, s>>>(x, n3, op.vox, op.Nb,
-                                                                                               N, W);
+                                                                                               N, W, comp_stride(op));
     k_phase_tables<<<1024, 256, 0, s>>>(dth, nt, dph, np, n0, n1, n2, op.h, cx, cy, cz, op.k0, ez, ey, ex);
     int* derr = (int*)alloc(sizeof(int));
     if (!derr) {

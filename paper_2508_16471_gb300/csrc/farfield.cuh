@@ -49,6 +49,9 @@ __host__ __device__ inline double hom_nc(const HomScalars& s, double dtau, doubl
 }
 
 int farfield_dirs(Operator& op, const c64* x, long long n3, int R, const double* ddirs, int D, int basis, c64* dout);
+// right-hand sides b[r] = chi E_inc(channel r) for r < n_rhs (rows n3 apart, components comp_stride(op) apart);
+// chans_dev receives the 9 doubles of each channel
+int build_rhs_rows(Operator& op, c64* b, long long n3, double* chans_dev, const vie_channel* chs, int n_rhs);
 // finite aperture: out[r][d] = sum_q wq[d Q + q] pol_d . F_r(dirs[d Q + q]) (device arrays; F of D Q directions)
 int farfield_na(Operator& op, const c64* x, long long n3, int R, const double* ddirs, const double* dw,
                 const c64* dpol, int D, int Q, c64* dout);

@@ -273,6 +273,68 @@ __device__ cplx<T>* fft_tile(cplx<T>* a, cplx<T>* b, const FFTPlan& p, const cpl
     return in;
 }
 
+// The same stages over three tiles at once (the three field components of
+// the fused x pass), each with its own scratch: three times the butterflies
+// per stage barrier, so narrow tiles keep every thread busy.  Tile c starts
+// at a + c cs (its scratch at b + c cs); the return value says where the
+// results are (0: a, 1: b).
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void stockham_stage3(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int cs,
+                                                int L, int Ns, unsigned int nsmag, int nl, int ld,
+                                                const cplx<T>* __restrict__ tw) {
+    const int nbf = L / R;
+    const int per = nbf * nl;
+    const int nlsh = log2_p2(nl);
+    for (int b3 = threadIdx.x; b3 < 3 * per; b3 += blockDim.x) {
+        const int c = b3 >= per ? (b3 >= 2 * per ? 2 : 1) : 0;
+        const int b = b3 - c * per;
+        const int l = b & (nl - 1);
+        const int j = b >> nlsh;
+        cplx<T> a[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) a[t] = in[c * cs + (j + t * nbf) * ld + l];
+        const int jq = div_mag(j, Ns, nsmag);
+        const int k = j - jq * Ns;
+        if (Ns > 1) {
+            const cplx<T>* w = tw + k * (R - 1);
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                cplx<T> wt = w[t - 1];
+                if (INV) wt.y = -wt.y;
+                a[t] = a[t] * wt;
+            }
+        }
+        dft<T, R, INV>(a);
+        const int base = jq * Ns * R + k;
+#pragma unroll
+        for (int t = 0; t < R; ++t) out[c * cs + (base + t * Ns) * ld + l] = a[t];
+    }
+}
+
+template <typename T, bool INV>
+__device__ int fft_tile3(cplx<T>* a, cplx<T>* b, int cs, const FFTPlan& p, const cplx<T>* tw, int nl, int ld) {
+    int cur = 0;
+    for (int s = 0; s < p.nst; ++s) {
+        const cplx<T>* in = cur ? b : a;
+        cplx<T>* out = cur ? a : b;
+        const cplx<T>* t = tw + p.twoff[s];
+        const int Ns = p.Ns[s];
+        const unsigned int mg = p.nsmag[s];
+        switch (p.R[s]) {
+            case 16: stockham_stage3<T, 16, INV>(in, out, cs, p.L, Ns, mg, nl, ld, t); break;
+            case 8: stockham_stage3<T, 8, INV>(in, out, cs, p.L, Ns, mg, nl, ld, t); break;
+            case 4: stockham_stage3<T, 4, INV>(in, out, cs, p.L, Ns, mg, nl, ld, t); break;
+            case 2: stockham_stage3<T, 2, INV>(in, out, cs, p.L, Ns, mg, nl, ld, t); break;
+            case 3: stockham_stage3<T, 3, INV>(in, out, cs, p.L, Ns, mg, nl, ld, t); break;
+            case 5: stockham_stage3<T, 5, INV>(in, out, cs, p.L, Ns, mg, nl, ld, t); break;
+            default: stockham_stage3<T, 7, INV>(in, out, cs, p.L, Ns, mg, nl, ld, t); break;
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    return cur;
+}
+
 template <typename T>
 __device__ __forceinline__ void load_twiddles(cplx<T>* dst, const cplx<T>* __restrict__ src, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];

@@ -323,13 +323,15 @@ template <typename T>
 __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int n0, long long inner, int P0, int P1, int P2,
                          const cplx<T>* __restrict__ khat, int H0, int H1, int H2, FFTPlan plan,
                          const cplx<T>* __restrict__ twg, int TW, const cplx<T>* __restrict__ dtab, int dstride,
-                         T ksq, int stw) {
+                         T ksq, int stw, int joint) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const cplx<T>* tw;
     const int L = plan.L;  // == P0
-    cplx<T>* D[4];
+    // three component tiles and one scratch (joint = 0), or three scratch tiles
+    // and stages over the three components at once (joint = 1)
+    cplx<T>* D[6];
     D[0] = tw_setup<T>(smraw, twg, plan, stw, &tw);
-    for (int i = 1; i < 4; ++i) D[i] = D[i - 1] + L * TW;
+    for (int i = 1; i < (joint ? 6 : 4); ++i) D[i] = D[i - 1] + L * TW;
     const long long ntile = (inner + TW - 1) / TW;
     const long long slot = blockIdx.x / ntile;
     const long long i0 = (blockIdx.x - slot * ntile) * TW;
@@ -345,11 +347,18 @@ __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int 
     __syncthreads();
     cplx<T>* cur[3] = {D[0], D[1], D[2]};
     cplx<T>* scr = D[3];
-    for (int c = 0; c < 3; ++c) {
-        cplx<T>* r = fft_tile<T, false>(cur[c], scr, plan, tw, TW, TW);
-        if (r != cur[c]) {
-            scr = cur[c];
-            cur[c] = r;
+    bool flip = false;  // joint: the components' data sit in D[3..5]
+    if (joint) {
+        flip = fft_tile3<T, false>(D[0], D[3], L * TW, plan, tw, TW, TW) != 0;
+        if (flip)
+            for (int c = 0; c < 3; ++c) cur[c] = D[3 + c];
+    } else {
+        for (int c = 0; c < 3; ++c) {
+            cplx<T>* r = fft_tile<T, false>(cur[c], scr, plan, tw, TW, TW);
+            if (r != cur[c]) {
+                scr = cur[c];
+                cur[c] = r;
+            }
         }
     }
     // spectral multiply (a thread keeps its column: blockDim is a multiple of TW)
@@ -389,11 +398,16 @@ __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int 
         cur[2][e] = kxz * a + kyz * b + kzz * cc;
     }
     __syncthreads();
-    for (int c = 0; c < 3; ++c) {
-        cplx<T>* r = fft_tile<T, true>(cur[c], scr, plan, tw, TW, TW);
-        if (r != cur[c]) {
-            scr = cur[c];
-            cur[c] = r;
+    if (joint) {
+        if (fft_tile3<T, true>(flip ? D[3] : D[0], flip ? D[0] : D[3], L * TW, plan, tw, TW, TW))
+            for (int c = 0; c < 3; ++c) cur[c] = (flip ? D[0] : D[3]) + c * L * TW;
+    } else {
+        for (int c = 0; c < 3; ++c) {
+            cplx<T>* r = fft_tile<T, true>(cur[c], scr, plan, tw, TW, TW);
+            if (r != cur[c]) {
+                scr = cur[c];
+                cur[c] = r;
+            }
         }
     }
     const unsigned int n0mag = mag_of(n0);
@@ -664,6 +678,7 @@ struct TileCfg {
     int stw = 1;
     size_t smem = 0;
     bool ok = false;
+    bool joint = false;  // fused x pass: stages over the three components at once
 };
 static const size_t SMEM_STAGE = 100 * 1024;
 template <typename T> static TileCfg finish_cfg(const FFTPlan& p, int w, size_t data) {
@@ -694,13 +709,21 @@ template <typename T> static TileCfg axis_cfg(const FFTPlan& p, long long inner)
     while (tw > 1 && tw / 2 >= inner) tw /= 2;
     return finish_cfg<T>(p, tw, row * tw);
 }
-// fused x pass: four buffers of L x TW (three components and a scratch)
+// fused x pass: six buffers of L x TW (three components, three scratch: the
+// joint three-component stages) when that leaves at least four columns per
+// tile, else four (three components and one scratch, components in turn)
 template <typename T> static TileCfg xfused_cfg(const FFTPlan& p, long long inner) {
-    const int budget = 96 * 1024;
-    int tw = budget / (4 * (int)sizeof(cplx<T>) * std::max(p.L, 1));
-    tw = std::max(1, std::min(32, pow2_floor(std::max(1, tw))));
-    while (tw > 1 && tw / 2 >= inner) tw /= 2;
-    return finish_cfg<T>(p, tw, 4 * sizeof(cplx<T>) * (size_t)p.L * tw);
+    const int budget = 100 * 1024;
+    for (int nbuf : {6, 4}) {
+        int tw = (nbuf == 6 ? budget : 96 * 1024) / (nbuf * (int)sizeof(cplx<T>) * std::max(p.L, 1));
+        tw = std::max(1, std::min(32, pow2_floor(std::max(1, tw))));
+        while (tw > 1 && tw / 2 >= inner) tw /= 2;
+        if (nbuf == 6 && tw < 4 && tw < inner) continue;
+        TileCfg c = finish_cfg<T>(p, tw, nbuf * sizeof(cplx<T>) * (size_t)p.L * tw);
+        c.joint = nbuf == 6;
+        if (c.ok || nbuf == 4) return c;
+    }
+    return TileCfg();
 }
 
 // Every generic pass must fit in shared memory at FP64 (the larger element).
@@ -978,6 +1001,7 @@ int op_set_list(Operator& op, const int* host_list, int nr) {
         op.list_cap = cap;
     }
     VIE_CUDA(cudaMemcpyAsync(op.d_list, host_list, sizeof(int) * nr, cudaMemcpyHostToDevice, op.stream));
+    op.h_list.assign(host_list, host_list + nr);
     return VIE_OK;
 }
 
@@ -1015,6 +1039,7 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
     }
     const double E = sizeof(cplx<T>);
     const double EI = sizeof(cplx<TI>);
+    const long long cst = comp_stride(op);  // component stride of w and y
     const double lineA = 3.0 * n0 * n1 * P2 * E;  // one slot of A
     const double lineB = 3.0 * n0 * P1 * P2 * E;  // one slot of B
     const double vec = 3.0 * op.Nb * EI;          // one compact vector
@@ -1030,7 +1055,7 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
         if (fz) {
             const long long nlines = (long long)ns * 3 * n0 * n1;
             tmr_begin(tid(TMR_ZFWD), op.stream);
-            VIE_TRY(fast_zfwd((const c32*)w, wr, list, op.idx_map, (c32*)A, n0, n1, n2, op.Nb, nlines, P2,
+            VIE_TRY(fast_zfwd((const c32*)w, wr, list, op.idx_map, (c32*)A, n0, n1, n2, cst, nlines, P2,
                               op.ax[2].roots32, op.stream, op.idx_stride));
             tmr_end(tid(TMR_ZFWD), op.stream, ns * (vec + lineA) + 4.0 * op.N);
             count_launch();
@@ -1042,7 +1067,7 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
             const int nt = fft_threads(k_zfwd<T, TI>, p.L, c.smem);
             tmr_begin(tid(TMR_ZFWD), op.stream);
             k_zfwd<T, TI><<<(unsigned)((nlines + c.w - 1) / c.w), nt, c.smem, op.stream>>>(
-                w, wr, list, op.idx_map, A, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), c.w, c.stw,
+                w, wr, list, op.idx_map, A, n0, n1, n2, cst, nlines, p, twp<T>(op.ax[2]), c.w, c.stw,
                 op.idx_stride);
             tmr_end(tid(TMR_ZFWD), op.stream, ns * (vec + lineA) + 4.0 * op.N);
             count_launch();
@@ -1080,7 +1105,7 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
             tmr_begin(tid(TMR_XFUSED), op.stream);
             k_xfused<T><<<(unsigned)grid, 256, c.smem, op.stream>>>(
                 B, n0, inner, P0, P1, P2, kh, op.H[0], op.H[1], op.H[2], p, twp<T>(op.ax[0]), c.w,
-                op.disc ? dtp<T>(op) : nullptr, op.dstride, (T)(op.k0 * op.k0), c.stw);
+                op.disc ? dtp<T>(op) : nullptr, op.dstride, (T)(op.k0 * op.k0), c.stw, c.joint ? 1 : 0);
             tmr_end(tid(TMR_XFUSED), op.stream, 2.0 * ns * lineB + 6.0 * op.H[0] * op.H[1] * op.H[2] * E);
             count_launch();
             VIE_CUDA(cudaGetLastError());
@@ -1102,7 +1127,7 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
             const long long nlines = (long long)ns * 3 * n0 * n1;
             tmr_begin(tid(TMR_ZINV), op.stream);
             VIE_TRY(fast_zinv((const c32*)A, (const c32*)w, wr, (c32*)y, yr, list, op.idx_map, (const float*)chi, n0, n1,
-                              n2, op.Nb, nlines, P2, op.ax[2].roots32, op.stream, op.chi_cs, op.idx_stride));
+                              n2, cst, nlines, P2, op.ax[2].roots32, op.stream, op.chi_cs, op.idx_stride));
             tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
@@ -1113,7 +1138,7 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
             const int nt = fft_threads(k_zinv<T, TI>, p.L, c.smem);
             tmr_begin(tid(TMR_ZINV), op.stream);
             k_zinv<T, TI><<<(unsigned)((nlines + c.w - 1) / c.w), nt, c.smem, op.stream>>>(
-                A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, op.Nb, nlines, p, twp<T>(op.ax[2]), c.w,
+                A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, cst, nlines, p, twp<T>(op.ax[2]), c.w,
                 op.chi_cs, c.stw, op.idx_stride);
             tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
             count_launch();
@@ -1125,6 +1150,10 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
 
 int op_apply(Operator& op, int prec, const void* w, long long wr, void* y, long long yr, const int* d_list, int nr) {
     if (nr <= 0) return VIE_OK;
+    if (op.batch) {
+        if (d_list != op.d_list) return fail(VIE_EINVAL, "a batch operator takes the list set by op_set_list");
+        return batch_apply(op, prec, w, wr, y, yr, nr);
+    }
     if (prec == VIE_PREC_FP64) return apply_t<double, double>(op, (const c64*)w, wr, (c64*)y, yr, d_list, nr);
     if (prec == VIE_PREC_F32X2) return apply_t<dfl, double>(op, (const c64*)w, wr, (c64*)y, yr, d_list, nr);
     return apply_t<float, float>(op, (const c32*)w, wr, (c32*)y, yr, d_list, nr);

@@ -458,6 +458,343 @@ __global__ void __launch_bounds__(Z_THREADS) k_zinv_r(const c32* __restrict__ A,
     }
 }
 
+// ---- multi-body passes: one launch over slots of different bodies ----------
+// A slot is one RHS of one body; all slots of a launch share the padded
+// sizes (the template lengths) but each has its own grid n, voxel map,
+// contrast, kernel spectrum, vectors and work areas (MSlot, vie_internal.cuh).
+// Slots of a body are consecutive.  Each CTA of the z and y passes belongs
+// to one slot (found by binary search over the slots' first CTA); the fused
+// x pass walks the slots of its column tile and restages the kernel tile
+// when the body changes.
+__device__ __forceinline__ int slot_of(const MSlot* __restrict__ sl, int ns, long long blk, int which) {
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const long long b0 = which ? sl[mid].yb0 : sl[mid].zb0;
+        if (b0 <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int L>
+__global__ void __launch_bounds__(Z_THREADS) k_zfwd_m(const MSlot* __restrict__ sl, int ns, c32* __restrict__ A,
+                                                      long long cst, const c32* __restrict__ tw4) {
+    constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2;
+    constexpr int NL = Z_THREADS / R2;
+    constexpr int RS = R2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c32* TA = reinterpret_cast<c32*>(smraw);
+    c32* S = TA + L;
+    stage_table(TA, tw4, L);
+    const int si = slot_of(sl, ns, blockIdx.x, 0);
+    const MSlot d = sl[si];
+    const long long plane = (long long)d.n0 * d.n1;
+    const long long nlines = 3 * plane;
+    const long long line0 = (long long)(blockIdx.x - d.zb0) * NL;
+    const int q2 = threadIdx.x % R2, l = threadIdx.x / R2;
+    const long long line = line0 + l;
+    c32 a[R1];
+    if (line < nlines) {
+        const int c = (int)(line / plane);
+        const long long xy = line - c * plane;
+        const c32* wr = d.w + c * cst;
+        const int* im = d.idx + xy * d.n2;
+#pragma unroll
+        for (int n1i = 0; n1i < R1 / 2; ++n1i) {
+            const int z = n1i * R2 + q2;
+            c32 v = z32();
+            if (z < d.n2) {
+                const int vi = im[z];
+                if (vi >= 0) v = wr[vi];
+            }
+            a[n1i] = v;
+        }
+    } else {
+#pragma unroll
+        for (int n1i = 0; n1i < R1 / 2; ++n1i) a[n1i] = z32();
+    }
+    __syncthreads();
+    dftp2_half_in<float, R1, false>(a);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) a[k1] = a[k1] * tw<false>(TA, k1 * R2 + q2);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) S[(l * R1 + k1) * RS + q2] = a[k1];
+    __syncthreads();
+    c32* Ad = A + d.a_off;
+    for (int it = threadIdx.x; it < NL * R1; it += Z_THREADS) {
+        const int k1 = it % R1, ll = it / R1;
+        c32 b[R2];
+#pragma unroll
+        for (int q = 0; q < R2; ++q) b[q] = S[(ll * R1 + k1) * RS + q];
+        dftp2<float, R2, false>(b);
+        const long long ln = line0 + ll;
+        if (ln < nlines) {
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) Ad[ln * L + k1 + R1 * k2] = b[k2];
+        }
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(Z_THREADS) k_zinv_m(const MSlot* __restrict__ sl, int ns, const c32* __restrict__ A,
+                                                      long long cst, const c32* __restrict__ tw4) {
+    constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2;
+    constexpr int NL = Z_THREADS / R2;
+    constexpr int RS = R2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c32* TB = reinterpret_cast<c32*>(smraw);
+    c32* S = TB + L;
+    stage_table(TB, tw4 + L, L);
+    const int si = slot_of(sl, ns, blockIdx.x, 0);
+    const MSlot d = sl[si];
+    const long long plane = (long long)d.n0 * d.n1;
+    const long long nlines = 3 * plane;
+    const long long line0 = (long long)(blockIdx.x - d.zb0) * NL;
+    const c32* Ad = A + d.a_off;
+    __syncthreads();
+    for (int it = threadIdx.x; it < NL * R1; it += Z_THREADS) {
+        const int k1 = it % R1, ll = it / R1;
+        const long long ln = line0 + ll;
+        c32 b[R2];
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) b[k2] = ln < nlines ? Ad[ln * L + k1 + R1 * k2] : z32();
+        dftp2<float, R2, true>(b);
+#pragma unroll
+        for (int q = 0; q < R2; ++q) S[(ll * R1 + k1) * RS + q] = b[q] * tw<true>(TB, q * R1 + k1);
+    }
+    __syncthreads();
+    const int q2 = threadIdx.x % R2, l = threadIdx.x / R2;
+    const long long line = line0 + l;
+    if (line >= nlines) return;
+    c32 a[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) a[k1] = S[(l * R1 + k1) * RS + q2];
+    dftp2_half_out<float, R1, true>(a);
+    const int c = (int)(line / plane);
+    const long long xy = line - c * plane;
+    const c32* wr = d.w + c * cst;
+    c32* yr = d.y + c * cst;
+    const int* im = d.idx + xy * d.n2;
+#pragma unroll
+    for (int n1i = 0; n1i < R1 / 2; ++n1i) {
+        const int z = n1i * R2 + q2;
+        if (z < d.n2) {
+            const int vi = im[z];
+            if (vi >= 0) {
+                const c32 u = a[n1i];
+                const c32 wv = wr[vi];
+                const float ch = d.chi[vi];
+                yr[vi] = c32{wv.x - ch * u.x, wv.y - ch * u.y};
+            }
+        }
+    }
+}
+
+// y pass over slots: forward A[slot] [3 n0][n1][P2] -> B[slot] [3 n0][P1][P2],
+// inverse B -> A (the half transforms: n1 <= L/2 always holds here)
+template <int L, bool INV>
+__global__ void __launch_bounds__(Fac<L>::R2 * AX_TW) k_axis_m(const MSlot* __restrict__ sl, int ns,
+                                                               c32* __restrict__ A, c32* __restrict__ B,
+                                                               long long inner, const c32* __restrict__ tw4) {
+    constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2, TW = AX_TW, NT = R2 * TW;
+    constexpr int SR = R2 * TW;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c32* T = reinterpret_cast<c32*>(smraw);
+    c32* S = T + L;
+    stage_table(T, tw4 + (INV ? L : 0), L);
+    const int si = slot_of(sl, ns, blockIdx.x, 1);
+    const MSlot d = sl[si];
+    const long long ntile = (inner + TW - 1) / TW;
+    const long long lb = blockIdx.x - d.yb0;
+    const long long o = lb / ntile;
+    const long long i0 = (lb - o * ntile) * TW;
+    const int n_in = INV ? L : d.n1, n_out = INV ? d.n1 : L;
+    const c32* in = INV ? B + d.b_off : A + d.a_off;
+    c32* out = INV ? A + d.a_off : B + d.b_off;
+    const int t = threadIdx.x % TW, n2 = threadIdx.x / TW;
+    __syncthreads();
+    if (!INV) {
+        c32 a[R1];
+        const bool ok = i0 + t < inner;
+#pragma unroll
+        for (int n1 = 0; n1 < R1 / 2; ++n1) {
+            const int p = n1 * R2 + n2;
+            a[n1] = (ok && p < n_in) ? in[(o * n_in + p) * inner + i0 + t] : z32();
+        }
+        dftp2_half_in<float, R1, false>(a);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) a[k1] = a[k1] * tw<false>(T, k1 * R2 + n2);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) S[k1 * SR + n2 * TW + t] = a[k1];
+        __syncthreads();
+        for (int it = threadIdx.x; it < R1 * TW; it += NT) {
+            const int k1 = it / TW, tt = it % TW;
+            c32 b[R2];
+#pragma unroll
+            for (int q = 0; q < R2; ++q) b[q] = S[k1 * SR + q * TW + tt];
+            dftp2<float, R2, false>(b);
+            if (i0 + tt < inner) {
+#pragma unroll
+                for (int k2 = 0; k2 < R2; ++k2) out[(o * n_out + k1 + R1 * k2) * inner + i0 + tt] = b[k2];
+            }
+        }
+    } else {
+        for (int it = threadIdx.x; it < R1 * TW; it += NT) {
+            const int k1 = it / TW, tt = it % TW;
+            const bool ok = i0 + tt < inner;
+            c32 b[R2];
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) b[k2] = ok ? in[(o * n_in + k1 + R1 * k2) * inner + i0 + tt] : z32();
+            dftp2<float, R2, true>(b);
+#pragma unroll
+            for (int q = 0; q < R2; ++q) S[k1 * SR + q * TW + tt] = b[q] * tw<true>(T, q * R1 + k1);
+        }
+        __syncthreads();
+        c32 a[R1];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) a[k1] = S[k1 * SR + n2 * TW + t];
+        dftp2_half_out<float, R1, true>(a);
+        if (i0 + t < inner) {
+#pragma unroll
+            for (int n1 = 0; n1 < R1 / 2; ++n1) {
+                const int p = n1 * R2 + n2;
+                if (p < n_out) out[(o * n_out + p) * inner + i0 + t] = a[n1];
+            }
+        }
+    }
+}
+
+// fused x pass over slots (D1): per column tile, every slot in turn; the
+// kernel tile is restaged whenever the slot's body (spectrum) changes
+template <int L>
+__global__ void __launch_bounds__(XF<L>::NT) k_xfused_m(const MSlot* __restrict__ sl, int ns, c32* __restrict__ B,
+                                                        long long inner, int P1, int P2, int H0, int H1, int H2,
+                                                        const c32* __restrict__ tw4) {
+    constexpr int R1 = XF<L>::R1, R2 = XF<L>::R2, TW = XF<L>::TW, NT = XF<L>::NT;
+    constexpr int SR = XF<L>::SR, SC = XF<L>::SC, HX = XF<L>::HX, HR = XF<L>::HR;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c32* TA = reinterpret_cast<c32*>(smraw);
+    c32* TB = TA + L;
+    c32* Kt = TB + L;           // [6][HX][TW]
+    c32* S = Kt + 6 * HX * TW;  // [3][R1][SR]
+    stage_table(TA, tw4, 2 * L);
+    const long long i0 = (long long)blockIdx.x * TW;
+    const long long HH = (long long)H0 * H1 * H2;
+    __shared__ long long coff[TW];
+    __shared__ unsigned char cneg[TW];
+    if (threadIdx.x < TW) {
+        const long long ii = i0 + threadIdx.x;
+        long long off = -1;
+        unsigned char ng = 0;
+        if (ii < inner) {
+            const int ky = (int)(ii / P2), kz = (int)(ii - (ii / P2) * P2);
+            const bool fly = 2 * ky > P1, flz = 2 * kz > P2;
+            off = (long long)(fly ? P1 - ky : ky) * H2 + (flz ? P2 - kz : kz);
+            ng = (unsigned char)((fly ? 2 : 0) | (flz ? 4 : 0) | ((fly ^ flz) ? 16 : 0));
+        }
+        coff[threadIdx.x] = off;
+        cneg[threadIdx.x] = ng;
+    }
+    const int t = threadIdx.x % TW, n2 = threadIdx.x / TW;
+    const bool okt = i0 + t < inner;
+    const long long rs = (long long)R2 * inner;
+    const c32* khat_cur = nullptr;
+    for (int slot = 0; slot < ns; ++slot) {
+        const MSlot d = sl[slot];
+        if (d.khat != khat_cur) {  // a new body: stage its kernel tile
+            __syncthreads();       // the previous body's tile is no longer read
+            constexpr int NE = 6 * HX * TW;
+            const long long rowst = (long long)H1 * H2;
+            for (int e = threadIdx.x; e < NE; e += NT) {
+                const int tt = e % TW, fx = (e / TW) % HX, qq = e / (TW * HX);
+                const long long off = coff[tt];
+                c32 w = off >= 0 ? d.khat[qq * HH + fx * rowst + off] : z32();
+                if ((cneg[tt] >> qq) & 1) w = c32{-w.x, -w.y};
+                Kt[e] = w;
+            }
+            khat_cur = d.khat;
+        }
+        __syncthreads();
+        const int n0 = d.n0;
+        const long long cs = (long long)n0 * inner;
+        c32* base = B + d.b_off;
+        c32* col = base + (long long)n2 * inner + i0 + t;
+        c32 a[3][R1];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int n1 = 0; n1 < HR; ++n1) a[c][n1] = (okt && n1 * R2 + n2 < n0) ? col[c * cs + n1 * rs] : z32();
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dftp2_half_in<float, R1, false>(a[c]);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) {
+            const c32 w = tw<false>(TA, k1 * R2 + n2);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a[c][k1] = a[c][k1] * w;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) S[c * SC + k1 * SR + n2 * TW + t] = a[c][k1];
+        __syncthreads();
+        for (int it = threadIdx.x; it < R1 * TW; it += NT) {
+            const int k1 = it / TW, tt = it % TW;
+            c32 bx[R2], by[R2], bz[R2];
+#pragma unroll
+            for (int q = 0; q < R2; ++q) {
+                bx[q] = S[0 * SC + k1 * SR + q * TW + tt];
+                by[q] = S[1 * SC + k1 * SR + q * TW + tt];
+                bz[q] = S[2 * SC + k1 * SR + q * TW + tt];
+            }
+            dftp2<float, R2, false>(bx);
+            dftp2<float, R2, false>(by);
+            dftp2<float, R2, false>(bz);
+            const c32* kp = Kt + k1 * TW + tt;
+            const c32* km = Kt + (L - k1) * TW + tt;
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) {
+                const bool flx = 2 * k2 > R2 || (2 * k2 == R2 && k1 > 0);
+                const c32* kt = flx ? km - R1 * k2 * TW : kp + R1 * k2 * TW;
+                c32 kxx = kt[0], kxy = kt[HX * TW], kxz = kt[2 * HX * TW];
+                const c32 kyy = kt[3 * HX * TW], kyz = kt[4 * HX * TW], kzz = kt[5 * HX * TW];
+                if (flx) {
+                    kxy = c32{-kxy.x, -kxy.y};
+                    kxz = c32{-kxz.x, -kxz.y};
+                }
+                const c32 a0 = bx[k2], b0 = by[k2], c0 = bz[k2];
+                bx[k2] = kxx * a0 + kxy * b0 + kxz * c0;
+                by[k2] = kxy * a0 + kyy * b0 + kyz * c0;
+                bz[k2] = kxz * a0 + kyz * b0 + kzz * c0;
+            }
+            dftp2<float, R2, true>(bx);
+            dftp2<float, R2, true>(by);
+            dftp2<float, R2, true>(bz);
+#pragma unroll
+            for (int q = 0; q < R2; ++q) {
+                const c32 w = tw<true>(TB, q * R1 + k1);
+                S[0 * SC + k1 * SR + q * TW + tt] = bx[q] * w;
+                S[1 * SC + k1 * SR + q * TW + tt] = by[q] * w;
+                S[2 * SC + k1 * SR + q * TW + tt] = bz[q] * w;
+            }
+        }
+        __syncthreads();
+        if (okt) {
+#pragma unroll 1
+            for (int c = 0; c < 3; ++c) {
+                c32 o[R1];
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1) o[k1] = S[c * SC + k1 * SR + n2 * TW + t];
+                dftp2_half_out<float, R1, true>(o);
+                c32* q = col + c * cs;
+#pragma unroll
+                for (int n1 = 0; n1 < HR; ++n1)
+                    if (n1 * R2 + n2 < n0) q[n1 * rs] = o[n1];
+            }
+        }
+    }
+}
+
 template <typename K> int set_smem(K k, size_t bytes) {
     if (bytes > 48 * 1024) VIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     return VIE_OK;
@@ -532,6 +869,41 @@ template <int L> int launch_zinv_r(const c32* A, const c32* w, long long wr, c32
     return VIE_OK;
 }
 
+template <int L> int launch_multi(const MSlot* dsl, int ns, long long zblocks, long long yblocks, c32* A, c32* B,
+                                   long long cst, int P1, int P2, const int* H, const c32* tw0, const c32* tw1,
+                                   const c32* tw2, cudaStream_t s) {
+    // all three axes share L here (cubic padded sizes)
+    constexpr int NLz = Z_THREADS / Fac<L>::R2;
+    const size_t smz = sizeof(c32) * (L + (size_t)NLz * Fac<L>::R1 * (Fac<L>::R2 + 1));
+    const size_t smy = sizeof(c32) * (L + (size_t)L * AX_TW);
+    const size_t smx = XF<L>::smem;
+    const long long inner = (long long)P1 * P2;
+    VIE_TRY(set_smem(k_zfwd_m<L>, smz));
+    VIE_TRY(set_smem(k_zinv_m<L>, smz));
+    VIE_TRY(set_smem(k_axis_m<L, false>, smy));
+    VIE_TRY(set_smem(k_axis_m<L, true>, smy));
+    VIE_TRY(set_smem(k_xfused_m<L>, smx));
+    tmr_begin(TMR_ZFWD, s);
+    k_zfwd_m<L><<<(unsigned)zblocks, Z_THREADS, smz, s>>>(dsl, ns, A, cst, tw2);
+    tmr_end(TMR_ZFWD, s);
+    tmr_begin(TMR_YFWD, s);
+    k_axis_m<L, false><<<(unsigned)yblocks, Fac<L>::R2 * AX_TW, smy, s>>>(dsl, ns, A, B, P2, tw1);
+    tmr_end(TMR_YFWD, s);
+    tmr_begin(TMR_XFUSED, s);
+    k_xfused_m<L><<<(unsigned)((inner + XF_TW - 1) / XF_TW), XF<L>::NT, smx, s>>>(dsl, ns, B, inner, P1, P2, H[0], H[1],
+                                                                                 H[2], tw0);
+    tmr_end(TMR_XFUSED, s);
+    tmr_begin(TMR_YINV, s);
+    k_axis_m<L, true><<<(unsigned)yblocks, Fac<L>::R2 * AX_TW, smy, s>>>(dsl, ns, A, B, P2, tw1);
+    tmr_end(TMR_YINV, s);
+    tmr_begin(TMR_ZINV, s);
+    k_zinv_m<L><<<(unsigned)zblocks, Z_THREADS, smz, s>>>(dsl, ns, A, cst, tw2);
+    tmr_end(TMR_ZINV, s);
+    count_launch(5);
+    VIE_CUDA(cudaGetLastError());
+    return VIE_OK;
+}
+
 #define VIE_DISPATCH_L(Lv, CALL) \
     switch (Lv) {                \
         case 16: { constexpr int LL = 16; CALL; } break; \
@@ -569,6 +941,23 @@ int fast_zinv(const c32* A, const c32* w, long long wr, c32* y, long long yr, co
     VIE_DISPATCH_L(L, VIE_TRY(launch_zinv_r<LL>(A, w, wr, y, yr, list, idx, chi, n0, n1, n2, Nb, nlines, tw4, s,
                                                 chi_cs, idx_stride)));
     return VIE_OK;
+}
+
+int multi_lines_per_cta(int L) {
+    int R1 = 0, R2 = 0;
+    fast_factors(L, &R1, &R2);
+    return Z_THREADS / R2;
+}
+
+int fast_multi_apply(const MSlot* dsl, int ns, long long zblocks, long long yblocks, c32* A, c32* B, long long cst,
+                     int L, const int* H, const c32* tw0, const c32* tw1, const c32* tw2, cudaStream_t s) {
+    switch (L) {
+        case 32: return launch_multi<32>(dsl, ns, zblocks, yblocks, A, B, cst, L, L, H, tw0, tw1, tw2, s);
+        case 64: return launch_multi<64>(dsl, ns, zblocks, yblocks, A, B, cst, L, L, H, tw0, tw1, tw2, s);
+        case 128: return launch_multi<128>(dsl, ns, zblocks, yblocks, A, B, cst, L, L, H, tw0, tw1, tw2, s);
+        case 256: return launch_multi<256>(dsl, ns, zblocks, yblocks, A, B, cst, L, L, H, tw0, tw1, tw2, s);
+        default: return fail(VIE_EINVAL, "multi-body launches take cubic padded sizes 32, 64, 128 or 256");
+    }
 }
 
 }  // namespace vie

@@ -60,7 +60,16 @@ struct Operator {
     // voxel maps per batch slot: slot list[s] reads idx_map + list[s] * idx_stride (0: one map for all slots;
     // the block operator of the block-Jacobi preconditioner keeps one map per block)
     long long idx_stride = 0;
+    // component stride of the compact vectors this operator reads and writes (0: Nb).  A multi-body batch
+    // (batch.cu) stores every body's vectors with the batch's largest body size as the stride.
+    long long cstride = 0;
+    // the RHS list last uploaded by op_set_list (host copy)
+    std::vector<int> h_list;
+    // non-null: this operator is the solver's view of a multi-body batch, and op_apply dispatches to it
+    struct BatchOps* batch = nullptr;
 };
+
+inline long long comp_stride(const Operator& op) { return op.cstride ? op.cstride : op.Nb; }
 
 // device allocation helpers (track bytes)
 int dev_alloc(Operator& op, void** p, size_t bytes);
@@ -87,6 +96,8 @@ int op_set_list(Operator& op, const int* host_list, int nr);  // uploads d_list
 // arithmetic on double inputs and outputs.
 int op_apply(Operator& op, int prec, const void* w, long long w_rstride, void* y, long long y_rstride,
              const int* d_list, int nr);
+// the same for a multi-body batch (batch.cu); d_list must be op.d_list as set by op_set_list
+int batch_apply(Operator& op, int prec, const void* w, long long w_rstride, void* y, long long y_rstride, int nr);
 void op_free(Operator& op);
 
 // FP32 fast passes (matvec_fast.cu), power-of-two lengths 16..512
@@ -108,6 +119,23 @@ int fast_zfwd(const c32* w, long long wr, const int* list, const int* idx, c32* 
 int fast_zinv(const c32* A, const c32* w, long long wr, c32* y, long long yr, const int* list, const int* idx,
               const float* chi, int n0, int n1, int n2, long long Nb, long long nlines, int L, const c32* roots,
               cudaStream_t s, long long chi_cs = 0, long long idx_stride = 0);
+
+// one slot (one RHS of one body) of a multi-body launch (batch.cu, matvec_fast.cu)
+struct MSlot {
+    const c32* w;            // input row of the RHS (components cst apart)
+    c32* y;                  // output row
+    const int* idx;          // the body's voxel map [n0][n1][n2]
+    const float* chi;        // the body's contrast [Nb]
+    const c32* khat;         // the body's kernel octant [6][H0][H1][H2]
+    long long a_off, b_off;  // offsets of the slot's work areas in A ([3][n0][n1][P2]) and B ([3][n0][P1][P2])
+    long long zb0, yb0;      // first CTA of the slot in the z and y passes
+    int n0, n1, n2, pad;
+};
+int multi_lines_per_cta(int L);
+// the five FP32 passes over ns slots of equal cubic padded size L, in one launch each
+int fast_multi_apply(const MSlot* d_slots, int ns, long long zblocks, long long yblocks, c32* A, c32* B,
+                     long long cst, int L, const int* H, const c32* tw0, const c32* tw1, const c32* tw2,
+                     cudaStream_t s);
 
 // tensor-core batched complex GEMM (tc_gemm.cu): C = A B, complex64, strided
 int tc_cgemm(int M, int N, int K, int batch, const c32* A, long long sAb, long long sAm, long long sAk, const c32* B,

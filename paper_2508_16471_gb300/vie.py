@@ -30,7 +30,9 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_guesses_rejected",
            "vie_net_create_io", "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune",
            "vie_setup_disc", "vie_farfield_na", "vie_timer_enable", "vie_timer_reset", "vie_timer_read", "vie_timer_name", "vie_timer_count",
-           "vie_set_block_precond", "vie_block_apply_device", "vie_block_layout"]
+           "vie_set_block_precond", "vie_block_apply_device", "vie_block_layout",
+           "vie_batch_create", "vie_batch_destroy", "vie_batch_stride", "vie_batch_info", "vie_batch_apply_device",
+           "vie_batch_solve", "vie_batch_get_current", "vie_batch_farfield_dirs"]
 
 
 class VieError(RuntimeError):
@@ -128,6 +130,16 @@ def load():
     L.vie_stream.restype = P
     L.vie_destroy.argtypes = [P]
     L.vie_destroy.restype = None
+    L.vie_batch_create.argtypes = [C.c_int, C.POINTER(_Grid), C.POINTER(dp), C.c_double, C.POINTER(P)]
+    L.vie_batch_destroy.argtypes = [P]
+    L.vie_batch_destroy.restype = None
+    L.vie_batch_stride.argtypes = [P]
+    L.vie_batch_stride.restype = C.c_longlong
+    L.vie_batch_info.argtypes = [P, C.c_int, C.POINTER(_Info)]
+    L.vie_batch_apply_device.argtypes = [P, P, P, C.c_int, C.c_int]
+    L.vie_batch_solve.argtypes = [P, C.POINTER(_Channel), C.c_int, C.POINTER(_Opts), C.POINTER(_Stats)]
+    L.vie_batch_get_current.argtypes = [P, C.c_int, C.c_int, dp]
+    L.vie_batch_farfield_dirs.argtypes = [P, C.c_int, dp, C.c_int, C.c_int, dp]
     L.vie_last_error.restype = C.c_char_p
     L.vie_timer_enable.argtypes = [C.c_int]
     L.vie_timer_enable.restype = None
@@ -381,6 +393,92 @@ class Handle:
     def apply_device(self, w_ptr: int, y_ptr: int, n_rhs: int, precision=PREC_MIXED):
         _check(load().vie_apply_device(self._h, C.c_void_p(w_ptr), C.c_void_p(y_ptr), int(n_rhs),
                                        int(precision)))
+
+
+class Batch:
+    """Many bodies of uneven grids (vie_batch_*): bodies = [(n, h, eps_r), ...]
+    with one k0; rows of batch vectors are body-major ([body][rhs][3][stride])."""
+
+    def __init__(self, bodies, k0=2.0 * np.pi):
+        L = load()
+        nb = len(bodies)
+        grids = (_Grid * nb)()
+        self._eps = []
+        ptrs = (C.POINTER(C.c_double) * nb)()
+        self.n = []
+        for i, (n, h, eps) in enumerate(bodies):
+            for a in range(3):
+                grids[i].n[a] = int(n[a])
+                grids[i].origin[a] = 0.0
+            grids[i].h = float(h)
+            e = np.ascontiguousarray(eps, dtype=np.float64).reshape(tuple(int(v) for v in n))
+            self._eps.append(e)
+            ptrs[i] = _dptr(e)
+            self.n.append(tuple(int(v) for v in n))
+        hp = C.c_void_p()
+        _check(L.vie_batch_create(nb, grids, ptrs, float(k0), C.byref(hp)))
+        self._h = hp
+        self.n_bodies = nb
+        self.n_rhs = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vie_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def stride(self):
+        return int(load().vie_batch_stride(self._h))
+
+    def info(self, body):
+        i = _Info()
+        _check(load().vie_batch_info(self._h, int(body), C.byref(i)))
+        return dict(n=tuple(i.n), P=tuple(i.P), n_body=int(i.n_body), n_rhs=int(i.n_rhs),
+                    device=int(i.device), device_bytes=float(i.device_bytes))
+
+    def apply_device(self, w_ptr: int, y_ptr: int, n_rhs: int, precision=PREC_MIXED):
+        _check(load().vie_batch_apply_device(self._h, C.c_void_p(w_ptr), C.c_void_p(y_ptr), int(n_rhs),
+                                             int(precision)))
+
+    def solve(self, channels, allow_noconv=False, **opts):
+        o = default_opts(**opts)
+        R = len(channels) * self.n_bodies
+        iters = np.zeros(R, dtype=np.int32)
+        rel = np.zeros(R, dtype=np.float64)
+        st = _Stats()
+        st.iters = iters.ctypes.data_as(C.POINTER(C.c_int))
+        st.relres = rel.ctypes.data_as(C.POINTER(C.c_double))
+        code = load().vie_batch_solve(self._h, _channels(channels), len(channels), C.byref(o), C.byref(st))
+        _check(code, allow=(VIE_ENOCONV,) if allow_noconv else ())
+        self.n_rhs = len(channels)
+        return dict(code=code, converged=st.converged, iters_max=st.iters_max, outer_max=st.outer_max,
+                    matvecs32=st.matvecs32, matvecs64=st.matvecs64, relres_max=st.relres_max,
+                    seconds=st.seconds, iters=iters.reshape(self.n_bodies, -1), relres=rel.reshape(self.n_bodies, -1))
+
+    def get_current(self, body, rhs):
+        out = np.zeros((3,) + self.n[body], dtype=np.complex128)
+        _check(load().vie_batch_get_current(self._h, int(body), int(rhs),
+                                            out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def farfield_dirs(self, body, dirs, basis=BASIS_CART):
+        d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+        out = np.zeros((self.n_rhs, len(d), 3), dtype=np.complex128)
+        _check(load().vie_batch_farfield_dirs(self._h, int(body), _dptr(d), len(d), int(basis),
+                                              out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
 
 
 class Net:
