@@ -80,10 +80,17 @@ def parse():
                    help="with --apply-only: apply the FP64 operator instead of the FP32 one")
     p.add_argument("--apply-f32x2", action="store_true",
                    help="with --apply-only: apply the double-float operator (the residual operator of the solves)")
-    p.add_argument("--workload", default="bodies128", choices=["bodies128", "metasurface-paper", "bodies-uneven"],
+    p.add_argument("--workload", default="bodies128", choices=["bodies128", "metasurface-paper", "bodies-uneven", "learned"],
                    help="metasurface-paper: one solve of the paper-scale PB metasurface (its own JSON line); "
-                        "bodies-uneven: the random-body set of uneven grids (32^3..96^3) in multi-body batches")
+                        "bodies-uneven: the random-body set of uneven grids (32^3..96^3) in multi-body batches; "
+                        "learned: train the initial-guess network on solver-generated solves, then the bench "
+                        "bodies with and without it")
     p.add_argument("--n-bodies", type=int, default=64, help="bodies-uneven: bodies (seeds 0..n-1)")
+    p.add_argument("--train-bodies", type=int, default=250,
+                   help="learned: training bodies (64^3, 16 RHS each; 250 bodies = 4000 solves)")
+    p.add_argument("--epochs", type=int, default=8, help="learned: training epochs")
+    p.add_argument("--channels", type=int, nargs=4, default=(20, 40, 80, 128),
+                   help="learned: U-Net widths per level (20 40 80 128: 1.9 M parameters)")
     p.add_argument("--batch", type=int, default=8, help="bodies-uneven: bodies per multi-body batch")
     p.add_argument("--box", type=float, nargs=3, default=(40.0, 12.0, 2.0),
                    help="metasurface-paper: box in wavelengths (paper x, y, z)")
@@ -813,6 +820,81 @@ def run_bodies_uneven(args):
     return 0
 
 
+def run_learned(args):
+    """The learned initial guess at its configured scale: a 4-level 3-D U-Net
+    (--channels, BF16 activations, FP32 accumulation) trained by the
+    library's kernels on solver-generated solves of 64^3 random bodies (1-lambda
+    box, seeds 10000+, 16 RHS each), then the 8 bench bodies (128^3, same box,
+    32 RHS) solved with x0 = 0 and with the network's start (the network sees
+    the same lambda/16 coarse voxels at both sizes: factor 4 at 64^3, 8 at
+    128^3).  Solves/s of the learned solves include the network inference."""
+    import numpy as np
+    import torch
+    from paper_2508_16471_gb300 import build as libbuild
+    from paper_2508_16471_gb300 import inputs
+    from paper_2508_16471_gb300 import learned
+    from paper_2508_16471_gb300 import vie as V
+    torch.cuda.set_device(0)
+    libbuild.build()
+    V.load()
+    log = lambda *a: print(*a, file=sys.stderr, flush=True)  # noqa: E731
+    n_tr, f_tr = 64, 4
+    D = n_tr // f_tr
+    t0 = time.perf_counter()
+    X, T, M, it_tr = learned.generate(n_tr, 1.0 / n_tr, list(range(10000, 10000 + args.train_bodies)), 8, f_tr)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    log(f"training data: {X.shape[0]} solves in {t_gen:.1f}s")
+    net = V.Net(tuple(args.channels), seed=0, bf16=True)
+    t0 = time.perf_counter()
+    hist = learned.train(net, X, T, M, D, epochs=args.epochs, batch=8, lr=2e-3, lr_decay=0.8)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    log(f"trained {net.num_params()} parameters, {args.epochs} epochs in {t_train:.1f}s, loss {hist[0]:.4f} -> "
+        f"{hist[-1]:.4f}")
+    del X, T, M
+    torch.cuda.empty_cache()
+    seeds = body_seeds(0, args.bodies)
+    wls = [inputs.random_body_workload(s_, n_axis=N_AXIS, h=H, n_dirs=N_DIRS) for s_ in seeds]
+    chs = [(c.khat, c.pol) for c in wls[0].channels]
+    R = len(chs)
+    g = wls[0].grid
+    opts = dict(tol=1e-6, restart=args.restart, max_iter=args.max_iter)
+    res = {"plain": [0.0, 0, []], "learned": [0.0, 0, []]}
+    rejected = 0
+    with V.Handle(g.n, g.h, wls[0].eps, wls[0].k0) as hd:
+        hd.attach_net(net, N_AXIS // D)
+        for i, wl in enumerate(wls):
+            hd.set_eps(wl.eps)
+            for mode in ("plain", "learned"):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = hd.solve(chs, allow_noconv=True, use_x0=2 if mode == "learned" else 0, **opts)
+                torch.cuda.synchronize()
+                r = res[mode]
+                r[0] += time.perf_counter() - t0
+                r[1] += int(st["converged"])
+                r[2].extend(st["iters"].tolist())
+            rejected += hd.guesses_rejected()
+    out = {m: {"solves_per_s": v[1] / v[0], "seconds": v[0], "solved": v[1], "iters_mean": float(np.mean(v[2]))}
+           for m, v in res.items()}
+    line = {"metric": "VIE solves/sec to FP64 residual 1e-6 (128^3 random bodies, 32 RHS/body), learned start vs "
+                      "zero start",
+            "value": out["learned"]["solves_per_s"], "unit": "solves/s", "higher_is_better": True, "n_gpus": 1,
+            "dtype": "f32+f64 (network bf16 storage, fp32 accumulate)", "data": "synthetic (seeded random bodies)",
+            "config": {"workload": f"{len(wls)} bench bodies (seeds {seeds[0]}..{seeds[-1]}), 128^3, 1 lambda box, "
+                                   f"{R} RHS", "train": f"{it_tr.size} solves of {args.train_bodies} 64^3 bodies "
+                                   f"(seeds 10000+), {args.epochs} epochs, batch 8, Adam lr 2e-3 x 0.8/epoch",
+                       "network": {"channels": list(args.channels), "params": net.num_params(),
+                                   "coarse_grid": f"{D}^3 (lambda/16 voxels)"}},
+            "learned": out["learned"], "plain": out["plain"], "guesses_rejected": rejected,
+            "gain_iters": 1.0 - out["learned"]["iters_mean"] / out["plain"]["iters_mean"],
+            "speedup": out["learned"]["solves_per_s"] / out["plain"]["solves_per_s"],
+            "train_seconds": t_train, "generate_seconds": t_gen, "loss_first_last": [hist[0], hist[-1]]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -821,6 +903,8 @@ def main():
         return run_metasurface_paper(args)
     if args.workload == "bodies-uneven":
         return run_bodies_uneven(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

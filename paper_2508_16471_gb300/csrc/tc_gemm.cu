@@ -17,8 +17,11 @@
 // (8-row x 16-byte core matrices), one elected thread issues tcgen05.mma with
 // shared-memory descriptors, completion is signalled through an mbarrier by
 // tcgen05.commit, and the epilogue reads the accumulator with tcgen05.ld.
-// Every wait is bounded; on timeout the kernel records an error flag, frees
-// its tensor memory and returns.
+// Two stage buffers alternate: while the tensor cores work on chunk c, the
+// threads convert and stage chunk c + 1 into the other buffer, waiting only
+// for the MMAs of chunk c - 1 that last read it.  Every wait is bounded; on
+// timeout the kernel records an error flag, frees its tensor memory and
+// returns.
 #include <atomic>
 #include <cstdint>
 
@@ -90,6 +93,49 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 
 }  // namespace
 
+// stage chunk kr0 of A (128 rows x TC_BK real) and of Bs^T (TC_BN real output
+// columns x TC_BK real) as tf32 hi / lo into one stage buffer
+__device__ __forceinline__ void tc_stage(uint8_t* sA_hi, uint8_t* sA_lo, uint8_t* sB_hi, uint8_t* sB_lo, int M, int N,
+                                         int K, const c32* __restrict__ A, long long sAm, long long sAk,
+                                         const c32* __restrict__ B, long long sBk, long long sBn, int m0, int nr0,
+                                         int kr0) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < TC_BM * (TC_BK / 2); e += TC_THREADS) {
+        const int row = e / (TC_BK / 2), kc = e % (TC_BK / 2);
+        const int m = m0 + row, k = kr0 / 2 + kc;
+        c32 v = {0.f, 0.f};
+        if (m < M && k < K) v = A[m * sAm + k * sAk];
+        const uint32_t hr = to_tf32(v.x), hi_ = to_tf32(v.y);
+        const uint32_t lr = to_tf32(v.x - __uint_as_float(hr)), li = to_tf32(v.y - __uint_as_float(hi_));
+        const uint32_t o0 = core_off(row, 2 * kc), o1 = core_off(row, 2 * kc + 1);
+        *reinterpret_cast<uint32_t*>(sA_hi + o0) = hr;
+        *reinterpret_cast<uint32_t*>(sA_hi + o1) = hi_;
+        *reinterpret_cast<uint32_t*>(sA_lo + o0) = lr;
+        *reinterpret_cast<uint32_t*>(sA_lo + o1) = li;
+    }
+    // Bs^T: row = real output column nr, K contiguous
+    for (int e = tid; e < (TC_BN / 2) * (TC_BK / 2); e += TC_THREADS) {
+        const int nc = e / (TC_BK / 2), kc = e % (TC_BK / 2);
+        const int n = nr0 / 2 + nc, k = kr0 / 2 + kc;
+        c32 v = {0.f, 0.f};
+        if (n < N && k < K) v = B[k * sBk + n * sBn];
+        // rows 2nc (re output) and 2nc+1 (im output); columns 2kc (A re) and 2kc+1 (A im)
+        const float vals[4] = {v.x, -v.y, v.y, v.x};
+        const int rr[4] = {2 * nc, 2 * nc, 2 * nc + 1, 2 * nc + 1};
+        const int kk[4] = {2 * kc, 2 * kc + 1, 2 * kc, 2 * kc + 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t h = to_tf32(vals[q]);
+            const uint32_t l = to_tf32(vals[q] - __uint_as_float(h));
+            const uint32_t o = core_off(rr[q], kk[q]);
+            *reinterpret_cast<uint32_t*>(sB_hi + o) = h;
+            *reinterpret_cast<uint32_t*>(sB_lo + o) = l;
+        }
+    }
+}
+
+constexpr uint32_t TC_STAGE_BYTES = (uint32_t)(2 * TC_BM + 2 * TC_BN) * TC_BK * 4;
+
 // grid: (ceil(2N / TC_BN), ceil(M / TC_BM), batch)
 __global__ void __launch_bounds__(TC_THREADS) k_tc_cgemm(int M, int N, int K, const c32* __restrict__ A, long long sAb,
                                                         long long sAm, long long sAk, const c32* __restrict__ B,
@@ -97,11 +143,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_cgemm(int M, int N, int K, co
                                                         c32* __restrict__ C, long long sCb, long long sCm,
                                                         long long sCn, int* __restrict__ err) {
     extern __shared__ __align__(1024) uint8_t tc_smem[];
-    uint8_t* sA_hi = tc_smem;
-    uint8_t* sA_lo = sA_hi + TC_BM * TC_BK * 4;
-    uint8_t* sB_hi = sA_lo + TC_BM * TC_BK * 4;
-    uint8_t* sB_lo = sB_hi + TC_BN * TC_BK * 4;
-    __shared__ __align__(8) uint64_t bar;
+    uint8_t* stage[2] = {tc_smem, tc_smem + TC_STAGE_BYTES};
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int failed;
 
@@ -119,7 +162,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_cgemm(int M, int N, int K, co
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;");
         failed = 0;
     }
@@ -129,69 +173,67 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_cgemm(int M, int N, int K, co
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = tc_idesc();
     const int KR = 2 * K;  // real K
-    uint32_t phase = 0;
-    int chunk = 0;
-    for (int kr0 = 0; kr0 < KR; kr0 += TC_BK, ++chunk) {
-        // stage A: 128 rows x TC_BK real (TC_BK/2 complex) -> hi / lo
-        for (int e = tid; e < TC_BM * (TC_BK / 2); e += TC_THREADS) {
-            const int row = e / (TC_BK / 2), kc = e % (TC_BK / 2);
-            const int m = m0 + row, k = kr0 / 2 + kc;
-            c32 v = {0.f, 0.f};
-            if (m < M && k < K) v = A[m * sAm + k * sAk];
-            const uint32_t hr = to_tf32(v.x), hi_ = to_tf32(v.y);
-            const uint32_t lr = to_tf32(v.x - __uint_as_float(hr)), li = to_tf32(v.y - __uint_as_float(hi_));
-            const uint32_t o0 = core_off(row, 2 * kc), o1 = core_off(row, 2 * kc + 1);
-            *reinterpret_cast<uint32_t*>(sA_hi + o0) = hr;
-            *reinterpret_cast<uint32_t*>(sA_hi + o1) = hi_;
-            *reinterpret_cast<uint32_t*>(sA_lo + o0) = lr;
-            *reinterpret_cast<uint32_t*>(sA_lo + o1) = li;
-        }
-        // stage B as Bs^T: row = real output column nr, K contiguous
-        for (int e = tid; e < (TC_BN / 2) * (TC_BK / 2); e += TC_THREADS) {
-            const int nc = e / (TC_BK / 2), kc = e % (TC_BK / 2);
-            const int n = nr0 / 2 + nc, k = kr0 / 2 + kc;
-            c32 v = {0.f, 0.f};
-            if (n < N && k < K) v = B[k * sBk + n * sBn];
-            // rows 2nc (re output) and 2nc+1 (im output); columns 2kc (A re) and 2kc+1 (A im)
-            const float vals[4] = {v.x, -v.y, v.y, v.x};
-            const int rr[4] = {2 * nc, 2 * nc, 2 * nc + 1, 2 * nc + 1};
-            const int kk[4] = {2 * kc, 2 * kc + 1, 2 * kc, 2 * kc + 1};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint32_t h = to_tf32(vals[q]);
-                const uint32_t l = to_tf32(vals[q] - __uint_as_float(h));
-                const uint32_t o = core_off(rr[q], kk[q]);
-                *reinterpret_cast<uint32_t*>(sB_hi + o) = h;
-                *reinterpret_cast<uint32_t*>(sB_lo + o) = l;
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
+    const int nch = (KR + TC_BK - 1) / TC_BK;
+    uint32_t phase[2] = {0, 0};
+    auto bufs = [&](int b, uint8_t** ah, uint8_t** al, uint8_t** bh, uint8_t** bl) {
+        *ah = stage[b];
+        *al = *ah + TC_BM * TC_BK * 4;
+        *bh = *al + TC_BM * TC_BK * 4;
+        *bl = *bh + TC_BN * TC_BK * 4;
+    };
+    {
+        uint8_t *ah, *al, *bh, *bl;
+        bufs(0, &ah, &al, &bh, &bl);
+        tc_stage(ah, al, bh, bl, M, N, K, A, sAm, sAk, B, sBk, sBn, m0, nr0, 0);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    for (int c = 0; c < nch; ++c) {
+        const int b = c & 1;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t ah = smem_u32(sA_hi), al = smem_u32(sA_lo), bh = smem_u32(sB_hi), bl = smem_u32(sB_lo);
+            uint8_t *ah, *al, *bh, *bl;
+            bufs(b, &ah, &al, &bh, &bl);
+            const uint32_t aH = smem_u32(ah), aL = smem_u32(al), bH = smem_u32(bh), bL = smem_u32(bl);
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 8; ++kk) {
                 const uint32_t off = (uint32_t)kk * 2 * 128;  // two K core matrices per MMA (K = 8)
-                const int acc0 = (chunk > 0 || kk > 0) ? 1 : 0;
-                mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc0);
-                mma_tf32(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1);
-                mma_tf32(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, 1);
+                const int acc0 = (c > 0 || kk > 0) ? 1 : 0;
+                mma_tf32(tmem, smem_desc(aH + off), smem_desc(bH + off), idesc, acc0);
+                mma_tf32(tmem, smem_desc(aH + off), smem_desc(bL + off), idesc, 1);
+                mma_tf32(tmem, smem_desc(aL + off), smem_desc(bH + off), idesc, 1);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&bar)));
+                smem_u32(&bar[b])));
         }
-        __syncthreads();
-        if (!mbar_wait(smem_u32(&bar), phase)) {
-            if (tid == 0) {
-                failed = 1;
-                atomicOr(err, 1);
+        if (c + 1 < nch) {
+            // the other buffer was last read by the MMAs of chunk c - 1
+            const int nb = b ^ 1;
+            if (c >= 1) {
+                if (!mbar_wait(smem_u32(&bar[nb]), phase[nb]) && tid == 0) {
+                    failed = 1;
+                    atomicOr(err, 1);
+                }
+                phase[nb] ^= 1;
             }
+            __syncthreads();
+            if (failed) break;
+            uint8_t *ah, *al, *bh, *bl;
+            bufs(nb, &ah, &al, &bh, &bl);
+            tc_stage(ah, al, bh, bl, M, N, K, A, sAm, sAk, B, sBk, sBn, m0, nr0, (c + 1) * TC_BK);
+            asm volatile("fence.proxy.async.shared::cta;");
         }
-        phase ^= 1;
         __syncthreads();
-        if (failed) break;
     }
+    // the last commit completes after every MMA before it
+    if (!failed && nch > 0) {
+        const int lb = (nch - 1) & 1;
+        if (!mbar_wait(smem_u32(&bar[lb]), phase[lb]) && tid == 0) {
+            failed = 1;
+            atomicOr(err, 1);
+        }
+    }
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!failed) {
         // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
@@ -227,7 +269,7 @@ int tc_cgemm(int M, int N, int K, int batch, const c32* A, long long sAb, long l
     if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return VIE_OK;
     dim3 g((2 * N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
     if (g.y > 65535 || g.z > 65535) return fail(VIE_EINVAL, "tensor-core GEMM grid too large");
-    const size_t sm = (size_t)(2 * TC_BM + 2 * TC_BN) * TC_BK * 4;
+    const size_t sm = 2 * (size_t)TC_STAGE_BYTES;  // two stage buffers
     static std::atomic<bool> init{false};  // repeated attribute calls from racing threads are harmless
     if (!init) {
         VIE_CUDA(cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
