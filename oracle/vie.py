@@ -389,6 +389,60 @@ def gmres(apply, b, tol=1e-12, restart=60, maxiter=5000, x0=None):
     return x.reshape(shape), dict(iters=it, relres=beta / bnorm, converged=beta <= tol * bnorm)
 
 
+def cocr(op, b, tol=1e-12, maxiter=100000):
+    """Solve A w = b (A = I - diag(chi) K, ``op`` an FFTOperator) by the
+    conjugate orthogonal conjugate residual method (Sogabe and Zhang, J.
+    Comput. Appl. Math. 199, 2007), a short recurrence for complex symmetric
+    systems.  K is complex symmetric (reciprocity), so on the body voxels
+    S = diag(chi)^-1 A = diag(1/chi) - K is too, and COCR runs on S w = b / chi
+    with the unconjugated product u^T v.  The residual of A follows as
+    b - A w = chi (b/chi - S w).  Stops when ||b - A w||_2 <= tol ||b||_2, checked
+    at the end against the operator itself.  Returns (w, info)."""
+    chi = op.chi
+    body = chi > 0
+    inv = np.zeros_like(chi)
+    inv[body] = 1.0 / chi[body]
+    mask = body[None].astype(float)
+
+    def S(v):
+        return (inv[None] * v - op.convolve(v)) * mask
+
+    bv = np.asarray(b, dtype=np.complex128).reshape((3,) + op.n)
+    bnorm = np.linalg.norm(bv)
+    x = np.zeros_like(bv)
+    if bnorm == 0.0:
+        return x, dict(iters=0, relres=0.0, converged=True)
+    r = inv[None] * bv
+    Sr = S(r)
+    p = r.copy()
+    Sp = Sr.copy()
+    rho = np.sum(r * Sr)
+    it = 0
+    while it < maxiter:
+        alpha = rho / np.sum(Sp * Sp)
+        x += alpha * p
+        r -= alpha * Sp
+        it += 1
+        if np.linalg.norm(chi[None] * r) <= tol * bnorm:
+            true = np.linalg.norm(bv - op(x)) / bnorm
+            if true <= tol:
+                return x, dict(iters=it, relres=true, converged=True)
+            r = inv[None] * (bv - op(x))  # restart the recurrence from the true residual
+            Sr = S(r)
+            p = r.copy()
+            Sp = Sr.copy()
+            rho = np.sum(r * Sr)
+            continue
+        Sr = S(r)
+        rho_new = np.sum(r * Sr)
+        beta = rho_new / rho
+        rho = rho_new
+        p = r + beta * p
+        Sp = Sr + beta * Sp
+    true = np.linalg.norm(bv - op(x)) / bnorm
+    return x, dict(iters=it, relres=true, converged=true <= tol)
+
+
 # --------------------------------------------------------------------------- #
 # far field and detector projection
 # --------------------------------------------------------------------------- #
@@ -499,8 +553,9 @@ def sphere_quadrature(L):
 def solve_channels(n, h, k0, eps_r, channels, tol=1e-12, restart=80, maxiter=20000,
                    method="fft", origin=(0.0, 0.0, 0.0), workers=None):
     """Solve the VIE for each channel (khat, pol).  ``method`` is 'fft'
-    (GMRES with the FFT operator), 'direct' (GMRES with the direct sum) or
-    'lu' (dense LU).  Returns (w[R,3,n0,n1,n2], infos)."""
+    (GMRES with the FFT operator), 'cocr' (COCR with the FFT operator),
+    'direct' (GMRES with the direct sum) or 'lu' (dense LU).  Returns
+    (w[R,3,n0,n1,n2], infos)."""
     chi = contrast(eps_r)
     out, infos = [], []
     if method == "lu":
@@ -516,6 +571,8 @@ def solve_channels(n, h, k0, eps_r, channels, tol=1e-12, restart=80, maxiter=200
             x = np.linalg.solve(A, b.reshape(-1)).reshape(b.shape)
             info = dict(iters=0, relres=np.linalg.norm(A @ x.reshape(-1) - b.reshape(-1)) /
                         np.linalg.norm(b), converged=True)
+        elif method == "cocr":
+            x, info = cocr(op, b, tol=tol, maxiter=maxiter)
         else:
             x, info = gmres(op, b, tol=tol, restart=restart, maxiter=maxiter)
         out.append(x)
