@@ -63,6 +63,9 @@ def parse():
     p.add_argument("--restart", type=int, default=64)
     p.add_argument("--inner-floor", type=float, default=0.7,
                    help="mixed mode: inner solves stop at inner_floor x tol x ||b|| at the latest")
+    p.add_argument("--arnoldi", type=int, default=1, choices=[0, 1],
+                   help="GMRES orthogonalisation: 0 classical Gram-Schmidt (two passes over the basis), "
+                        "1 one-sweep Arnoldi (one pass, shifted recurrence)")
     p.add_argument("--reorth-eta", type=float, default=0.1,
                    help="GMRES re-orthogonalisation threshold (second Gram-Schmidt pass when ||w'||^2 < eta ||w||^2)")
     p.add_argument("--inner-tol", type=float, default=1e-6,
@@ -341,7 +344,7 @@ def run_ours(args):
         wl = inputs.random_body_workload(SEED0, n_axis=N_AXIS, h=H, n_dirs=N_DIRS)
         chs0 = [(c.khat, c.pol) for c in wl.channels][:args.profile_solve]
         with V.Handle(wl.grid.n, wl.grid.h, wl.eps, wl.k0) as hd0:
-            hd0.solve(chs0, tol=1e-6, restart=args.restart, max_iter=12, allow_noconv=True)
+            hd0.solve(chs0, tol=1e-6, restart=args.restart, max_iter=12, allow_noconv=True, arnoldi=args.arnoldi)
         return 0
 
     seeds = body_seeds(rank, args.bodies)
@@ -356,7 +359,8 @@ def run_ours(args):
     stream = torch.cuda.ExternalStream(hd.stream())
     solver = {"gmres": V.SOLVER_GMRES, "bicgstab": V.SOLVER_BICGSTAB, "cocr": V.SOLVER_COCR}[args.solver]
     opts = dict(tol=1e-6, restart=args.restart, precision=V.PREC_MIXED, max_iter=args.max_iter,
-                inner_tol=args.inner_tol, reorth_eta=args.reorth_eta, inner_floor=args.inner_floor, solver=solver)
+                inner_tol=args.inner_tol, reorth_eta=args.reorth_eta, inner_floor=args.inner_floor, solver=solver,
+                arnoldi=args.arnoldi if solver == V.SOLVER_GMRES else 0)
 
     def step(i):
         hd.set_eps_device(eps_dev[i % len(eps_dev)].data_ptr())
@@ -441,7 +445,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st = hd.solve(chs, allow_noconv=True, tol=1e-6, restart=args.restart, precision=V.PREC_FP64,
-                      max_iter=args.max_iter)
+                      max_iter=args.max_iter, arnoldi=args.arnoldi)
         torch.cuda.synchronize()
         tp = time.perf_counter() - t0
         plain = {"value": int(st["converged"]) / tp, "unit": UNIT, "rhs": R, "body_seed": seeds[b0],
@@ -524,7 +528,9 @@ def run_ours(args):
         "data": "synthetic (seeded random bodies)",
         "config": {"workload": f"random bodies {N_AXIS}^3, h=lambda/128 (1 lambda box), eps_r in [1.5,6], "
                                f"{R} RHS/body ({N_DIRS} Fibonacci directions x 2 pol), tol 1e-6",
-                   "solver": (f"mixed FP32 matvec / FP64 Arnoldi GMRES({args.restart})" if args.solver == "gmres"
+                   "solver": (f"mixed FP32 matvec / FP64 Arnoldi GMRES({args.restart}), "
+                              + ("one-sweep" if args.arnoldi else "classical Gram-Schmidt")
+                              if args.solver == "gmres"
                               else f"mixed FP32 matvec {args.solver.upper()}") + " + FP64 refinement",
                    "bodies_per_rank": args.bodies, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (no flush)"},

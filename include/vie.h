@@ -128,6 +128,18 @@ typedef struct vie_solve_opts {
     double inner_floor; /* mixed mode: an inner solve stops once its recurrence
                           residual is below max(inner_tol ||r||, inner_floor tol
                           ||b||) (default 0.7, in (0, 1])                         */
+    int arnoldi;       /* orthogonalisation of GMRES without a preconditioner:
+                          1 (default) one-sweep Arnoldi: the operator is applied
+                          to the not yet orthogonalised vector and the Arnoldi
+                          relation of the shifted operator A - I gives the next
+                          Hessenberg column, so one pass over the basis per step
+                          orthogonalises, normalises and takes the inner
+                          products (Pythagorean norm; two explicit classical
+                          passes where beta^2 < reorth_eta ||B v||^2); 0
+                          classical Gram-Schmidt, inner products then update
+                          (two passes per step, a second pair where the
+                          reorth_eta test asks for it).  FGMRES (precond 1, 2),
+                          BiCGStab and COCR ignore it                             */
 } vie_solve_opts;
 
 typedef struct vie_solve_stats {

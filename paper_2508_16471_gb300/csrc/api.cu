@@ -160,6 +160,7 @@ void vie_default_opts(vie_solve_opts* o) {
     o->resid_fp64 = 0;
     o->reorth_eta = 0.1;
     o->inner_floor = 0.7;
+    o->arnoldi = 1;
 }
 
 const char* vie_last_error(void) { return g_err.c_str(); }
@@ -268,6 +269,7 @@ int vie_solve(vie_handle* hd, const vie_channel* ch, int n_rhs, const vie_solve_
         return fail(VIE_ESTATE, "precond = 2 needs vie_set_block_precond, mixed precision, GMRES and use_x0 0 or 1");
     if (!(o.reorth_eta >= 0) || !std::isfinite(o.reorth_eta)) return fail(VIE_EINVAL, "reorth_eta must be >= 0");
     if (!(o.inner_floor > 0) || !(o.inner_floor <= 1)) return fail(VIE_EINVAL, "inner_floor must be in (0, 1]");
+    if (o.arnoldi != 0 && o.arnoldi != 1) return fail(VIE_EINVAL, "arnoldi must be 0 or 1");
     if (o.solver != VIE_SOLVER_GMRES && o.solver != VIE_SOLVER_BICGSTAB && o.solver != VIE_SOLVER_COCR)
         return fail(VIE_EINVAL, "solver must be VIE_SOLVER_GMRES, VIE_SOLVER_BICGSTAB or VIE_SOLVER_COCR");
     if (o.solver == VIE_SOLVER_BICGSTAB && (o.restart < 8 || o.precond || o.use_x0 == 2))

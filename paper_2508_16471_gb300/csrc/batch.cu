@@ -306,7 +306,7 @@ int vie_batch_solve(vie_batch* bt, const vie_channel* ch, int n_rhs, const vie_s
     else vie_default_opts(&o);
     if (!(o.tol > 0) || o.restart < 1 || o.restart > MAX_RESTART || o.max_iter < 1 || !(o.inner_tol > 0) ||
         o.precision != VIE_PREC_MIXED || o.solver != VIE_SOLVER_GMRES || o.precond != 0 || o.use_x0 != 0 ||
-        !(o.inner_floor > 0) || !(o.inner_floor <= 1) || !(o.reorth_eta >= 0))
+        !(o.inner_floor > 0) || !(o.inner_floor <= 1) || !(o.reorth_eta >= 0) || (o.arnoldi != 0 && o.arnoldi != 1))
         return fail(VIE_EINVAL, "batched solves take mixed-precision GMRES from x0 = 0 without a preconditioner");
     for (int r = 0; r < n_rhs; ++r) {
         double kn = 0;

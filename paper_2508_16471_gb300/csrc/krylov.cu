@@ -63,6 +63,85 @@ __device__ __forceinline__ double warp_sum_comp(float v) {
 }
 __device__ __forceinline__ double warp_sum_comp(double v) { return warp_sum(v); }
 
+// Warp sums of eight values per lane by reduce-scatter: at each of the levels
+// 16, 8, 4 a lane keeps half of its values and adds its partner's copy of
+// that half (sending the other half), so 4 + 2 + 1 exchanges leave each lane
+// one value q (bits 4, 3, 2 of the lane index); two full exchanges (levels 2,
+// 1) finish it.  Returns the sum of value q, which every lane of the group of
+// four that holds it receives.  FP32 values travel as TwoSum (sum, error)
+// pairs, as in warp_sum_comp; FP64 ones are added plainly.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float so, float co) {
+    const float t = s + so;
+    const float bb = t - s;
+    const float err = (s - (t - bb)) + (so - bb);
+    c = c + co + err;
+    s = t;
+}
+__device__ __forceinline__ double warp_sum8(const float (&v)[8], int lane, int& q) {
+    float s[4], c[4];
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float so = __shfl_xor_sync(0xffffffffu, up ? v[k] : v[k + 4], 16);
+            s[k] = up ? v[k + 4] : v[k];
+            c[k] = 0.f;
+            two_sum_acc(s[k], c[k], so, 0.f);
+        }
+    }
+#pragma unroll
+    for (int lev = 0; lev < 2; ++lev) {
+        const int o = lev ? 4 : 8;
+        const int h = lev ? 1 : 2;
+        const bool up = lane & o;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k >= h) break;
+            const float ss = up ? s[k] : s[k + h], cs = up ? c[k] : c[k + h];
+            const float so = __shfl_xor_sync(0xffffffffu, ss, o);
+            const float co = __shfl_xor_sync(0xffffffffu, cs, o);
+            if (up) {
+                s[k] = s[k + h];
+                c[k] = c[k + h];
+            }
+            two_sum_acc(s[k], c[k], so, co);
+        }
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s[0], o);
+        const float co = __shfl_xor_sync(0xffffffffu, c[0], o);
+        two_sum_acc(s[0], c[0], so, co);
+    }
+    q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    return (double)s[0] + (double)c[0];
+}
+__device__ __forceinline__ double warp_sum8(const double (&v)[8], int lane, int& q) {
+    double s[4];
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            s[k] = (up ? v[k + 4] : v[k]) + __shfl_xor_sync(0xffffffffu, up ? v[k] : v[k + 4], 16);
+    }
+#pragma unroll
+    for (int lev = 0; lev < 2; ++lev) {
+        const int o = lev ? 4 : 8;
+        const int h = lev ? 1 : 2;
+        const bool up = lane & o;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k >= h) break;
+            const double so = __shfl_xor_sync(0xffffffffu, up ? s[k] : s[k + h], o);
+            s[k] = (up ? s[k + h] : s[k]) + so;
+        }
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) s[0] += __shfl_xor_sync(0xffffffffu, s[0], o);
+    q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    return s[0];
+}
+
 // partial[(r*mp1 + i)*nblk + b] = sum over block b of conj(V_i) . V_{j+1}
 // (blocks of KCH_D elements).  Each thread sums its KE_D products in the basis
 // precision T (the stored vectors carry no more than that); the sums across
@@ -240,19 +319,29 @@ __global__ void k_reorth_check(const double* __restrict__ normpart, int nblk, co
 }
 
 // One thread per listed RHS: finish step j (Givens rotations, residual estimate).
+// With beta2 (the one-sweep Arnoldi) the new subdiagonal entry is sqrt(beta2)
+// and the column is also kept unrotated in Hu, for the shifted operator
+// (diagonal entry minus hu_shift).
 __global__ void k_finish(const double* __restrict__ normpart, int nblk, c64* __restrict__ H, double* __restrict__ cs,
                          c64* __restrict__ sn, c64* __restrict__ g, double* __restrict__ inv, int* __restrict__ kcount,
                          int* __restrict__ flag, const double* __restrict__ target, int j, const int* __restrict__ list,
-                         int nr, int m) {
+                         int nr, int m, const double* __restrict__ beta2 = nullptr, c64* __restrict__ Hu = nullptr,
+                         double hu_shift = 0.0) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nr) return;
     const int r = list[s];
     const int mp1 = m + 1;
     double t = 0;
-    for (int b = 0; b < nblk; ++b) t += normpart[(long long)r * nblk + b];
+    if (beta2) t = fmax(beta2[r], 0.0);
+    else
+        for (int b = 0; b < nblk; ++b) t += normpart[(long long)r * nblk + b];
     const double hn = sqrt(t);
     c64* Hc = H + (long long)r * mp1 * m + (long long)j * mp1;  // column j
     Hc[j + 1] = c64{hn, 0};
+    if (Hu) {
+        c64* Hk = Hu + (long long)r * mp1 * m + (long long)j * mp1;
+        for (int i = 0; i <= j + 1; ++i) Hk[i] = c64{Hc[i].x - (i == j ? hu_shift : 0.0), Hc[i].y};
+    }
     double* c = cs + (long long)r * m;
     c64* sr = sn + (long long)r * m;
     c64* gr = g + (long long)r * mp1;
@@ -612,6 +701,333 @@ __global__ void k_start_cycle(const c64* __restrict__ res, long long rs, cplx<T>
         for (int i = threadIdx.x; i <= m; i += KB) g[(long long)r * (m + 1) + i] = i == 0 ? c64{nr, 0} : c64{0, 0};
 }
 
+// ---- one-sweep Arnoldi -----------------------------------------------------
+// Classical Gram-Schmidt reads the basis twice per step (inner products, then
+// the update).  This variant applies the operator to the pending vector
+// y = A v_j itself, before it is orthogonalised: with v_{j+1} = (y - V l)/beta
+// (l the lag coefficients, beta^2 = ||y||^2 - ||l||^2) and the Arnoldi
+// relation A V = V_{j+1} Hbar (Hbar before the Givens rotations),
+//   A v_{j+1} = (A y - V_{j+1} Hbar l) / beta,
+// so one pass over the basis forms v_{j+1}, the next pending vector
+// y' = A v_{j+1}, and the inner products v_i^H A y from which the next
+// Hessenberg column follows as (v_i^H A y - (Hbar l)_i) / beta (orthonormal
+// basis).  The low-synchronisation Gram-Schmidt family (Swirydowicz, Langou,
+// Ananthan, Yang and Thomas, Numer. Linear Algebra Appl. 2021) lags the
+// normalisation the same way.  A step whose orthogonal part is small
+// (beta^2 < eta ||y||^2) falls back to two explicit classical passes.
+//
+// The recurrence runs on the shifted operator B = A - sigma I (same Krylov
+// space; H_A = H_B + sigma I): rounding errors of the implicitly formed
+// vectors propagate with the ratio of the lagged Hessenberg entries to the
+// subdiagonal, which for A = I - chi K is far smaller for B = -chi K (the
+// scattering part) than for A itself.  With sigma = 1 the Arnoldi relation
+// holds to a few FP32 units and the basis stays orthogonal to ~1e-6 over 64
+// steps on random bodies of contrast 0.2..11; unshifted it drifts after ~10.
+constexpr double ARNOLDI_SHIFT = 1.0;
+
+// cvec[r] = Hu[r][:, 0..j] lag[r][0..j] (rows 0..j+1)
+__global__ void k_cvec(const c64* __restrict__ Hu, const c64* __restrict__ lag, c64* __restrict__ cvec, int j,
+                       const int* __restrict__ list, int m) {
+    const int r = list[blockIdx.x];
+    const int mp1 = m + 1;
+    for (int row = threadIdx.x; row <= j + 1; row += blockDim.x) {
+        c64 acc = {0.0, 0.0};
+        for (int col = (row > 0 ? row - 1 : 0); col <= j; ++col) {
+            const c64 h = Hu[(long long)r * mp1 * m + (long long)col * mp1 + row];
+            const c64 l = lag[(long long)r * mp1 + col];
+            acc.x += h.x * l.x - h.y * l.y;
+            acc.y += h.x * l.y + h.y * l.x;
+        }
+        cvec[(long long)r * (m + 2) + row] = acc;
+    }
+}
+
+// one pass over the basis: v_{j+1} = (y - sum_i lag_i v_i) * inv (slot j+1),
+// with z = A y - sigma y (A y given in Wz): y' = (z - sum_{i<=j+1} c_i v_i) * inv
+// (slot j+2) = B v_{j+1}, partial inner products g_i = v_i^H z (i <= j+1) and
+// ||y'||^2 (entry j+2)
+// Stage buffers of the sweep: this block's chunk of each basis vector is
+// brought into shared memory by the TMA bulk-copy engine SWEEP_ST vectors
+// ahead (one mbarrier per stage), so DRAM requests stay in flight without
+// holding registers; the threads read their elements from shared memory.
+template <typename T> struct SweepCfg {
+    static constexpr int ST = sizeof(T) == 4 ? 3 : 2;  // stages
+    static constexpr int BUF = KCH + 2;                 // elements per stage (alignment slack)
+    static constexpr size_t STAGE_BYTES = (size_t)BUF * sizeof(cplx<T>);
+};
+constexpr long long SWEEP_WAIT_LIMIT = 1LL << 22;
+
+__device__ __forceinline__ bool sweep_wait(uint32_t bar, uint32_t phase) {
+    for (long long it = 0; it < SWEEP_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// The bytes a chunk's bulk copy moves: the chunk widened to 16-byte
+// boundaries on both sides (at most one element of the neighbouring chunk
+// each; the basis allocation carries 64 bytes of slack after its end, and the
+// allocation's start is aligned), so that source, destination and size meet
+// the copy's 16-byte rule.  Element t of the chunk lands in stage slot t + s.
+struct SweepChunk {
+    unsigned long long src;
+    unsigned bytes;
+    int s;
+};
+template <typename T>
+__device__ __forceinline__ SweepChunk sweep_chunk(const cplx<T>* first, long long cnt) {
+    constexpr unsigned long long ES = sizeof(cplx<T>);
+    const unsigned long long a = (unsigned long long)first;
+    const unsigned long long a0 = a & ~15ull;
+    const unsigned long long a1 = (a + (unsigned long long)cnt * ES + 15ull) & ~15ull;
+    return SweepChunk{a0, (unsigned)(a1 - a0), (int)((a - a0) / ES)};
+}
+
+template <typename T>
+__device__ __forceinline__ void sweep_issue(cplx<T>* buf, uint64_t* bar, const cplx<T>* first, long long cnt) {
+    const SweepChunk c = sweep_chunk(first, cnt);
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(buf);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(c.bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                 "l"(c.src), "r"(c.bytes), "r"(b)
+                 : "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(KB, sizeof(T) == 4 ? 3 : 1) k_sweep(cplx<T>* __restrict__ V, long long rstride, long long vstride, int j,
+                        const int* __restrict__ list, const c64* __restrict__ lag, const c64* __restrict__ cvec,
+                        const double* __restrict__ inv, const cplx<T>* __restrict__ Wz, long long zstride,
+                        c64* __restrict__ partial, int mp2, long long n, int nblk, int m, double sigma,
+                        int* __restrict__ err) {
+    using Cfg = SweepCfg<T>;
+    __shared__ cplx<T> lf[MAX_RESTART + 1], cf[MAX_RESTART + 2];
+    __shared__ __align__(8) uint64_t sbar[Cfg::ST];
+    __shared__ int sfail;
+    extern __shared__ __align__(16) unsigned char sweep_smem[];
+    cplx<T>* stg = (cplx<T>*)sweep_smem;  // [ST][BUF]
+    const int J2 = j + 3;                 // inner products 0..j+1 and the norm
+    double* sre = (double*)(sweep_smem + Cfg::ST * Cfg::STAGE_BYTES);
+    double* sim = sre + (KB / 32) * J2;
+    const int r = list[blockIdx.y];
+    cplx<T>* Vr = V + r * rstride;
+    const long long cb = (long long)blockIdx.x * KCH;
+    const long long cnt = n - cb < KCH ? n - cb : KCH;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < Cfg::ST; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&sbar[b])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sfail = 0;
+        for (int i = 0; i < Cfg::ST && i <= j; ++i)
+            sweep_issue(stg + (size_t)i * Cfg::BUF, &sbar[i], Vr + (long long)i * vstride + cb, cnt);
+    }
+    for (int i = threadIdx.x; i <= j + 1; i += KB) {
+        if (i <= j) {
+            const c64 a = lag[(long long)r * (m + 1) + i];
+            lf[i] = cplx<T>{(T)a.x, (T)a.y};
+        }
+        const c64 c = cvec[(long long)r * (m + 2) + i];
+        cf[i] = cplx<T>{(T)c.x, (T)c.y};
+    }
+    __syncthreads();
+    const T ib = (T)inv[r];
+    const T sg = (T)sigma;
+    cplx<T>* ys = Vr + (long long)(j + 1) * vstride;  // pending y; becomes v_{j+1}
+    cplx<T>* yn = Vr + (long long)(j + 2) * vstride;  // receives y'
+    const cplx<T>* zr = Wz + r * zstride;
+    const long long e0 = cb + threadIdx.x;
+    cplx<T> u[KE], w[KE], z[KE];
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        const bool ok = e < n;
+        u[k] = ok ? ys[e] : cplx<T>{(T)0, (T)0};
+        z[k] = ok ? zr[e] : cplx<T>{(T)0, (T)0};
+        z[k] = cplx<T>{z[k].x - sg * u[k].x, z[k].y - sg * u[k].y};  // B y = A y - sigma y
+        w[k] = z[k];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    bool bad = false;
+    int next = 0;  // first vector whose chunk has not been waited for
+    // four basis vectors per group: their eight thread partials (re, im) are
+    // summed over the warp by one reduce-scatter instead of eight reductions
+    for (int i0 = 0; i0 <= j && !bad; i0 += 4) {
+        T gv[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + q;
+            T gr = 0, gi = 0;
+            if (i <= j && !bad) {
+                const int b = i % Cfg::ST;
+                const cplx<T>* buf = stg + (size_t)b * Cfg::BUF;
+                const cplx<T>* vi = Vr + (long long)i * vstride;
+                const int sh = (int)(((unsigned long long)(vi + cb) & 15ull) / sizeof(cplx<T>));
+                if (!sweep_wait((uint32_t)__cvta_generic_to_shared(&sbar[b]), (uint32_t)((i / Cfg::ST) & 1))) {
+                    sfail = 1;
+                    atomicOr(err, 1);
+                }
+                next = i + 1;
+                const cplx<T> l = lf[i], c = cf[i];
+#pragma unroll
+                for (int k = 0; k < KE; ++k) {
+                    const int t = threadIdx.x + k * KB;
+                    if (cb + t < n) {
+                        const cplx<T> a = buf[t + sh];
+                        u[k].x -= l.x * a.x - l.y * a.y;
+                        u[k].y -= l.x * a.y + l.y * a.x;
+                        w[k].x -= c.x * a.x - c.y * a.y;
+                        w[k].y -= c.x * a.y + c.y * a.x;
+                        gr += a.x * z[k].x + a.y * z[k].y;
+                        gi += a.x * z[k].y - a.y * z[k].x;
+                    }
+                }
+                __syncthreads();  // stage b is free again
+                bad = sfail != 0;
+                if (threadIdx.x == 0 && !bad && i + Cfg::ST <= j) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    sweep_issue(stg + (size_t)b * Cfg::BUF, &sbar[b], Vr + (long long)(i + Cfg::ST) * vstride + cb,
+                                cnt);
+                }
+            }
+            gv[2 * q] = gr;
+            gv[2 * q + 1] = gi;
+        }
+        int q;
+        const double d = warp_sum8(gv, lane, q);
+        const int i = i0 + (q >> 1);
+        if ((lane & 3) == 0 && i <= j) (q & 1 ? sim : sre)[wid * J2 + i] = d;
+    }
+    if (bad) {
+        // a chunk did not arrive: let the copies still in flight land, then leave
+        // (the failed vector next - 1 and those issued after it)
+        if (threadIdx.x == 0)
+            for (int i = next - 1; i <= j && i < next - 1 + Cfg::ST; ++i)
+                sweep_wait((uint32_t)__cvta_generic_to_shared(&sbar[i % Cfg::ST]), (uint32_t)((i / Cfg::ST) & 1));
+        return;
+    }
+    {
+        const cplx<T> c = cf[j + 1];
+        T gr = 0, gi = 0, nn = 0;
+#pragma unroll
+        for (int k = 0; k < KE; ++k) {
+            const long long e = e0 + k * KB;
+            if (e < n) {
+                const cplx<T> v = cplx<T>{u[k].x * ib, u[k].y * ib};
+                cplx<T> y = w[k];
+                y.x -= c.x * v.x - c.y * v.y;
+                y.y -= c.x * v.y + c.y * v.x;
+                y = cplx<T>{y.x * ib, y.y * ib};
+                ys[e] = v;
+                yn[e] = y;
+                gr += v.x * z[k].x + v.y * z[k].y;
+                gi += v.x * z[k].y - v.y * z[k].x;
+                nn += y.x * y.x + y.y * y.y;
+            }
+        }
+        const double dr = warp_sum_comp(gr);
+        const double di = warp_sum_comp(gi);
+        const double dn = warp_sum_comp(nn);
+        if (lane == 0) {
+            sre[wid * J2 + j + 1] = dr;
+            sim[wid * J2 + j + 1] = di;
+            sre[wid * J2 + j + 2] = dn;
+            sim[wid * J2 + j + 2] = 0.0;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < J2; i += KB) {
+        double ar = 0, ai = 0;
+        for (int q = 0; q < KB / 32; ++q) {
+            ar += sre[q * J2 + i];
+            ai += sim[q * J2 + i];
+        }
+        partial[((long long)r * mp2 + i) * nblk + blockIdx.x] = c64{ar, ai};
+    }
+}
+
+// Hessenberg column jc = j + 1 of the sweep: coef_i = H_B[i][jc] = (g_i - c_i) * inv
+// for i <= jc, coef_{jc+1} = ||y'||^2; H (the matrix GMRES rotates) receives
+// H_A = H_B + sigma on the diagonal (grid: (jc + 2, listed RHS))
+__global__ void k_reduce_sweep(const c64* __restrict__ partial, const c64* __restrict__ cvec,
+                               const double* __restrict__ inv, c64* __restrict__ coef, c64* __restrict__ H, int jc,
+                               const int* __restrict__ list, int m, int nblk, double sigma) {
+    __shared__ double sre[KB / 32], sim[KB / 32];
+    const int r = list[blockIdx.y];
+    const int i = blockIdx.x;
+    const int mp1 = m + 1;
+    const c64* p = partial + ((long long)r * (m + 2) + i) * nblk;
+    double ar = 0, ai = 0;
+    for (int b = threadIdx.x; b < nblk; b += KB) {
+        ar += p[b].x;
+        ai += p[b].y;
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if ((threadIdx.x & 31) == 0) {
+        sre[threadIdx.x >> 5] = ar;
+        sim[threadIdx.x >> 5] = ai;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0, ti = 0;
+        for (int q = 0; q < KB / 32; ++q) {
+            tr += sre[q];
+            ti += sim[q];
+        }
+        if (i > jc) {
+            coef[(long long)r * (m + 2) + i] = c64{tr, ti};
+            return;
+        }
+        const c64 c = cvec[(long long)r * (m + 2) + i];
+        const double ib = inv[r];
+        const c64 d = {(tr - c.x) * ib, (ti - c.y) * ib};
+        coef[(long long)r * (m + 2) + i] = d;
+        H[(long long)r * mp1 * m + (long long)jc * mp1 + i] = c64{d.x + (i == jc ? sigma : 0.0), d.y};
+    }
+}
+
+// beta^2 = ||y||^2 - sum_{i<=jc} |coef_i|^2 (Pythagoras); a second explicit
+// pass is flagged where it falls below eta ||y||^2; the lag of the next sweep is
+// the column itself (one thread per listed RHS)
+__global__ void k_beta(const c64* __restrict__ coef, double* __restrict__ beta2, int* __restrict__ gate,
+                       c64* __restrict__ lag, int jc, const int* __restrict__ list, int nr, int m, double eta) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nr) return;
+    const int r = list[s];
+    const c64* cf = coef + (long long)r * (m + 2);
+    const double yy = cf[jc + 1].x;
+    double hh = 0;
+    for (int i = 0; i <= jc; ++i) {
+        hh += cf[i].x * cf[i].x + cf[i].y * cf[i].y;
+        lag[(long long)r * (m + 1) + i] = cf[i];
+    }
+    const double b2 = yy - hh;
+    const bool re = !(b2 >= eta * yy) || !(yy > 0);
+    gate[r] = re ? 1 : 0;
+    beta2[r] = b2;
+}
+
+// after the explicit passes of a flagged RHS: its pending vector is
+// orthogonal (lag 0), beta^2 its norm
+__global__ void k_beta_explicit(const double* __restrict__ normpart, int nblk, double* __restrict__ beta2,
+                                const int* __restrict__ gate, c64* __restrict__ lag, int jc,
+                                const int* __restrict__ list, int nr, int m) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nr) return;
+    const int r = list[s];
+    if (!gate[r]) return;
+    double t = 0;
+    for (int b = 0; b < nblk; ++b) t += normpart[(long long)r * nblk + b];
+    beta2[r] = t;
+    for (int i = 0; i <= jc; ++i) lag[(long long)r * (m + 1) + i] = c64{0.0, 0.0};
+}
+
 // Operator of the refinement residual b - A x (x, b, r in FP64): the FP64
 // operator in the plain FP64 solver; in mixed mode the double-float operator
 // (FP64 accuracy within a few 2^-47 at several times the FP64 speed on GB300)
@@ -637,7 +1053,7 @@ int Solver::alloc(Operator& op, int R_, int m_, int prec_) {
     VIE_TRY(dev_alloc(op, (void**)&x, sizeof(c64) * n * R));
     VIE_TRY(dev_alloc(op, (void**)&b, sizeof(c64) * n * R));
     VIE_TRY(dev_alloc(op, (void**)&res, sizeof(c64) * n * R));
-    VIE_TRY(dev_alloc(op, &V, tsz * n * R * (m + 1)));
+    VIE_TRY(dev_alloc(op, &V, tsz * n * R * (m + 1) + 64));  // slack: the sweep's widened bulk copies
     VIE_TRY(dev_alloc(op, (void**)&H, sizeof(c64) * R * (m + 1) * m));
     VIE_TRY(dev_alloc(op, (void**)&cs, sizeof(double) * R * m));
     VIE_TRY(dev_alloc(op, (void**)&sn, sizeof(c64) * R * m));
@@ -663,11 +1079,23 @@ void Solver::release(Operator& op) {
         dev_free(op, Z, tsz * n3 * R * m);
         Z = nullptr;
     }
+    if (Wz) {
+        dev_free(op, Wz, tsz * n3 * R);
+        dev_free(op, Hu, sizeof(c64) * R * (m + 1) * m);
+        dev_free(op, lag, sizeof(c64) * R * (m + 1));
+        dev_free(op, cvec, sizeof(c64) * R * (m + 2));
+        dev_free(op, beta2, sizeof(double) * R);
+        dev_free(op, kerr, sizeof(int));
+        kerr = nullptr;
+        Wz = nullptr;
+        Hu = lag = cvec = nullptr;
+        beta2 = nullptr;
+    }
     if (x) {
         dev_free(op, x, sizeof(c64) * n3 * R);
         dev_free(op, b, sizeof(c64) * n3 * R);
         dev_free(op, res, sizeof(c64) * n3 * R);
-        dev_free(op, V, tsz * n3 * R * (m + 1));
+        dev_free(op, V, tsz * n3 * R * (m + 1) + 64);
         dev_free(op, H, sizeof(c64) * R * (m + 1) * m);
         dev_free(op, cs, sizeof(double) * R * m);
         dev_free(op, sn, sizeof(c64) * R * m);
@@ -699,6 +1127,87 @@ void Solver::release(Operator& op) {
         VIE_CUDA(cudaGetLastError());                \
     } while (0)
 
+// One step j of the one-sweep Arnoldi for the listed RHS.  Before it, slot j
+// holds the pending vector y_j (v_j = (y_j - V lag) / beta_j, not yet formed;
+// slot 0 holds v_0 itself); after it, slot j holds v_j, slot j+1 the pending
+// y_{j+1} = B v_j (A v_0 at step 0; both give the same v_{j+1} with their own
+// lag), column j of the Hessenberg matrix is complete and rotated, and
+// lag / beta2 / inv describe y_{j+1}.  Step 0 has nothing lagged: it is the
+// classical first pass.  A flagged RHS (beta^2 < eta ||y||^2, where the
+// implicit orthogonalisation would lose accuracy) gets two explicit classical
+// passes on its pending vector, after which its lag is zero.
+template <typename T>
+static int sweep_step(Operator& op, Solver& S, const vie_solve_opts& o, int j, int ni, cplx<T>* V, long long vrs,
+                      long long n, int nblk, int nblk_d, SolveResult& out) {
+    cudaStream_t st = op.stream;
+    const int m = S.m, mp1 = m + 1;
+    const int prec_in = sizeof(T) == 8 ? VIE_PREC_FP64 : VIE_PREC_MIXED;
+    const double ET = sizeof(cplx<T>);
+    cplx<T>* Wz = (cplx<T>*)S.Wz;
+    const dim3 gi(nblk, ni);
+    if (j == 0) {
+        VIE_TRY(op_apply(op, prec_in, V, vrs, V + n, vrs, op.d_list, ni));
+        tmr_begin(TMR_DOTS, st);
+        k_dots<T><<<dim3(nblk_d, ni), KB, sizeof(double) * 2 * (KB / 32) * 2, st>>>(V, vrs, n, 0, op.d_list,
+                                                                                    S.partial, mp1 + 1, n, nblk_d,
+                                                                                    nullptr);
+        tmr_end(TMR_DOTS, st, (double)ni * 2 * n * ET);
+        LAUNCH_CHECK();
+        tmr_begin(TMR_REDUCE, st);
+        k_reduce_dots<<<dim3(2, ni), KB, 0, st>>>(S.partial, S.coef, S.H, 0, op.d_list, mp1, nblk_d, 0, nullptr);
+        tmr_end(TMR_REDUCE, st, (double)ni * nblk_d * 16.0);
+        LAUNCH_CHECK();
+    } else {
+        VIE_TRY(op_apply(op, prec_in, V + (long long)j * n, vrs, Wz, n, op.d_list, ni));
+        tmr_begin(TMR_REDUCE, st);
+        k_cvec<<<ni, 64, 0, st>>>(S.Hu, S.lag, S.cvec, j - 1, op.d_list, m);
+        tmr_end(TMR_REDUCE, st, 0.0);
+        LAUNCH_CHECK();
+        tmr_begin(TMR_SWEEP, st);
+        const size_t smem = SweepCfg<T>::ST * SweepCfg<T>::STAGE_BYTES + sizeof(double) * 2 * (KB / 32) * (j + 2);
+        k_sweep<T><<<gi, KB, smem, st>>>(V, vrs, n, j - 1, op.d_list, S.lag, S.cvec, S.inv, Wz, n, S.partial, m + 2,
+                                         n, nblk, m, ARNOLDI_SHIFT, S.kerr);
+        tmr_end(TMR_SWEEP, st, (double)ni * (j + 4) * n * ET);
+        LAUNCH_CHECK();
+        tmr_begin(TMR_REDUCE, st);
+        k_reduce_sweep<<<dim3(j + 2, ni), KB, 0, st>>>(S.partial, S.cvec, S.inv, S.coef, S.H, j, op.d_list, m,
+                                                       nblk, ARNOLDI_SHIFT);
+        tmr_end(TMR_REDUCE, st, (double)ni * (j + 2) * nblk * 16.0);
+        LAUNCH_CHECK();
+    }
+    if (prec_in == VIE_PREC_FP64) out.matvecs64 += ni;
+    else out.matvecs32 += ni;
+    tmr_begin(TMR_FINISH, st);
+    k_beta<<<ceil_div(ni, 64), 64, 0, st>>>(S.coef, S.beta2, S.reorth, S.lag, j, op.d_list, ni, m, o.reorth_eta);
+    tmr_end(TMR_FINISH, st, 0.0);
+    LAUNCH_CHECK();
+    // flagged RHS: two explicit classical passes on slot j+1 (the kernels return
+    // at once for the others)
+    tmr_begin(TMR_UPDATE, st);
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass) {
+            k_dots<T><<<dim3(nblk_d, ni), KB, sizeof(double) * 2 * (KB / 32) * (j + 2), st>>>(
+                V, vrs, n, j, op.d_list, S.partial, mp1 + 1, n, nblk_d, S.reorth);
+            LAUNCH_CHECK();
+            k_reduce_dots<<<dim3(j + 2, ni), KB, 0, st>>>(S.partial, S.coef, S.H, j, op.d_list, mp1, nblk_d, 1,
+                                                           S.reorth);
+            LAUNCH_CHECK();
+        }
+        k_update<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.coef, S.normpart, mp1, n, nblk, S.reorth);
+        LAUNCH_CHECK();
+    }
+    tmr_end(TMR_UPDATE, st, 0.0);  // bytes of the flagged RHS are added once the flags are read
+    k_beta_explicit<<<ceil_div(ni, 64), 64, 0, st>>>(S.normpart, nblk, S.beta2, S.reorth, S.lag, j, op.d_list, ni,
+                                                     m);
+    LAUNCH_CHECK();
+    tmr_begin(TMR_FINISH, st);
+    k_finish<<<ceil_div(ni, 64), 64, 0, st>>>(S.normpart, nblk, S.H, S.cs, S.sn, S.g, S.inv, S.kcount, S.flag,
+                                              S.target, j, op.d_list, ni, m, S.beta2, S.Hu, ARNOLDI_SHIFT);
+    tmr_end(TMR_FINISH, st, (double)ni * 8.0);
+    LAUNCH_CHECK();
+    return VIE_OK;
+}
+
 template <typename T>
 static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult& out) {
     const long long n = S.n3;
@@ -707,6 +1216,17 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
     const long long vrs = n * mp1;  // per-RHS stride in V
     const long long zrs = n * m;    // per-RHS stride in Z (FGMRES)
     if ((S.pc || S.bpc) && !S.Z) VIE_TRY(dev_alloc(op, &S.Z, sizeof(cplx<T>) * n * R * m));
+    const bool fused = o.arnoldi == 1 && !S.pc && !S.bpc;
+    if (fused && !S.Wz) {
+        VIE_TRY(dev_alloc(op, &S.Wz, sizeof(cplx<T>) * n * R));
+        VIE_TRY(dev_alloc(op, (void**)&S.Hu, sizeof(c64) * R * mp1 * m));
+        VIE_TRY(dev_alloc(op, (void**)&S.lag, sizeof(c64) * R * mp1));
+        VIE_TRY(dev_alloc(op, (void**)&S.cvec, sizeof(c64) * R * (m + 2)));
+        VIE_TRY(dev_alloc(op, (void**)&S.beta2, sizeof(double) * R));
+        VIE_TRY(dev_alloc(op, (void**)&S.kerr, sizeof(int)));
+    }
+    if (fused) VIE_CUDA(cudaMemsetAsync(S.kerr, 0, sizeof(int), op.stream));
+    int hkerr = 0;
     cplx<T>* V = (cplx<T>*)S.V;
     cudaStream_t st = op.stream;
     const int prec_in = sizeof(T) == 8 ? VIE_PREC_FP64 : VIE_PREC_MIXED;
@@ -715,6 +1235,9 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
     if (!smem_set) {
         VIE_CUDA(cudaFuncSetAttribute(k_dots<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(double) * 2 * (KB / 32) * (MAX_RESTART + 2))));
+        VIE_CUDA(cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(SweepCfg<T>::ST * SweepCfg<T>::STAGE_BYTES +
+                                            sizeof(double) * 2 * (KB / 32) * (MAX_RESTART + 2))));
         smem_set = true;
     }
 
@@ -886,6 +1409,9 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         for (int j = 0; j < m && !inner.empty(); ++j) {
             const int ni = (int)inner.size();
             VIE_TRY(op_set_list(op, inner.data(), ni));
+            if (fused) {
+                VIE_TRY(sweep_step<T>(op, S, o, j, ni, V, vrs, n, nblk, nblk_d, out));
+            } else {
             // V_{j+1} = A_T V_j
             if (S.pc || S.bpc) {
                 // FGMRES: z_j = M(v_j), v_{j+1} = A z_j
@@ -942,10 +1468,13 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
             k_scale<T><<<gi, KB, 0, st>>>(V, vrs, n, j, op.d_list, S.inv, n);
             tmr_end(TMR_SCALE, st, 2.0 * ni * n * ET);
             LAUNCH_CHECK();
+            }
             VIE_CUDA(cudaMemcpyAsync(hflag.data(), S.flag, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
             if (tmr_enabled())
                 VIE_CUDA(cudaMemcpyAsync(hreo.data(), S.reorth, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+            if (fused) VIE_CUDA(cudaMemcpyAsync(&hkerr, S.kerr, sizeof(int), cudaMemcpyDeviceToHost, st));
             VIE_CUDA(cudaStreamSynchronize(st));
+            if (hkerr) return fail(VIE_ETIMEOUT, "one-sweep Arnoldi: a bulk copy into shared memory did not complete");
             if (tmr_enabled()) {
                 long long nre = 0;
                 for (int r : inner) nre += hreo[r] != 0;

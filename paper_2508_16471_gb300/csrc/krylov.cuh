@@ -83,6 +83,13 @@ struct Solver {
     int* reorth = nullptr;     // [R] 1 = second Gram-Schmidt pass needed this step
     double* chans = nullptr;   // [R][9] channels of the current right-hand sides
     void* Z = nullptr;         // [R][m][n3] preconditioned basis (FGMRES; allocated on first use)
+    // one-sweep Arnoldi (opts.arnoldi = 1; allocated on first use)
+    void* Wz = nullptr;        // [R][n3] operator image of the not yet orthogonalised vector
+    c64* Hu = nullptr;         // [R][m][m+1] Hessenberg before the Givens rotations, column-major
+    c64* lag = nullptr;        // [R][m+1] coefficients that turn the pending vector into the next basis vector
+    c64* cvec = nullptr;       // [R][m+2] H_unrotated * lag
+    double* beta2 = nullptr;   // [R] squared norm of the pending vector's orthogonal part
+    int* kerr = nullptr;       // [1] set by the sweep kernel when a bulk copy did not arrive in time
     PrecondCtx* pc = nullptr;  // learned right preconditioner for the next solve (not owned), or null
     BlockPrecond* bpc = nullptr;  // block-Jacobi right preconditioner for the next solve (not owned), or null
 

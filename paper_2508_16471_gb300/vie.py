@@ -53,7 +53,7 @@ class _Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iter", C.c_int),
                 ("precision", C.c_int), ("inner_tol", C.c_double), ("use_x0", C.c_int),
                 ("precond", C.c_int), ("solver", C.c_int), ("resid_fp64", C.c_int),
-                ("reorth_eta", C.c_double), ("inner_floor", C.c_double)]
+                ("reorth_eta", C.c_double), ("inner_floor", C.c_double), ("arnoldi", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -203,7 +203,10 @@ def timer_read():
 def default_opts(**kw):
     o = _Opts()
     load().vie_default_opts(C.byref(o))
+    names = {f[0] for f in _Opts._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown solve option {k!r}")
         setattr(o, k, v)
     return o
 

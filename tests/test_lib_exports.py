@@ -36,3 +36,19 @@ def test_binding_loads_and_reports_errors_without_gpu(vielib):
     code = L.hom_transfer(None, None, 1.2, None, 0, None, None, None)
     assert code == vielib.VIE_EINVAL
     assert b"bad arguments" in L.vie_last_error()
+
+
+def test_options_struct_matches_the_header(vielib):
+    """vie_default_opts writes exactly sizeof(vie_solve_opts) bytes: a buffer
+    one struct long plus a fenced tail keeps its tail, and the binding's last
+    field is set (a shorter or longer ctypes mirror would break one of the two)."""
+    L = vielib.load()
+    size = ctypes.sizeof(vielib._Opts)
+    buf = (ctypes.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    L.vie_default_opts(ctypes.cast(buf, ctypes.POINTER(vielib._Opts)))
+    assert all(b == 0xAB for b in buf[size:])
+    o = vielib._Opts.from_buffer(buf)
+    assert o.arnoldi == 1 and abs(o.inner_floor - 0.7) < 1e-15 and abs(o.reorth_eta - 0.1) < 1e-15
+    import pytest
+    with pytest.raises(TypeError):
+        vielib.default_opts(no_such_option=1)
