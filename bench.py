@@ -60,7 +60,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--bodies", type=int, default=8)
-    p.add_argument("--restart", type=int, default=64)
+    p.add_argument("--restart", type=int, default=None,
+                   help="GMRES restart length (default: 160 for the 128^3 bodies, the fastest measured; 64 otherwise)")
     p.add_argument("--inner-floor", type=float, default=0.7,
                    help="mixed mode: inner solves stop at inner_floor x tol x ||b|| at the latest")
     p.add_argument("--arnoldi", type=int, default=1, choices=[0, 1],
@@ -83,7 +84,7 @@ def parse():
                    help="with --apply-only: apply the FP64 operator instead of the FP32 one")
     p.add_argument("--apply-f32x2", action="store_true",
                    help="with --apply-only: apply the double-float operator (the residual operator of the solves)")
-    p.add_argument("--workload", default="bodies128", choices=["bodies128", "metasurface-paper", "bodies-uneven", "learned"],
+    p.add_argument("--workload", default="bodies128", choices=["bodies128", "metasurface-paper", "bodies-uneven", "learned", "net"],
                    help="metasurface-paper: one solve of the paper-scale PB metasurface (its own JSON line); "
                         "bodies-uneven: the random-body set of uneven grids (32^3..96^3) in multi-body batches; "
                         "learned: train the initial-guess network on solver-generated solves, then the bench "
@@ -105,7 +106,10 @@ def parse():
     p.add_argument("--inner", type=int, default=8, help="metasurface-paper: inner COCR steps per block solve")
     p.add_argument("--profile-solve", type=int, default=0,
                    help="profiling aid: a 12-iteration solve with this many RHS on the first bench body, then exit")
-    return p.parse_args()
+    args = p.parse_args()
+    if args.restart is None:
+        args.restart = 160 if args.workload == "bodies128" else 64
+    return args
 
 
 def dist_env():
@@ -440,11 +444,14 @@ def run_ours(args):
     # mixed precision (t_first), so the two times divide the same work
     plain = None
     b0 = args.warmup % len(eps_dev)  # the body of the first timed step
+    # the FP64 basis of 32 RHS takes 16 bytes per entry: GMRES(128) at most keeps it
+    # (with the FP64 work arrays) well inside the device memory
+    plain_restart = min(args.restart, 128)
     if not args.no_plain and rank == 0:
         hd.set_eps_device(eps_dev[b0].data_ptr())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = hd.solve(chs, allow_noconv=True, tol=1e-6, restart=args.restart, precision=V.PREC_FP64,
+        st = hd.solve(chs, allow_noconv=True, tol=1e-6, restart=plain_restart, precision=V.PREC_FP64,
                       max_iter=args.max_iter, arnoldi=args.arnoldi)
         torch.cuda.synchronize()
         tp = time.perf_counter() - t0
@@ -452,7 +459,7 @@ def run_ours(args):
                  "subset": f"body seed {seeds[b0]} (the first timed step), all {R} RHS",
                  "converged": int(st["converged"]), "seconds": tp,
                  "iters_mean": float(np.mean(st["iters"])), "iters_rhs0": int(st["iters"][0]),
-                 "precision": "f64",
+                 "precision": "f64", "restart": plain_restart,
                  "mixed_seconds_same_set": t_first,
                  "mixed_iters_mean_same_set": float(np.mean(first_all_iters)) if first_all_iters else None,
                  "speedup_same_set": (tp / t_first) if t_first else None}
@@ -901,6 +908,62 @@ def run_learned(args):
     return 0
 
 
+def run_net(args):
+    """The learned part's network alone at its configured width (channels
+    --channels, BF16 storage, 16^3 coarse grid, batch 8 as in training):
+    forward and forward + backward per call, with the 3x3x3 convolutions on
+    the tensor cores (tcgen05 implicit GEMM) and on the CUDA cores; TFLOP/s
+    counts the convolution products only (2 x voxels x Cin x Cout x taps)."""
+    import numpy as np
+    import torch
+    from paper_2508_16471_gb300 import build as libbuild
+    from paper_2508_16471_gb300 import vie as V
+    libbuild.build()
+    V.load()
+    ch = tuple(args.channels)
+    B, D = 8, 16
+    rng = np.random.default_rng(0)
+    x = torch.from_numpy(rng.standard_normal((B, 10, D, D, D)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((B, 6, D, D, D)).astype(np.float32)).cuda()
+    m = torch.ones(B, D, D, D, device="cuda")
+    y = torch.empty(B, 6, D, D, D, device="cuda")
+    c0, c1, c2, c3 = ch
+    layers = [(10, c0, 0), (c0, c0, 0), (c0, c1, 1), (c1, c1, 1), (c1, c2, 2), (c2, c2, 2), (c2, c3, 3), (c3, c3, 3),
+              (c3 + c2, c2, 2), (c2, c2, 2), (c2 + c1, c1, 1), (c1, c1, 1), (c1 + c0, c0, 0), (c0, c0, 0)]
+    fl = sum(2.0 * B * (D >> lv) ** 3 * ci * co * 27 for ci, co, lv in layers) + 2.0 * B * D ** 3 * c0 * 6
+    res = {}
+    for tc in (True, False):
+        net = V.Net(ch, seed=1, bf16=True)
+        net.set_tensor_cores(tc)
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            net.forward(x.data_ptr(), y.data_ptr(), B, D)
+            net.train_step(x.data_ptr(), t.data_ptr(), m.data_ptr(), B, D, 0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            net.forward(x.data_ptr(), y.data_ptr(), B, D)
+        torch.cuda.synchronize()
+        tf = (time.perf_counter() - t0) / args.steps
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            net.train_step(x.data_ptr(), t.data_ptr(), m.data_ptr(), B, D, 0.0)
+        torch.cuda.synchronize()
+        tt = (time.perf_counter() - t0) / args.steps
+        res["tensor_cores" if tc else "cuda_cores"] = {
+            "forward_ms": 1e3 * tf, "train_step_ms": 1e3 * tt, "forward_conv_TFLOPs": fl / tf / 1e12,
+            "train_conv_TFLOPs": 3 * fl / tt / 1e12}
+        net.close()
+    line = {"metric": "U-Net training steps/s (BF16 storage, FP32 accumulation)", "value": 1e3 / res["tensor_cores"]["train_step_ms"],
+            "unit": "steps/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "bf16", "data": "synthetic", "config": {"workload": f"U-Net {list(ch)}, batch {B}, {D}^3 grid",
+                                                              "conv_flops_per_forward": fl},
+            "tensor_cores": res["tensor_cores"], "cuda_cores": res["cuda_cores"],
+            "speedup_train": res["cuda_cores"]["train_step_ms"] / res["tensor_cores"]["train_step_ms"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -911,6 +974,8 @@ def main():
         return run_bodies_uneven(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "net":
+        return run_net(args)
     return run_ours(args)
 
 

@@ -424,6 +424,14 @@ int vie_net_create(const int channels[4], unsigned long long seed, int bf16, vie
 int vie_net_create_io(const int channels[4], int cin, unsigned long long seed, int bf16, vie_net** out);
 void vie_net_destroy(vie_net* net);
 long long vie_net_num_params(const vie_net* net);
+/* bf16 networks: run the 3x3x3 and 1x1x1 convolutions (forward, data and
+ * weight gradients) as implicit GEMMs on the tensor cores (tcgen05.mma
+ * kind::f16, BF16 operands, FP32 accumulation in tensor memory) when on != 0
+ * (the default), or on the CUDA-core kernels.  Layers with more than 128
+ * output or 256 input channels always take the CUDA cores.  VIE_EINVAL for a
+ * NULL net; a tensor-core wait that runs out makes the next forward or
+ * gradient call return VIE_ETIMEOUT. */
+int vie_net_set_tensor_cores(vie_net* net, int on);
 /* host float32 arrays of vie_net_num_params() entries: per layer w[co][ci][k^3] then b[co] */
 int vie_net_get_params(const vie_net* net, float* host);
 int vie_net_set_params(vie_net* net, const float* host);

@@ -869,6 +869,12 @@ void vie_net_destroy(vie_net* n) { delete n; }
 
 long long vie_net_num_params(const vie_net* n) { return n ? n->net.nparams : 0; }
 
+int vie_net_set_tensor_cores(vie_net* n, int on) {
+    if (!n) return fail(VIE_EINVAL, "NULL network");
+    n->net.tc = on ? 1 : 0;
+    return VIE_OK;
+}
+
 int vie_net_get_params(const vie_net* n, float* host) {
     if (!n || !host) return fail(VIE_EINVAL, "NULL argument");
     long long o = 0;

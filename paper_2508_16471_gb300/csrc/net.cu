@@ -26,6 +26,7 @@
 #include <cstring>
 #include <random>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "net.cuh"
@@ -159,6 +160,28 @@ __global__ void k_wgrad(const S* __restrict__ gy, long long gbs, const S* __rest
 }
 
 // y[b][c][coarse] = mean of the 2x2x2 fine block (D = fine edge)
+// gb[co] += sum over the batch and the voxels of gy[b][co][v] (grid: (Co, chunks))
+template <typename S>
+__global__ void k_bgrad(const S* __restrict__ gy, long long gbs, float* __restrict__ gb, int V, int B) {
+    __shared__ float ws[8];
+    const int co = blockIdx.x;
+    const long long n = (long long)B * V;
+    float acc = 0.f;
+    for (long long t = blockIdx.y * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.y * blockDim.x) {
+        const int b = (int)(t / V);
+        acc += ldf(gy + b * gbs + (long long)co * V + (t - (long long)b * V));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += ws[q];
+        atomicAdd(gb + co, t);
+    }
+}
+
 template <typename S>
 __global__ void k_pool(const S* __restrict__ x, long long xbs, S* __restrict__ y, long long ybs, int C, int D, int B) {
     const int d = D / 2, Vc = d * d * d;
@@ -310,6 +333,13 @@ int Net::init(const int* ch, unsigned long long seed, int store_bf16, int cin_) 
         nparams += nw + L[l].co;
     }
     VIE_TRY(alloc((void**)&d_loss, 4));
+    long long wbe = 16;
+    for (int l = 0; l < NL; ++l)
+        wbe = std::max(wbe, std::max(conv_tc_weight_elems(L[l].ci, L[l].co, L[l].ks),
+                                     conv_tc_weight_elems(L[l].co, L[l].ci, L[l].ks)));
+    VIE_TRY(alloc(&wB, 2 * wbe));
+    VIE_TRY(alloc((void**)&d_err, sizeof(int)));
+    VIE_CUDA(cudaMemset(d_err, 0, sizeof(int)));
     t = 0;
     return VIE_OK;
 }
@@ -370,6 +400,19 @@ int Net::reserve(int B_, int D_) {
         VIE_TRY(alloc(&act[i], es * B_ * sizes[i][0] * sizes[i][1]));
         VIE_TRY(alloc(&grd[i], es * B_ * sizes[i][0] * sizes[i][1]));
     }
+    // FP32 split-K accumulation for the small-grid tensor-core convolutions
+    // (at most 2^25 floats; a layer that needs more is not split)
+    if (acc32) {
+        for (size_t q = 0; q < owned.size(); ++q)
+            if (owned[q] == acc32) {
+                cudaFree(acc32);
+                owned.erase(owned.begin() + q);
+                break;
+            }
+        acc32 = nullptr;
+    }
+    acc32_elems = std::min<long long>((long long)B_ * 256 * V0, 1LL << 25);
+    VIE_TRY(alloc((void**)&acc32, sizeof(float) * acc32_elems));
     return VIE_OK;
 }
 
@@ -379,6 +422,11 @@ template <typename S> int Net::conv_fwd(int l, int src, int src_c0, int dst, int
     const long long V = (long long)Dl * Dl * Dl;
     const S* x = (const S*)act[src] + (long long)src_c0 * V;
     S* y = (S*)act[dst] + (long long)dst_c0 * V;
+    if constexpr (std::is_same_v<S, __nv_bfloat16>) {
+        if (tc && conv_tc_fits(ly.ci, ly.co))
+            return conv_tc_fwd(x, ch_[src] * V, ly.w, 0, ly.b, y, ch_[dst] * V, ly.ci, ly.co, Dl, ly.ks, relu, B,
+                               (__nv_bfloat16*)wB, acc32, acc32_elems, d_err, s);
+    }
     dim3 g((unsigned)((V + CONV_T - 1) / CONV_T), (ly.co + CONV_CO - 1) / CONV_CO, B);
     k_conv<S><<<g, CONV_T, 0, s>>>(x, ch_[src] * V, bly_w(l), ly.b, y, ch_[dst] * V, ly.ci, ly.co, Dl, ly.ks, relu);
     count_launch();
@@ -446,6 +494,20 @@ int Net::conv_bwd(int l, int src, int src_c0, int dst, int dst_c0, int Dl, int B
     }
     const S* x = (const S*)act[src] + (long long)src_c0 * V;
     const int KK = ly.ks * ly.ks * ly.ks;
+    if constexpr (std::is_same_v<S, __nv_bfloat16>) {
+        if (tc && conv_tc_fits(ly.ci, ly.co)) {
+            VIE_TRY(conv_tc_wgrad(g, gbs, x, ch_[src] * V, ly.gw, ly.ci, ly.co, Dl, ly.ks, B, d_err, s));
+            const int chunks = (int)std::max<long long>(1, std::min<long long>(64, (long long)B * V / 4096));
+            k_bgrad<S><<<dim3(ly.co, chunks), 256, 0, s>>>(g, gbs, ly.gb, (int)V, B);
+            count_launch();
+            if (want_dx)
+                VIE_TRY(conv_tc_fwd(g, gbs, ly.w, 1, nullptr, (S*)grd[src] + (long long)src_c0 * V, ch_[src] * V,
+                                    ly.co, ly.ci, Dl, ly.ks, 0, B, (__nv_bfloat16*)wB, acc32, acc32_elems, d_err,
+                                    s));
+            VIE_CUDA(cudaGetLastError());
+            return VIE_OK;
+        }
+    }
     const int total = ly.co * ly.ci * KK;
     const long long work = (long long)B * V;
     int chunks = (int)std::min<long long>(work, std::max<long long>(1, (long long)(600000 + total - 1) / total));
@@ -512,8 +574,26 @@ template <typename S> int Net::backward_t(int B, cudaStream_t s) {
     return VIE_OK;
 }
 
-int Net::forward(int B, cudaStream_t s) { return bf16 ? forward_t<__nv_bfloat16>(B, s) : forward_t<float>(B, s); }
-int Net::backward(int B, cudaStream_t s) { return bf16 ? backward_t<__nv_bfloat16>(B, s) : backward_t<float>(B, s); }
+// a tensor-core wait that ran out (reported once, then cleared)
+static int tc_status(int* d_err, cudaStream_t s) {
+    int h = 0;
+    VIE_CUDA(cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        VIE_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+        return fail(VIE_ETIMEOUT, "tensor-core convolution: a wait for the MMAs ran out");
+    }
+    return VIE_OK;
+}
+
+int Net::forward(int B, cudaStream_t s) {
+    VIE_TRY(bf16 ? forward_t<__nv_bfloat16>(B, s) : forward_t<float>(B, s));
+    return bf16 && tc ? tc_status(d_err, s) : VIE_OK;
+}
+int Net::backward(int B, cudaStream_t s) {
+    VIE_TRY(bf16 ? backward_t<__nv_bfloat16>(B, s) : backward_t<float>(B, s));
+    return bf16 && tc ? tc_status(d_err, s) : VIE_OK;
+}
 
 int Net::set_input(const float* x_dev, int B, cudaStream_t s) {
     const long long n = (long long)B * cin * D * D * D;

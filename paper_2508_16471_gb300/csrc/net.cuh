@@ -1,6 +1,8 @@
 // Learned initial guess network (see net.cu).
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <vector>
 
 #include "krylov.cuh"
@@ -33,6 +35,12 @@ struct Net {
     float* d_loss = nullptr;
     float mask_sum = 1.f;
     std::vector<void*> owned;
+    // BF16 storage: convolutions on the tensor cores (conv_tc.cu) unless switched off
+    int tc = 1;
+    void* wB = nullptr;       // BF16 weights of one layer in the tensor-core chunk layout
+    int* d_err = nullptr;     // set by a tensor-core kernel whose wait ran out
+    float* acc32 = nullptr;   // FP32 split-K accumulation of the small-grid convolutions
+    long long acc32_elems = 0;
 
     ~Net();
     int alloc(void** p, size_t bytes);
@@ -53,6 +61,19 @@ struct Net {
     template <typename S> int conv_bwd(int l, int src, int src_c0, int dst, int dst_c0, int Dl, int B, int relu,
                                        int want_dx, cudaStream_t s);
 };
+
+// Tensor-core (tcgen05, BF16 operands, FP32 accumulation) convolutions of the
+// network; see conv_tc.cu.  wB holds conv_tc_weight_elems(Ci, Co, ks) BF16.
+int conv_tc_npad(int n);
+long long conv_tc_weight_elems(int Ci, int Co, int ks);
+// acc: FP32 scratch of acc_elems floats for the split-K path on small grids
+// (needs B Co D^3; NULL: never split)
+int conv_tc_fwd(const __nv_bfloat16* x, long long xbs, const float* w, int flip, const float* bias,
+                __nv_bfloat16* y, long long ybs, int Ci, int Co, int D, int ks, int relu, int B,
+                __nv_bfloat16* wB, float* acc, long long acc_elems, int* err, cudaStream_t s);
+int conv_tc_wgrad(const __nv_bfloat16* gy, long long gbs, const __nv_bfloat16* x, long long xbs, float* gw, int Ci,
+                  int Co, int D, int ks, int B, int* err, cudaStream_t s);
+bool conv_tc_fits(int Ci, int Co);
 
 // features of the solver's RHS on the coarse grid (edge n/f per axis):
 // x [rhs][10][D^3] = (chi averaged over each f^3 block, Re/Im of the

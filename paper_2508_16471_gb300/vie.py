@@ -25,7 +25,7 @@ EXPORTS = ["vie_default_opts", "vie_setup", "vie_set_eps", "vie_set_eps_device",
            "vie_farfield", "vie_farfield_dirs", "vie_farfield_dirs_device", "hom_transfer",
            "vie_hom_map", "vie_get_current", "vie_apply", "vie_apply_device", "vie_fft_lines",
            "vie_get_info", "vie_kernel_launches", "vie_stream", "vie_destroy", "vie_last_error",
-           "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_apply_noalloc", "vie_net_create", "vie_net_destroy", "vie_net_num_params",
+           "vie_set_fft_path", "vie_set_farfield_engine", "vie_cgemm", "vie_apply_noalloc", "vie_net_create", "vie_net_destroy", "vie_net_num_params", "vie_net_set_tensor_cores",
            "vie_net_get_params", "vie_net_set_params", "vie_net_forward", "vie_net_gradients",
            "vie_net_train_step", "vie_net_features", "vie_attach_net", "vie_guesses_rejected",
            "vie_net_create_io", "vie_attach_precond", "vie_precond_pairs", "vie_solve_many", "vie_autotune",
@@ -103,6 +103,7 @@ def load():
     L.vie_net_destroy.restype = None
     L.vie_net_num_params.argtypes = [P]
     L.vie_net_num_params.restype = C.c_longlong
+    L.vie_net_set_tensor_cores.argtypes = [P, C.c_int]
     L.vie_net_get_params.argtypes = [P, fp]
     L.vie_net_set_params.argtypes = [P, fp]
     L.vie_net_forward.argtypes = [P, P, P, C.c_int, C.c_int]
@@ -515,6 +516,9 @@ class Net:
 
     def num_params(self):
         return int(load().vie_net_num_params(self._p))
+
+    def set_tensor_cores(self, on):
+        _check(load().vie_net_set_tensor_cores(self._p, 1 if on else 0))
 
     def get_params(self):
         a = np.zeros(self.num_params(), dtype=np.float32)

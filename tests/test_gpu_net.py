@@ -42,13 +42,19 @@ def _data(B, D, seed, cin=10):
 # B*D^3 = 1024 voxel products of varying sign, so its relative error is
 # u * (cancellation ~ sqrt(1024)) * depth, several percent and largest at the
 # first layer; the all-parameter gradient is held to the tighter bound.
-@pytest.mark.parametrize("bf16,tol_y,tol_g,tol_all,cin", [(False, 2e-5, 2e-4, 2e-4, 10), (True, 3e-2, 0.25, 0.08, 10),
-                                                          (False, 2e-5, 2e-4, 2e-4, 7)])
-def test_forward_and_gradients_match_oracle(vielib, bf16, tol_y, tol_g, tol_all, cin):
-    """cin = 10: the initial-guess network; cin = 7: the preconditioner network."""
+@pytest.mark.parametrize("bf16,tol_y,tol_g,tol_all,cin,tc", [(False, 2e-5, 2e-4, 2e-4, 10, True),
+                                                             (True, 3e-2, 0.25, 0.08, 10, True),
+                                                             (True, 3e-2, 0.25, 0.08, 10, False),
+                                                             (True, 3e-2, 0.25, 0.08, 7, True),
+                                                             (False, 2e-5, 2e-4, 2e-4, 7, True)])
+def test_forward_and_gradients_match_oracle(vielib, bf16, tol_y, tol_g, tol_all, cin, tc):
+    """cin = 10: the initial-guess network; cin = 7: the preconditioner network;
+    BF16 storage with the convolutions on the tensor cores (tc) or on the CUDA
+    cores."""
     import torch
     specs = onet.layer_specs(c=CH, cin=cin)
     net = vielib.Net(CH, seed=5, bf16=bf16, cin=cin)
+    net.set_tensor_cores(tc)
     # non-zero biases so that their gradients and the ReLU masks are exercised
     p = net.get_params()
     rng = np.random.default_rng(6)
@@ -81,6 +87,45 @@ def test_forward_and_gradients_match_oracle(vielib, bf16, tol_y, tol_g, tol_all,
         a, b = g[o:o + n], g_or[o:o + n]
         o += n
         assert np.linalg.norm(a - b) <= tol_g * max(np.linalg.norm(b), 1e-12), (name, np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_tensor_core_convolutions_match_cuda_cores_at_configured_width(vielib):
+    """The tensor-core convolutions (implicit GEMM, tcgen05 kind::f16) against
+    the CUDA-core ones at the configured channel counts (20, 40, 80, 128: up to
+    208 input channels in the decoder, 16 input-channel chunks with zero
+    padding at the 10-channel input, 6 output channels at the head), BF16
+    storage in both: the outputs and every gradient agree to the BF16 rounding
+    of the activations, whose FP32 sums only differ in order.  B = 10 at 16^3
+    puts the finest level on the direct epilogue (320 CTAs) and the coarser
+    ones on the split-K path with FP32 accumulation."""
+    import torch
+    ch = (20, 40, 80, 128)
+    B, D = 10, 16
+    x, t, m = _data(B, D, 21)
+    xd, td, md = (torch.from_numpy(a).cuda().contiguous() for a in (x, t, m))
+    out = {}
+    for tc in (True, False):
+        net = vielib.Net(ch, seed=3, bf16=True)
+        p = net.get_params()
+        rng = np.random.default_rng(4)
+        o = 0
+        for name, ci, co, k in onet.layer_specs(c=ch, cin=10):
+            o += co * ci * k ** 3
+            p[o:o + co] = rng.standard_normal(co) * 0.1  # non-zero biases
+            o += co
+        net.set_params(p)
+        net.set_tensor_cores(tc)
+        yd = torch.empty(B, 6, D, D, D, device="cuda")
+        torch.cuda.synchronize()
+        net.forward(xd.data_ptr(), yd.data_ptr(), B, D)
+        torch.cuda.synchronize()
+        loss, g = net.gradients(xd.data_ptr(), td.data_ptr(), md.data_ptr(), B, D)
+        out[tc] = (yd.cpu().numpy(), loss, g)
+        net.close()
+    (y1, l1, g1), (y0, l0, g0) = out[True], out[False]
+    assert np.linalg.norm(y1 - y0) <= 1e-2 * np.linalg.norm(y0)
+    assert abs(l1 - l0) <= 1e-2 * abs(l0)
+    assert np.linalg.norm(g1 - g0) <= 3e-2 * np.linalg.norm(g0)
 
 
 def test_training_reduces_loss(vielib):
