@@ -911,9 +911,11 @@ def run_learned(args):
 def run_net(args):
     """The learned part's network alone at its configured width (channels
     --channels, BF16 storage, 16^3 coarse grid, batch 8 as in training):
-    forward and forward + backward per call, with the 3x3x3 convolutions on
-    the tensor cores (tcgen05 implicit GEMM) and on the CUDA cores; TFLOP/s
-    counts the convolution products only (2 x voxels x Cin x Cout x taps)."""
+    forward and training step (forward, backward, Adam with a negligible
+    learning rate so that the weights stay put) per call, with the 3x3x3
+    convolutions on the tensor cores (tcgen05 implicit GEMM) and on the CUDA
+    cores; TFLOP/s counts the convolution products only (2 x voxels x Cin x
+    Cout x taps; three such products per training step)."""
     import numpy as np
     import torch
     from paper_2508_16471_gb300 import build as libbuild
@@ -938,7 +940,7 @@ def run_net(args):
         torch.cuda.synchronize()
         for _ in range(args.warmup):
             net.forward(x.data_ptr(), y.data_ptr(), B, D)
-            net.train_step(x.data_ptr(), t.data_ptr(), m.data_ptr(), B, D, 0.0)
+            net.train_step(x.data_ptr(), t.data_ptr(), m.data_ptr(), B, D, 1e-12)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -947,7 +949,7 @@ def run_net(args):
         tf = (time.perf_counter() - t0) / args.steps
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            net.train_step(x.data_ptr(), t.data_ptr(), m.data_ptr(), B, D, 0.0)
+            net.train_step(x.data_ptr(), t.data_ptr(), m.data_ptr(), B, D, 1e-12)
         torch.cuda.synchronize()
         tt = (time.perf_counter() - t0) / args.steps
         res["tensor_cores" if tc else "cuda_cores"] = {
