@@ -426,11 +426,14 @@ __global__ void k_lsq(const c64* __restrict__ H, const c64* __restrict__ g, c64*
     }
 }
 
-// x += sum_{i<k} y_i V_i  (x in FP64; the combination is formed in T)
+// x += sum_{i<k} y_i V_i  (x in FP64; the combination is formed in T); where
+// keep[r] is set the correction itself is also stored (in T) in dz, for the
+// incremental refinement residual
 template <typename T>
 __global__ void k_xupdate(c64* __restrict__ x, long long xstride, const cplx<T>* __restrict__ V, long long rstride,
                           long long vstride, const c64* __restrict__ y, const int* __restrict__ kcount,
-                          const int* __restrict__ list, int m, long long n) {
+                          const int* __restrict__ list, int m, long long n, cplx<T>* __restrict__ dz = nullptr,
+                          const int* __restrict__ keep = nullptr) {
     __shared__ cplx<T> ys[MAX_RESTART];
     const int r = list[blockIdx.y];
     const int k = kcount[r];
@@ -454,6 +457,37 @@ __global__ void k_xupdate(c64* __restrict__ x, long long xstride, const cplx<T>*
         }
         const c64 xv = xr[e];
         xr[e] = c64{xv.x + (double)acc.x, xv.y + (double)acc.y};
+        if (dz && keep[r]) dz[r * n + e] = acc;
+    }
+}
+
+// incremental refinement residual r -= A dz (A dz in T, in basis slot 0);
+// normpart as k_residual
+template <typename T>
+__global__ void k_residual_inc(c64* __restrict__ res, long long stride, const cplx<T>* __restrict__ V, long long vrs,
+                               const int* __restrict__ list, double* __restrict__ normpart, long long n, int nblk) {
+    __shared__ double ws[KB / 32];
+    const int rr = list[blockIdx.y];
+    const long long e0 = (long long)blockIdx.x * KCH + threadIdx.x;
+    double nrm = 0;
+#pragma unroll
+    for (int k = 0; k < KE; ++k) {
+        const long long e = e0 + k * KB;
+        if (e < n) {
+            const c64 rv = res[rr * stride + e];
+            const cplx<T> ad = V[rr * vrs + e];
+            const c64 v{rv.x - (double)ad.x, rv.y - (double)ad.y};
+            res[rr * stride + e] = v;
+            nrm += v.x * v.x + v.y * v.y;
+        }
+    }
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < KB / 32; ++q) t += ws[q];
+        normpart[(long long)rr * nblk + blockIdx.x] = t;
     }
 }
 
@@ -1106,6 +1140,12 @@ void Solver::release(Operator& op) {
         dev_free(op, Z, tsz * n3 * R * m);
         Z = nullptr;
     }
+    if (dz) {
+        dev_free(op, dz, tsz * n3 * R);
+        dev_free(op, keep, sizeof(int) * R);
+        dz = nullptr;
+        keep = nullptr;
+    }
     if (Wz) {
         dev_free(op, Wz, tsz * n3 * R);
         dev_free(op, Hu, sizeof(c64) * R * (m + 1) * m);
@@ -1319,6 +1359,22 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
     // the working precision's accuracy (rel < 1e-5), so every later restart
     // of this RHS uses the FP64 residual (a working-precision one would stall)
     std::vector<int> need64(R, 1), stopped(R, 0), sticky64(R, 0);
+    // Incremental refinement residual (mixed precision): a cycle that starts
+    // from an exact residual r (FP64 accuracy) of at most INC_MAX ||b|| keeps
+    // its correction d (x' = x + d); the next residual is then r - A_T d with
+    // the working-precision operator.  Its error, (A_T - A) d, is the FP32
+    // operator's relative error (<= 2e-5 at worst) times ||A d|| ~ ||r||, so
+    // at most ~2e-9 ||b||: as exact as the double-float operator for the 1e-6
+    // judgement, at 1/13 of its cost.  The first residual of every RHS after
+    // its first cycle still comes from the double-float (or FP64) operator.
+    constexpr double INC_MAX = 1e-4;
+    const bool use_inc = prec_in == VIE_PREC_MIXED;
+    std::vector<char> res_exact(R, 0);  // S.res is the FP64-accurate residual of x
+    std::vector<int> keep(R, 0);        // the last cycle's correction is in S.dz
+    if (use_inc && !S.dz) {
+        VIE_TRY(dev_alloc(op, &S.dz, sizeof(cplx<T>) * n * R));
+        VIE_TRY(dev_alloc(op, (void**)&S.keep, sizeof(int) * R));
+    }
     out.matvecs32 = out.matvecs64 = 0;
     out.guesses_rejected = 0;
     while (true) {
@@ -1329,12 +1385,14 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         const int na = (int)act.size();
         VIE_TRY(op_set_list(op, act.data(), na));
         dim3 ga(nblk, na);
-        // exact residuals: x = 0 (r = b), or the FP64 operator
-        std::vector<int> act64, actlo;
+        // exact residuals: x = 0 (r = b), the FP64-accuracy operator, or the
+        // incremental update of an exact one
+        std::vector<int> act64, actlo, actinc;
         std::vector<char> exact(R, 0);
         for (int r : act) {
-            exact[r] = first || need64[r] || guess_pending || prec_in == VIE_PREC_FP64;
-            (exact[r] ? act64 : actlo).push_back(r);
+            exact[r] = first || keep[r] || need64[r] || guess_pending || prec_in == VIE_PREC_FP64;
+            if (!first && keep[r]) actinc.push_back(r);
+            else (exact[r] ? act64 : actlo).push_back(r);
         }
         if (first) {
             // x = 0: r = b
@@ -1353,6 +1411,18 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
                 k_residual<<<dim3(nblk, n64), KB, 0, st>>>(S.b, S.res, n, op.d_list, S.normpart, n, nblk, 0);
                 tmr_end(TMR_RESIDUAL, st, 3.0 * n64 * n * 16.0);
                 LAUNCH_CHECK();
+            }
+            if (!actinc.empty()) {
+                // r -= A_T d (basis slot 0 receives A_T d)
+                const int ni = (int)actinc.size();
+                VIE_TRY(op_set_list(op, actinc.data(), ni));
+                VIE_TRY(op_apply(op, prec_in, (cplx<T>*)S.dz, n, V, vrs, op.d_list, ni));
+                out.matvecs32 += ni;
+                tmr_begin(TMR_RESIDUAL, st);
+                k_residual_inc<T><<<dim3(nblk, ni), KB, 0, st>>>(S.res, n, V, vrs, op.d_list, S.normpart, n, nblk);
+                tmr_end(TMR_RESIDUAL, st, (double)ni * n * (32.0 + ET));
+                LAUNCH_CHECK();
+                for (int r : actinc) keep[r] = 0;
             }
             if (!actlo.empty()) {
                 // restart residual r = b - A_T x (working precision)
@@ -1373,6 +1443,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
             VIE_TRY(op_set_list(op, act.data(), na));
         }
         first = false;
+        for (int r : act) res_exact[r] = exact[r];
         tmr_begin(TMR_OTHER, st);
         k_norm_finish<<<ceil_div(na, 128), 128, 0, st>>>(S.normpart, nblk, S.rnorm, op.d_list, na);
         tmr_end(TMR_OTHER, st);
@@ -1423,6 +1494,15 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
             htarget[r] = t;
         }
         VIE_CUDA(cudaMemcpyAsync(S.target, htarget.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+        bool any_keep = false;
+        if (use_inc) {
+            for (int r = 0; r < R; ++r) keep[r] = 0;
+            for (int r : cyc) {
+                keep[r] = res_exact[r] && hr[r] <= INC_MAX * hb[r];
+                any_keep |= keep[r] != 0;
+            }
+            if (any_keep) VIE_CUDA(cudaMemcpyAsync(S.keep, keep.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+        }
         int nc = (int)cyc.size();
         VIE_TRY(op_set_list(op, cyc.data(), nc));
         tmr_begin(TMR_START, st);
@@ -1526,9 +1606,12 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
         tmr_end(TMR_OTHER, st);
         LAUNCH_CHECK();
         tmr_begin(TMR_XUPDATE, st);
+        cplx<T>* dz = any_keep ? (cplx<T>*)S.dz : nullptr;
         if (S.pc || S.bpc)
-            k_xupdate<T><<<dim3(nblk, nc), KB, 0, st>>>(S.x, n, (cplx<T>*)S.Z, zrs, n, S.y, S.kcount, op.d_list, m, n);
-        else k_xupdate<T><<<dim3(nblk, nc), KB, 0, st>>>(S.x, n, V, vrs, n, S.y, S.kcount, op.d_list, m, n);
+            k_xupdate<T><<<dim3(nblk, nc), KB, 0, st>>>(S.x, n, (cplx<T>*)S.Z, zrs, n, S.y, S.kcount, op.d_list, m, n,
+                                                        dz, S.keep);
+        else k_xupdate<T><<<dim3(nblk, nc), KB, 0, st>>>(S.x, n, V, vrs, n, S.y, S.kcount, op.d_list, m, n, dz,
+                                                         S.keep);
         tmr_end(TMR_XUPDATE, st, (double)steps_sum * n * ET + 2.0 * nc * n * 16.0);
         LAUNCH_CHECK();
         // met the target or spent the budget: FP64 check; ran out of m steps: restart residual

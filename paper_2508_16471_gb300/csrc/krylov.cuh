@@ -90,6 +90,9 @@ struct Solver {
     c64* cvec = nullptr;       // [R][m+2] H_unrotated * lag
     double* beta2 = nullptr;   // [R] squared norm of the pending vector's orthogonal part
     int* kerr = nullptr;       // [1] set by the sweep kernel when a bulk copy did not arrive in time
+    // incremental refinement residual (mixed precision; allocated on first use)
+    void* dz = nullptr;        // [R][n3] the last cycle's correction, working precision
+    int* keep = nullptr;       // [R] 1 = dz holds this RHS's correction
     PrecondCtx* pc = nullptr;  // learned right preconditioner for the next solve (not owned), or null
     BlockPrecond* bpc = nullptr;  // block-Jacobi right preconditioner for the next solve (not owned), or null
 

@@ -246,6 +246,32 @@ def test_one_sweep_arnoldi_matches_classical(vielib, prec):
     assert abs(i1 - i0) <= 0.05 * i0, (i0, i1)
 
 
+@pytest.mark.parametrize("tol", [1e-6, 1e-9])
+def test_reported_residual_is_the_fp64_residual(vielib, tol):
+    """The refinement residual that decides convergence (double-float operator
+    after the first cycle, then the incremental update r - A_T d of the later,
+    small corrections) equals the residual of the returned currents under the
+    FP64 operator: reported and recomputed relative residuals agree to 1e-9 of
+    ||b||, and every RHS meets the tolerance.  48^3 random body (1-lambda box),
+    8 RHS."""
+    wl = inputs.random_body_workload(20006, n_axis=48, h=1.0 / 48.0, n_dirs=4)
+    g = wl.grid
+    chs = [(c.khat, c.pol) for c in wl.channels]
+    chi = ovie.contrast(wl.eps)
+    with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
+        st = hd.solve(chs, tol=tol, restart=64, precision=vielib.PREC_MIXED, max_iter=20000)
+        assert st["converged"] == len(chs)
+        # a second refinement step, whose residual is the incremental one
+        assert st["outer_max"] >= 2
+        X = np.stack([hd.get_current(r) for r in range(len(chs))])
+        AX = hd.apply(X, precision=vielib.PREC_FP64)
+    for r, ch in enumerate(chs):
+        b = ovie.rhs(chi, ovie.incident_field(g.n, g.h, wl.k0, *ch))
+        res = np.linalg.norm(b - AX[r]) / np.linalg.norm(b)
+        assert res <= tol * (1 + 1e-3), (r, res)
+        assert abs(res - st["relres"][r]) <= 1e-9, (r, res, st["relres"][r])
+
+
 @pytest.mark.parametrize("seed", [27, 30, 14])
 def test_uneven_random_bodies(vielib, seed):
     """Random-body configuration (lambda/20 cells, 1-3 ellipsoids/cuboids,
