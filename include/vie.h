@@ -365,7 +365,7 @@ int vie_fft_lines(const double* in, double* out, int L, int count, int inverse, 
 int vie_get_info(const vie_handle* hd, vie_info* info);
 
 /* ---- multi-body batches (many bodies of uneven grids in one launch) ----
- * North_star's batching pattern applied to bodies: a batch holds bodies of
+ * Batching applied to bodies as well as right-hand sides: a batch holds bodies of
  * different grids (each its own n, h, origin and eps_r; one k0), each padded
  * to a power of two per body (the smallest >= 2n - 1 over its axes, 32..256,
  * so n <= 128 per axis).  Body b's RHS j is row b * n_rhs + j of batch-wide

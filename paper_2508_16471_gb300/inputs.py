@@ -8,8 +8,8 @@ deterministic for a given seed (PCG64).
 Lengths are in units of the free-space wavelength (k0 = 2*pi) unless stated.
 
 Workloads (sizes follow the paper's examples, Sec. III):
-  * ``sphere_config1``  -- 16^3, h = 1/20, R = 0.4, eps_r = 2.25, two channels.
-  * ``sphere_config2``  -- 64^3, h = 1/32, R = 1.0, eps_r = 4.0, 8 channels.
+  * ``sphere16_workload``  -- 16^3, h = 1/20, R = 0.4, eps_r = 2.25, two channels.
+  * ``sphere64_workload``  -- 64^3, h = 1/32, R = 1.0, eps_r = 4.0, 8 channels.
   * ``metasurface``     -- 256x256x32 PB-phase nanofin array (Sec. III-B, Eq. 32).
   * ``metasurface_paper`` -- the same design at the paper's scale, 40 x 12 x 2
     wavelengths at 62 cells per wavelength (2480 x 744 x 124 cells).
@@ -251,7 +251,7 @@ def spherical_basis(theta: float, phi: float):
     return rhat, eth, eph
 
 
-def channels_config1():
+def channels_two_plane_waves():
     """Two channels: x-polarised along +z, z-polarised along +x."""
     return [Channel(np.array([0.0, 0.0, 1.0]), np.array([1.0, 0.0, 0.0], complex)),
             Channel(np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.0, 1.0], complex))]
@@ -264,7 +264,7 @@ def channels_paper_sphere():
             Channel(np.array([0.0, 1.0, 0.0]), np.array([1.0, 0.0, 0.0], complex))]
 
 
-def channels_config2():
+def channels_four_angles_two_pol():
     """8 channels: khat at theta in {0,45,90,135} deg in the xz-plane,
     polarisation e_theta then e_phi for each."""
     out = []
@@ -353,18 +353,18 @@ class Workload:
     extra: dict = field(default_factory=dict)
 
 
-def sphere_config1() -> Workload:
+def sphere16_workload() -> Workload:
     g = Grid((16, 16, 16), 1.0 / 20.0)
-    return Workload("sphere16_R0.4_eps2.25", g, sphere(g, 0.4, 2.25), channels_config1(),
+    return Workload("sphere16_R0.4_eps2.25", g, sphere(g, 0.4, 2.25), channels_two_plane_waves(),
                     extra=dict(theta_deg=np.arange(0.0, 180.0 + 1e-9, 5.0),
                                phi_deg=np.arange(0.0, 355.0 + 1e-9, 5.0),
                                detectors_deg=((60.0, 0.0), (60.0, 180.0)),
                                sigma=1.2, dtau=np.arange(-5.0, 5.0 + 1e-9, 0.01)))
 
 
-def sphere_config2() -> Workload:
+def sphere64_workload() -> Workload:
     g = Grid((64, 64, 64), 1.0 / 32.0)
-    return Workload("sphere64_R1.0_eps4", g, sphere(g, 1.0, 4.0), channels_config2(),
+    return Workload("sphere64_R1.0_eps4", g, sphere(g, 1.0, 4.0), channels_four_angles_two_pol(),
                     extra=dict(theta_deg=np.arange(0.0, 180.0 + 1e-9, 1.0),
                                phi_deg=np.arange(0.0, 359.0 + 1e-9, 1.0)))
 

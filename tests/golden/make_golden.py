@@ -38,7 +38,7 @@ def _workload(name):
     if name == "sphere64":
         # the resonant sphere: restarted GMRES needs about 2e4 iterations to 1e-10 (restart 150), the
         # short-recurrence COCR about 1e3
-        wl = inputs.sphere_config2()
+        wl = inputs.sphere64_workload()
         th, ph = inputs.angle_grid(wl.extra["theta_deg"], wl.extra["phi_deg"])  # 181 x 360
         return wl, th, ph, "cocr", 0
     if name == "body64":

@@ -57,15 +57,15 @@ def _solve_and_farfield(vielib, wl, th, ph, restart):
     return F.astype(np.complex128), W, chs
 
 
-def test_config2_full_grid_farfield_vs_oracle_solution(vielib):
+def test_sphere64_full_grid_farfield_vs_oracle_solution(vielib):
     gold = _load("sphere64")
-    wl = inputs.sphere_config2()
+    wl = inputs.sphere64_workload()
     th, ph = gold["theta"], gold["phi"]
     assert gold["F_theta_phi"].shape == (8, 181, 360, 2) and float(gold["tol"]) <= 1e-10
     assert np.allclose(gold["khat"], np.stack([c.khat for c in wl.channels]))
     F, _, _ = _solve_and_farfield(vielib, wl, th, ph, restart=256)
     rel, mx = _check(F, gold["F_theta_phi"].astype(np.complex128))
-    print(f"C2 181x360 far field vs oracle solution: l2 {rel:.2e}, max {mx:.2e}")
+    print(f"sphere 64^3, 181x360 far field vs oracle solution: l2 {rel:.2e}, max {mx:.2e}")
 
 
 def test_random_body64_farfield_and_equation_vs_oracle(vielib):

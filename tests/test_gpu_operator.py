@@ -73,7 +73,7 @@ def test_apply_small_ragged_grids(vielib, n):
 
 
 def test_apply_sphere16(vielib):
-    wl = inputs.sphere_config1()
+    wl = inputs.sphere16_workload()
     _check_apply(vielib, wl.grid.n, wl.grid.h, wl.eps, R=3)
 
 
@@ -125,7 +125,7 @@ def _sampled_parity(vielib, n, h, eps, R, seed, nsamp, prec_list):
 
 
 def test_apply_sphere64_sampled(vielib):
-    wl = inputs.sphere_config2()
+    wl = inputs.sphere64_workload()
     _sampled_parity(vielib, wl.grid.n, wl.grid.h, wl.eps, 2, 11, 24,
                     (vielib.PREC_FP64, vielib.PREC_MIXED, vielib.PREC_F32X2))
 

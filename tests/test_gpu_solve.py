@@ -29,8 +29,8 @@ def _maxrel(a, b):
 
 
 @pytest.fixture(scope="module")
-def config1():
-    wl = inputs.sphere_config1()
+def sphere16():
+    wl = inputs.sphere16_workload()
     g = wl.grid
     chs = [(c.khat, c.pol) for c in wl.channels]
     w_or, infos = ovie.solve_channels(g.n, g.h, wl.k0, wl.eps, chs, tol=1e-12)
@@ -39,8 +39,8 @@ def config1():
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_config1_currents_and_farfield(vielib, config1, prec):
-    wl, chs, w_or = config1
+def test_sphere16_currents_and_farfield(vielib, sphere16, prec):
+    wl, chs, w_or = sphere16
     g = wl.grid
     th, ph = inputs.angle_grid(wl.extra["theta_deg"], wl.extra["phi_deg"])
     dirs = inputs.directions_from_angles(th, ph)
@@ -58,10 +58,10 @@ def test_config1_currents_and_farfield(vielib, config1, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_bicgstab_config1_currents(vielib, config1, prec):
+def test_bicgstab_sphere16_currents(vielib, sphere16, prec):
     """The paper's solver (BiCGStab, Sec. II-C) inside the same FP64 refinement
     reaches the oracle's currents of the 16^3 sphere."""
-    wl, chs, w_or = config1
+    wl, chs, w_or = sphere16
     g = wl.grid
     with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
         st = hd.solve(chs, tol=1e-10, restart=40, precision=prec, solver=vielib.SOLVER_BICGSTAB)
@@ -71,11 +71,11 @@ def test_bicgstab_config1_currents(vielib, config1, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_cocr_config1_currents(vielib, config1, prec):
+def test_cocr_sphere16_currents(vielib, sphere16, prec):
     """COCR (the short recurrence for A symmetric in the chi-weighted bilinear
     form) inside the same FP64 refinement reaches the oracle's currents of the
     16^3 sphere, with five vector slots (restart = 4)."""
-    wl, chs, w_or = config1
+    wl, chs, w_or = sphere16
     g = wl.grid
     with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
         st = hd.solve(chs, tol=1e-10, restart=4, precision=prec, solver=vielib.SOLVER_COCR)
@@ -84,8 +84,8 @@ def test_cocr_config1_currents(vielib, config1, prec):
     assert _maxrel(w, w_or) < 1e-8
 
 
-def test_cocr_rejects_bad_options(vielib, config1):
-    wl, chs, _ = config1
+def test_cocr_rejects_bad_options(vielib, sphere16):
+    wl, chs, _ = sphere16
     g = wl.grid
     with vielib.Handle(g.n, g.h, wl.eps, wl.k0) as hd:
         with pytest.raises(vielib.VieError):
@@ -94,8 +94,8 @@ def test_cocr_rejects_bad_options(vielib, config1):
             hd.solve(chs, restart=8, solver=3)
 
 
-def test_config1_g2_and_coincidences(vielib, config1):
-    wl, chs, w_or = config1
+def test_sphere16_g2_and_coincidences(vielib, sphere16):
+    wl, chs, w_or = sphere16
     g = wl.grid
     dets = np.stack([inputs.spherical_basis(math.radians(t), math.radians(p))[0]
                      for t, p in wl.extra["detectors_deg"]])
@@ -114,10 +114,10 @@ def test_config1_g2_and_coincidences(vielib, config1):
     assert abs(vis - ohom.visibility(E_or)) < 1e-6
 
 
-def test_config1_y_polarised_variant_gives_trivial_zero(vielib):
+def test_sphere16_y_polarised_variant_gives_trivial_zero(vielib):
     """y-pol along +x has no z far field on the y = 0 plane (mirror symmetry):
     g2 = 0 with N~c undefined (single-path zero, Sec. III-A)."""
-    wl = inputs.sphere_config1()
+    wl = inputs.sphere16_workload()
     g = wl.grid
     chs = [((0, 0, 1.0), (1.0, 0, 0)), ((1.0, 0, 0), (0, 1.0, 0))]
     dets = np.stack([inputs.spherical_basis(math.radians(t), math.radians(p))[0]
@@ -202,10 +202,10 @@ def _sampled_residual_check(vielib, wl, chs_idx, restart, seed, ff_dirs=None, so
             assert _rel(F[q], F_or) < 1e-8
 
 
-def test_config2_solution_satisfies_oracle_equation(vielib):
+def test_sphere64_solution_satisfies_oracle_equation(vielib):
     """64^3 sphere, R = 1 lambda, eps_r = 4 (a resonant case: restarted GMRES
     needs restart 256 here); all 8 channels batched, mixed precision."""
-    wl = inputs.sphere_config2()
+    wl = inputs.sphere64_workload()
     th, ph = np.radians(np.arange(0.0, 181.0, 15.0)), np.radians(np.arange(0.0, 360.0, 30.0))
     _sampled_residual_check(vielib, wl, (0, 5), restart=256, seed=3,
                             ff_dirs=inputs.directions_from_angles(th, ph))
@@ -395,12 +395,12 @@ def test_solve_many_rejects_repeated_handle(vielib):
         assert e.value.code == vielib.VIE_EINVAL
 
 
-def test_finite_aperture_detectors(vielib, config1):
+def test_finite_aperture_detectors(vielib, sphere16):
     """Eq. NAfield: aperture-collected amplitudes of the 16^3 sphere's two
     channels (z-polarised detectors at (60, 0) and (60, 180) deg, Gaussian
     aperture of half-angle 15 deg) against the oracle's on the oracle currents,
     the resulting g2 against the oracle's, and the point-detector limit."""
-    wl, chs, w_or = config1
+    wl, chs, w_or = sphere16
     g = wl.grid
     cen = np.stack([inputs.spherical_basis(math.radians(t), math.radians(p))[0]
                     for t, p in wl.extra["detectors_deg"]])

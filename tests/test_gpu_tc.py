@@ -27,7 +27,7 @@ def test_cgemm_engines(vielib, M, N, K, engine):
 
 
 def test_farfield_engines_agree_with_oracle(vielib):
-    wl = inputs.sphere_config1()
+    wl = inputs.sphere16_workload()
     g = wl.grid
     chs = [(c.khat, c.pol) for c in wl.channels]
     th, ph = inputs.angle_grid(wl.extra["theta_deg"], wl.extra["phi_deg"])

@@ -180,7 +180,7 @@ def test_oracle_cocr_matches_dense_lu_and_gmres():
     w_co, inf = ovie.solve_channels(n, 0.07, k0, eps, chs, method="cocr", tol=1e-12)
     assert all(i["converged"] and i["relres"] <= 1e-12 for i in inf)
     assert np.abs(w_co - w_lu).max() <= 1e-9 * np.abs(w_lu).max()
-    wl = inputs.sphere_config1()
+    wl = inputs.sphere16_workload()
     g = wl.grid
     chs1 = [(c.khat, c.pol) for c in wl.channels]
     w_g, _ = ovie.solve_channels(g.n, g.h, wl.k0, wl.eps, chs1, tol=1e-12)

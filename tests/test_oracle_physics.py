@@ -180,7 +180,7 @@ def test_rayleigh_limit_g2():
 def test_g2_invariant_under_phase_origin_shift():
     g = inputs.Grid((4, 4, 4), 0.08)
     eps = _random_body(g.n, 14)
-    chs = [(c.khat, c.pol) for c in inputs.channels_config1()]
+    chs = [(c.khat, c.pol) for c in inputs.channels_two_plane_waves()]
     r = np.array([[0.5, 0.5, math.sqrt(0.5)], [-0.5, 0.5, math.sqrt(0.5)]])
     vals = []
     for origin in ((0, 0, 0), (0.13, -0.21, 0.34)):
