@@ -83,7 +83,7 @@ void count_launch(long long n = 1);
 // optional per-kernel event timing (vie_timer_*)
 enum TimerId {
     TMR_ZFWD = 0, TMR_YFWD, TMR_XFUSED, TMR_YINV, TMR_ZINV, TMR_DOTS, TMR_REDUCE, TMR_UPDATE,
-    TMR_FINISH, TMR_SCALE, TMR_XUPDATE, TMR_RESIDUAL, TMR_START, TMR_RHS, TMR_OTHER, TMR_MV64, TMR_REORTH, TMR_MVDF, TMR_SWEEP,
+    TMR_FINISH, TMR_SCALE, TMR_XUPDATE, TMR_RESIDUAL, TMR_START, TMR_RHS, TMR_OTHER, TMR_MV64, TMR_REORTH, TMR_MVDF, TMR_SWEEP, TMR_FFGEMM, TMR_FFOTHER,
     TMR_COUNT
 };
 bool tmr_enabled();

@@ -373,61 +373,85 @@ int cc_cgemm(int M, int N, int K, int batch, const c32* A, long long sAb, long l
 
 // phase tables: ez[t][z] = e^{-i k0 cos(th_t) z}, ey[t][p][y] = e^{-i k0 sin th sin ph y},
 // ex[t][p][x] = e^{-i k0 sin th cos ph x}
-__global__ void k_phase_tables(const double* __restrict__ th, int nt, const double* __restrict__ ph, int np, int n0,
-                               int n1, int n2, double h, double cx, double cy, double cz, double k0, c32* ez, c32* ey,
-                               c32* ex) {
+// Phase factors exp(-i k0 d_a (c_a + j h)) of the separable far-field sum, per
+// (theta) for z and per (theta, phi) for y and x.  The phase is formed in FP64
+// and reduced to [-pi, pi] in FP64 (so that its FP32 rounding costs at most
+// 2e-7 rad whatever the box size); the factor is then taken in FP32, the
+// precision of the tables.
+// trig[0..nt) = cos theta, [nt..2nt) = sin theta, then sin phi and cos phi (np each)
+__global__ void k_trig_tables(const double* __restrict__ th, int nt, const double* __restrict__ ph, int np,
+                              double* __restrict__ trig) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nt) sincos(th[i], &trig[nt + i], &trig[i]);
+    else if (i < nt + np) sincos(ph[i - nt], &trig[2 * nt + i - nt], &trig[2 * nt + np + i - nt]);
+}
+
+__global__ void k_phase_tables(const double* __restrict__ trig, int nt, int np, int n0, int n1, int n2, double h,
+                               double cx, double cy, double cz, double k0, c32* ez, c32* ey, c32* ex) {
+    const double* cth = trig;
+    const double* sth = trig + nt;
+    const double* sph = trig + 2 * nt;
+    const double* cph = trig + 2 * nt + np;
     const long long totz = (long long)nt * n2, toty = (long long)nt * np * n1, totx = (long long)nt * np * n0;
+    constexpr double TWO_PI = 6.283185307179586;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < totz + toty + totx;
          i += (long long)gridDim.x * blockDim.x) {
         double arg;
+        c32* out;
         if (i < totz) {
             const int t = (int)(i / n2), z = (int)(i % n2);
-            arg = -k0 * cos(th[t]) * (cz + z * h);
-            double s, c;
-            sincos(arg, &s, &c);
-            ez[i] = c32{(float)c, (float)s};
+            arg = -k0 * cth[t] * (cz + z * h);
+            out = ez + i;
         } else if (i < totz + toty) {
             const long long q = i - totz;
             const int y = (int)(q % n1);
             const int p = (int)((q / n1) % np);
             const int t = (int)(q / ((long long)n1 * np));
-            arg = -k0 * sin(th[t]) * sin(ph[p]) * (cy + y * h);
-            double s, c;
-            sincos(arg, &s, &c);
-            ey[q] = c32{(float)c, (float)s};
+            arg = -k0 * sth[t] * sph[p] * (cy + y * h);
+            out = ey + q;
         } else {
             const long long q = i - totz - toty;
             const int x = (int)(q % n0);
             const int p = (int)((q / n0) % np);
             const int t = (int)(q / ((long long)n0 * np));
-            arg = -k0 * sin(th[t]) * cos(ph[p]) * (cx + x * h);
-            double s, c;
-            sincos(arg, &s, &c);
-            ex[q] = c32{(float)c, (float)s};
+            arg = -k0 * sth[t] * cph[p] * (cx + x * h);
+            out = ex + q;
         }
+        const float r = (float)(arg - TWO_PI * rint(arg / TWO_PI));
+        float sn, cs;
+        sincosf(r, &sn, &cs);
+        *out = c32{cs, sn};
     }
 }
 
-// S[rc][t][p] = sum_x B[t][rc*n0 + x][p] ex[t][p][x]; then projection
+// S[rc][t][p] = sum_x Bt[t][p][rc*n0 + x] ex[t][p][x]; then projection.  One
+// warp per output: its lanes read consecutive x (coalesced) and reduce.
 __global__ void k_ff_xreduce(const c32* __restrict__ Bt, const c32* __restrict__ ex, int nt, int np, int n0, int RC,
                              c64* __restrict__ Sraw /* [R][nt*np][3] */) {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     const long long tot = (long long)nt * np * RC;
-    if (i >= tot) return;
-    const int p = (int)(i % np);
-    const int rc = (int)((i / np) % RC);
-    const int t = (int)(i / ((long long)np * RC));
-    const c32* e = ex + ((long long)t * np + p) * n0;
-    const c32* b = Bt + ((long long)t * RC * n0 + (long long)rc * n0) * np + p;
+    if (w >= tot) return;
+    const int rc = (int)(w % RC);
+    const long long tp = w / RC;  // t * np + p
+    const c32* e = ex + tp * n0;
+    const c32* b = Bt + tp * RC * n0 + (long long)rc * n0;
     float ar = 0.f, ai = 0.f;
-    for (int x = 0; x < n0; ++x) {
-        const c32 bv = b[(long long)x * np];
+    for (int x = lane; x < n0; x += 32) {
+        const c32 bv = b[x];
         const c32 ev = e[x];
         ar += bv.x * ev.x - bv.y * ev.y;
         ai += bv.x * ev.y + bv.y * ev.x;
     }
-    const int r = rc / 3, c = rc % 3;
-    Sraw[(((long long)r * nt + t) * np + p) * 3 + c] = c64{ar, ai};
+    for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) {
+        const int t = (int)(tp / np), p = (int)(tp % np);
+        const int r = rc / 3, c = rc % 3;
+        Sraw[(((long long)r * nt + t) * np + p) * 3 + c] = c64{ar, ai};
+    }
 }
 
 __global__ void k_grid_dirs(const double* __restrict__ th, int nt, const double* __restrict__ ph, int np,
@@ -448,72 +472,86 @@ int farfield_grid(Operator& op, const c64* x, long long n3, int R, const double*
     const int n0 = op.n[0], n1 = op.n[1], n2 = op.n[2];
     const long long N = op.N;
     const int RC = 3 * R;
-    std::vector<void*> bufs;
-    auto alloc = [&](size_t bytes) -> void* {
-        void* p = nullptr;
-        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
-        bufs.push_back(p);
-        return p;
+    // one workspace per operator, grown to the largest request and kept
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
     };
-    auto cleanup = [&]() {
-        for (void* p : bufs) cudaFree(p);
-    };
-    c32* W = (c32*)alloc(sizeof(c32) * N * RC);
-    c32* ez = (c32*)alloc(sizeof(c32) * (size_t)nt * n2);
-    c32* ey = (c32*)alloc(sizeof(c32) * (size_t)nt * np * n1);
-    c32* ex = (c32*)alloc(sizeof(c32) * (size_t)nt * np * n0);
-    c32* A = (c32*)alloc(sizeof(c32) * (size_t)RC * n0 * n1 * nt);
-    c32* Bt = (c32*)alloc(sizeof(c32) * (size_t)nt * RC * n0 * np);
-    c64* Sraw = (c64*)alloc(sizeof(c64) * 3 * (size_t)R * nt * np);
-    double* dirs = (double*)alloc(sizeof(double) * 3 * (size_t)nt * np);
-    if (!W || !ez || !ey || !ex || !A || !Bt || !Sraw || !dirs) {
-        cleanup();
-        return fail(VIE_ENOMEM, "far-field workspace allocation failed");
+    const size_t oW = carve(sizeof(c32) * N * RC);
+    const size_t oz = carve(sizeof(c32) * (size_t)nt * n2);
+    const size_t oy = carve(sizeof(c32) * (size_t)nt * np * n1);
+    const size_t ox = carve(sizeof(c32) * (size_t)nt * np * n0);
+    const size_t oA = carve(sizeof(c32) * (size_t)RC * n0 * n1 * nt);
+    const size_t oB = carve(sizeof(c32) * (size_t)nt * RC * n0 * np);
+    const size_t oS = carve(sizeof(c64) * 3 * (size_t)R * nt * np);
+    const size_t od = carve(sizeof(double) * 3 * (size_t)nt * np);
+    const size_t ot = carve(sizeof(double) * 2 * (size_t)(nt + np));
+    const size_t oe = carve(sizeof(int));
+    if (op.ff_ws_bytes < off) {
+        if (op.ff_ws) dev_free(op, op.ff_ws, op.ff_ws_bytes);
+        op.ff_ws = nullptr;
+        op.ff_ws_bytes = 0;
+        VIE_TRY(dev_alloc(op, &op.ff_ws, off));
+        op.ff_ws_bytes = off;
     }
+    char* ws = (char*)op.ff_ws;
+    c32* W = (c32*)(ws + oW);
+    c32* ez = (c32*)(ws + oz);
+    c32* ey = (c32*)(ws + oy);
+    c32* ex = (c32*)(ws + ox);
+    c32* A = (c32*)(ws + oA);
+    c32* Bt = (c32*)(ws + oB);
+    c64* Sraw = (c64*)(ws + oS);
+    double* dirs = (double*)(ws + od);
+    double* trig = (double*)(ws + ot);
+    int* derr = (int*)(ws + oe);
     cudaStream_t s = op.stream;
     const double cx = op.origin[0] - 0.5 * (n0 - 1) * op.h;
     const double cy = op.origin[1] - 0.5 * (n1 - 1) * op.h;
     const double cz = op.origin[2] - 0.5 * (n2 - 1) * op.h;
+    tmr_begin(TMR_FFOTHER, s);
     cudaMemsetAsync(W, 0, sizeof(c32) * N * RC, s);
     k_scatter_full<<<dim3(std::max(1, std::min(2048, ceil_div(op.Nb, 256))), RC), 256, 0, s>>>(x, n3, op.vox, op.Nb,
                                                                                                N, W, comp_stride(op));
-    k_phase_tables<<<1024, 256, 0, s>>>(dth, nt, dph, np, n0, n1, n2, op.h, cx, cy, cz, op.k0, ez, ey, ex);
-    int* derr = (int*)alloc(sizeof(int));
-    if (!derr) {
-        cleanup();
-        return fail(VIE_ENOMEM, "far-field workspace allocation failed");
-    }
+    k_trig_tables<<<ceil_div(nt + np, 256), 256, 0, s>>>(dth, nt, dph, np, trig);
+    k_phase_tables<<<1024, 256, 0, s>>>(trig, nt, np, n0, n1, n2, op.h, cx, cy, cz, op.k0, ez, ey, ex);
     cudaMemsetAsync(derr, 0, sizeof(int), s);
+    tmr_end(TMR_FFOTHER, s, 0.0);
     int st = VIE_OK;
-    // stage A: M = RC*n0*n1, K = n2, N = nt
+    tmr_begin(TMR_FFGEMM, s);
+    // Intermediates are laid out with the row index m fastest, so that the
+    // GEMM epilogues (one thread per row) store coalesced and the next
+    // contraction reads its K index contiguously.
+    // stage A: M = RC*n0*n1 rows (rc, x, y), K = n2, N = nt; A[t][m]
+    const int MA = RC * n0 * n1;
     {
-        const int M = RC * n0 * n1;
-        st = op.ff_engine == 0 ? tc_cgemm(M, nt, n2, 1, W, 0, n2, 1, ez, 0, 1, n2, A, 0, nt, 1, derr, s)
-                               : cc_cgemm(M, nt, n2, 1, W, 0, n2, 1, ez, 0, 1, n2, A, 0, nt, 1, s);
+        st = op.ff_engine == 0 ? tc_cgemm(MA, nt, n2, 1, W, 0, n2, 1, ez, 0, 1, n2, A, 0, 1, MA, derr, s)
+                               : cc_cgemm(MA, nt, n2, 1, W, 0, n2, 1, ez, 0, 1, n2, A, 0, 1, MA, s);
     }
-    // stage B: per t: M = RC*n0, K = n1, N = np; A(m,y) = A[(m*n1 + y)*nt + t]
+    // stage B: per t: M = RC*n0 rows (rc, x), K = n1 (y, contiguous in A[t]), N = np; Bt[t][p][m]
     if (st == VIE_OK) {
         const int M = RC * n0;
         st = op.ff_engine == 0
-                 ? tc_cgemm(M, np, n1, nt, A, 1, (long long)n1 * nt, nt, ey, (long long)np * n1, 1, n1, Bt,
-                            (long long)M * np, np, 1, derr, s)
-                 : cc_cgemm(M, np, n1, nt, A, 1, (long long)n1 * nt, nt, ey, (long long)np * n1, 1, n1, Bt,
-                            (long long)M * np, np, 1, s);
+                 ? tc_cgemm(M, np, n1, nt, A, MA, n1, 1, ey, (long long)np * n1, 1, n1, Bt, (long long)M * np, 1, M,
+                            derr, s)
+                 : cc_cgemm(M, np, n1, nt, A, MA, n1, 1, ey, (long long)np * n1, 1, n1, Bt, (long long)M * np, 1, M,
+                            s);
     }
-    if (st != VIE_OK) {
-        cleanup();
-        return st;
-    }
-    k_ff_xreduce<<<ceil_div((long long)nt * np * RC, 256), 256, 0, s>>>(Bt, ex, nt, np, n0, RC, Sraw);
+    tmr_end(TMR_FFGEMM, s, 0.0);
+    if (st != VIE_OK) return st;
+    tmr_begin(TMR_FFOTHER, s);
+    k_ff_xreduce<<<ceil_div((long long)nt * np * RC * 32, 256), 256, 0, s>>>(Bt, ex, nt, np, n0, RC, Sraw);
     k_grid_dirs<<<ceil_div(nt * np, 256), 256, 0, s>>>(dth, nt, dph, np, dirs);
     k_ff_project<<<ceil_div((long long)nt * np * R, 256), 256, 0, s>>>(Sraw, dirs, nt * np, R, ff_constant(op), basis,
                                                                        dout, op.disc ? 0.5 * op.k0 * op.h : 0.0);
-    count_launch(5);
+    tmr_end(TMR_FFOTHER, s, 0.0);
+    count_launch(6);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
-    cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "far field (grid)");
     if (herr) return fail(VIE_ETIMEOUT, "tensor-core GEMM: a bounded wait on the MMA barrier gave up");
     return VIE_OK;

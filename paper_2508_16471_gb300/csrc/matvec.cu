@@ -1193,6 +1193,9 @@ int op_replan(Operator& op, const int P[3]) {
 }
 
 void op_free(Operator& op) {
+    cudaFree(op.ff_ws);
+    op.ff_ws = nullptr;
+    op.ff_ws_bytes = 0;
     for (int a = 0; a < 3; ++a) {
         cudaFree(op.ax[a].tw32);
         cudaFree(op.ax[a].tw64);

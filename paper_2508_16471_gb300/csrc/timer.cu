@@ -57,7 +57,7 @@ void flush() {
 }
 const char* kNames[TMR_COUNT] = {"zfwd", "yfwd", "xfused", "yinv", "zinv", "dots", "reduce_dots", "update",
                                  "finish", "scale", "xupdate", "residual", "start_cycle", "rhs", "other",
-                                 "matvec_fp64", "reorth_steps", "matvec_f32x2", "sweep"};
+                                 "matvec_fp64", "reorth_steps", "matvec_f32x2", "sweep", "farfield_gemm", "farfield_other"};
 }  // namespace
 
 bool tmr_enabled() { return T().on; }

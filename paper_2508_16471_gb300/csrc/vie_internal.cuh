@@ -57,6 +57,8 @@ struct Operator {
     cdf* dtabdf = nullptr;
     int dstride = 0;
     int ff_engine = 0;       // far-field contractions: 0 tcgen05 3xTF32, 1 CUDA-core FP32
+    void* ff_ws = nullptr;   // far-field workspace (grows to the largest grid of directions asked for)
+    size_t ff_ws_bytes = 0;
     // voxel maps per batch slot: slot list[s] reads idx_map + list[s] * idx_stride (0: one map for all slots;
     // the block operator of the block-Jacobi preconditioner keeps one map per block)
     long long idx_stride = 0;
