@@ -32,10 +32,10 @@ namespace vie {
 namespace {
 
 constexpr int TC_BM = 128;  // rows per CTA (one accumulator lane per row)
-constexpr int TC_BN = 64;   // real columns per CTA (32 complex outputs)
-constexpr int TC_BK = 32;   // real K per chunk (16 complex)
+constexpr int TC_BN = 256;  // real columns per CTA (128 complex outputs): A is staged once per 128 outputs
+constexpr int TC_BK = 16;   // real K per chunk (8 complex; two MMAs of K = 8)
 constexpr int TC_THREADS = 128;
-constexpr uint32_t TC_TMEM_COLS = 64;
+constexpr uint32_t TC_TMEM_COLS = 256;  // two CTAs per SM fill the 512 columns
 constexpr long long TC_WAIT_LIMIT = 1LL << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
