@@ -515,6 +515,18 @@ __global__ void k_octant(const c64* __restrict__ Kc, c64* __restrict__ o64, c32*
 }
 
 // ---------------------------------------------------------------------------
+// number of z lines (x, y) with at least one body voxel
+__global__ void k_line_count(const int* __restrict__ idx_map, long long nl, int n2, long long* __restrict__ count) {
+    const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    const int* im = idx_map + l * n2;
+    for (int z = 0; z < n2; ++z)
+        if (im[z] >= 0) {
+            atomicAdd((unsigned long long*)count, 1ull);
+            return;
+        }
+}
+
 // body compaction: idx_map, vox, chi from a device eps grid
 // ---------------------------------------------------------------------------
 constexpr int SCAN_B = 1024;
@@ -954,9 +966,17 @@ int op_set_body_device(Operator& op, const double* eps) {
             k_body_write<<<nb, SCAN_B, 0, op.stream>>>(eps, N, bcount, op.idx_map, op.vox, op.chi32, op.chi64,
                                                        op.n[1], op.n[2], op.disc, Nb);
             count_launch();
+            // fraction of z lines that hold a body voxel (the z-inverse pass reads only those)
+            const long long nl = (long long)op.n[0] * op.n[1];
+            cudaMemsetAsync(total, 0, sizeof(long long), op.stream);
+            k_line_count<<<ceil_div(nl, 256), 256, 0, op.stream>>>(op.idx_map, nl, op.n[2], total);
+            count_launch();
+            long long nz = nl;
+            cudaMemcpyAsync(&nz, total, sizeof(long long), cudaMemcpyDeviceToHost, op.stream);
             st = to_dfl(op.chi64, op.chidf, nchi, op.stream);
             cudaError_t e = cudaStreamSynchronize(op.stream);
             if (st == VIE_OK && e != cudaSuccess) st = cuda_fail(e, "body compaction");
+            op.line_frac = nl > 0 ? (double)nz / (double)nl : 1.0;
         }
     }
     cudaFree(bcount);
@@ -1128,7 +1148,7 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
             tmr_begin(tid(TMR_ZINV), op.stream);
             VIE_TRY(fast_zinv((const c32*)A, (const c32*)w, wr, (c32*)y, yr, list, op.idx_map, (const float*)chi, n0, n1,
                               n2, cst, nlines, P2, op.ax[2].roots32, op.stream, op.chi_cs, op.idx_stride));
-            tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
+            tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA * op.line_frac + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
         } else {
@@ -1140,7 +1160,7 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
             k_zinv<T, TI><<<(unsigned)((nlines + c.w - 1) / c.w), nt, c.smem, op.stream>>>(
                 A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, cst, nlines, p, twp<T>(op.ax[2]), c.w,
                 op.chi_cs, c.stw, op.idx_stride);
-            tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
+            tmr_end(tid(TMR_ZINV), op.stream, ns * (lineA * op.line_frac + 2.0 * vec) + op.Nb * sizeof(T) + 4.0 * op.N);
             count_launch();
             VIE_CUDA(cudaGetLastError());
         }

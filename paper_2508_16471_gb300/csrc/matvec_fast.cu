@@ -360,6 +360,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_zfwd_r(const c32* __restrict__ w,
     const int q2 = threadIdx.x % R2, l = threadIdx.x / R2;
     const long long line = line0 + l;
     c32 a[R1];
+    bool any = false;
     if (line < nlines) {
         const long long sc = line / plane;
         const long long xy = line - sc * plane;
@@ -372,7 +373,10 @@ __global__ void __launch_bounds__(Z_THREADS) k_zfwd_r(const c32* __restrict__ w,
             c32 v = z32();
             if (z < n2) {
                 const int vi = im[z];
-                if (vi >= 0) v = wr[vi];
+                if (vi >= 0) {
+                    v = wr[vi];
+                    any = true;
+                }
             }
             a[n1i] = v;
         }
@@ -380,7 +384,12 @@ __global__ void __launch_bounds__(Z_THREADS) k_zfwd_r(const c32* __restrict__ w,
 #pragma unroll
         for (int n1i = 0; n1i < R1 / 2; ++n1i) a[n1i] = z32();
     }
-    __syncthreads();
+    if (!__syncthreads_or(any)) {
+        // no body voxel on this CTA's lines: their spectra are zero
+        for (long long i = threadIdx.x; i < (long long)NL * L; i += Z_THREADS)
+            if (line0 + i / L < nlines) A[line0 * L + i] = z32();
+        return;
+    }
     dftp2_half_in<float, R1, false>(a);
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) a[k1] = a[k1] * tw<false>(TA, k1 * R2 + q2);
@@ -414,9 +423,29 @@ __global__ void __launch_bounds__(Z_THREADS) k_zinv_r(const c32* __restrict__ A,
     extern __shared__ __align__(16) unsigned char smraw[];
     c32* TB = reinterpret_cast<c32*>(smraw);
     c32* S = TB + L;
-    stage_table(TB, tw4 + L, L);
     const long long line0 = (long long)blockIdx.x * NL;
-    __syncthreads();
+    // this thread's voxel indices of the scatter (read first: a CTA whose lines
+    // hold no body voxel has nothing to write and skips its transforms)
+    const int q2 = threadIdx.x % R2, l = threadIdx.x / R2;
+    const long long line = line0 + l;
+    const long long plane = (long long)n0 * n1;
+    const long long sc = line / plane;
+    const long long xy = line - sc * plane;
+    const int slot = (int)(sc / 3), c = (int)(sc - (sc / 3) * 3);
+    const long long rr = line < nlines ? list[slot] : 0;
+    int vis[R1 / 2];
+    bool any = false;
+    {
+        const int* im = idx_map + rr * idx_stride + xy * n2;
+#pragma unroll
+        for (int n1i = 0; n1i < R1 / 2; ++n1i) {
+            const int z = n1i * R2 + q2;
+            vis[n1i] = (line < nlines && z < n2) ? im[z] : -1;
+            any |= vis[n1i] >= 0;
+        }
+    }
+    stage_table(TB, tw4 + L, L);
+    if (!__syncthreads_or(any)) return;
     for (int it = threadIdx.x; it < NL * R1; it += Z_THREADS) {
         const int k1 = it % R1, ll = it / R1;
         const long long ln = line0 + ll;
@@ -428,26 +457,18 @@ __global__ void __launch_bounds__(Z_THREADS) k_zinv_r(const c32* __restrict__ A,
         for (int q = 0; q < R2; ++q) S[(ll * R1 + k1) * RS + q] = b[q] * tw<true>(TB, q * R1 + k1);
     }
     __syncthreads();
-    const int q2 = threadIdx.x % R2, l = threadIdx.x / R2;
-    const long long line = line0 + l;
     if (line >= nlines) return;
     c32 a[R1];
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) a[k1] = S[(l * R1 + k1) * RS + q2];
     dftp2_half_out<float, R1, true>(a);  // only z < n2 <= L/2 is kept
-    const long long plane = (long long)n0 * n1;
-    const long long sc = line / plane;
-    const long long xy = line - sc * plane;
-    const int slot = (int)(sc / 3), c = (int)(sc - (sc / 3) * 3);
-    const long long rr = list[slot];
     const c32* wr = w + rr * w_rstride + c * Nb;
     c32* yr = y + rr * y_rstride + c * Nb;
-    const int* im = idx_map + rr * idx_stride + xy * n2;
 #pragma unroll
     for (int n1i = 0; n1i < R1 / 2; ++n1i) {
         const int z = n1i * R2 + q2;
         if (z < n2) {
-            const int vi = im[z];
+            const int vi = vis[n1i];
             if (vi >= 0) {
                 const c32 u = a[n1i];
                 const c32 wv = wr[vi];

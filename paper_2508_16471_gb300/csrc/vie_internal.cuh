@@ -46,6 +46,7 @@ struct Operator {
     int list_cap = 0;
     cudaStream_t stream = nullptr;
     double bytes = 0;        // device bytes held
+    double line_frac = 1.0;  // fraction of z lines holding a body voxel (algorithmic bytes of the z-inverse pass)
     int fft_path = 0;        // 0: register four-step where the length allows, 1: generic only
     int P_fixed[3] = {0, 0, 0};  // padded lengths chosen by the autotuner (0: padded_size)
     // discretisation: 0 = D1 (voxel-centred unknowns, dyadic kernel), 1 = D2
