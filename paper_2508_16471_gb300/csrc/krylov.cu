@@ -77,7 +77,7 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float so, float 
     c = c + co + err;
     s = t;
 }
-__device__ __forceinline__ float2 warp_sum8_pair(const float (&v)[8], int lane, int& q) {
+__device__ __forceinline__ double warp_sum8(const float (&v)[8], int lane, int& q) {
     float s[4], c[4];
     {
         const bool up = lane & 16;
@@ -114,7 +114,7 @@ __device__ __forceinline__ float2 warp_sum8_pair(const float (&v)[8], int lane, 
         two_sum_acc(s[0], c[0], so, co);
     }
     q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-    return make_float2(s[0], c[0]);  // the sum is s + c, formed in FP64 by the caller
+    return (double)s[0] + (double)c[0];
 }
 __device__ __forceinline__ double warp_sum8(const double (&v)[8], int lane, int& q) {
     double s[4];
@@ -933,16 +933,9 @@ __global__ void __launch_bounds__(KB, sizeof(T) == 4 ? 3 : 1) k_sweep(cplx<T>* _
             gv[2 * q + 1] = gi;
         }
         int q;
-        if constexpr (sizeof(T) == 4) {
-            // the (sum, error) pair goes to shared memory as it is: no FP64 work in the loop
-            const float2 d = warp_sum8_pair(gv, lane, q);
-            const int i = i0 + (q >> 1);
-            if ((lane & 3) == 0 && i <= j) reinterpret_cast<float2*>(q & 1 ? sim : sre)[wid * J2 + i] = d;
-        } else {
-            const double d = warp_sum8(gv, lane, q);
-            const int i = i0 + (q >> 1);
-            if ((lane & 3) == 0 && i <= j) (q & 1 ? sim : sre)[wid * J2 + i] = d;
-        }
+        const double d = warp_sum8(gv, lane, q);
+        const int i = i0 + (q >> 1);
+        if ((lane & 3) == 0 && i <= j) (q & 1 ? sim : sre)[wid * J2 + i] = d;
     }
     if (bad) {
         // a chunk did not arrive: let the copies still in flight land, then leave
@@ -975,38 +968,18 @@ __global__ void __launch_bounds__(KB, sizeof(T) == 4 ? 3 : 1) k_sweep(cplx<T>* _
         const double di = warp_sum_comp(gi);
         const double dn = warp_sum_comp(nn);
         if (lane == 0) {
-            if constexpr (sizeof(T) == 4) {
-                auto pair = [](double x) {
-                    const float h = (float)x;
-                    return make_float2(h, (float)(x - (double)h));
-                };
-                float2* pre = reinterpret_cast<float2*>(sre);
-                float2* pim = reinterpret_cast<float2*>(sim);
-                pre[wid * J2 + j + 1] = pair(dr);
-                pim[wid * J2 + j + 1] = pair(di);
-                pre[wid * J2 + j + 2] = pair(dn);
-                pim[wid * J2 + j + 2] = make_float2(0.f, 0.f);
-            } else {
-                sre[wid * J2 + j + 1] = dr;
-                sim[wid * J2 + j + 1] = di;
-                sre[wid * J2 + j + 2] = dn;
-                sim[wid * J2 + j + 2] = 0.0;
-            }
+            sre[wid * J2 + j + 1] = dr;
+            sim[wid * J2 + j + 1] = di;
+            sre[wid * J2 + j + 2] = dn;
+            sim[wid * J2 + j + 2] = 0.0;
         }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < J2; i += KB) {
         double ar = 0, ai = 0;
         for (int q = 0; q < KB / 32; ++q) {
-            if constexpr (sizeof(T) == 4) {
-                const float2 a = reinterpret_cast<const float2*>(sre)[q * J2 + i];
-                const float2 b = reinterpret_cast<const float2*>(sim)[q * J2 + i];
-                ar += (double)a.x + (double)a.y;
-                ai += (double)b.x + (double)b.y;
-            } else {
-                ar += sre[q * J2 + i];
-                ai += sim[q * J2 + i];
-            }
+            ar += sre[q * J2 + i];
+            ai += sim[q * J2 + i];
         }
         partial[((long long)r * mp2 + i) * nblk + blockIdx.x] = c64{ar, ai};
     }
