@@ -94,15 +94,15 @@ __host__ __device__ constexpr uint32_t tmem_cols(int n) {
     return n <= 32 ? 32u : n <= 64 ? 64u : n <= 128 ? 128u : 256u;
 }
 
-__device__ __forceinline__ int tap_off(int tap, int ks, int& ox, int& oy, int& oz) {
+// offsets (-1, 0, 1 per axis) of tap 0..26 of a 3x3x3 kernel; 0 for a 1x1x1 one
+__device__ __forceinline__ void tap_off(int tap, int ks, int& ox, int& oy, int& oz) {
     if (ks == 1) {
         ox = oy = oz = 0;
-        return 0;
+        return;
     }
     ox = tap / 9 - 1;
     oy = (tap / 3) % 3 - 1;
     oz = tap % 3 - 1;
-    return 0;
 }
 
 // Allocate / free tensor memory (warp 0) and set up the mbarriers (thread 0).
@@ -410,13 +410,13 @@ __global__ void __launch_bounds__(CT_THREADS) k_wgrad_tc(const __nv_bfloat16* __
 namespace {
 size_t conv_tc_smem(int Npad) { return (size_t)CT_STAGES * (CT_M * CT_K * 2 + (size_t)Npad * CT_K * 2); }
 
-int set_attr(const void* f, size_t sm, std::atomic<bool>& done) {
+// the dynamic shared memory of the largest tile, set once per kernel
+int set_attr(const void* f, std::atomic<bool>& done) {
     if (!done) {
         VIE_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)conv_tc_smem(CT_NMAX)));
         done = true;
     }
-    (void)sm;
     return VIE_OK;
 }
 }  // namespace
@@ -446,7 +446,7 @@ int conv_tc_fwd(const __nv_bfloat16* x, long long xbs, const float* w, int flip,
     count_launch();
     VIE_CUDA(cudaGetLastError());
     static std::atomic<bool> attr{false};
-    VIE_TRY(set_attr((const void*)k_conv_tc, 0, attr));
+    VIE_TRY(set_attr((const void*)k_conv_tc, attr));
     const long long V = (long long)D * D * D;
     const long long base = ((V + CT_M - 1) / CT_M) * B;  // (tile, batch) CTAs
     const int nall = KK * ((Ci + CT_K - 1) / CT_K);
@@ -476,7 +476,7 @@ int conv_tc_wgrad(const __nv_bfloat16* gy, long long gbs, const __nv_bfloat16* x
     const int Npad = conv_tc_npad(Ci);
     if (Npad > CT_NMAX || Co > CT_M || Co < 1 || B < 1) return fail(VIE_EINVAL, "tensor-core weight gradient: bad sizes");
     static std::atomic<bool> attr{false};
-    VIE_TRY(set_attr((const void*)k_wgrad_tc, 0, attr));
+    VIE_TRY(set_attr((const void*)k_wgrad_tc, attr));
     const long long tot = (long long)B * D * D * D;
     const int KK = ks * ks * ks;
     // K per CTA: about eight CTAs per SM over all taps, at least 256
