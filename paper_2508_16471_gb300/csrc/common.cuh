@@ -4,11 +4,27 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 #include <string>
 
 #include "../../include/vie.h"
 
 namespace vie {
+
+// True the first time it is asked, per flag, for the current device (one bit
+// per device, ordinals below 64): kernel attributes such as the dynamic
+// shared-memory limit are set per device.
+inline bool first_on_device(std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return true;
+    }
+    const unsigned long long bit = 1ull << dev;
+    return (done.fetch_or(bit) & bit) == 0;
+}
+
 
 template <typename T> struct cplx { T x, y; };
 template <> struct __align__(8) cplx<float> { float x, y; };

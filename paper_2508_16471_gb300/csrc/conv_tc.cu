@@ -411,12 +411,10 @@ namespace {
 size_t conv_tc_smem(int Npad) { return (size_t)CT_STAGES * (CT_M * CT_K * 2 + (size_t)Npad * CT_K * 2); }
 
 // the dynamic shared memory of the largest tile, set once per kernel
-int set_attr(const void* f, std::atomic<bool>& done) {
-    if (!done) {
+int set_attr(const void* f, std::atomic<unsigned long long>& done) {
+    if (first_on_device(done))
         VIE_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)conv_tc_smem(CT_NMAX)));
-        done = true;
-    }
     return VIE_OK;
 }
 }  // namespace
@@ -445,7 +443,7 @@ int conv_tc_fwd(const __nv_bfloat16* x, long long xbs, const float* w, int flip,
                                                                                           wB);
     count_launch();
     VIE_CUDA(cudaGetLastError());
-    static std::atomic<bool> attr{false};
+    static std::atomic<unsigned long long> attr{0};
     VIE_TRY(set_attr((const void*)k_conv_tc, attr));
     const long long V = (long long)D * D * D;
     const long long base = ((V + CT_M - 1) / CT_M) * B;  // (tile, batch) CTAs
@@ -475,7 +473,7 @@ int conv_tc_wgrad(const __nv_bfloat16* gy, long long gbs, const __nv_bfloat16* x
                   int Co, int D, int ks, int B, int* err, cudaStream_t s) {
     const int Npad = conv_tc_npad(Ci);
     if (Npad > CT_NMAX || Co > CT_M || Co < 1 || B < 1) return fail(VIE_EINVAL, "tensor-core weight gradient: bad sizes");
-    static std::atomic<bool> attr{false};
+    static std::atomic<unsigned long long> attr{0};
     VIE_TRY(set_attr((const void*)k_wgrad_tc, attr));
     const long long tot = (long long)B * D * D * D;
     const int KK = ks * ks * ks;

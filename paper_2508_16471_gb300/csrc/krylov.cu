@@ -1271,14 +1271,13 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
     cudaStream_t st = op.stream;
     const int prec_in = sizeof(T) == 8 ? VIE_PREC_FP64 : VIE_PREC_MIXED;
     const double ET = sizeof(cplx<T>);
-    static std::atomic<bool> smem_set{false};
-    if (!smem_set) {
+    static std::atomic<unsigned long long> smem_set{0};
+    if (first_on_device(smem_set)) {
         VIE_CUDA(cudaFuncSetAttribute(k_dots<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(double) * 2 * (KB / 32) * (MAX_RESTART + 2))));
         VIE_CUDA(cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(SweepCfg<T>::ST * SweepCfg<T>::STAGE_BYTES +
                                             sizeof(double) * 2 * (KB / 32) * (MAX_RESTART + 2))));
-        smem_set = true;
     }
 
     std::vector<int> outer_active(R), it(R, 0), outer(R, 0);

@@ -764,11 +764,8 @@ template <> const cdf* dtp<dfl>(const Operator& op) { return op.dtabdf; }
 template <typename T, bool INV>
 static int launch_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_in, int n_out, const FFTPlan& p,
                         const cplx<T>* tw, cudaStream_t s) {
-    static std::atomic<bool> init{false};  // repeated attribute calls from racing threads are harmless
-    if (!init) {
-        VIE_TRY(allow_smem(k_lines<T, INV>));
-        init = true;
-    }
+    static std::atomic<unsigned long long> init{0};  // repeated attribute calls from racing threads are harmless
+    if (first_on_device(init)) VIE_TRY(allow_smem(k_lines<T, INV>));
     const TileCfg c = lines_cfg<T>(p);
     if (!c.ok) return fail(VIE_EINVAL, "FFT length " + std::to_string(p.L) + " does not fit in shared memory");
     const long long grid = (count + c.w - 1) / c.w;
@@ -784,11 +781,8 @@ template <typename T, bool INV>
 static int launch_axis(const cplx<T>* in, cplx<T>* out, long long outer, int n_in, int n_out, long long inner,
                        const FFTPlan& p, const cplx<T>* tw, cudaStream_t s, int tid = TMR_OTHER) {
     const double bytes = (double)sizeof(cplx<T>) * outer * inner * (double)(n_in + n_out);
-    static std::atomic<bool> init{false};  // repeated attribute calls from racing threads are harmless
-    if (!init) {
-        VIE_TRY(allow_smem(k_axis<T, INV>));
-        init = true;
-    }
+    static std::atomic<unsigned long long> init{0};  // repeated attribute calls from racing threads are harmless
+    if (first_on_device(init)) VIE_TRY(allow_smem(k_axis<T, INV>));
     const TileCfg c = axis_cfg<T>(p, inner);
     if (!c.ok) return fail(VIE_EINVAL, "FFT length " + std::to_string(p.L) + " does not fit in shared memory");
     const long long grid = outer * ((inner + c.w - 1) / c.w);
@@ -1034,12 +1028,11 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
     const int pi = F32 ? 0 : 1;  // work arrays: double and double-float elements are both 16 bytes
     VIE_TRY(op_reserve(op, pi, nr));
     MatvecWork& W = op.work[pi];
-    static std::atomic<bool> init{false};  // repeated attribute calls from racing threads are harmless
-    if (!init) {
+    static std::atomic<unsigned long long> init{0};  // repeated attribute calls from racing threads are harmless
+    if (first_on_device(init)) {
         VIE_TRY(allow_smem(k_zfwd<T, TI>));
         VIE_TRY(allow_smem(k_zinv<T, TI>));
         VIE_TRY(allow_smem(k_xfused<T>));
-        init = true;
     }
     const int n0 = op.n[0], n1 = op.n[1], n2 = op.n[2];
     const int P0 = op.P[0], P1 = op.P[1], P2 = op.P[2];

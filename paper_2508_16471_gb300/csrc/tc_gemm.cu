@@ -270,11 +270,9 @@ int tc_cgemm(int M, int N, int K, int batch, const c32* A, long long sAb, long l
     dim3 g((2 * N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
     if (g.y > 65535 || g.z > 65535) return fail(VIE_EINVAL, "tensor-core GEMM grid too large");
     const size_t sm = 2 * (size_t)TC_STAGE_BYTES;  // two stage buffers
-    static std::atomic<bool> init{false};  // repeated attribute calls from racing threads are harmless
-    if (!init) {
+    static std::atomic<unsigned long long> init{0};  // repeated attribute calls from racing threads are harmless
+    if (first_on_device(init))
         VIE_CUDA(cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        init = true;
-    }
     k_tc_cgemm<<<g, TC_THREADS, sm, s>>>(M, N, K, A, sAb, sAm, sAk, B, sBb, sBk, sBn, C, sCb, sCm, sCn, d_err);
     count_launch();
     VIE_CUDA(cudaGetLastError());
