@@ -37,7 +37,7 @@ def _worker(rank, world, port, bodies, out):
 def test_replica_sharding_and_job_aggregate_gloo():
     world, bodies = 2, 3
     port = _free_port()
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.spawn(_worker, args=(world, port, bodies, out), nprocs=world, join=True)
         res = dict(out)
