@@ -61,7 +61,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--bodies", type=int, default=8)
     p.add_argument("--restart", type=int, default=None,
-                   help="GMRES restart length (default: 160 for the 128^3 bodies, the fastest measured; 64 otherwise)")
+                   help="GMRES restart length (default: 160 for the random-body workloads, the fastest measured "
+                        "with the one-sweep Arnoldi; 64 for the metasurface)")
     p.add_argument("--inner-floor", type=float, default=0.7,
                    help="mixed mode: inner solves stop at inner_floor x tol x ||b|| at the latest")
     p.add_argument("--arnoldi", type=int, default=1, choices=[0, 1],
@@ -108,7 +109,7 @@ def parse():
                    help="profiling aid: a 12-iteration solve with this many RHS on the first bench body, then exit")
     args = p.parse_args()
     if args.restart is None:
-        args.restart = 160 if args.workload == "bodies128" else 64
+        args.restart = 160 if args.workload in ("bodies128", "bodies-uneven", "learned") else 64
     return args
 
 
