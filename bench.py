@@ -785,7 +785,19 @@ def run_bodies_uneven(args):
     chs = [(c.khat, c.pol) for c in inputs.channels_fibonacci(8)]
     R = len(chs)
     opts = dict(tol=1e-6, restart=args.restart, max_iter=args.max_iter)
-    groups = [order[i:i + args.batch] for i in range(0, len(order), args.batch)]
+    # groups of up to --batch bodies in size order, closed early where the batch's Krylov basis
+    # (rows x (m + 1) x 3 N_b of the largest body, complex64) would pass 100 GB
+    nbody = [int(np.count_nonzero(bodies[i][2] > 1.0)) for i in range(len(bodies))]
+    groups, cur = [], []
+    for i in order:
+        nmax = max([nbody[k] for k in cur] + [nbody[i]])
+        if cur and (len(cur) >= args.batch or
+                    (len(cur) + 1) * R * (args.restart + 1) * 3 * nmax * 8 > 100e9):
+            groups.append(cur)
+            cur = []
+        cur.append(i)
+    if cur:
+        groups.append(cur)
     t_batch, solved, iters, launches = 0.0, 0, [], 0
     clocks = ClockSampler(0)
     clocks.start()
@@ -823,6 +835,7 @@ def run_bodies_uneven(args):
             "config": {"workload": f"{len(bodies)} random bodies (seeds 0..{len(bodies) - 1}), n in "
                                    f"{min(sizes)}..{max(sizes)} (drawn 32..96), h = lambda/n, eps_r in [1.5, 6], "
                                    f"{R} RHS each", "batch": args.batch,
+                       "batch_sizes": [len(gp) for gp in groups],
                        "solver": f"mixed FP32 matvec / FP64 Arnoldi GMRES({args.restart}) + double-float residual"},
             "bodies_per_s": len(bodies) * (solved / (R * len(bodies))) / t_batch, "seconds": t_batch,
             "solved": solved, "rhs_total": R * len(bodies), "iters_mean": float(np.mean(iters)),
