@@ -82,6 +82,16 @@ template <typename T> __device__ __forceinline__ T cos32(int m) {
     }
 }
 
+// a (1 -+ i) / sqrt2 = a w_8 (three = false) or a (-1 -+ i) / sqrt2 = a w_8^3
+// (three = true); the lower sign for the inverse.  Types with a faster form
+// overload it.
+template <typename T> __device__ __forceinline__ cplx<T> root8(cplx<T> a, bool inv, bool three) {
+    const T h = (T)VIE_SQRT1_2;
+    if (!three)
+        return inv ? cplx<T>{h * (a.x - a.y), h * (a.x + a.y)} : cplx<T>{h * (a.x + a.y), h * (a.y - a.x)};
+    return inv ? cplx<T>{-h * (a.x + a.y), h * (a.x - a.y)} : cplx<T>{h * (a.y - a.x), -h * (a.x + a.y)};
+}
+
 // a * w_N^k, w_N = exp(-+ 2 pi i / N), N a divisor of 32, 0 <= k < N.  Used
 // with k known after unrolling: the multiples of pi/4 reduce to sign swaps
 // or one shared scaling, instead of a full complex product with 0 / +-1
@@ -92,10 +102,8 @@ template <typename T, int N, bool INV> __device__ __forceinline__ cplx<T> rootmu
     if (4 * k == N) return mul_mi<T, INV>(a);
     if (2 * k == N) return cplx<T>{-a.x, -a.y};
     if (4 * k == 3 * N) return mul_mi<T, !INV>(a);
-    if (8 * k == N)  // (1 -+ i) / sqrt2
-        return INV ? cplx<T>{h * (a.x - a.y), h * (a.x + a.y)} : cplx<T>{h * (a.x + a.y), h * (a.y - a.x)};
-    if (8 * k == 3 * N)  // (-1 -+ i) / sqrt2
-        return INV ? cplx<T>{-h * (a.x + a.y), h * (a.x - a.y)} : cplx<T>{h * (a.y - a.x), -h * (a.x + a.y)};
+    if (8 * k == N) return root8(a, INV, false);
+    if (8 * k == 3 * N) return root8(a, INV, true);
     // general root: angle 2 pi m / 32, m = 32 k / N in (0, 32)
     const int m = k * (32 / N);
     const int q = m & 7, oct = m >> 3;  // octant and offset within it
