@@ -319,8 +319,14 @@ __global__ void k_zinv(const cplx<T>* __restrict__ A, const cplx<TI>* __restrict
 // B [slot][3][n0][inner], inner = P1 * P2; updated in place for x < n0.
 // Two CTAs per SM: the transform stages are separated by CTA barriers, so a
 // second resident CTA keeps the (FP64-bound) pipes busy while one waits.
+// Threads of the generic fused x pass: 256, or 192 for double-float, whose
+// tile width (100 KB over six L x TW buffers of 16-byte elements: TW L = 1024)
+// gives its joint three-component radix-16 stages 3 (L/16) TW = 192
+// butterflies, and whose registers then fit without spilling at two CTAs per SM.
+template <typename T> struct XG { static constexpr int NT = std::is_same<T, dfl>::value ? 192 : 256; };
+
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int n0, long long inner, int P0, int P1, int P2,
+__global__ void __launch_bounds__(XG<T>::NT, 2) k_xfused(cplx<T>* __restrict__ B, int n0, long long inner, int P0, int P1, int P2,
                          const cplx<T>* __restrict__ khat, int H0, int H1, int H2, FFTPlan plan,
                          const cplx<T>* __restrict__ twg, int TW, const cplx<T>* __restrict__ dtab, int dstride,
                          T ksq, int stw, int joint) {
@@ -332,9 +338,13 @@ __global__ void __launch_bounds__(256, 2) k_xfused(cplx<T>* __restrict__ B, int 
     cplx<T>* D[6];
     D[0] = tw_setup<T>(smraw, twg, plan, stw, &tw);
     for (int i = 1; i < (joint ? 6 : 4); ++i) D[i] = D[i - 1] + L * TW;
+    // slots vary fastest across the grid, so the CTAs running at one time
+    // share few column tiles and their kernel entries stay in L2
     const long long ntile = (inner + TW - 1) / TW;
-    const long long slot = blockIdx.x / ntile;
-    const long long i0 = (blockIdx.x - slot * ntile) * TW;
+    const long long nsl = gridDim.x / ntile;
+    const long long tile = blockIdx.x / nsl;
+    const long long slot = blockIdx.x - tile * nsl;
+    const long long i0 = tile * TW;
     cplx<T>* base = B + slot * 3 * (long long)n0 * inner;
     const int twsh = log2_p2(TW);
     for (int e = threadIdx.x; e < 3 * L * TW; e += blockDim.x) {
@@ -658,7 +668,19 @@ template <typename KernelT> static int allow_smem(KernelT k) {
 // to as many threads as the register file allows for the CTAs that fit by
 // shared memory (at most 512): more warps hide the stage barriers and each
 // stage takes fewer sequential butterflies per thread.
-template <typename KernelT> static int fft_threads(KernelT k, int L, size_t smem) {
+// Threads of a generic line or column pass.  Double-float tiles are narrow
+// (16-byte elements), so 256 threads would leave most of them idle at every
+// stage: there the CTA gets one thread per butterfly of its widest stage
+// ((L / largest radix) x lines, a multiple of 32, 64 to 256).
+template <typename T, typename KernelT>
+static int fft_threads(KernelT k, const FFTPlan& p, int nl, size_t smem) {
+    const int L = p.L;
+    if (std::is_same<T, dfl>::value && L <= 1024) {
+        int rmax = 2;
+        for (int st = 0; st < p.nst; ++st) rmax = std::max(rmax, p.R[st]);
+        const int bf = (L / rmax) * nl;
+        return std::max(64, std::min(256, (bf + 31) / 32 * 32));
+    }
     if (L <= 1024) return 256;
     cudaFuncAttributes a;
     if (cudaFuncGetAttributes(&a, k) != cudaSuccess || a.numRegs <= 0) {
@@ -770,7 +792,7 @@ static int launch_lines(const cplx<T>* in, cplx<T>* out, long long count, int n_
     if (!c.ok) return fail(VIE_EINVAL, "FFT length " + std::to_string(p.L) + " does not fit in shared memory");
     const long long grid = (count + c.w - 1) / c.w;
     if (grid <= 0) return VIE_OK;
-    const int nt = fft_threads(k_lines<T, INV>, p.L, c.smem);
+    const int nt = fft_threads<T>(k_lines<T, INV>, p, c.w, c.smem);
     k_lines<T, INV><<<(unsigned)grid, nt, c.smem, s>>>(in, out, count, n_in, n_out, p, tw, c.w, c.stw);
     count_launch();
     VIE_CUDA(cudaGetLastError());
@@ -787,7 +809,7 @@ static int launch_axis(const cplx<T>* in, cplx<T>* out, long long outer, int n_i
     if (!c.ok) return fail(VIE_EINVAL, "FFT length " + std::to_string(p.L) + " does not fit in shared memory");
     const long long grid = outer * ((inner + c.w - 1) / c.w);
     if (grid <= 0) return VIE_OK;
-    const int nt = fft_threads(k_axis<T, INV>, p.L, c.smem);
+    const int nt = fft_threads<T>(k_axis<T, INV>, p, c.w, c.smem);
     tmr_begin(tid, s);
     k_axis<T, INV><<<(unsigned)grid, nt, c.smem, s>>>(in, out, inner, n_in, n_out, p, tw, c.w, c.stw);
     tmr_end(tid, s, bytes);
@@ -1077,7 +1099,7 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
             const FFTPlan& p = op.ax[2].plan;
             const TileCfg c = lines_cfg<T>(p);
             const long long nlines = (long long)ns * 3 * n0 * n1;
-            const int nt = fft_threads(k_zfwd<T, TI>, p.L, c.smem);
+            const int nt = fft_threads<T>(k_zfwd<T, TI>, p, c.w, c.smem);
             tmr_begin(tid(TMR_ZFWD), op.stream);
             k_zfwd<T, TI><<<(unsigned)((nlines + c.w - 1) / c.w), nt, c.smem, op.stream>>>(
                 w, wr, list, op.idx_map, A, n0, n1, n2, cst, nlines, p, twp<T>(op.ax[2]), c.w, c.stw,
@@ -1116,7 +1138,7 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
             const TileCfg c = xfused_cfg<T>(p, inner);
             const long long grid = (long long)ns * ((inner + c.w - 1) / c.w);
             tmr_begin(tid(TMR_XFUSED), op.stream);
-            k_xfused<T><<<(unsigned)grid, 256, c.smem, op.stream>>>(
+            k_xfused<T><<<(unsigned)grid, XG<T>::NT, c.smem, op.stream>>>(
                 B, n0, inner, P0, P1, P2, kh, op.H[0], op.H[1], op.H[2], p, twp<T>(op.ax[0]), c.w,
                 op.disc ? dtp<T>(op) : nullptr, op.dstride, (T)(op.k0 * op.k0), c.stw, c.joint ? 1 : 0);
             tmr_end(tid(TMR_XFUSED), op.stream, 2.0 * ns * lineB + 6.0 * op.H[0] * op.H[1] * op.H[2] * E);
@@ -1148,7 +1170,7 @@ static int apply_t(Operator& op, const cplx<TI>* w, long long wr, cplx<TI>* y, l
             const FFTPlan& p = op.ax[2].plan;
             const TileCfg c = lines_cfg<T>(p);
             const long long nlines = (long long)ns * 3 * n0 * n1;
-            const int nt = fft_threads(k_zinv<T, TI>, p.L, c.smem);
+            const int nt = fft_threads<T>(k_zinv<T, TI>, p, c.w, c.smem);
             tmr_begin(tid(TMR_ZINV), op.stream);
             k_zinv<T, TI><<<(unsigned)((nlines + c.w - 1) / c.w), nt, c.smem, op.stream>>>(
                 A, w, wr, y, yr, list, op.idx_map, chi, n0, n1, n2, cst, nlines, p, twp<T>(op.ax[2]), c.w,
