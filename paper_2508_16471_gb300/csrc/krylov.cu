@@ -1337,7 +1337,7 @@ static int gmres_t(Operator& op, Solver& S, const vie_solve_opts& o, SolveResult
     // the working-precision operator.  Its error, (A_T - A) d, is the FP32
     // operator's relative error (<= 2e-5 at worst) times ||A d|| ~ ||r||, so
     // at most ~2e-9 ||b||: as exact as the double-float operator for the 1e-6
-    // judgement, at 1/13 of its cost.  The first residual of every RHS after
+    // judgement, at about a tenth of its cost.  The first residual of every RHS after
     // its first cycle still comes from the double-float (or FP64) operator.
     constexpr double INC_MAX = 1e-4;
     const bool use_inc = prec_in == VIE_PREC_MIXED;
